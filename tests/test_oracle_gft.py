@@ -1,0 +1,290 @@
+"""Pins for oracle.gft against the paper's closed forms, printed values and
+theorems: DCT-II for uniform paths (Sec. I, Sec. V-B), real DFT eigenspaces
+for cycles (Sec. V-C), the separable 2-D DCT for uniform 4-connected grids
+(Sec. V-D), the printed 4-cycle basis (Sec. III), DST-VII/DCT-IV sub-blocks,
+Lemma 1 and Thm. 2 spectral pairings for bipartite graphs, Thm. 3 / Eq. 13
+exactness on every family, and brute force over all involutions for n <= 8.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import gft_workloads as W
+from oracle import gft, graph, jacobi
+from _helpers import align, clusters, projector_distance, read_golden_matrix, rel_l2, sign_normalize
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def dct2(N):
+    U = np.zeros((N, N))
+    for k in range(N):
+        c = math.sqrt((1.0 if k == 0 else 2.0) / N)
+        for i in range(N):
+            U[i, k] = c * math.cos(math.pi * k * (i + 0.5) / N)
+    return U
+
+
+def _check_basis(L, lam, U, atol=1e-12):
+    n = L.shape[0]
+    assert np.max(np.abs(U.T @ U - np.eye(n))) <= 1e-13
+    assert np.max(np.abs(L @ U - U * lam)) <= atol * max(1.0, np.abs(L).max())
+    assert np.all(np.diff(lam) >= -1e-12)
+
+
+@pytest.mark.parametrize("N", [2, 3, 8, 13, 32])
+def test_path_dense_gft_is_dct2(N):
+    """Uniform line graph: GFT = DCT-II, lam_k = 2 - 2cos(pi k / N)."""
+    g = W.path(N)
+    L = graph.laplacian(g.W, g.s)
+    lam, U = gft.dense_gft(L)
+    assert np.allclose(lam, [2 - 2 * math.cos(math.pi * k / N) for k in range(N)], atol=1e-13)
+    assert np.allclose(sign_normalize(U), sign_normalize(dct2(N)), atol=1e-12)
+
+
+def test_path8_fast_gft_subblocks():
+    """Config-1 plan: one stage of 4 Haar units; G+ is the 4-node uniform path
+    (DCT-II(4)); G- is a 4-node path with a self-loop 2 at the node next to
+    the axis, spectrum 2-2cos(pi(2k+1)/8) and DCT-IV vectors."""
+    g = W.path(8)
+    L = graph.laplacian(g.W, g.s)
+    f = gft.fast_gft(L, g.phis)
+    assert f.fact.stages == [[(0, 7), (1, 6), (2, 5), (3, 4)]]
+    plus, minus = f.fact.leaves
+    assert plus.labels == [0, 1, 2, 3] and minus.labels == [7, 6, 5, 4]
+    assert np.allclose(f.leaf_lams[0], [2 - 2 * math.cos(math.pi * k / 4) for k in range(4)], atol=1e-13)
+    assert np.allclose(f.leaf_lams[1], [2 - 2 * math.cos(math.pi * (2 * k + 1) / 8) for k in range(4)], atol=1e-13)
+    assert np.allclose(sign_normalize(f.leaf_vecs[0]), sign_normalize(dct2(4)), atol=1e-12)
+    # G- in its own order (label 7 first): node j of G- is 7-j, the self-loop
+    # sits on local index 3 (label 4); DCT-IV with the free end at index 0
+    dct4 = np.array([[math.cos(math.pi * (2 * k + 1) * (2 * j + 1) / 16) for k in range(4)]
+                     for j in range(4)]) * math.sqrt(2 / 4)
+    assert np.allclose(sign_normalize(f.leaf_vecs[1]), sign_normalize(dct4), atol=1e-12)
+    # the whole fast basis is DCT-II(8) up to sign
+    assert np.allclose(sign_normalize(f.U), sign_normalize(dct2(8)), atol=1e-12)
+
+
+@pytest.mark.parametrize("N", [4, 6, 12, 16, 20])
+def test_cycle_real_dft_eigenspaces(N):
+    """Cycle: eigenspaces span{cos(2 pi k i/N), sin(2 pi k i/N)} with
+    lam_k = 2 - 2cos(2 pi k/N) (Sec. V-C); the fast basis (one stage, two
+    when 4 | N) spans the same eigenspaces."""
+    g = W.cycle(N)
+    L = graph.laplacian(g.W, g.s)
+    f = gft.fast_gft(L, g.phis)
+    _check_basis(L, f.lam, f.U)
+    lam_cf = np.sort([2 - 2 * math.cos(2 * math.pi * k / N) for k in range(N)])
+    assert np.allclose(f.lam, lam_cf, atol=1e-12)
+    # closed-form orthonormal real DFT basis, sorted by eigenvalue
+    vecs, lams = [], []
+    i = np.arange(N)
+    for k in range(N // 2 + 1):
+        c = np.cos(2 * math.pi * k * i / N)
+        vecs.append(c / np.linalg.norm(c))
+        lams.append(2 - 2 * math.cos(2 * math.pi * k / N))
+        if 0 < k < N / 2:
+            s = np.sin(2 * math.pi * k * i / N)
+            vecs.append(s / np.linalg.norm(s))
+            lams.append(lams[-1])
+    order = np.argsort(lams, kind="stable")
+    Ucf = np.array(vecs).T[:, order]
+    assert projector_distance(f.U, Ucf, f.lam) < 1e-11
+    assert len(f.fact.stages) == (2 if N % 4 == 0 else 1)
+
+
+def test_cycle_subgraphs_are_dct2_and_dst2():
+    """First stage of the cycle: G+ is a uniform path of N/2 nodes (DCT-II
+    spectrum), G- a path with self-loop 2 at both ends (DST-II spectrum)."""
+    N = 12
+    g = W.cycle(N)
+    L = graph.laplacian(g.W, g.s)
+    f = gft.fast_gft(L, g.phis[:1])
+    h = N // 2
+    assert np.allclose(f.leaf_lams[0], [2 - 2 * math.cos(math.pi * k / h) for k in range(h)], atol=1e-13)
+    assert np.allclose(f.leaf_lams[1], [2 - 2 * math.cos(math.pi * (k + 1) / h) for k in range(h)], atol=1e-13)
+
+
+def test_printed_c4_basis():
+    """Sec. III prints U_C4; lam = 0 and lam = 4 columns are fixed up to sign,
+    the lam = 2 pair only as a subspace."""
+    meta, M = read_golden_matrix(os.path.join(GOLDEN, "u_c4.txt"))
+    Uc4 = M * meta["scale"][0]
+    g = W.cycle(4)
+    L = graph.laplacian(g.W, g.s)
+    for lam, U in (gft.dense_gft(L), (lambda f: (f.lam, f.U))(gft.fast_gft(L, g.phis))):
+        assert np.allclose(lam, meta["eigenvalues"], atol=1e-13)
+        for c in (0, 3):
+            assert np.allclose(abs(U[:, c] @ Uc4[:, c]), 1.0, atol=1e-13)
+        assert projector_distance(U, Uc4, lam) < 1e-12
+    # the printed matrix itself is a GFT of C4
+    assert np.allclose(L @ Uc4, Uc4 * np.array(meta["eigenvalues"]), atol=1e-15)
+
+
+@pytest.mark.parametrize("N1,N2", [(4, 4), (5, 3), (6, 6)])
+def test_grid_is_separable_2d_dct(N1, N2):
+    """Uniform 4-connected grid: GFT = 2-D DCT, lam = lam_k + lam_l (Sec. V-D);
+    LR then UD stages reach the same eigenspaces."""
+    g = W.grid(N1, N2)
+    L = graph.laplacian(g.W, g.s)
+    f = gft.fast_gft(L, g.phis)
+    _check_basis(L, f.lam, f.U)
+    A, B = dct2(N1), dct2(N2)
+    la = [2 - 2 * math.cos(math.pi * k / N1) for k in range(N1)]
+    lb = [2 - 2 * math.cos(math.pi * k / N2) for k in range(N2)]
+    lams = np.array([la[a] + lb[b] for a in range(N1) for b in range(N2)])
+    Ucf = np.kron(A, B)     # column (a, b) is u_a(k) u_b(l) at label k*N2 + l
+    order = np.argsort(lams, kind="stable")
+    assert np.allclose(f.lam, lams[order], atol=1e-12)
+    assert projector_distance(f.U, Ucf[:, order], f.lam) < 1e-11
+
+
+def test_skeleton25_plan_and_dst7_components():
+    """Skeleton: one stage with Z = spine; G- splits into two 5-node paths
+    with a unit self-loop at the root, whose GFT is DST-VII(5),
+    lam = 2 - 2cos(pi(2k+1)/11) (Sec. V-E)."""
+    g = W.skeleton25()
+    L = graph.laplacian(g.W, g.s)
+    f = gft.fast_gft(L, g.phis, split_components=True)
+    sizes = [len(b.labels) for b in f.fact.leaves]
+    assert sizes == [15, 5, 5]
+    assert f.fact.leaves[1].labels == [10, 11, 12, 13, 14]
+    assert f.fact.leaves[2].labels == [20, 21, 22, 23, 24]
+    dst7_lam = [2 - 2 * math.cos(math.pi * (2 * k + 1) / 11) for k in range(5)]
+    dst7 = np.array([[math.sin(math.pi * (2 * k + 1) * (j + 1) / 11) for k in range(5)] for j in range(5)])
+    dst7 /= np.linalg.norm(dst7, axis=0)
+    for k in (1, 2):
+        assert np.allclose(f.leaf_lams[k], dst7_lam, atol=1e-13)
+        assert np.allclose(sign_normalize(f.leaf_vecs[k]), sign_normalize(dst7), atol=1e-12)
+    lam_d, U_d = gft.dense_gft(L)
+    assert np.allclose(f.lam, lam_d, atol=1e-12)
+    assert projector_distance(f.U, U_d, lam_d) < 1e-10
+    _check_basis(L, f.lam, f.U)
+
+
+def test_lemma1_k_regular_bipartite_pairing():
+    """Lemma 1: for a k-RBG, (u1, u2) -> (u1, -u2) maps lam to 2k - lam.
+    The 3-cube is 3-regular bipartite."""
+    n = 8
+    Wm = np.zeros((n, n))
+    for v in range(n):
+        for b in range(3):
+            Wm[v, v ^ (1 << b)] = 1.0
+    parity = [bin(v).count("1") % 2 for v in range(n)]
+    perm = [v for v in range(n) if parity[v] == 0] + [v for v in range(n) if parity[v] == 1]
+    L = graph.laplacian(Wm, np.zeros(n))[np.ix_(perm, perm)]
+    lam, V = jacobi.jacobi_eigh(L)
+    assert np.allclose(np.sort(lam), np.sort(6 - lam), atol=1e-12)
+    for c in range(n):
+        u = V[:, c].copy()
+        u[4:] *= -1
+        assert np.allclose(L @ u, (6 - lam[c]) * u, atol=1e-12)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_thm2_normalized_bipartite_spectrum(seed):
+    """Thm. 2 rests on the normalised Laplacian of a bipartite graph having a
+    spectrum symmetric about 1 (lam <-> 2 - lam)."""
+    g = W.bipartite(16, p=0.5, seed=seed)
+    L = graph.laplacian(g.W, g.s)
+    d = np.diag(L)
+    assert np.all(d > 0)
+    Ln = L / np.sqrt(np.outer(d, d))
+    lam, _ = jacobi.jacobi_eigh(Ln)
+    assert np.allclose(np.sort(lam), np.sort(2 - lam), atol=1e-12)
+
+
+def _families():
+    return [W.path(9), W.path(16), W.cycle(10), W.cycle(24), W.grid(4), W.grid(5, 4),
+            W.grid(6, weights="sym_uniform", seed=4), W.skeleton25(), W.bipartite(20, 0.3, seed=1),
+            W.planted_symmetric(11, np.array([10, 9, 2, 7, 4, 5, 6, 3, 8, 1, 0]), seed=2)]
+
+
+@pytest.mark.parametrize("g", _families(), ids=lambda g: g.name)
+@pytest.mark.parametrize("split", [False, True])
+def test_fast_equals_dense_on_families(g, split):
+    """Thm. 3 / Eq. 13: the fast basis diagonalises L, carries its spectrum,
+    and matches the dense GFT eigenspace by eigenspace; staged application
+    equals the dense product; inverse and Parseval hold."""
+    L = graph.laplacian(g.W, g.s)
+    f = gft.fast_gft(L, g.phis, split_components=split)
+    assert max(f.fact.offblock) <= 1e-13 * max(1.0, np.abs(L).max())
+    lam_d, U_d = gft.dense_gft(L)
+    assert np.allclose(f.lam, lam_d, atol=1e-12 * max(1.0, lam_d.max()))
+    _check_basis(L, f.lam, f.U)
+    assert projector_distance(f.U, U_d, lam_d) < 1e-9
+    X = W.signals(7, g.n, 5).astype(np.float64)
+    Ys = gft.forward_staged(f, X)
+    assert np.max(np.abs(Ys - X @ f.U)) < 1e-13
+    Yd = gft.forward_dense(U_d, X)
+    assert rel_l2(Ys, align(Yd, f.U, U_d, lam_d)) < 1e-12
+    assert np.allclose(np.linalg.norm(Ys, axis=1), np.linalg.norm(X, axis=1), rtol=1e-13)
+    assert np.max(np.abs(gft.inverse_staged(f, Ys) - X)) < 1e-13
+    # union of leaf spectra = spectrum of L
+    assert np.allclose(np.sort(np.concatenate(f.leaf_lams)), lam_d, atol=1e-12 * max(1.0, lam_d.max()))
+
+
+def test_canonical_signs_consistent_between_routes():
+    """Simple eigenvalues: both routes give the same vector, sign included."""
+    g = W.grid(6, weights="sym_uniform", seed=8)
+    L = graph.laplacian(g.W, g.s)
+    f = gft.fast_gft(L, g.phis)
+    lam_d, U_d = gft.dense_gft(L)
+    for S in clusters(lam_d):
+        if len(S) == 1:
+            assert np.allclose(f.U[:, S[0]], U_d[:, S[0]], atol=1e-10)
+
+
+def test_involution_count_matches_paper_formula():
+    """Sec. V-F: T(n) = sum_k n! / (2^k (n-2k)! k!); T(8) = 764."""
+    for n in range(0, 9):
+        T = sum(math.factorial(n) // (2 ** k * math.factorial(n - 2 * k) * math.factorial(k))
+                for k in range(n // 2 + 1))
+        assert W.involution_count(n) == T
+        assert sum(1 for _ in W.all_involutions(n)) == T
+    assert W.involution_count(8) == 764
+
+
+@pytest.mark.parametrize("n,seed", [(6, 0), (7, 1), (8, 2)])
+def test_brute_force_all_involutions(n, seed):
+    """Every involution of n <= 8 nodes: off-blocks of B^T L B vanish iff the
+    graph is phi-symmetric (Thm. 3 and its converse via P_phi L = L P_phi);
+    every accepted phi yields an exact GFT; the planted phi is accepted."""
+    planted = np.arange(n)
+    planted[0], planted[n - 1] = n - 1, 0
+    planted[1], planted[3] = 3, 1
+    g = W.planted_symmetric(n, planted, density=0.6, seed=seed)
+    L = graph.laplacian(g.W, g.s)
+    accepted = []
+    for phi in W.all_involutions(n):
+        sym = graph.laplacian_is_phi_symmetric(L, phi, 1e-12)
+        assert sym == graph.is_phi_symmetric(g.W, g.s, phi, 1e-12)
+        _, _, off = graph.block_diagonalize(L, phi)
+        assert (off <= 1e-12) == sym
+        if sym and graph.p_phi(phi) > 0:
+            accepted.append(tuple(int(v) for v in phi))
+            f = gft.fast_gft(L, [phi])
+            _check_basis(L, f.lam, f.U)
+    assert tuple(int(v) for v in planted) in accepted
+
+
+def test_output_order_cluster_rule():
+    """Ascending eigenvalues; values within the cluster tolerance are ordered
+    by (leaf, index within leaf) regardless of rounding."""
+    entries = [(2.0 + 1e-13, 0, 0), (0.5, 0, 1), (2.0, 1, 0), (1.0, 1, 1), (2.0 - 1e-13, 2, 0), (3.0, 2, 1)]
+    pos = gft.output_order(entries)
+    # order: 0.5 (e1), 1.0 (e3), cluster {e0, e2, e4} by leaf, 3.0 (e5)
+    assert list(pos) == [2, 0, 3, 1, 4, 5]
+
+
+def test_decompose_rejects_bad_inputs():
+    g = W.path(6)
+    L = graph.laplacian(g.W, g.s)
+    with pytest.raises(ValueError):
+        gft.decompose(L, [[1, 2, 0, 3, 4, 5]])           # not an involution
+    with pytest.raises(ValueError):
+        gft.decompose(L, [[1, 0, 2, 3, 4, 5]])           # not a symmetry
+    # second stage must map each block onto itself
+    with pytest.raises(ValueError):
+        gft.decompose(L, [W.reversal(6), [5, 1, 2, 3, 4, 0]])
