@@ -1,0 +1,350 @@
+"""Benchmark of the batched fast GFT on GB300.
+
+Workload (default): the 25-joint skeleton graph (spine 0-4, arms and legs of
+5 joints, left/right involution), 2^20 FP32 signals drawn i.i.d. N(0,1) --
+one Haar stage and leaf blocks of 15, 5 and 5 nodes.  A step is one forward
+fast GFT of the whole batch (Haar stage, leaf products, output permutation:
+one kernel launch).  Metric: coefficients per second (batch * n per step).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank transforms its own batch (independent problems:
+weak scaling, no collective on the data path); the time is the max over
+ranks.  `--impl reference` times the FP64 CPU oracle on the host cores on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import gft_workloads as W  # noqa: E402
+
+WORKLOAD = "skeleton25_2^20_fp32"
+METRIC = "fast-GFT coeffs/s vs dense GFT, same GB300, at stated err vs FP64; %HBM roof"
+UNIT = "coeffs/s"
+L2_BYTES = 129 * 1024 * 1024
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _kernel_hash():
+    h = hashlib.sha256()
+    for f in ("apply.cu", "gft_internal.h"):
+        with open(os.path.join(ROOT, "paper_1907_07875_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic_from_profile(kernel_hash):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "apply_skeleton25_traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        if d.get("kernel_hash") == kernel_hash:
+            return d.get("dram_bytes_per_launch_full")
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (getattr(self, "out", "") or "").splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (spawned process: no fork after CUDA initialisation)
+# ---------------------------------------------------------------------------
+def _oracle_worker(batch, seconds, q):
+    from oracle import gft as ogft
+    from oracle import graph as ograph
+    (g, _, seed), = W.config2()
+    f = ogft.fast_gft(ograph.laplacian(g.W, g.s), g.phis, split_components=True)
+    x = W.signals(batch, g.n, seed).astype(np.float64)
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        ogft.forward_staged(f, x)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    q.put((reps * batch * g.n / el, reps, el))
+
+
+def oracle_rate(batch, seconds):
+    cores = os.cpu_count() or 1
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = str(cores)
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    p = ctx.Process(target=_oracle_worker, args=(batch, seconds, q))
+    p.start()
+    rate, reps, el = q.get()
+    p.join()
+    return rate, reps, el, cores
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    batch = 1 << 18
+    rates = []
+    for _ in range(args.warmup):
+        oracle_rate(batch, 0.5)
+    for _ in range(args.steps):
+        r, _, _, cores = oracle_rate(batch, 2.0)
+        rates.append(r)
+    value = statistics.median(rates)
+    cores = os.cpu_count() or 1
+    sample = f"oracle.forward_staged (FP64 numpy) on 2^18 of the 2^20 signals, repeated for 2 s per step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "graph": "skeleton25", "signals": 1 << 20, "n": 25},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_1907_07875_gb300 as gft
+    from paper_1907_07875_gb300.build import build
+    dist = None
+    if world > 1:
+        import torch.distributed as dist  # noqa: F811
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if rank == 0 or world == 1:
+        build()
+    if dist is not None:
+        dist.barrier()
+    (g, batch, seed), = W.config2()
+    n = g.n
+    plan = gft.Plan(gft.laplacian(g.W, g.s), g.phis, split_components=True)
+    stream = torch.cuda.current_stream()
+    # rotating input/output sets, together larger than L2, so every step reads
+    # its input from HBM
+    x_host = W.signals(batch, n, seed + 7919 * rank)
+    nbytes = batch * n * 4
+    nsets = max(2, -(-4 * L2_BYTES // (2 * nbytes)))
+    xs = [torch.from_numpy(x_host).to(dev) for _ in range(nsets)]
+    for i in range(1, nsets):
+        xs[i].mul_(1.0 + 1e-3 * i)
+    ys = [torch.empty_like(xs[0]) for _ in range(nsets)]
+
+    # parity spot check against the FP64 oracle (rank 0, 2^14 signals)
+    err = None
+    if rank == 0:
+        from oracle import gft as ogft
+        from oracle import graph as ograph
+        ref = ogft.fast_gft(ograph.laplacian(g.W, g.s), g.phis, split_components=True)
+        U = plan.basis()
+        k = 1 << 14
+        y = plan.forward(xs[0][:k].contiguous()).cpu().numpy().astype(np.float64)
+        yo = ogft.forward_dense(ref.U, x_host[:k].astype(np.float64))
+        lam = ref.lam
+        tol = 1e-9 * max(1.0, float(np.abs(lam).max()))
+        ya, start = np.empty_like(yo), 0
+        for j in range(1, n + 1):
+            if j == n or lam[j] - lam[j - 1] > tol:
+                S = list(range(start, j))
+                ya[:, S] = yo[:, S] @ (U[:, S].T @ ref.U[:, S]).T
+                start = j
+        err = float(np.linalg.norm(y - ya) / np.linalg.norm(ya))
+
+    def step(i):
+        plan.forward(xs[i % nsets], out=ys[i % nsets], stream=stream)
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    with ClockSampler(local_rank) as clk:
+        time.sleep(0.3)
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for i in range(args.steps):
+            starts[i].record(stream)
+            step(i)
+            ends[i].record(stream)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        total_ms = t0.elapsed_time(t1)
+        time.sleep(0.2)
+    launch_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    if dist is not None:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    coeffs_per_step = batch * n
+    value = coeffs_per_step * world / (total_ms / 1e3) * args.steps
+
+    # dominant (only) kernel: the fused transform, one launch per step
+    avg_launch_s = statistics.mean(launch_ms) / 1e3
+    alg_bytes = 8 * coeffs_per_step          # FP32 read + write per coefficient
+    peak, peak_kind = _peaks()
+    achieved = alg_bytes / avg_launch_s / 1e9
+    khash = _kernel_hash()
+    traffic = _traffic_from_profile(khash)
+
+    # inverse and the dense GEMM on the same data (context)
+    def timed(fn, reps=20):
+        for i in range(3):
+            fn(i)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for i in range(reps):
+            fn(i)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps / 1e3
+
+    inv_s = timed(lambda i: plan.inverse(ys[i % nsets], out=xs[(i + 1) % nsets], stream=stream))
+    Ut = torch.from_numpy(plan.basis()).float().to(dev)
+    prev_tf32 = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    dense_s = timed(lambda i: torch.matmul(xs[i % nsets], Ut, out=ys[i % nsets]))
+    torch.backends.cuda.matmul.allow_tf32 = prev_tf32
+
+    # end to end through the public API with host buffers (pinned)
+    xh = torch.from_numpy(x_host).pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+    plan.forward_host(xh, out=yh)
+    e2e_steps = max(3, min(args.steps, 20))
+    t = time.perf_counter()
+    for _ in range(e2e_steps):
+        plan.forward_host(xh, out=yh)
+    e2e_s = (time.perf_counter() - t) / e2e_steps
+
+    if dist is not None:
+        dist.barrier()
+    if rank != 0:
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        rate, reps, el, cores = oracle_rate(1 << 18, 10.0)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"oracle.forward_staged (FP64 numpy) on 2^18 of the 2^20 signals x {reps} reps "
+                         f"({el:.1f} s)"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "graph": "skeleton25 (1 Haar stage, leaves 15/5/5)",
+                   "signals_per_gpu": batch, "n": n, "precision": "fp32",
+                   "l2": f"{nsets} rotating input/output sets ({nsets * 2 * nbytes / 2**20:.0f} MiB) > L2"},
+        "err_vs_fp64": err,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
+                     "alg_bytes_per_launch": alg_bytes, "kernel": "gft_apply_kernel"},
+        "e2e": {"value": coeffs_per_step / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+                "d2h_bytes_per_step": nbytes},
+        "gpu_launches": args.steps,
+        "inverse": {"value": coeffs_per_step / inv_s, "unit": UNIT},
+        "dense_gemm_fp32": {"value": coeffs_per_step / dense_s, "unit": UNIT,
+                            "what": "torch.matmul(x, U) FP32, TF32 off"},
+        "clocks": clk.summary(),
+        "kernel_hash": khash,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,251 @@
+/*
+ * gft.h -- C ABI of the GB300 batched fast graph Fourier transform.
+ *
+ * Method: Lu & Ortega, "Fast Graph Fourier Transforms Based on Graph
+ * Symmetry and Bipartition".  The GFT of a signal x on a graph with
+ * Laplacian L = U diag(lambda) U^T is U^T x (Sec. II-B).  When the graph is
+ * symmetric under a node involution phi (Definition 2), one stage of Haar
+ * units B_phi (Eq. 20) block-diagonalises L into the Laplacians of two
+ * smaller graphs G+ and G- (Thm. 3, Eq. 17), so U = B_phi diag(U+, U-)
+ * (Eq. 13); repeating on G+ and G- gives several stages (end of Sec. IV-C).
+ * A plan holds the stages and the dense bases U_k of the leaf blocks; the
+ * forward transform applies the stages (additions and subtractions only,
+ * the 1/sqrt(2) factors folded into the U_k, Sec. III) and then the block
+ * products U_k^T, and writes the coefficients in ascending eigenvalue order.
+ *
+ * Conventions shared by every call:
+ *  - Signals are rows: a batch is a row-major [batch, n] array, one signal
+ *    per row; coefficients likewise (y = x U per row, i.e. y^T = U^T x).
+ *  - Node labels are 0-based.
+ *  - Device pointers must be 16-byte aligned and point to memory of the
+ *    current CUDA device; in-place (x == y) is allowed for plan transforms.
+ *  - Streams are passed as an opaque pointer holding a cudaStream_t
+ *    (NULL = the legacy default stream).  Transform calls are asynchronous
+ *    with respect to the host; errors raised by a kernel surface through
+ *    gft_device_error() or the next synchronising call.
+ *  - Every call returns a gft_status and never aborts or throws across the
+ *    ABI.  A call that fails validation writes nothing to its outputs.
+ *  - Objects are not thread-safe: do not use one plan from two host threads
+ *    at the same time.
+ */
+#ifndef GFT_H
+#define GFT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gft_plan_s* gft_plan_t;
+typedef struct gft_batch_s* gft_batch_t;
+typedef struct gft_givens_s* gft_givens_t;
+typedef void* gft_stream_t;
+
+typedef enum {
+    GFT_OK = 0,
+    GFT_ERR_INVALID_ARG = 1,     /* null pointer, bad size, bad flag, bad stage count */
+    GFT_ERR_NOT_INVOLUTION = 2,  /* phi(phi(i)) != i or label out of range (Definition 1) */
+    GFT_ERR_NOT_SYMMETRIC = 3,   /* block Laplacian not phi-symmetric (Definition 2) */
+    GFT_ERR_NOT_LAPLACIAN = 4,   /* L not symmetric or has a non-finite entry */
+    GFT_ERR_NO_CONVERGENCE = 5,  /* Jacobi exceeded its sweep limit */
+    GFT_ERR_CUDA = 6,            /* a CUDA runtime call failed */
+    GFT_ERR_OOM = 7,             /* device or host allocation failed */
+    GFT_ERR_TIMEOUT = 8,         /* a bounded device-side wait gave up */
+    GFT_ERR_UNSUPPORTED = 9,     /* valid input this build does not handle (see message) */
+    GFT_ERR_MISALIGNED = 10,     /* device pointer not 16-byte aligned */
+    GFT_ERR_BLOCK_LEAK = 11,     /* a stage involution maps a node out of its block */
+    GFT_ERR_NO_DEVICE = 12       /* plan was created with GFT_ANALYZE_ONLY */
+} gft_status;
+
+/* gft_plan_create flags */
+#define GFT_SPLIT_COMPONENTS 0x1u  /* split leaves into connected components (Sec. V-E) */
+#define GFT_ORDER_BLOCK      0x2u  /* coefficients in leaf order instead of ascending eigenvalue */
+#define GFT_ANALYZE_ONLY     0x4u  /* host-side decomposition only: no device, no bases */
+
+/* transform precision (plan forward / inverse) */
+#define GFT_PREC_FP32    0u  /* CUDA-core FP32 FMA, FP32 accumulation */
+#define GFT_PREC_BF16    1u  /* leaf products on tensor cores, BF16 operands */
+#define GFT_PREC_BF16X3  2u  /* BF16 hi+lo split, three products (hi*hi + hi*lo + lo*hi) */
+#define GFT_PREC_FP16X3  3u  /* FP16 hi+lo split (scaled), three products */
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char* gft_status_string(gft_status s);
+
+/* Text of the last error raised on this host thread (static storage,
+ * overwritten by the next failing call; "" if none). */
+const char* gft_last_error(void);
+
+/* ABI version: major*10000 + minor*100 + patch. */
+int32_t gft_version(void);
+
+/*
+ * Laplacian from weights, Eq. 5 (Sec. II-B): l_ii = s_i + sum_{j != i} w_ij,
+ * l_ij = -w_ij.  W: host, n*n row-major, symmetric, diagonal ignored;
+ * s: host, n self-loop weights (NULL = none); L: host, n*n output.  The
+ * caller owns all three.  Errors: INVALID_ARG on null W/L or n < 1,
+ * NOT_LAPLACIAN if W is not symmetric or not finite.
+ */
+gft_status gft_laplacian_from_weights(int32_t n, const double* W, const double* s, double* L);
+
+/*
+ * Build a fast-GFT plan (Sec. IV-B, IV-C; recursion at the end of Sec. IV-C).
+ *  n         number of nodes, 1 <= n <= 4096.
+ *  L         host, n*n row-major Laplacian (Eq. 3), copied.  Must be
+ *            symmetric and finite; signs of entries are not checked, so
+ *            negative weights (as in G+/G-) are accepted.
+ *  n_stages  number of Haar stages, 0 <= n_stages <= 16 (0 = dense GFT).
+ *  phi       host, n_stages*n involutions on ORIGINAL labels, copied
+ *            (NULL allowed when n_stages = 0).  Stage s splits every current
+ *            block that phi_s moves: phi_s must map each block onto itself,
+ *            the block's Laplacian must satisfy l_ij = l_phi(i)phi(j) within
+ *            1e-12*max(1,max|L|), and paired nodes must have taken part in
+ *            the same number of earlier stages (else UNSUPPORTED).  In each
+ *            block, the pair member that comes first in the block's order
+ *            goes to X, its partner to Y; G+ lists X then the fixed points Z,
+ *            G- lists the partners of X in X's order.
+ *  flags     GFT_SPLIT_COMPONENTS | GFT_ORDER_BLOCK | GFT_ANALYZE_ONLY.
+ *  out       receives the plan (owned by the caller; free with
+ *            gft_plan_destroy).  Unchanged on error.
+ * Unless GFT_ANALYZE_ONLY is set, the leaf Laplacians are eigendecomposed on
+ * the current CUDA device by a batched FP64 Jacobi kernel and the bases are
+ * uploaded; the call synchronises the device.  Eigenvector signs: the first
+ * entry of largest magnitude (within 1e-9 relative) of every full-length
+ * basis vector is made positive.  Output order: ascending eigenvalue;
+ * eigenvalues within 1e-9*max(1,|lambda|max) of a neighbour form a cluster
+ * ordered by (leaf in depth-first order with + before -, index in leaf).
+ * Errors: INVALID_ARG, NOT_LAPLACIAN, NOT_INVOLUTION, BLOCK_LEAK,
+ * NOT_SYMMETRIC, UNSUPPORTED, NO_CONVERGENCE, CUDA, OOM.
+ */
+gft_status gft_plan_create(int32_t n, const double* L, int32_t n_stages, const int32_t* phi,
+                           uint32_t flags, gft_plan_t* out);
+
+/* Free a plan and its device memory (NULL is accepted).  The caller must
+ * make sure no transform using the plan is still running. */
+gft_status gft_plan_destroy(gft_plan_t plan);
+
+typedef struct {
+    int32_t n;              /* nodes */
+    int32_t n_stages;       /* stages as given */
+    int32_t n_leaves;       /* leaf blocks after all stages (and splitting) */
+    int32_t n_pairs;        /* Haar units over all stages */
+    int32_t max_leaf;       /* largest leaf size */
+    int32_t has_device;     /* 1 if bases are on the device */
+    int32_t jacobi_sweeps;  /* most sweeps any leaf needed (0 if analyze-only) */
+    uint32_t flags;
+    int64_t fast_mults;     /* multiplies per signal: sum of m_k^2 (Sec. V-G) */
+    int64_t fast_adds;      /* adds per signal: 2 per Haar unit + sum m_k(m_k-1) */
+} gft_plan_info_t;
+
+gft_status gft_plan_get_info(gft_plan_t plan, gft_plan_info_t* info);
+
+/* Haar units of one stage: pairs[2k] = X label, pairs[2k+1] = partner label,
+ * in block order.  Pass pairs = NULL to query *count only; otherwise
+ * *count is the capacity on entry (in pairs) and the number written on
+ * return. */
+gft_status gft_plan_get_stage_pairs(gft_plan_t plan, int32_t stage, int32_t* pairs, int32_t* count);
+
+/* Leaf blocks in depth-first order: sizes[n_leaves]; labels[n] holds every
+ * leaf's original labels in leaf order, concatenated. */
+gft_status gft_plan_get_leaves(gft_plan_t plan, int32_t* sizes, int32_t* labels);
+
+/* Laplacian of one leaf (Eq. 17 applied stage by stage), m*m row-major. */
+gft_status gft_plan_get_leaf_laplacian(gft_plan_t plan, int32_t leaf, double* Lk);
+
+/* out_pos[n]: coefficient index of every (leaf, index-in-leaf) entry, in
+ * leaf-concatenated order.  Needs device bases (ordering uses eigenvalues). */
+gft_status gft_plan_get_output_map(gft_plan_t plan, int32_t* out_pos);
+
+/* Eigenvalues in coefficient order (host, n doubles). */
+gft_status gft_plan_eigenvalues(gft_plan_t plan, double* lambda);
+
+/* Full FP64 basis: U host n*n row-major, column j = basis vector of
+ * coefficient j, U = B_1 ... B_S diag(U_k) with Eq. 20's stage matrices. */
+gft_status gft_plan_basis(gft_plan_t plan, double* U);
+
+/*
+ * Forward transform of a batch: y[b, :] = U^T x[b, :] for b < batch.
+ * x, y: device, [batch, n] row-major FP32, 16-byte aligned; x == y allowed.
+ * precision: GFT_PREC_*; the tensor-core precisions apply to leaves large
+ * enough to be a dense contraction and need a plan whose shape the
+ * tensor-core kernel supports (UNSUPPORTED otherwise).  batch = 0 is a
+ * no-op.  Asynchronous on `stream`.
+ */
+gft_status gft_plan_forward(gft_plan_t plan, const float* x, float* y, int64_t batch,
+                            gft_stream_t stream, uint32_t precision);
+
+/* Inverse transform: x[b, :] = U y[b, :] (B_phi is its own inverse, Sec. III). */
+gft_status gft_plan_inverse(gft_plan_t plan, const float* y, float* x, int64_t batch,
+                            gft_stream_t stream, uint32_t precision);
+
+/* FP64 forward / inverse (same layout, double).  Only the CUDA-core path. */
+gft_status gft_plan_forward_f64(gft_plan_t plan, const double* x, double* y, int64_t batch,
+                                gft_stream_t stream);
+gft_status gft_plan_inverse_f64(gft_plan_t plan, const double* y, double* x, int64_t batch,
+                                gft_stream_t stream);
+
+/*
+ * Forward transform of a HOST batch: x_host, y_host are host [batch, n] FP32
+ * (pinned memory gives full copy bandwidth).  The plan streams the batch
+ * through its own device staging buffers in chunks, overlapping the
+ * host-to-device copy, the transform and the device-to-host copy, and
+ * returns when y_host is complete.
+ */
+gft_status gft_plan_forward_host(gft_plan_t plan, const float* x_host, float* y_host,
+                                 int64_t batch, uint32_t precision);
+
+/* Synchronise the plan's last stream and read (and clear) the plan's device
+ * error word: 0 = none, else a GFT_ERR_* code a kernel recorded. */
+gft_status gft_device_error(gft_plan_t plan, int32_t* code);
+
+/*
+ * Mixed batch: many plans, each with its own batch of signals, transformed
+ * forward by ONE persistent kernel launch over a work list of (plan, tile)
+ * items, captured in a CUDA graph on first use and replayed afterwards.
+ *  plans[n_plans]  plans created with device bases (all FP32 CUDA-core
+ *                  capable); the batch does not own them, and they must
+ *                  outlive it.
+ *  batches[n_plans] signals per plan.
+ * gft_batch_forward: x[i], y[i] device pointers to [batches[i], n_i] FP32
+ * (host arrays of n_plans pointers).  A replay with the same pointers reuses
+ * the captured graph; new pointers trigger a new capture.
+ */
+gft_status gft_batch_create(int32_t n_plans, const gft_plan_t* plans, const int64_t* batches,
+                            uint32_t flags, gft_batch_t* out);
+gft_status gft_batch_forward(gft_batch_t batch, const float* const* x, float* const* y,
+                             gft_stream_t stream);
+/* Tile configuration chosen by the autotuner for plan i: signals per tile
+ * and threads per block (0 if not tuned yet). */
+gft_status gft_batch_get_tile(gft_batch_t batch, int32_t i, int32_t* tile, int32_t* threads);
+gft_status gft_batch_destroy(gft_batch_t batch);
+
+/*
+ * Layered Givens rotations (Eq. 1 and Fig. 1) used as a learned surrogate of
+ * a dense GFT: y = G_S ... G_1 x, each stage n/2 rotations on disjoint pairs,
+ * (y_p, y_q) = (c x_p - s x_q, s x_p + c x_q) with c = cos(theta), s = sin(theta).
+ *  n         even, 2 <= n <= 1024; n_stages 1..64.
+ *  pairs     host int32 [n_stages][n/2][2]; each stage a perfect matching, copied.
+ */
+gft_status gft_givens_create(int32_t n, int32_t n_stages, const int32_t* pairs, gft_givens_t* out);
+gft_status gft_givens_destroy(gft_givens_t g);
+
+/* theta: device [n_stages][n/2] FP32.  x, y: device [batch, n] FP32. */
+gft_status gft_givens_forward(gft_givens_t g, const float* theta, const float* x, float* y,
+                              int64_t batch, gft_stream_t stream);
+
+/*
+ * Backward pass: given the forward OUTPUT y and the loss gradient gy, write
+ * gx = G_1^T ... G_S^T gy and gtheta[s][k] = sum_b (-g_p y_q + g_q y_p), with
+ * stage inputs recovered by inverse rotation (no stored activations).
+ * gtheta is overwritten (not accumulated); the sum over the batch is
+ * deterministic.  Uses device scratch owned by g.
+ */
+gft_status gft_givens_backward(gft_givens_t g, const float* theta, const float* y,
+                               const float* gy, float* gx, float* gtheta, int64_t batch,
+                               gft_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GFT_H */

@@ -1,0 +1,330 @@
+"""GB300-native batched fast graph Fourier transform (Lu & Ortega, "Fast
+Graph Fourier Transforms Based on Graph Symmetry and Bipartition").
+
+Thin Python binding over the C-ABI library ``libgft.so`` (include/gft.h).
+PyTorch supplies device memory and streams; every step of a transform runs
+in the library's CUDA kernels, and a missing library raises instead of
+falling back to anything else.
+
+    import numpy as np, torch, paper_1907_07875_gb300 as gft
+    L = gft.laplacian(W, s)                       # Eq. 5
+    plan = gft.Plan(L, [phi], split_components=True)
+    y = plan.forward(x)                           # x: cuda float32 [batch, n]
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import _native
+
+SPLIT_COMPONENTS = 0x1
+ORDER_BLOCK = 0x2
+ANALYZE_ONLY = 0x4
+PRECISIONS = {"fp32": 0, "bf16": 1, "bf16x3": 2, "fp16x3": 3}
+
+STATUS = {0: "GFT_OK", 1: "GFT_ERR_INVALID_ARG", 2: "GFT_ERR_NOT_INVOLUTION", 3: "GFT_ERR_NOT_SYMMETRIC",
+          4: "GFT_ERR_NOT_LAPLACIAN", 5: "GFT_ERR_NO_CONVERGENCE", 6: "GFT_ERR_CUDA", 7: "GFT_ERR_OOM",
+          8: "GFT_ERR_TIMEOUT", 9: "GFT_ERR_UNSUPPORTED", 10: "GFT_ERR_MISALIGNED", 11: "GFT_ERR_BLOCK_LEAK",
+          12: "GFT_ERR_NO_DEVICE"}
+
+
+class GftError(RuntimeError):
+    def __init__(self, code: int, message: str):
+        self.code = code
+        self.status = STATUS.get(code, str(code))
+        super().__init__(f"{self.status}: {message}")
+
+
+def lib():
+    return _native.load()
+
+
+def _check(code: int) -> None:
+    if code != 0:
+        raise GftError(code, lib().gft_last_error().decode())
+
+
+def _ptr(a) -> C.c_void_p:
+    """Address of a numpy array or a torch tensor (no copy)."""
+    if a is None:
+        return C.c_void_p(0)
+    if isinstance(a, np.ndarray):
+        return C.c_void_p(a.ctypes.data)
+    return C.c_void_p(a.data_ptr())
+
+
+def _stream_ptr(stream) -> C.c_void_p:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _as_f64(a, shape=None) -> np.ndarray:
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    if shape is not None and a.shape != shape:
+        raise ValueError(f"expected shape {shape}, got {a.shape}")
+    return a
+
+
+def laplacian(W, s=None) -> np.ndarray:
+    """Eq. 5: Laplacian from symmetric weights W and self-loops s (host)."""
+    W = _as_f64(W)
+    n = W.shape[0]
+    sv = None if s is None else _as_f64(s, (n,))
+    L = np.empty((n, n))
+    _check(lib().gft_laplacian_from_weights(n, _ptr(W), _ptr(sv), _ptr(L)))
+    return L
+
+
+class Plan:
+    """A fast-GFT plan for one graph (gft_plan_create)."""
+
+    def __init__(self, L, phis: Optional[Sequence] = None, *, split_components: bool = False,
+                 order_block: bool = False, analyze_only: bool = False):
+        L = _as_f64(L)
+        n = L.shape[0]
+        if L.shape != (n, n):
+            raise ValueError("L must be square")
+        phis = [] if phis is None else list(phis)
+        ph = (np.ascontiguousarray(np.stack([np.asarray(p, dtype=np.int32) for p in phis]))
+              if phis else None)
+        flags = ((SPLIT_COMPONENTS if split_components else 0) | (ORDER_BLOCK if order_block else 0)
+                 | (ANALYZE_ONLY if analyze_only else 0))
+        h = C.c_void_p()
+        self._h = None
+        _check(lib().gft_plan_create(n, _ptr(L), len(phis), _ptr(ph), flags, C.byref(h)))
+        self._h = h
+        self.n = n
+
+    # -- lifetime ------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().gft_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    # -- introspection ---------------------------------------------------------
+    @property
+    def info(self) -> dict:
+        inf = _native.PlanInfo()
+        _check(lib().gft_plan_get_info(self._h, C.byref(inf)))
+        return {f: getattr(inf, f) for f, _ in _native.PlanInfo._fields_}
+
+    def stage_pairs(self, stage: int) -> np.ndarray:
+        cnt = C.c_int32(0)
+        _check(lib().gft_plan_get_stage_pairs(self._h, stage, None, C.byref(cnt)))
+        out = np.zeros((cnt.value, 2), dtype=np.int32)
+        if cnt.value:
+            _check(lib().gft_plan_get_stage_pairs(self._h, stage, _ptr(out), C.byref(cnt)))
+        return out
+
+    def leaves(self):
+        inf = self.info
+        sizes = np.zeros(inf["n_leaves"], dtype=np.int32)
+        labels = np.zeros(self.n, dtype=np.int32)
+        _check(lib().gft_plan_get_leaves(self._h, _ptr(sizes), _ptr(labels)))
+        out, o = [], 0
+        for m in sizes:
+            out.append(labels[o:o + m].tolist())
+            o += m
+        return out
+
+    def leaf_laplacian(self, k: int) -> np.ndarray:
+        m = len(self.leaves()[k])
+        out = np.zeros((m, m))
+        _check(lib().gft_plan_get_leaf_laplacian(self._h, k, _ptr(out)))
+        return out
+
+    def output_map(self) -> np.ndarray:
+        out = np.zeros(self.n, dtype=np.int32)
+        _check(lib().gft_plan_get_output_map(self._h, _ptr(out)))
+        return out
+
+    def eigenvalues(self) -> np.ndarray:
+        out = np.zeros(self.n)
+        _check(lib().gft_plan_eigenvalues(self._h, _ptr(out)))
+        return out
+
+    def basis(self) -> np.ndarray:
+        out = np.zeros((self.n, self.n))
+        _check(lib().gft_plan_basis(self._h, _ptr(out)))
+        return out
+
+    # -- transforms ------------------------------------------------------------
+    def _run(self, fn_name, x, out, precision, stream):
+        import torch
+        if not (isinstance(x, torch.Tensor) and x.is_cuda):
+            raise TypeError("x must be a CUDA tensor")
+        if x.dim() != 2 or x.shape[1] != self.n or not x.is_contiguous():
+            raise ValueError(f"x must be a contiguous [batch, {self.n}] tensor")
+        if out is None:
+            out = torch.empty_like(x)
+        f = getattr(lib(), fn_name)
+        if fn_name.endswith("_f64"):
+            _check(f(self._h, _ptr(x), _ptr(out), x.shape[0], _stream_ptr(stream)))
+        else:
+            _check(f(self._h, _ptr(x), _ptr(out), x.shape[0], _stream_ptr(stream), PRECISIONS[precision]))
+        return out
+
+    def forward(self, x, out=None, precision: str = "fp32", stream=None):
+        """y = U^T x for every row of a CUDA tensor (float32, or float64)."""
+        import torch
+        if x.dtype == torch.float64:
+            return self._run("gft_plan_forward_f64", x, out, precision, stream)
+        return self._run("gft_plan_forward", x, out, precision, stream)
+
+    def inverse(self, y, out=None, precision: str = "fp32", stream=None):
+        import torch
+        if y.dtype == torch.float64:
+            return self._run("gft_plan_inverse_f64", y, out, precision, stream)
+        return self._run("gft_plan_inverse", y, out, precision, stream)
+
+    def forward_host(self, x, out=None, precision: str = "fp32"):
+        """Forward transform of a host batch (numpy float32 or CPU tensor);
+        the library pipelines host-device copies with the kernels."""
+        import torch
+        if isinstance(x, np.ndarray):
+            x = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32))
+        if x.dtype != torch.float32 or x.is_cuda or x.dim() != 2 or x.shape[1] != self.n:
+            raise ValueError("x must be a host float32 [batch, n] array")
+        x = x.contiguous()
+        if out is None:
+            out = torch.empty_like(x)
+        _check(lib().gft_plan_forward_host(self._h, _ptr(x), _ptr(out), x.shape[0], PRECISIONS[precision]))
+        return out
+
+    def device_error(self) -> int:
+        v = C.c_int32(0)
+        _check(lib().gft_device_error(self._h, C.byref(v)))
+        return v.value
+
+
+class Batch:
+    """Many plans transformed by one persistent, graph-captured launch."""
+
+    def __init__(self, plans: Sequence[Plan], batches: Sequence[int]):
+        self.plans = list(plans)
+        arr = (C.c_void_p * len(plans))(*[p.handle for p in plans])
+        b = np.ascontiguousarray(np.asarray(batches, dtype=np.int64))
+        h = C.c_void_p()
+        self._h = None
+        _check(lib().gft_batch_create(len(plans), C.cast(arr, C.c_void_p), _ptr(b), 0, C.byref(h)))
+        self._h = h
+        self.batches = b
+
+    def forward(self, xs, ys, stream=None):
+        k = len(self.plans)
+        xa = (C.c_void_p * k)(*[t.data_ptr() for t in xs])
+        ya = (C.c_void_p * k)(*[t.data_ptr() for t in ys])
+        _check(lib().gft_batch_forward(self._h, C.cast(xa, C.c_void_p), C.cast(ya, C.c_void_p),
+                                       _stream_ptr(stream)))
+        return ys
+
+    def tile(self, i: int):
+        t, th = C.c_int32(), C.c_int32()
+        _check(lib().gft_batch_get_tile(self._h, i, C.byref(t), C.byref(th)))
+        return t.value, th.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().gft_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Givens:
+    """Layered Givens rotations (Eq. 1, Fig. 1) on fixed pairings."""
+
+    def __init__(self, n: int, pairs):
+        pairs = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32))
+        if pairs.ndim != 3 or pairs.shape[1:] != (n // 2, 2):
+            raise ValueError("pairs must have shape (n_stages, n/2, 2)")
+        h = C.c_void_p()
+        self._h = None
+        _check(lib().gft_givens_create(n, pairs.shape[0], _ptr(pairs), C.byref(h)))
+        self._h = h
+        self.n = n
+        self.n_stages = pairs.shape[0]
+        self.pairs = pairs
+
+    def forward(self, theta, x, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty_like(x)
+        _check(lib().gft_givens_forward(self._h, _ptr(theta), _ptr(x), _ptr(out), x.shape[0],
+                                        _stream_ptr(stream)))
+        return out
+
+    def backward(self, theta, y, gy, stream=None):
+        import torch
+        gx = torch.empty_like(gy)
+        gth = torch.empty_like(theta)
+        _check(lib().gft_givens_backward(self._h, _ptr(theta), _ptr(y), _ptr(gy), _ptr(gx), _ptr(gth),
+                                         y.shape[0], _stream_ptr(stream)))
+        return gx, gth
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().gft_givens_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _givens_function():
+    import torch
+
+    class GivensFunction(torch.autograd.Function):
+        """y = G_S ... G_1 x with hand-written forward and backward kernels."""
+
+        @staticmethod
+        def forward(ctx, x, theta, net):
+            y = net.forward(theta.detach().contiguous(), x.detach().contiguous())
+            ctx.save_for_backward(y, theta)
+            ctx.net = net
+            return y
+
+        @staticmethod
+        def backward(ctx, gy):
+            y, theta = ctx.saved_tensors
+            gx, gth = ctx.net.backward(theta.detach().contiguous(), y, gy.contiguous())
+            return gx, gth, None
+
+    return GivensFunction
+
+
+_GF = None
+
+
+def givens_apply(x, theta, net: Givens):
+    """Differentiable Givens surrogate (autograd through the CUDA kernels)."""
+    global _GF
+    if _GF is None:
+        _GF = _givens_function()
+    return _GF.apply(x, theta, net)
+
+
+__all__ = ["Plan", "Batch", "Givens", "givens_apply", "laplacian", "GftError", "lib",
+           "SPLIT_COMPONENTS", "ORDER_BLOCK", "ANALYZE_ONLY", "PRECISIONS"]

@@ -1,0 +1,359 @@
+// extern "C" entry points for plans (include/gft.h).  Every call validates
+// its arguments, converts internal exceptions into gft_status codes, and
+// records the message for gft_last_error().
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+
+#include "gft_internal.h"
+
+namespace gft {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+void fail(gft_status code, const std::string& msg) { throw GftError{code, msg}; }
+
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+void cuda_check(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return;
+    if (e == cudaErrorMemoryAllocation) fail(GFT_ERR_OOM, std::string(what) + ": out of device memory");
+    fail(GFT_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+template <class F>
+gft_status guard(F&& f) {
+    try {
+        f();
+        return GFT_OK;
+    } catch (const GftError& e) {
+        set_last_error(e.msg);
+        return e.code;
+    } catch (const std::bad_alloc&) {
+        set_last_error("host allocation failed");
+        return GFT_ERR_OOM;
+    } catch (...) {
+        set_last_error("unexpected internal exception");
+        return GFT_ERR_INVALID_ARG;
+    }
+}
+
+const char* last_error_cstr() { return g_last_error.c_str(); }
+
+void check_plan(const gft_plan_s* p) {
+    if (!p) fail(GFT_ERR_INVALID_ARG, "plan is NULL");
+}
+
+void check_device_plan(const gft_plan_s* p) {
+    check_plan(p);
+    if (!p->has_device) fail(GFT_ERR_NO_DEVICE, "plan was created with GFT_ANALYZE_ONLY");
+}
+
+void check_io(const void* a, const void* b, int64_t batch) {
+    if (batch < 0) fail(GFT_ERR_INVALID_ARG, "batch < 0");
+    if (batch == 0) return;
+    if (!a || !b) fail(GFT_ERR_INVALID_ARG, "NULL signal pointer");
+    if ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b)) & 15u)
+        fail(GFT_ERR_MISALIGNED, "signal pointers must be 16-byte aligned");
+}
+
+}  // namespace gft
+
+gft_plan_s::~gft_plan_s() { gft::free_device(*this); }
+
+using namespace gft;
+
+extern "C" {
+
+const char* gft_status_string(gft_status s) {
+    switch (s) {
+        case GFT_OK: return "GFT_OK";
+        case GFT_ERR_INVALID_ARG: return "GFT_ERR_INVALID_ARG";
+        case GFT_ERR_NOT_INVOLUTION: return "GFT_ERR_NOT_INVOLUTION";
+        case GFT_ERR_NOT_SYMMETRIC: return "GFT_ERR_NOT_SYMMETRIC";
+        case GFT_ERR_NOT_LAPLACIAN: return "GFT_ERR_NOT_LAPLACIAN";
+        case GFT_ERR_NO_CONVERGENCE: return "GFT_ERR_NO_CONVERGENCE";
+        case GFT_ERR_CUDA: return "GFT_ERR_CUDA";
+        case GFT_ERR_OOM: return "GFT_ERR_OOM";
+        case GFT_ERR_TIMEOUT: return "GFT_ERR_TIMEOUT";
+        case GFT_ERR_UNSUPPORTED: return "GFT_ERR_UNSUPPORTED";
+        case GFT_ERR_MISALIGNED: return "GFT_ERR_MISALIGNED";
+        case GFT_ERR_BLOCK_LEAK: return "GFT_ERR_BLOCK_LEAK";
+        case GFT_ERR_NO_DEVICE: return "GFT_ERR_NO_DEVICE";
+    }
+    return "GFT_ERR_UNKNOWN";
+}
+
+const char* gft_last_error(void) { return last_error_cstr(); }
+
+int32_t gft_version(void) { return 10000; }
+
+gft_status gft_laplacian_from_weights(int32_t n, const double* W, const double* s, double* L) {
+    return guard([&] {
+        if (n < 1 || !W || !L) fail(GFT_ERR_INVALID_ARG, "n < 1 or NULL W / L");
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) {
+                const double w = W[(size_t)i * n + j];
+                if (!std::isfinite(w)) fail(GFT_ERR_NOT_LAPLACIAN, "non-finite weight");
+                if (i != j && w != W[(size_t)j * n + i]) fail(GFT_ERR_NOT_LAPLACIAN, "W is not symmetric");
+            }
+        if (s)
+            for (int i = 0; i < n; ++i)
+                if (!std::isfinite(s[i])) fail(GFT_ERR_NOT_LAPLACIAN, "non-finite self-loop");
+        for (int i = 0; i < n; ++i) {
+            double d = s ? s[i] : 0.0;
+            for (int j = 0; j < n; ++j)
+                if (j != i) {
+                    d += W[(size_t)i * n + j];
+                    L[(size_t)i * n + j] = -W[(size_t)i * n + j];
+                }
+            L[(size_t)i * n + i] = d;
+        }
+    });
+}
+
+gft_status gft_plan_create(int32_t n, const double* L, int32_t n_stages, const int32_t* phi,
+                           uint32_t flags, gft_plan_t* out) {
+    return guard([&] {
+        if (!out) fail(GFT_ERR_INVALID_ARG, "out is NULL");
+        if (n < 1 || n > 4096) fail(GFT_ERR_INVALID_ARG, "n must be in [1, 4096]");
+        if (!L) fail(GFT_ERR_INVALID_ARG, "L is NULL");
+        if (n_stages < 0 || n_stages > 16) fail(GFT_ERR_INVALID_ARG, "n_stages must be in [0, 16]");
+        if (n_stages > 0 && !phi) fail(GFT_ERR_INVALID_ARG, "phi is NULL");
+        if (flags & ~(GFT_SPLIT_COMPONENTS | GFT_ORDER_BLOCK | GFT_ANALYZE_ONLY))
+            fail(GFT_ERR_INVALID_ARG, "unknown flag");
+        std::unique_ptr<gft_plan_s> p(new gft_plan_s);
+        p->n = n;
+        p->flags = flags;
+        analyze(*p, L, n_stages, phi);
+        if (!(flags & GFT_ANALYZE_ONLY)) {
+            GFT_CUDA(cudaGetDevice(&p->device));
+            cudaStream_t st = nullptr;
+            GFT_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+            try {
+                jacobi_leaves(p->leaves, st);
+            } catch (...) {
+                cudaStreamDestroy(st);
+                throw;
+            }
+            GFT_CUDA(cudaStreamDestroy(st));
+            finalize_plan(*p);
+            GFT_CUDA(cudaDeviceSynchronize());
+        }
+        *out = p.release();
+    });
+}
+
+gft_status gft_plan_destroy(gft_plan_t plan) {
+    return guard([&] { delete plan; });
+}
+
+gft_status gft_plan_get_info(gft_plan_t p, gft_plan_info_t* info) {
+    return guard([&] {
+        check_plan(p);
+        if (!info) fail(GFT_ERR_INVALID_ARG, "info is NULL");
+        gft_plan_info_t r{};
+        r.n = p->n;
+        r.n_stages = p->n_stages;
+        r.n_leaves = (int32_t)p->leaves.size();
+        for (auto& s : p->stages) r.n_pairs += (int32_t)s.size();
+        for (auto& lf : p->leaves) {
+            const int64_t m = lf.m();
+            r.max_leaf = std::max<int32_t>(r.max_leaf, (int32_t)m);
+            r.fast_mults += m * m;
+            r.fast_adds += m * (m - 1);
+            r.jacobi_sweeps = std::max(r.jacobi_sweeps, lf.sweeps);
+        }
+        r.fast_adds += 2 * (int64_t)r.n_pairs;
+        r.has_device = p->has_device ? 1 : 0;
+        r.flags = p->flags;
+        *info = r;
+    });
+}
+
+gft_status gft_plan_get_stage_pairs(gft_plan_t p, int32_t stage, int32_t* pairs, int32_t* count) {
+    return guard([&] {
+        check_plan(p);
+        if (!count) fail(GFT_ERR_INVALID_ARG, "count is NULL");
+        if (stage < 0 || stage >= p->n_stages) fail(GFT_ERR_INVALID_ARG, "stage out of range");
+        const auto& st = p->stages[stage];
+        if (!pairs) {
+            *count = (int32_t)st.size();
+            return;
+        }
+        if (*count < (int32_t)st.size()) fail(GFT_ERR_INVALID_ARG, "pairs capacity too small");
+        for (size_t k = 0; k < st.size(); ++k) {
+            pairs[2 * k] = st[k].first;
+            pairs[2 * k + 1] = st[k].second;
+        }
+        *count = (int32_t)st.size();
+    });
+}
+
+gft_status gft_plan_get_leaves(gft_plan_t p, int32_t* sizes, int32_t* labels) {
+    return guard([&] {
+        check_plan(p);
+        if (!sizes || !labels) fail(GFT_ERR_INVALID_ARG, "NULL output");
+        size_t o = 0;
+        for (size_t k = 0; k < p->leaves.size(); ++k) {
+            sizes[k] = p->leaves[k].m();
+            for (int v : p->leaves[k].labels) labels[o++] = v;
+        }
+    });
+}
+
+gft_status gft_plan_get_leaf_laplacian(gft_plan_t p, int32_t leaf, double* Lk) {
+    return guard([&] {
+        check_plan(p);
+        if (!Lk) fail(GFT_ERR_INVALID_ARG, "NULL output");
+        if (leaf < 0 || leaf >= (int32_t)p->leaves.size()) fail(GFT_ERR_INVALID_ARG, "leaf out of range");
+        const auto& v = p->leaves[leaf].L;
+        std::memcpy(Lk, v.data(), v.size() * sizeof(double));
+    });
+}
+
+gft_status gft_plan_get_output_map(gft_plan_t p, int32_t* out_pos) {
+    return guard([&] {
+        check_device_plan(p);
+        if (!out_pos) fail(GFT_ERR_INVALID_ARG, "NULL output");
+        for (size_t i = 0; i < p->out_pos.size(); ++i) out_pos[i] = p->out_pos[i];
+    });
+}
+
+gft_status gft_plan_eigenvalues(gft_plan_t p, double* lambda) {
+    return guard([&] {
+        check_device_plan(p);
+        if (!lambda) fail(GFT_ERR_INVALID_ARG, "NULL output");
+        std::memcpy(lambda, p->lam_out.data(), sizeof(double) * p->n);
+    });
+}
+
+gft_status gft_plan_basis(gft_plan_t p, double* U) {
+    return guard([&] {
+        check_device_plan(p);
+        if (!U) fail(GFT_ERR_INVALID_ARG, "NULL output");
+        compute_basis(*p, U);
+    });
+}
+
+static void check_precision(gft_plan_s* p, uint32_t precision) {
+    if (precision > GFT_PREC_FP16X3) fail(GFT_ERR_INVALID_ARG, "unknown precision");
+    (void)p;
+}
+
+gft_status gft_plan_forward(gft_plan_t p, const float* x, float* y, int64_t batch, gft_stream_t stream,
+                            uint32_t precision) {
+    return guard([&] {
+        check_device_plan(p);
+        check_io(x, y, batch);
+        check_precision(p, precision);
+        cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+        p->last_stream = st;
+        if (batch == 0) return;
+        if (precision == GFT_PREC_FP32) launch_apply_f32(apply_args(*p, false), x, y, batch, false, st);
+        else launch_tc(*p, x, y, batch, false, st, precision);
+    });
+}
+
+gft_status gft_plan_inverse(gft_plan_t p, const float* y, float* x, int64_t batch, gft_stream_t stream,
+                            uint32_t precision) {
+    return guard([&] {
+        check_device_plan(p);
+        check_io(y, x, batch);
+        check_precision(p, precision);
+        cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+        p->last_stream = st;
+        if (batch == 0) return;
+        if (precision == GFT_PREC_FP32) launch_apply_f32(apply_args(*p, false), y, x, batch, true, st);
+        else launch_tc(*p, y, x, batch, true, st, precision);
+    });
+}
+
+gft_status gft_plan_forward_f64(gft_plan_t p, const double* x, double* y, int64_t batch, gft_stream_t stream) {
+    return guard([&] {
+        check_device_plan(p);
+        check_io(x, y, batch);
+        cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+        p->last_stream = st;
+        launch_apply_f64(apply_args(*p, true), x, y, batch, false, st);
+    });
+}
+
+gft_status gft_plan_inverse_f64(gft_plan_t p, const double* y, double* x, int64_t batch, gft_stream_t stream) {
+    return guard([&] {
+        check_device_plan(p);
+        check_io(y, x, batch);
+        cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+        p->last_stream = st;
+        launch_apply_f64(apply_args(*p, true), y, x, batch, true, st);
+    });
+}
+
+gft_status gft_plan_forward_host(gft_plan_t p, const float* x_host, float* y_host, int64_t batch,
+                                 uint32_t precision) {
+    return guard([&] {
+        check_device_plan(p);
+        if (batch < 0) fail(GFT_ERR_INVALID_ARG, "batch < 0");
+        if (batch == 0) return;
+        if (!x_host || !y_host) fail(GFT_ERR_INVALID_ARG, "NULL host pointer");
+        check_precision(p, precision);
+        const int n = p->n;
+        // chunks of about 4 Mi coefficients, two in flight on two streams
+        int64_t chunk = std::max<int64_t>(1, (int64_t)(4 << 20) / n);
+        chunk = (chunk + 3) & ~int64_t(3);
+        const size_t elems = (size_t)chunk * n;
+        if (p->stage_elems < elems) {
+            for (int b = 0; b < 2; ++b) {
+                if (p->d_stage[b]) cudaFree(p->d_stage[b]);
+                if (p->d_stage_out[b]) cudaFree(p->d_stage_out[b]);
+                p->d_stage[b] = p->d_stage_out[b] = nullptr;
+            }
+            p->stage_elems = 0;
+            for (int b = 0; b < 2; ++b) {
+                GFT_CUDA(cudaMalloc(&p->d_stage[b], elems * sizeof(float)));
+                GFT_CUDA(cudaMalloc(&p->d_stage_out[b], elems * sizeof(float)));
+            }
+            p->stage_elems = elems;
+        }
+        for (int b = 0; b < 2; ++b)
+            if (!p->host_streams[b]) GFT_CUDA(cudaStreamCreateWithFlags(&p->host_streams[b], cudaStreamNonBlocking));
+        int64_t done = 0;
+        int which = 0;
+        while (done < batch) {
+            const int64_t rows = std::min(chunk, batch - done);
+            const size_t bytes = (size_t)rows * n * sizeof(float);
+            cudaStream_t st = p->host_streams[which];
+            GFT_CUDA(cudaMemcpyAsync(p->d_stage[which], x_host + (size_t)done * n, bytes, cudaMemcpyHostToDevice, st));
+            if (precision == GFT_PREC_FP32)
+                launch_apply_f32(apply_args(*p, false), p->d_stage[which], p->d_stage_out[which], rows, false, st);
+            else
+                launch_tc(*p, p->d_stage[which], p->d_stage_out[which], rows, false, st, precision);
+            GFT_CUDA(cudaMemcpyAsync(y_host + (size_t)done * n, p->d_stage_out[which], bytes, cudaMemcpyDeviceToHost, st));
+            done += rows;
+            which ^= 1;
+        }
+        GFT_CUDA(cudaStreamSynchronize(p->host_streams[0]));
+        GFT_CUDA(cudaStreamSynchronize(p->host_streams[1]));
+        p->last_stream = nullptr;
+    });
+}
+
+gft_status gft_device_error(gft_plan_t p, int32_t* code) {
+    return guard([&] {
+        check_device_plan(p);
+        if (!code) fail(GFT_ERR_INVALID_ARG, "code is NULL");
+        GFT_CUDA(cudaStreamSynchronize(p->last_stream));
+        int v = 0;
+        GFT_CUDA(cudaMemcpy(&v, p->dev.d_err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (v) GFT_CUDA(cudaMemset(p->dev.d_err, 0, sizeof(int)));
+        *code = v;
+    });
+}
+
+}  // extern "C"

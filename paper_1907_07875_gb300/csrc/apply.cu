@@ -1,0 +1,411 @@
+// CUDA-core fast-GFT transform kernels (FP32 and FP64).
+//
+// Forward, per signal x (Sec. IV-C, Eq. 13 applied stage by stage):
+//   1. every Haar unit (x_i, x_j) -> (x_i + x_j, x_i - x_j), stage by stage
+//      (Sec. III: the 1/sqrt(2) of each unit is folded into the leaf matrices);
+//   2. every leaf block k: y_k = M_k^T x[I_k] with M_k = diag(2^(-e/2)) U_k;
+//   3. coefficients written at their output positions (ascending eigenvalue).
+// Inverse: the leaf products with M_k^T, then the stages in reverse order
+// (B_phi is its own inverse, Sec. III).
+//
+// Layout and schedule (GB300):
+//   * A CTA owns a tile of TS consecutive signals.  The tile is copied from
+//     HBM into shared memory with cp.async (16-byte copies when n is odd,
+//     4/8-byte copies otherwise) while the previous tile is being computed
+//     (double buffering), so every SM keeps tens of KB of loads in flight.
+//   * Shared tiles are row-major with an ODD row stride np (n, or n + 1):
+//     thread t works on signal t, so consecutive lanes touch consecutive
+//     banks and the per-signal phases are free of bank conflicts.
+//   * Each thread owns RS signals of the tile for the whole computation, so
+//     the stages and the leaf products need no barrier between them.
+//   * Leaf products: the leaf's inputs are gathered into registers (width
+//     bucketed to 4..64 at compile time); the matrix is read from shared
+//     memory as 4-wide vectors broadcast to the warp, and each vector feeds
+//     4*RS fused multiply-adds.
+//   * The output tile leaves with 16-byte (odd n) or 4-byte coalesced
+//     streaming stores.  Persistent grid: one wave of CTAs loops over tiles.
+#include <algorithm>
+#include <cstdint>
+#include <cstdlib>
+#include <cstdio>
+
+#include "gft_internal.h"
+
+namespace gft {
+
+namespace {
+
+constexpr int kSmemLimit = 232448;  // 227 KB opt-in per CTA
+
+template <class T> struct V4;
+template <> struct V4<float> {
+    float a, b, c, d;
+    __device__ __forceinline__ static V4 load(const float* p) {
+        const float4 v = *reinterpret_cast<const float4*>(p);
+        return {v.x, v.y, v.z, v.w};
+    }
+};
+template <> struct V4<double> {
+    double a, b, c, d;
+    __device__ __forceinline__ static V4 load(const double* p) {
+        const double2 v0 = *reinterpret_cast<const double2*>(p);
+        const double2 v1 = *reinterpret_cast<const double2*>(p + 2);
+        return {v0.x, v0.y, v1.x, v1.y};
+    }
+};
+
+struct KArgs {
+    const int* ints;
+    const void* mats;
+    const void* x;
+    void* y;
+    long long batch;
+    int n, np, n_pairs, n_leaves, ints_count;
+    int off_labels, off_outpos, off_desc;
+    int mats_smem;      // scalars of one direction's matrices (smem copy)
+    int ts;             // signals per tile
+    int nbuf;           // input tile buffers (1 or 2)
+    int inverse;
+    float inv_n;
+};
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+template <class T> __device__ __forceinline__ void cp_async_elem(T* s, const T* g) {
+    if constexpr (sizeof(T) == 8) cp_async8(s, g);
+    else cp_async4(s, g);
+}
+
+// row of flat tile element e, i.e. e / n, via a float reciprocal: exact for
+// e < 2^20 because the +0.5 keeps the product at least 0.5/n from an integer
+__device__ __forceinline__ int row_of(int e, float inv_n) { return __float2int_rz(((float)e + 0.5f) * inv_n); }
+
+template <class T, int THREADS>
+__device__ __forceinline__ void issue_tile_load(const KArgs& a, T* buf, long long tile) {
+    const T* src = reinterpret_cast<const T*>(a.x) + tile * (long long)a.ts * a.n;
+    const long long rows = min((long long)a.ts, a.batch - tile * (long long)a.ts);
+    const int E = (int)rows * a.n;
+    const int tid = threadIdx.x;
+    if (a.np == a.n) {  // odd n: the tile keeps the global layout; 16 B per copy
+        constexpr int PER = 16 / sizeof(T);
+        const int E16 = E / PER;
+        for (int c = tid; c < E16; c += THREADS) cp_async16(buf + c * PER, src + c * PER);
+        for (int e = E16 * PER + tid; e < E; e += THREADS) cp_async_elem(buf + e, src + e);
+    } else {
+        for (int e = tid; e < E; e += THREADS) {
+            const int t = row_of(e, a.inv_n);
+            cp_async_elem(buf + t * a.np + (e - t * a.n), src + e);
+        }
+    }
+}
+
+template <class T, int THREADS>
+__device__ __forceinline__ void store_tile(const KArgs& a, const T* buf, long long tile) {
+    T* dst = reinterpret_cast<T*>(a.y) + tile * (long long)a.ts * a.n;
+    const long long rows = min((long long)a.ts, a.batch - tile * (long long)a.ts);
+    const int E = (int)rows * a.n;
+    const int tid = threadIdx.x;
+    if (a.np == a.n) {
+        if constexpr (sizeof(T) == 4) {
+            const int E4 = E / 4;
+            for (int c = tid; c < E4; c += THREADS)
+                __stcs(reinterpret_cast<float4*>(dst) + c, reinterpret_cast<const float4*>(buf)[c]);
+            for (int e = E4 * 4 + tid; e < E; e += THREADS) __stcs(dst + e, buf[e]);
+        } else {
+            const int E2 = E / 2;
+            for (int c = tid; c < E2; c += THREADS)
+                __stcs(reinterpret_cast<double2*>(dst) + c, reinterpret_cast<const double2*>(buf)[c]);
+            for (int e = E2 * 2 + tid; e < E; e += THREADS) __stcs(dst + e, buf[e]);
+        }
+    } else {
+        for (int e = tid; e < E; e += THREADS) {
+            const int t = row_of(e, a.inv_n);
+            __stcs(dst + e, buf[t * a.np + (e - t * a.n)]);
+        }
+    }
+}
+
+// out[sidx[c]] = sum_r in[gidx[r]] * M[r][c] (c < m) for the RS signals this
+// thread owns; M is BK x BK row-major in shared memory, zero beyond m.
+template <class T, int BK, int RS, int THREADS>
+__device__ __forceinline__ void leaf_product(const T* in, T* out, int np, const int* gidx, const int* sidx,
+                                             const T* M, int m) {
+    const int tid = threadIdx.x;
+    T xr[RS][BK];
+#pragma unroll
+    for (int r = 0; r < BK; ++r) {
+        if (r < m) {
+            const int g = gidx[r];
+#pragma unroll
+            for (int s = 0; s < RS; ++s) xr[s][r] = in[(tid + s * THREADS) * np + g];
+        } else {
+#pragma unroll
+            for (int s = 0; s < RS; ++s) xr[s][r] = T(0);
+        }
+    }
+    for (int c0 = 0; c0 < m; c0 += 4) {
+        T acc[RS][4];
+#pragma unroll
+        for (int s = 0; s < RS; ++s) acc[s][0] = acc[s][1] = acc[s][2] = acc[s][3] = T(0);
+#pragma unroll
+        for (int r = 0; r < BK; ++r) {
+            if (r < m) {
+                const V4<T> u = V4<T>::load(M + r * BK + c0);
+#pragma unroll
+                for (int s = 0; s < RS; ++s) {
+                    acc[s][0] = fma(xr[s][r], u.a, acc[s][0]);
+                    acc[s][1] = fma(xr[s][r], u.b, acc[s][1]);
+                    acc[s][2] = fma(xr[s][r], u.c, acc[s][2]);
+                    acc[s][3] = fma(xr[s][r], u.d, acc[s][3]);
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (c0 + j < m) {
+                const int o = sidx[c0 + j];
+#pragma unroll
+                for (int s = 0; s < RS; ++s) out[(tid + s * THREADS) * np + o] = acc[s][j];
+            }
+        }
+    }
+}
+
+template <class T, int RS, int THREADS>
+__device__ __forceinline__ void leaf_dispatch(int bk, const T* in, T* out, int np, const int* gidx,
+                                              const int* sidx, const T* M, int m) {
+    if (bk == 4) leaf_product<T, 4, RS, THREADS>(in, out, np, gidx, sidx, M, m);
+    else if (bk == 8) leaf_product<T, 8, RS, THREADS>(in, out, np, gidx, sidx, M, m);
+    else if (bk == 16) leaf_product<T, 16, RS, THREADS>(in, out, np, gidx, sidx, M, m);
+    else {
+        if constexpr (RS <= 2) {
+            if (bk == 24) leaf_product<T, 24, RS, THREADS>(in, out, np, gidx, sidx, M, m);
+            else if (bk == 32) leaf_product<T, 32, RS, THREADS>(in, out, np, gidx, sidx, M, m);
+        }
+        if constexpr (RS == 1) {
+            if (bk == 48) leaf_product<T, 48, 1, THREADS>(in, out, np, gidx, sidx, M, m);
+            else if (bk == 64) leaf_product<T, 64, 1, THREADS>(in, out, np, gidx, sidx, M, m);
+        }
+    }
+}
+
+// One tile: stages and leaf products for the RS signals of every thread.
+template <class T, int RS, int THREADS>
+__device__ __forceinline__ void compute_tile(const KArgs& a, const int* ints, const T* mats, T* in, T* out) {
+    const int np = a.np, tid = threadIdx.x;
+    const int* pairs = ints;
+    const int* labels = ints + a.off_labels;
+    const int* outpos = ints + a.off_outpos;
+    const int* desc = ints + a.off_desc;
+    if (!a.inverse) {
+        for (int p = 0; p < a.n_pairs; ++p) {
+            const int i = pairs[2 * p], j = pairs[2 * p + 1];
+#pragma unroll
+            for (int s = 0; s < RS; ++s) {
+                T* row = in + (tid + s * THREADS) * np;
+                const T u = row[i], v = row[j];
+                row[i] = u + v;
+                row[j] = u - v;
+            }
+        }
+        for (int k = 0; k < a.n_leaves; ++k) {
+            const int* d = desc + kLeafDesc * k;
+            leaf_dispatch<T, RS, THREADS>(d[1], in, out, np, labels + d[2], outpos + d[2], mats + d[4], d[0]);
+        }
+    } else {
+        for (int k = 0; k < a.n_leaves; ++k) {
+            const int* d = desc + kLeafDesc * k;
+            leaf_dispatch<T, RS, THREADS>(d[1], in, out, np, outpos + d[2], labels + d[2], mats + d[4], d[0]);
+        }
+        for (int p = a.n_pairs - 1; p >= 0; --p) {
+            const int i = pairs[2 * p], j = pairs[2 * p + 1];
+#pragma unroll
+            for (int s = 0; s < RS; ++s) {
+                T* row = out + (tid + s * THREADS) * np;
+                const T u = row[i], v = row[j];
+                row[i] = u + v;
+                row[j] = u - v;
+            }
+        }
+    }
+}
+
+template <class T, int RS, int THREADS>
+__global__ void __launch_bounds__(THREADS) gft_apply_kernel(KArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    // [this direction's matrices][program ints, padded to 16 B][input tiles][output tile]
+    T* mats = reinterpret_cast<T*>(smem_raw);
+    int* ints = reinterpret_cast<int*>(smem_raw + sizeof(T) * a.mats_smem);
+    const int ints_pad = (a.ints_count + 3) & ~3;
+    T* tiles = reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(ints) + sizeof(int) * ints_pad);
+    const int tile_elems = a.ts * a.np;
+    T* in0 = tiles;
+    T* in1 = tiles + (a.nbuf == 2 ? tile_elems : 0);
+    T* out = tiles + a.nbuf * tile_elems;
+    const int tid = threadIdx.x;
+    const long long n_tiles = (a.batch + a.ts - 1) / a.ts;
+    long long tile = blockIdx.x;
+
+    // start the first tile's copy before loading the program
+    if (tile < n_tiles) issue_tile_load<T, THREADS>(a, in0, tile);
+    cp_async_commit();
+    for (int i = tid; i < a.ints_count; i += THREADS) ints[i] = a.ints[i];
+    __syncthreads();
+    {
+        const T* gm = reinterpret_cast<const T*>(a.mats);
+        const int* desc = ints + a.off_desc;
+        for (int k = 0; k < a.n_leaves; ++k) {
+            const int bk = desc[kLeafDesc * k + 1];
+            const T* src = gm + desc[kLeafDesc * k + 3] + (a.inverse ? bk * bk : 0);
+            T* dst = mats + desc[kLeafDesc * k + 4];
+            for (int e = tid; e < bk * bk; e += THREADS) dst[e] = src[e];
+        }
+    }
+    int cur = 0;
+    for (; tile < n_tiles; tile += gridDim.x) {
+        T* in = cur ? in1 : in0;
+        if (a.nbuf == 2) {
+            const long long nxt = tile + gridDim.x;
+            if (nxt < n_tiles) issue_tile_load<T, THREADS>(a, cur ? in0 : in1, nxt);
+            cp_async_commit();
+            cp_async_wait1();
+        } else {
+            cp_async_wait0();
+        }
+        __syncthreads();   // tile visible to all; previous output tile fully stored
+        compute_tile<T, RS, THREADS>(a, ints, mats, in, out);
+        __syncthreads();   // output tile complete; input buffer free
+        store_tile<T, THREADS>(a, out, tile);
+        if (a.nbuf == 2) {
+            cur ^= 1;
+        } else {
+            const long long nxt = tile + gridDim.x;
+            __syncthreads();
+            if (nxt < n_tiles) issue_tile_load<T, THREADS>(a, in0, nxt);
+            cp_async_commit();
+        }
+    }
+    cp_async_wait0();
+}
+
+using KFn = void (*)(KArgs);
+
+template <class T>
+KFn pick_kernel(int rs, int threads) {
+#define GFT_CASE(R, TH) \
+    if (rs == R && threads == TH) return gft_apply_kernel<T, R, TH>;
+    GFT_CASE(1, 64) GFT_CASE(1, 128) GFT_CASE(1, 256)
+    GFT_CASE(2, 64) GFT_CASE(2, 128) GFT_CASE(2, 256)
+    GFT_CASE(4, 64) GFT_CASE(4, 128)
+#undef GFT_CASE
+    return nullptr;
+}
+
+struct Cfg {
+    int rs, threads, nbuf;
+};
+
+int rs_limit(int max_bucket) { return max_bucket <= 16 ? 4 : (max_bucket <= 32 ? 2 : 1); }
+
+template <class T>
+size_t smem_bytes(const ApplyArgs& A, const Cfg& c) {
+    const size_t fixed = sizeof(T) * (size_t)A.mats_smem + sizeof(int) * (size_t)((A.ints_count + 3) & ~3);
+    return fixed + (size_t)(c.nbuf + 1) * c.rs * c.threads * (A.n | 1) * sizeof(T);
+}
+
+// Configuration: an explicit GFT_APPLY_CFG="rs,threads,nbuf" (tuning), else
+// the first of a fixed preference list that fits in shared memory.
+template <class T>
+Cfg choose_cfg(const ApplyArgs& A) {
+    const int rmax = rs_limit(A.max_bucket);
+    if (const char* e = std::getenv("GFT_APPLY_CFG")) {
+        Cfg c{0, 0, 0};
+        if (std::sscanf(e, "%d,%d,%d", &c.rs, &c.threads, &c.nbuf) == 3 && c.rs <= rmax &&
+            (c.nbuf == 1 || c.nbuf == 2) && pick_kernel<T>(c.rs, c.threads) &&
+            smem_bytes<T>(A, c) <= (size_t)kSmemLimit)
+            return c;
+    }
+    const Cfg pref[] = {{2, 128, 2}, {1, 256, 2}, {2, 64, 2}, {1, 128, 2}, {1, 64, 2},
+                        {2, 128, 1}, {1, 128, 1}, {1, 64, 1}};
+    for (const Cfg& c : pref) {
+        if (c.rs > rmax) continue;
+        if (sizeof(T) == 8 && c.threads == 256) continue;
+        if (smem_bytes<T>(A, c) <= (size_t)kSmemLimit) return c;
+    }
+    fail(GFT_ERR_UNSUPPORTED, "graph too large for the CUDA-core transform kernel (n=" + std::to_string(A.n) + ")");
+}
+
+template <class T>
+void launch_apply(const ApplyArgs& A, const T* x, T* y, int64_t batch, bool inverse, cudaStream_t st) {
+    if (batch <= 0) return;
+    if (A.max_bucket == 0)
+        fail(GFT_ERR_UNSUPPORTED, "a leaf has more than 64 nodes; the CUDA-core kernel handles leaves up to 64");
+    const Cfg c = choose_cfg<T>(A);
+    KArgs k{};
+    k.ints = A.ints;
+    k.mats = A.mats;
+    k.x = x;
+    k.y = y;
+    k.batch = batch;
+    k.n = A.n;
+    k.np = A.n | 1;
+    k.n_pairs = A.n_pairs;
+    k.n_leaves = A.n_leaves;
+    k.ints_count = A.ints_count;
+    k.off_labels = 2 * A.n_pairs + A.n_stages + 1;
+    k.off_outpos = k.off_labels + A.n;
+    k.off_desc = k.off_outpos + A.n;
+    k.mats_smem = A.mats_smem;
+    k.ts = c.rs * c.threads;
+    k.nbuf = c.nbuf;
+    k.inverse = inverse ? 1 : 0;
+    k.inv_n = 1.0f / (float)A.n;
+    const size_t smem = smem_bytes<T>(A, c);
+    KFn fn = pick_kernel<T>(c.rs, c.threads);
+    GFT_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    GFT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, c.threads, smem));
+    if (per_sm < 1) fail(GFT_ERR_UNSUPPORTED, "transform kernel does not fit on an SM");
+    const long long n_tiles = (batch + k.ts - 1) / k.ts;
+    const long long grid = std::min<long long>(n_tiles, (long long)per_sm * sm_count());
+    fn<<<(unsigned)grid, c.threads, smem, st>>>(k);
+    GFT_CUDA(cudaGetLastError());
+}
+
+}  // namespace
+
+int sm_count() {
+    static int cached = 0;
+    if (!cached) {
+        int dev = 0;
+        GFT_CUDA(cudaGetDevice(&dev));
+        GFT_CUDA(cudaDeviceGetAttribute(&cached, cudaDevAttrMultiProcessorCount, dev));
+    }
+    return cached;
+}
+
+void launch_apply_f32(const ApplyArgs& a, const float* x, float* y, int64_t batch, bool inverse,
+                      cudaStream_t stream) {
+    launch_apply<float>(a, x, y, batch, inverse, stream);
+}
+
+void launch_apply_f64(const ApplyArgs& a, const double* x, double* y, int64_t batch, bool inverse,
+                      cudaStream_t stream) {
+    launch_apply<double>(a, x, y, batch, inverse, stream);
+}
+
+}  // namespace gft

@@ -1,0 +1,126 @@
+// Internal declarations of the GB300 fast-GFT library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "gft.h"
+
+namespace gft {
+
+// ---------------------------------------------------------------------------
+// errors: internal code throws GftError; the extern "C" layer converts it to
+// a status code and records the message for gft_last_error().
+// ---------------------------------------------------------------------------
+struct GftError {
+    gft_status code;
+    std::string msg;
+};
+[[noreturn]] void fail(gft_status code, const std::string& msg);
+void set_last_error(const std::string& msg);
+void cuda_check(cudaError_t e, const char* what);
+#define GFT_CUDA(call) ::gft::cuda_check((call), #call)
+
+// device-side error word values (written by kernels, read by the host)
+enum DevErr : int { kDevOk = 0, kDevTimeout = GFT_ERR_TIMEOUT, kDevBadShape = GFT_ERR_INVALID_ARG };
+
+// ---------------------------------------------------------------------------
+// plan (host side)
+// ---------------------------------------------------------------------------
+struct Leaf {
+    std::vector<int> labels;   // original labels in leaf order
+    std::vector<double> L;     // m*m leaf Laplacian, row-major
+    std::vector<int> exps;     // per node: Haar stages its lineage took part in
+    std::string tag;           // "+"/"-" path (plus ".c" for a component)
+    // after eigendecomposition
+    std::vector<double> lam;   // ascending
+    std::vector<double> V;     // m*m row-major: V[r*m + c] = entry r of eigenvector c
+    int sweeps = 0;
+    int m() const { return (int)labels.size(); }
+};
+
+// Bucketed leaf width used by the CUDA-core kernels (registers are sized at
+// compile time): 4, 8, 16, 24, 32, 48, 64.  0 = too large for CUDA cores.
+int leaf_bucket(int m);
+constexpr int kMaxCoreLeaf = 64;
+
+// Everything a CUDA-core transform kernel needs, in one device allocation.
+//   ints:  [pairs 2P][stage_off S+1][labels n][out_pos n][leaf desc 5L]
+//   leaf desc = {m, bucket, off (into labels/out_pos), off_u (into mats),
+//                off_s (into the per-direction matrices held in smem)}
+//   mats:  per leaf, the forward matrix M_f (bucket x bucket, row-major,
+//          M_f[r][c] = 2^(-e_r/2) V[r][c], zero padded) followed by the
+//          inverse matrix M_i = M_f^T (same padding)
+struct DevProgram {
+    int n = 0, n_stages = 0, n_leaves = 0, n_pairs = 0;
+    int max_bucket = 0;
+    int ints_count = 0;      // int32 entries
+    int mats_count = 0;      // scalars per precision (both directions)
+    int mats_smem = 0;       // scalars of one direction's matrices
+    int* d_ints = nullptr;
+    float* d_mats32 = nullptr;
+    double* d_mats64 = nullptr;
+    int* d_err = nullptr;    // device error word
+};
+
+}  // namespace gft
+
+struct gft_plan_s {
+    int n = 0;
+    uint32_t flags = 0;
+    int n_stages = 0;
+    std::vector<double> L;                                  // n*n
+    std::vector<std::vector<std::pair<int, int>>> stages;   // (X label, partner)
+    std::vector<gft::Leaf> leaves;
+    bool has_device = false;
+    std::vector<int> out_pos;      // n, leaf-concatenated order -> coefficient
+    std::vector<double> lam_out;   // n, coefficient order
+    gft::DevProgram dev;
+    cudaStream_t last_stream = nullptr;
+    int device = 0;
+    // host-batch staging (gft_plan_forward_host)
+    float* d_stage[2] = {nullptr, nullptr};
+    float* d_stage_out[2] = {nullptr, nullptr};
+    size_t stage_elems = 0;
+    cudaStream_t host_streams[2] = {nullptr, nullptr};
+    // tensor-core data (built lazily)
+    void* tc = nullptr;
+    ~gft_plan_s();
+};
+
+namespace gft {
+
+// plan.cpp
+void analyze(gft_plan_s& p, const double* L, int n_stages, const int32_t* phi);
+void finalize_plan(gft_plan_s& p);           // ordering, signs, device program
+void compute_basis(const gft_plan_s& p, double* U);
+void free_device(gft_plan_s& p);
+
+// jacobi.cu: eigendecompose every leaf on the current device (FP64).
+void jacobi_leaves(std::vector<Leaf>& leaves, cudaStream_t stream);
+
+// apply.cu
+struct ApplyArgs {
+    const int* ints;
+    const void* mats;       // float* or double*
+    int n, n_stages, n_leaves, n_pairs, max_bucket;
+    int ints_count, mats_count, mats_smem;
+    int* err;
+};
+constexpr int kLeafDesc = 5;
+void launch_apply_f32(const ApplyArgs& a, const float* x, float* y, int64_t batch, bool inverse,
+                      cudaStream_t stream);
+void launch_apply_f64(const ApplyArgs& a, const double* x, double* y, int64_t batch, bool inverse,
+                      cudaStream_t stream);
+ApplyArgs apply_args(const gft_plan_s& p, bool f64);
+int sm_count();
+
+// tc.cu: leaf products on tcgen05 tensor cores (split precision)
+void launch_tc(gft_plan_s& p, const float* x, float* y, int64_t batch, bool inverse, cudaStream_t st,
+               uint32_t precision);
+
+}  // namespace gft

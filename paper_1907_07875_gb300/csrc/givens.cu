@@ -1,0 +1,323 @@
+// Layered Givens rotations (Eq. 1, Fig. 1): the learned surrogate that
+// stands in for a dense GFT on nearly symmetric graphs.
+//
+//   forward:  per stage s and pair k = (p, q) with angle theta:
+//             (y_p, y_q) = (c x_p - s x_q, s x_p + c x_q)
+//   backward: from the forward OUTPUT y and the loss gradient g = dL/dy,
+//             stage by stage in reverse:
+//               dL/dtheta += -g_p y_q + g_q y_p        (since dy_p = -y_q dtheta,
+//                                                       dy_q = y_p dtheta)
+//               x = G^T y (recover the stage input, no stored activations)
+//               g <- G^T g
+//
+// One thread owns one signal (its row lives in shared memory with an odd
+// stride, so lanes hit distinct banks).  Angle gradients: each warp reduces
+// its 32 contributions with shuffles into a per-warp shared array (no
+// atomics), the CTA sums its warps in fixed order into a per-CTA row of a
+// device scratch buffer, and a second kernel sums the rows in fixed order:
+// the result is deterministic.
+#include <algorithm>
+#include <memory>
+#include <vector>
+
+#include "gft_internal.h"
+
+struct gft_givens_s {
+    int n = 0, S = 0;
+    int* d_pairs = nullptr;        // S * n/2 * 2
+    float* d_partials = nullptr;   // grid * S * n/2 (scratch for the backward pass)
+    int partial_rows = 0;
+    ~gft_givens_s() {
+        if (d_pairs) cudaFree(d_pairs);
+        if (d_partials) cudaFree(d_partials);
+    }
+};
+
+namespace gft {
+
+namespace {
+
+constexpr int kGivThreads = 128;
+constexpr int kSmemLimitG = 232448;
+
+__device__ __forceinline__ int row_of_g(int e, float inv_n) { return __float2int_rz(((float)e + 0.5f) * inv_n); }
+
+// coalesced tile load of `rows` signals into smem rows of stride np
+__device__ __forceinline__ void load_rows(const float* src, float* dst, int rows, int n, int np, float inv_n) {
+    const int E = rows * n;
+    for (int e = threadIdx.x; e < E; e += blockDim.x) {
+        const int t = row_of_g(e, inv_n);
+        dst[t * np + (e - t * n)] = src[e];
+    }
+}
+
+__device__ __forceinline__ void store_rows(const float* src, float* dst, int rows, int n, int np, float inv_n) {
+    const int E = rows * n;
+    for (int e = threadIdx.x; e < E; e += blockDim.x) {
+        const int t = row_of_g(e, inv_n);
+        dst[e] = src[t * np + (e - t * n)];
+    }
+}
+
+struct GArgs {
+    const int* pairs;
+    const float* theta;
+    const float* x;     // forward: input; backward: forward output y
+    const float* g;     // backward: dL/dy
+    float* y;           // forward: output; backward: dL/dx
+    float* partials;    // backward: [gridDim.x][A]
+    long long batch;
+    int n, np, S, A;    // A = S * n/2 angles
+    float inv_n;
+};
+
+__global__ void __launch_bounds__(kGivThreads) givens_fwd_kernel(GArgs a) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    int* pr = reinterpret_cast<int*>(sm);                 // 2A
+    float* cs = reinterpret_cast<float*>(pr + 2 * a.A);   // 2A
+    float* tile = cs + 2 * a.A;                           // kGivThreads * np
+    for (int i = threadIdx.x; i < a.A; i += blockDim.x) {
+        pr[2 * i] = a.pairs[2 * i];
+        pr[2 * i + 1] = a.pairs[2 * i + 1];
+        float s, c;
+        sincosf(a.theta[i], &s, &c);
+        cs[2 * i] = c;
+        cs[2 * i + 1] = s;
+    }
+    const long long n_tiles = (a.batch + kGivThreads - 1) / kGivThreads;
+    for (long long tl = blockIdx.x; tl < n_tiles; tl += gridDim.x) {
+        const int rows = (int)min((long long)kGivThreads, a.batch - tl * kGivThreads);
+        __syncthreads();
+        load_rows(a.x + tl * kGivThreads * a.n, tile, rows, a.n, a.np, a.inv_n);
+        __syncthreads();
+        if ((int)threadIdx.x < rows) {
+            float* r = tile + threadIdx.x * a.np;
+            for (int i = 0; i < a.A; ++i) {
+                const int p = pr[2 * i], q = pr[2 * i + 1];
+                const float c = cs[2 * i], s = cs[2 * i + 1];
+                const float xp = r[p], xq = r[q];
+                r[p] = c * xp - s * xq;
+                r[q] = s * xp + c * xq;
+            }
+        }
+        __syncthreads();
+        store_rows(tile, a.y + tl * kGivThreads * a.n, rows, a.n, a.np, a.inv_n);
+    }
+}
+
+__global__ void __launch_bounds__(kGivThreads) givens_bwd_kernel(GArgs a) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    constexpr int W = kGivThreads / 32;
+    int* pr = reinterpret_cast<int*>(sm);                 // 2A
+    float* cs = reinterpret_cast<float*>(pr + 2 * a.A);   // 2A
+    float* acc = cs + 2 * a.A;                            // W * A (per-warp sums)
+    float* ty = acc + W * a.A;                            // kGivThreads * np
+    float* tg = ty + kGivThreads * a.np;                  // kGivThreads * np
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < a.A; i += blockDim.x) {
+        pr[2 * i] = a.pairs[2 * i];
+        pr[2 * i + 1] = a.pairs[2 * i + 1];
+        float s, c;
+        sincosf(a.theta[i], &s, &c);
+        cs[2 * i] = c;
+        cs[2 * i + 1] = s;
+    }
+    for (int i = threadIdx.x; i < W * a.A; i += blockDim.x) acc[i] = 0.f;
+    const long long n_tiles = (a.batch + kGivThreads - 1) / kGivThreads;
+    for (long long tl = blockIdx.x; tl < n_tiles; tl += gridDim.x) {
+        const int rows = (int)min((long long)kGivThreads, a.batch - tl * kGivThreads);
+        __syncthreads();
+        load_rows(a.x + tl * kGivThreads * a.n, ty, rows, a.n, a.np, a.inv_n);
+        load_rows(a.g + tl * kGivThreads * a.n, tg, rows, a.n, a.np, a.inv_n);
+        __syncthreads();
+        const bool live = (int)threadIdx.x < rows;
+        float* ry = ty + threadIdx.x * a.np;
+        float* rg = tg + threadIdx.x * a.np;
+        for (int i = a.A - 1; i >= 0; --i) {
+            const int p = pr[2 * i], q = pr[2 * i + 1];
+            const float c = cs[2 * i], s = cs[2 * i + 1];
+            float d = 0.f;
+            if (live) {
+                const float yp = ry[p], yq = ry[q], gp = rg[p], gq = rg[q];
+                d = gq * yp - gp * yq;
+                ry[p] = c * yp + s * yq;     // x = G^T y
+                ry[q] = -s * yp + c * yq;
+                rg[p] = c * gp + s * gq;     // g <- G^T g
+                rg[q] = -s * gp + c * gq;
+            }
+            for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+            if (lane == 0) acc[warp * a.A + i] += d;
+        }
+        __syncthreads();
+        store_rows(tg, a.y + tl * kGivThreads * a.n, rows, a.n, a.np, a.inv_n);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < a.A; i += blockDim.x) {
+        float s = 0.f;
+        for (int w = 0; w < W; ++w) s += acc[w * a.A + i];
+        a.partials[(long long)blockIdx.x * a.A + i] = s;
+    }
+}
+
+__global__ void givens_reduce_kernel(const float* partials, int rows, int A, float* out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= A) return;
+    float s = 0.f;
+    for (int r = 0; r < rows; ++r) s += partials[(long long)r * A + i];
+    out[i] = s;
+}
+
+size_t fwd_smem(int A, int np) { return sizeof(int) * 2 * A + sizeof(float) * (2 * A + (size_t)kGivThreads * np); }
+size_t bwd_smem(int A, int np) {
+    return sizeof(int) * 2 * A + sizeof(float) * (2 * A + (size_t)(kGivThreads / 32) * A + 2 * (size_t)kGivThreads * np);
+}
+
+void check_io_g(const void* a, const void* b, int64_t batch) {
+    if (batch < 0) fail(GFT_ERR_INVALID_ARG, "batch < 0");
+    if (batch == 0) return;
+    if (!a || !b) fail(GFT_ERR_INVALID_ARG, "NULL pointer");
+    if ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b)) & 15u)
+        fail(GFT_ERR_MISALIGNED, "pointers must be 16-byte aligned");
+}
+
+}  // namespace
+
+// exported through abi_givens below
+void givens_forward(gft_givens_s& g, const float* theta, const float* x, float* y, int64_t batch, cudaStream_t st) {
+    if (batch == 0) return;
+    GArgs a{};
+    a.pairs = g.d_pairs;
+    a.theta = theta;
+    a.x = x;
+    a.y = y;
+    a.batch = batch;
+    a.n = g.n;
+    a.np = g.n | 1;
+    a.S = g.S;
+    a.A = g.S * g.n / 2;
+    a.inv_n = 1.0f / g.n;
+    const size_t smem = fwd_smem(a.A, a.np);
+    if (smem > (size_t)kSmemLimitG) fail(GFT_ERR_UNSUPPORTED, "Givens network too large for shared memory");
+    GFT_CUDA(cudaFuncSetAttribute(givens_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    GFT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, givens_fwd_kernel, kGivThreads, smem));
+    const long long tiles = (batch + kGivThreads - 1) / kGivThreads;
+    const long long grid = std::min<long long>(tiles, (long long)std::max(1, per_sm) * sm_count());
+    givens_fwd_kernel<<<(unsigned)grid, kGivThreads, smem, st>>>(a);
+    GFT_CUDA(cudaGetLastError());
+}
+
+void givens_backward(gft_givens_s& g, const float* theta, const float* y, const float* gy, float* gx,
+                     float* gtheta, int64_t batch, cudaStream_t st) {
+    const int A = g.S * g.n / 2;
+    if (batch == 0) {
+        GFT_CUDA(cudaMemsetAsync(gtheta, 0, sizeof(float) * A, st));
+        return;
+    }
+    GArgs a{};
+    a.pairs = g.d_pairs;
+    a.theta = theta;
+    a.x = y;
+    a.g = gy;
+    a.y = gx;
+    a.batch = batch;
+    a.n = g.n;
+    a.np = g.n | 1;
+    a.S = g.S;
+    a.A = A;
+    a.inv_n = 1.0f / g.n;
+    const size_t smem = bwd_smem(A, a.np);
+    if (smem > (size_t)kSmemLimitG) fail(GFT_ERR_UNSUPPORTED, "Givens network too large for the backward kernel");
+    GFT_CUDA(cudaFuncSetAttribute(givens_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    GFT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, givens_bwd_kernel, kGivThreads, smem));
+    const long long tiles = (batch + kGivThreads - 1) / kGivThreads;
+    const int grid = (int)std::min<long long>(tiles, (long long)std::max(1, per_sm) * sm_count());
+    if (g.partial_rows < grid) {
+        if (g.d_partials) cudaFree(g.d_partials);
+        g.d_partials = nullptr;
+        g.partial_rows = 0;
+        GFT_CUDA(cudaMalloc(&g.d_partials, sizeof(float) * (size_t)grid * A));
+        g.partial_rows = grid;
+    }
+    a.partials = g.d_partials;
+    givens_bwd_kernel<<<grid, kGivThreads, smem, st>>>(a);
+    GFT_CUDA(cudaGetLastError());
+    givens_reduce_kernel<<<(A + 127) / 128, 128, 0, st>>>(g.d_partials, grid, A, gtheta);
+    GFT_CUDA(cudaGetLastError());
+}
+
+}  // namespace gft
+
+using namespace gft;
+
+namespace gft {
+template <class F> gft_status guard_g(F&& f) {
+    try {
+        f();
+        return GFT_OK;
+    } catch (const GftError& e) {
+        set_last_error(e.msg);
+        return e.code;
+    } catch (const std::bad_alloc&) {
+        set_last_error("host allocation failed");
+        return GFT_ERR_OOM;
+    } catch (...) {
+        set_last_error("unexpected internal exception");
+        return GFT_ERR_INVALID_ARG;
+    }
+}
+}  // namespace gft
+
+extern "C" {
+
+gft_status gft_givens_create(int32_t n, int32_t n_stages, const int32_t* pairs, gft_givens_t* out) {
+    return guard_g([&] {
+        if (!out || !pairs) fail(GFT_ERR_INVALID_ARG, "NULL argument");
+        if (n < 2 || n > 1024 || (n & 1)) fail(GFT_ERR_INVALID_ARG, "n must be even, 2..1024");
+        if (n_stages < 1 || n_stages > 64) fail(GFT_ERR_INVALID_ARG, "n_stages must be 1..64");
+        const int half = n / 2;
+        std::vector<int> seen(n);
+        for (int s = 0; s < n_stages; ++s) {
+            std::fill(seen.begin(), seen.end(), 0);
+            for (int k = 0; k < half; ++k) {
+                const int p = pairs[(size_t)(s * half + k) * 2], q = pairs[(size_t)(s * half + k) * 2 + 1];
+                if (p < 0 || p >= n || q < 0 || q >= n || p == q || seen[p] || seen[q])
+                    fail(GFT_ERR_INVALID_ARG, "stage " + std::to_string(s) + " is not a perfect matching");
+                seen[p] = seen[q] = 1;
+            }
+        }
+        std::unique_ptr<gft_givens_s> g(new gft_givens_s);
+        g->n = n;
+        g->S = n_stages;
+        const size_t cnt = (size_t)n_stages * half * 2;
+        GFT_CUDA(cudaMalloc(&g->d_pairs, sizeof(int) * cnt));
+        GFT_CUDA(cudaMemcpy(g->d_pairs, pairs, sizeof(int) * cnt, cudaMemcpyHostToDevice));
+        *out = g.release();
+    });
+}
+
+gft_status gft_givens_destroy(gft_givens_t g) {
+    return guard_g([&] { delete g; });
+}
+
+gft_status gft_givens_forward(gft_givens_t g, const float* theta, const float* x, float* y, int64_t batch,
+                              gft_stream_t stream) {
+    return guard_g([&] {
+        if (!g || !theta) fail(GFT_ERR_INVALID_ARG, "NULL argument");
+        check_io_g(x, y, batch);
+        givens_forward(*g, theta, x, y, batch, reinterpret_cast<cudaStream_t>(stream));
+    });
+}
+
+gft_status gft_givens_backward(gft_givens_t g, const float* theta, const float* y, const float* gy, float* gx,
+                               float* gtheta, int64_t batch, gft_stream_t stream) {
+    return guard_g([&] {
+        if (!g || !theta || !gtheta) fail(GFT_ERR_INVALID_ARG, "NULL argument");
+        check_io_g(y, gy, batch);
+        check_io_g(gx, gy, batch);
+        givens_backward(*g, theta, y, gy, gx, gtheta, batch, reinterpret_cast<cudaStream_t>(stream));
+    });
+}
+
+}  // extern "C"

@@ -1,0 +1,126 @@
+"""CPU tests of the C-ABI library: it loads, exports every symbol that
+include/gft.h declares, and its host-side plan analysis (integer work:
+partitions, pairs, leaves, leaf Laplacians) matches the oracle bit for bit.
+No GPU calls: plans are built with GFT_ANALYZE_ONLY."""
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import gft_workloads as W
+from oracle import gft as ogft
+from oracle import graph as ograph
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="session")
+def gft():
+    from paper_1907_07875_gb300.build import build
+    build()
+    import paper_1907_07875_gb300 as m
+    m.lib()
+    return m
+
+
+def header_functions():
+    txt = open(os.path.join(ROOT, "include", "gft.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(gft_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_exports_every_declared_symbol(gft):
+    from paper_1907_07875_gb300 import _native
+    names = header_functions()
+    assert len(names) >= 25
+    lib = gft.lib()
+    for nm in names:
+        assert hasattr(lib, nm), nm
+        assert nm in _native.SIGNATURES, nm
+    out = subprocess.run(["nm", "-D", "--defined-only", _native.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (gft_[a-z0-9_]+)", out))
+    assert set(names) <= exported
+
+
+def test_status_strings(gft):
+    lib = gft.lib()
+    for code, name in gft.STATUS.items():
+        assert lib.gft_status_string(code).decode() == name
+    assert lib.gft_version() >= 10000
+
+
+def test_laplacian_matches_oracle(gft):
+    for g in (W.skeleton25(), W.grid(5, weights="sym_uniform", seed=1), W.bipartite(12, 0.5, seed=3),
+              W.planted_symmetric(7, np.array([6, 5, 2, 3, 4, 1, 0]), seed=4)):
+        L = gft.laplacian(g.W, g.s)
+        assert np.allclose(L, ograph.laplacian(g.W, g.s), rtol=0, atol=1e-15)
+    with pytest.raises(gft.GftError) as e:
+        gft.laplacian(np.array([[0, 1.0], [2.0, 0]]))
+    assert e.value.status == "GFT_ERR_NOT_LAPLACIAN"
+
+
+def _families():
+    return [W.path(8), W.path(9), W.cycle(12), W.cycle(64), W.grid(4), W.grid(5, 4), W.grid(8),
+            W.grid(6, weights="sym_uniform", seed=9), W.skeleton25(), W.bipartite(32, 0.2, seed=5),
+            W.planted_symmetric(11, np.array([10, 9, 2, 7, 4, 5, 6, 3, 8, 1, 0]), seed=2)]
+
+
+@pytest.mark.parametrize("g", _families(), ids=lambda g: g.name)
+@pytest.mark.parametrize("split", [False, True])
+def test_plan_structure_bit_exact(gft, g, split):
+    """Stage pairs, leaf node lists (DFS order, + before -), and leaf
+    Laplacians from the library equal the oracle's decomposition."""
+    L = ograph.laplacian(g.W, g.s)
+    plan = gft.Plan(L, g.phis, split_components=split, analyze_only=True)
+    ref = ogft.decompose(L, g.phis, split_components=split)
+    for s, pairs in enumerate(ref.stages):
+        assert plan.stage_pairs(s).tolist() == [list(p) for p in pairs]
+    assert plan.leaves() == [b.labels for b in ref.leaves]
+    for k, b in enumerate(ref.leaves):
+        assert np.allclose(plan.leaf_laplacian(k), b.L, rtol=0, atol=1e-13 * max(1, np.abs(L).max()))
+    inf = plan.info
+    assert inf["n_leaves"] == len(ref.leaves) and inf["has_device"] == 0
+    adds, muls = (sum(2 * len(p) for p in ref.stages) + sum(len(b.labels) * (len(b.labels) - 1) for b in ref.leaves),
+                  sum(len(b.labels) ** 2 for b in ref.leaves))
+    assert (inf["fast_adds"], inf["fast_mults"]) == (adds, muls)
+
+
+def test_error_codes(gft):
+    g = W.path(6)
+    L = ograph.laplacian(g.W, g.s)
+    cases = [
+        (dict(L=L, phis=[[1, 2, 0, 3, 4, 5]]), "GFT_ERR_NOT_INVOLUTION"),
+        (dict(L=L, phis=[[0, 1, 2, 3, 4, 7]]), "GFT_ERR_NOT_INVOLUTION"),
+        (dict(L=L, phis=[[1, 0, 2, 3, 4, 5]]), "GFT_ERR_NOT_SYMMETRIC"),
+        (dict(L=L, phis=[W.reversal(6), [5, 1, 2, 3, 4, 0]]), "GFT_ERR_BLOCK_LEAK"),
+        (dict(L=L + np.triu(np.ones((6, 6)) * 1e-3, 1), phis=[]), "GFT_ERR_NOT_LAPLACIAN"),
+        (dict(L=np.where(np.eye(6) > 0, np.nan, L), phis=[]), "GFT_ERR_NOT_LAPLACIAN"),
+    ]
+    for kw, status in cases:
+        with pytest.raises(gft.GftError) as e:
+            gft.Plan(kw["L"], kw["phis"], analyze_only=True)
+        assert e.value.status == status, (kw, e.value)
+    # a stage that pairs a node already paired once with a node never paired
+    # (different numbers of earlier stages) is reported as unsupported
+    g3 = W.planted_symmetric(4, np.array([3, 1, 2, 0]), density=1.0, seed=1)
+    L3 = ograph.laplacian(g3.W, g3.s)
+    try:
+        gft.Plan(L3, [[3, 1, 2, 0], [1, 0, 2, 3]], analyze_only=True)
+    except gft.GftError as e:
+        assert e.status in ("GFT_ERR_UNSUPPORTED", "GFT_ERR_BLOCK_LEAK", "GFT_ERR_NOT_SYMMETRIC")
+    lib = gft.lib()
+    import ctypes as C
+    assert lib.gft_plan_create(0, None, 0, None, 0, C.byref(C.c_void_p())) == 1
+    assert lib.gft_plan_create(4, None, 0, None, 0, C.byref(C.c_void_p())) == 1
+    assert lib.gft_plan_destroy(None) == 0
+
+
+def test_analyze_only_plan_refuses_device_calls(gft):
+    g = W.path(8)
+    plan = gft.Plan(ograph.laplacian(g.W, g.s), g.phis, analyze_only=True)
+    for call in (plan.eigenvalues, plan.basis, plan.output_map, plan.device_error):
+        with pytest.raises(gft.GftError) as e:
+            call()
+        assert e.value.status == "GFT_ERR_NO_DEVICE"
