@@ -193,7 +193,7 @@ def run_ours(args, rank, world, local_rank):
     # its input from HBM
     x_host = W.signals(batch, n, seed + 7919 * rank)
     nbytes = batch * n * 4
-    nsets = max(2, -(-4 * L2_BYTES // (2 * nbytes)))
+    nsets = 2 if args.profile else max(2, -(-4 * L2_BYTES // (2 * nbytes)))
     xs = [torch.from_numpy(x_host).to(dev) for _ in range(nsets)]
     for i in range(1, nsets):
         xs[i].mul_(1.0 + 1e-3 * i)
@@ -201,7 +201,7 @@ def run_ours(args, rank, world, local_rank):
 
     # parity spot check against the FP64 oracle (rank 0, 2^14 signals)
     err = None
-    if rank == 0:
+    if rank == 0 and not args.profile:
         from oracle import gft as ogft
         from oracle import graph as ograph
         ref = ogft.fast_gft(ograph.laplacian(g.W, g.s), g.phis, split_components=True)
@@ -244,6 +244,11 @@ def run_ours(args, rank, world, local_rank):
         total_ms = t0.elapsed_time(t1)
         time.sleep(0.2)
     launch_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    if args.profile:
+        if rank == 0:
+            print(json.dumps({"profile_run": True, "ms_per_step": total_ms / args.steps,
+                              "config": {"workload": WORKLOAD, "sets": nsets}}), flush=True)
+        return
     if dist is not None:
         t = torch.tensor([total_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -334,6 +339,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="forward steps only, 2 buffer sets (for ncu captures)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -35,7 +35,7 @@ _REF_CACHE = {}
 
 
 def oracle_ref(g, split):
-    key = (g.name, split, tuple(tuple(p) for p in g.phis))
+    key = (g.W.tobytes(), g.s.tobytes(), split, tuple(tuple(int(v) for v in p) for p in g.phis))
     if key not in _REF_CACHE:
         _REF_CACHE[key] = ogft.fast_gft(ograph.laplacian(g.W, g.s), g.phis, split_components=split)
     return _REF_CACHE[key]
