@@ -49,7 +49,7 @@ def _peaks():
 
 def _kernel_hash():
     h = hashlib.sha256()
-    for f in ("apply.cu", "gft_internal.h"):
+    for f in ("apply.cu", "jit.cpp", "gft_internal.h"):
         with open(os.path.join(ROOT, "paper_1907_07875_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -230,7 +230,6 @@ def run_ours(args, rank, world, local_rank):
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     with ClockSampler(local_rank) as clk:
-        time.sleep(0.3)
         torch.cuda.synchronize()
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
@@ -242,7 +241,6 @@ def run_ours(args, rank, world, local_rank):
         t1.record(stream)
         torch.cuda.synchronize()
         total_ms = t0.elapsed_time(t1)
-        time.sleep(0.2)
     launch_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     if args.profile:
         if rank == 0:
@@ -316,7 +314,8 @@ def run_ours(args, rank, world, local_rank):
         "err_vs_fp64": err,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
-                     "alg_bytes_per_launch": alg_bytes, "kernel": "gft_apply_kernel"},
+                     "alg_bytes_per_launch": alg_bytes,
+                     "kernel": "gft_jit_fwd_* (plan-specialised)" if plan.info["jit"] else "gft_apply_kernel"},
         "e2e": {"value": coeffs_per_step / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                 "d2h_bytes_per_step": nbytes},
         "gpu_launches": args.steps,
@@ -335,7 +334,7 @@ def run_ours(args, rank, world, local_rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--steps", type=int, default=20000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")

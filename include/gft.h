@@ -62,6 +62,7 @@ typedef enum {
 #define GFT_SPLIT_COMPONENTS 0x1u  /* split leaves into connected components (Sec. V-E) */
 #define GFT_ORDER_BLOCK      0x2u  /* coefficients in leaf order instead of ascending eigenvalue */
 #define GFT_ANALYZE_ONLY     0x4u  /* host-side decomposition only: no device, no bases */
+#define GFT_NO_JIT           0x8u  /* never build plan-specialised kernels (interpreter only) */
 
 /* transform precision (plan forward / inverse) */
 #define GFT_PREC_FP32    0u  /* CUDA-core FP32 FMA, FP32 accumulation */
@@ -109,7 +110,12 @@ gft_status gft_laplacian_from_weights(int32_t n, const double* W, const double* 
  *            gft_plan_destroy).  Unchanged on error.
  * Unless GFT_ANALYZE_ONLY is set, the leaf Laplacians are eigendecomposed on
  * the current CUDA device by a batched FP64 Jacobi kernel and the bases are
- * uploaded; the call synchronises the device.  Eigenvector signs: the first
+ * uploaded; the call synchronises the device.  For graphs of at most 64
+ * nodes (sum of squared leaf sizes <= 2048) and without GFT_NO_JIT, the
+ * call also generates a kernel specialised to this plan (indices and
+ * folded leaf matrices as constants), compiles it with NVRTC for sm_103a,
+ * and times several launch shapes on a scratch batch to keep the fastest;
+ * transforms then use it, otherwise the table-driven kernel.  Eigenvector signs: the first
  * entry of largest magnitude (within 1e-9 relative) of every full-length
  * basis vector is made positive.  Output order: ascending eigenvalue;
  * eigenvalues within 1e-9*max(1,|lambda|max) of a neighbour form a cluster
@@ -135,6 +141,10 @@ typedef struct {
     uint32_t flags;
     int64_t fast_mults;     /* multiplies per signal: sum of m_k^2 (Sec. V-G) */
     int64_t fast_adds;      /* adds per signal: 2 per Haar unit + sum m_k(m_k-1) */
+    int32_t jit;            /* 1 if a plan-specialised kernel is in use */
+    int32_t tile_signals;   /* FP32 forward launch shape chosen by the autotuner: */
+    int32_t threads;        /*   signals per tile and threads per block (0 if none) */
+    int32_t reserved;
 } gft_plan_info_t;
 
 gft_status gft_plan_get_info(gft_plan_t plan, gft_plan_info_t* info);
@@ -193,6 +203,10 @@ gft_status gft_plan_inverse_f64(gft_plan_t plan, const double* y, double* x, int
  */
 gft_status gft_plan_forward_host(gft_plan_t plan, const float* x_host, float* y_host,
                                  int64_t batch, uint32_t precision);
+
+/* Source text of the plan-specialised kernel module (FP32 if f64 == 0,
+ * else FP64): pass buf = NULL to query the length (including the NUL). */
+gft_status gft_plan_kernel_source(gft_plan_t plan, int32_t f64, char* buf, int64_t* len);
 
 /* Synchronise the plan's last stream and read (and clear) the plan's device
  * error word: 0 = none, else a GFT_ERR_* code a kernel recorded. */

@@ -23,6 +23,7 @@ from . import _native
 SPLIT_COMPONENTS = 0x1
 ORDER_BLOCK = 0x2
 ANALYZE_ONLY = 0x4
+NO_JIT = 0x8
 PRECISIONS = {"fp32": 0, "bf16": 1, "bf16x3": 2, "fp16x3": 3}
 
 STATUS = {0: "GFT_OK", 1: "GFT_ERR_INVALID_ARG", 2: "GFT_ERR_NOT_INVOLUTION", 3: "GFT_ERR_NOT_SYMMETRIC",
@@ -84,7 +85,7 @@ class Plan:
     """A fast-GFT plan for one graph (gft_plan_create)."""
 
     def __init__(self, L, phis: Optional[Sequence] = None, *, split_components: bool = False,
-                 order_block: bool = False, analyze_only: bool = False):
+                 order_block: bool = False, analyze_only: bool = False, jit: bool = True):
         L = _as_f64(L)
         n = L.shape[0]
         if L.shape != (n, n):
@@ -93,7 +94,7 @@ class Plan:
         ph = (np.ascontiguousarray(np.stack([np.asarray(p, dtype=np.int32) for p in phis]))
               if phis else None)
         flags = ((SPLIT_COMPONENTS if split_components else 0) | (ORDER_BLOCK if order_block else 0)
-                 | (ANALYZE_ONLY if analyze_only else 0))
+                 | (ANALYZE_ONLY if analyze_only else 0) | (0 if jit else NO_JIT))
         h = C.c_void_p()
         self._h = None
         _check(lib().gft_plan_create(n, _ptr(L), len(phis), _ptr(ph), flags, C.byref(h)))
@@ -205,6 +206,14 @@ class Plan:
             out = torch.empty_like(x)
         _check(lib().gft_plan_forward_host(self._h, _ptr(x), _ptr(out), x.shape[0], PRECISIONS[precision]))
         return out
+
+    def kernel_source(self, f64: bool = False) -> str:
+        """Source of the plan-specialised kernel module (NVRTC input)."""
+        n = C.c_int64(0)
+        _check(lib().gft_plan_kernel_source(self._h, int(f64), None, C.byref(n)))
+        buf = C.create_string_buffer(n.value)
+        _check(lib().gft_plan_kernel_source(self._h, int(f64), buf, C.byref(n)))
+        return buf.value.decode()
 
     def device_error(self) -> int:
         v = C.c_int32(0)
@@ -327,4 +336,4 @@ def givens_apply(x, theta, net: Givens):
 
 
 __all__ = ["Plan", "Batch", "Givens", "givens_apply", "laplacian", "GftError", "lib",
-           "SPLIT_COMPONENTS", "ORDER_BLOCK", "ANALYZE_ONLY", "PRECISIONS"]
+           "SPLIT_COMPONENTS", "ORDER_BLOCK", "ANALYZE_ONLY", "NO_JIT", "PRECISIONS"]

@@ -16,7 +16,8 @@ class PlanInfo(C.Structure):
     _fields_ = [("n", C.c_int32), ("n_stages", C.c_int32), ("n_leaves", C.c_int32),
                 ("n_pairs", C.c_int32), ("max_leaf", C.c_int32), ("has_device", C.c_int32),
                 ("jacobi_sweeps", C.c_int32), ("flags", C.c_uint32),
-                ("fast_mults", C.c_int64), ("fast_adds", C.c_int64)]
+                ("fast_mults", C.c_int64), ("fast_adds", C.c_int64), ("jit", C.c_int32),
+                ("tile_signals", C.c_int32), ("threads", C.c_int32), ("reserved", C.c_int32)]
 
 
 P = C.c_void_p
@@ -45,6 +46,7 @@ SIGNATURES = {
     "gft_plan_inverse_f64": (c_status, [c_plan, P, P, C.c_int64, P]),
     "gft_plan_forward_host": (c_status, [c_plan, P, P, C.c_int64, C.c_uint32]),
     "gft_device_error": (c_status, [c_plan, I32P]),
+    "gft_plan_kernel_source": (c_status, [c_plan, C.c_int32, P, I64P]),
     "gft_batch_create": (c_status, [C.c_int32, P, P, C.c_uint32, C.POINTER(C.c_void_p)]),
     "gft_batch_forward": (c_status, [C.c_void_p, P, P, P]),
     "gft_batch_get_tile": (c_status, [C.c_void_p, C.c_int32, I32P, I32P]),

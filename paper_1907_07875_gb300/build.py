@@ -72,7 +72,9 @@ def build(force: bool = False, extra_flags=None) -> str:
     if jobs or force or not os.path.exists(LIB_PATH) or any(
             os.path.getmtime(o) > os.path.getmtime(LIB_PATH) for o in objs):
         tmp = LIB_PATH + ".tmp"
-        cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs]
+        cuda_lib = os.path.join(os.path.dirname(os.path.dirname(nvcc())), "lib64")
+        cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-L", cuda_lib, "-lnvrtc",
+               "-Xlinker", "-rpath," + cuda_lib]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -126,7 +126,7 @@ gft_status gft_plan_create(int32_t n, const double* L, int32_t n_stages, const i
         if (!L) fail(GFT_ERR_INVALID_ARG, "L is NULL");
         if (n_stages < 0 || n_stages > 16) fail(GFT_ERR_INVALID_ARG, "n_stages must be in [0, 16]");
         if (n_stages > 0 && !phi) fail(GFT_ERR_INVALID_ARG, "phi is NULL");
-        if (flags & ~(GFT_SPLIT_COMPONENTS | GFT_ORDER_BLOCK | GFT_ANALYZE_ONLY))
+        if (flags & ~(GFT_SPLIT_COMPONENTS | GFT_ORDER_BLOCK | GFT_ANALYZE_ONLY | GFT_NO_JIT))
             fail(GFT_ERR_INVALID_ARG, "unknown flag");
         std::unique_ptr<gft_plan_s> p(new gft_plan_s);
         p->n = n;
@@ -143,7 +143,9 @@ gft_status gft_plan_create(int32_t n, const double* L, int32_t n_stages, const i
                 throw;
             }
             GFT_CUDA(cudaStreamDestroy(st));
-            finalize_plan(*p);
+            finalize_host(*p);
+            upload_plan(*p);
+            jit_build(*p);
             GFT_CUDA(cudaDeviceSynchronize());
         }
         *out = p.release();
@@ -173,6 +175,7 @@ gft_status gft_plan_get_info(gft_plan_t p, gft_plan_info_t* info) {
         r.fast_adds += 2 * (int64_t)r.n_pairs;
         r.has_device = p->has_device ? 1 : 0;
         r.flags = p->flags;
+        jit_info(*p, &r.jit, &r.tile_signals, &r.threads);
         *info = r;
     });
 }
@@ -256,8 +259,12 @@ gft_status gft_plan_forward(gft_plan_t p, const float* x, float* y, int64_t batc
         cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
         p->last_stream = st;
         if (batch == 0) return;
-        if (precision == GFT_PREC_FP32) launch_apply_f32(apply_args(*p, false), x, y, batch, false, st);
-        else launch_tc(*p, x, y, batch, false, st, precision);
+        if (precision == GFT_PREC_FP32) {
+            if (!jit_launch(*p, false, x, y, batch, false, st))
+                launch_apply_f32(apply_args(*p, false), x, y, batch, false, st);
+        } else {
+            launch_tc(*p, x, y, batch, false, st, precision);
+        }
     });
 }
 
@@ -270,8 +277,12 @@ gft_status gft_plan_inverse(gft_plan_t p, const float* y, float* x, int64_t batc
         cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
         p->last_stream = st;
         if (batch == 0) return;
-        if (precision == GFT_PREC_FP32) launch_apply_f32(apply_args(*p, false), y, x, batch, true, st);
-        else launch_tc(*p, y, x, batch, true, st, precision);
+        if (precision == GFT_PREC_FP32) {
+            if (!jit_launch(*p, false, y, x, batch, true, st))
+                launch_apply_f32(apply_args(*p, false), y, x, batch, true, st);
+        } else {
+            launch_tc(*p, y, x, batch, true, st, precision);
+        }
     });
 }
 
@@ -281,7 +292,8 @@ gft_status gft_plan_forward_f64(gft_plan_t p, const double* x, double* y, int64_
         check_io(x, y, batch);
         cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
         p->last_stream = st;
-        launch_apply_f64(apply_args(*p, true), x, y, batch, false, st);
+        if (!jit_launch(*p, true, x, y, batch, false, st))
+            launch_apply_f64(apply_args(*p, true), x, y, batch, false, st);
     });
 }
 
@@ -291,7 +303,8 @@ gft_status gft_plan_inverse_f64(gft_plan_t p, const double* y, double* x, int64_
         check_io(y, x, batch);
         cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
         p->last_stream = st;
-        launch_apply_f64(apply_args(*p, true), y, x, batch, true, st);
+        if (!jit_launch(*p, true, y, x, batch, true, st))
+            launch_apply_f64(apply_args(*p, true), y, x, batch, true, st);
     });
 }
 
@@ -330,8 +343,10 @@ gft_status gft_plan_forward_host(gft_plan_t p, const float* x_host, float* y_hos
             const size_t bytes = (size_t)rows * n * sizeof(float);
             cudaStream_t st = p->host_streams[which];
             GFT_CUDA(cudaMemcpyAsync(p->d_stage[which], x_host + (size_t)done * n, bytes, cudaMemcpyHostToDevice, st));
-            if (precision == GFT_PREC_FP32)
-                launch_apply_f32(apply_args(*p, false), p->d_stage[which], p->d_stage_out[which], rows, false, st);
+            if (precision == GFT_PREC_FP32) {
+                if (!jit_launch(*p, false, p->d_stage[which], p->d_stage_out[which], rows, false, st))
+                    launch_apply_f32(apply_args(*p, false), p->d_stage[which], p->d_stage_out[which], rows, false, st);
+            }
             else
                 launch_tc(*p, p->d_stage[which], p->d_stage_out[which], rows, false, st, precision);
             GFT_CUDA(cudaMemcpyAsync(y_host + (size_t)done * n, p->d_stage_out[which], bytes, cudaMemcpyDeviceToHost, st));
@@ -341,6 +356,22 @@ gft_status gft_plan_forward_host(gft_plan_t p, const float* x_host, float* y_hos
         GFT_CUDA(cudaStreamSynchronize(p->host_streams[0]));
         GFT_CUDA(cudaStreamSynchronize(p->host_streams[1]));
         p->last_stream = nullptr;
+    });
+}
+
+gft_status gft_plan_kernel_source(gft_plan_t p, int32_t f64, char* buf, int64_t* len) {
+    return guard([&] {
+        check_device_plan(p);
+        if (!len) fail(GFT_ERR_INVALID_ARG, "len is NULL");
+        if (!jit_eligible(*p)) fail(GFT_ERR_UNSUPPORTED, "no plan-specialised kernel for this plan");
+        const std::string s = jit_source(*p, f64 != 0);
+        if (!buf) {
+            *len = (int64_t)s.size() + 1;
+            return;
+        }
+        if (*len < (int64_t)s.size() + 1) fail(GFT_ERR_INVALID_ARG, "buffer too small");
+        std::memcpy(buf, s.c_str(), s.size() + 1);
+        *len = (int64_t)s.size() + 1;
     });
 }
 

@@ -18,12 +18,16 @@
 //     banks and the per-signal phases are free of bank conflicts.
 //   * Each thread owns RS signals of the tile for the whole computation, so
 //     the stages and the leaf products need no barrier between them.
-//   * Leaf products: the leaf's inputs are gathered into registers (width
-//     bucketed to 4..64 at compile time); the matrix is read from shared
-//     memory as 4-wide vectors broadcast to the warp, and each vector feeds
-//     4*RS fused multiply-adds.
-//   * The output tile leaves with 16-byte (odd n) or 4-byte coalesced
-//     streaming stores.  Persistent grid: one wave of CTAs loops over tiles.
+//   * Leaf products run IN PLACE: a leaf's inputs are gathered into
+//     registers (width bucketed to 4..64 at compile time), and its outputs
+//     overwrite those same slots.  The matrix is read from shared memory as
+//     4-wide vectors broadcast to the warp; each vector feeds 4*RS FMAs.
+//     No separate output tile is needed, which keeps more warps resident.
+//   * The output permutation (ascending eigenvalue) is folded into the
+//     store: coefficient j of a signal is read from slot src[j] and written
+//     with coalesced 16-byte streaming stores.  The inverse applies the same
+//     permutation while loading.  Persistent grid: one wave of CTAs loops
+//     over tiles.
 #include <algorithm>
 #include <cstdint>
 #include <cstdlib>
@@ -61,7 +65,7 @@ struct KArgs {
     void* y;
     long long batch;
     int n, np, n_pairs, n_leaves, ints_count;
-    int off_labels, off_outpos, off_desc;
+    int off_labels, off_outpos, off_src, off_desc;
     int mats_smem;      // scalars of one direction's matrices (smem copy)
     int ts;             // signals per tile
     int nbuf;           // input tile buffers (1 or 2)
@@ -95,12 +99,17 @@ template <class T> __device__ __forceinline__ void cp_async_elem(T* s, const T* 
 __device__ __forceinline__ int row_of(int e, float inv_n) { return __float2int_rz(((float)e + 0.5f) * inv_n); }
 
 template <class T, int THREADS>
-__device__ __forceinline__ void issue_tile_load(const KArgs& a, T* buf, long long tile) {
+__device__ __forceinline__ void issue_tile_load(const KArgs& a, const int* src_slot, T* buf, long long tile) {
     const T* src = reinterpret_cast<const T*>(a.x) + tile * (long long)a.ts * a.n;
     const long long rows = min((long long)a.ts, a.batch - tile * (long long)a.ts);
     const int E = (int)rows * a.n;
     const int tid = threadIdx.x;
-    if (a.np == a.n) {  // odd n: the tile keeps the global layout; 16 B per copy
+    if (a.inverse) {  // coefficient j of signal t goes to slot src[j] of row t
+        for (int e = tid; e < E; e += THREADS) {
+            const int t = row_of(e, a.inv_n);
+            cp_async_elem(buf + t * a.np + src_slot[e - t * a.n], src + e);
+        }
+    } else if (a.np == a.n) {  // odd n: the tile keeps the global layout; 16 B per copy
         constexpr int PER = 16 / sizeof(T);
         const int E16 = E / PER;
         for (int c = tid; c < E16; c += THREADS) cp_async16(buf + c * PER, src + c * PER);
@@ -113,45 +122,62 @@ __device__ __forceinline__ void issue_tile_load(const KArgs& a, T* buf, long lon
     }
 }
 
+template <class T> struct Vec4Store;
+template <> struct Vec4Store<float> {
+    __device__ __forceinline__ static void st(float* p, float a, float b, float c, float d) {
+        __stcs(reinterpret_cast<float4*>(p), make_float4(a, b, c, d));
+    }
+};
+template <> struct Vec4Store<double> {
+    __device__ __forceinline__ static void st(double* p, double a, double b, double c, double d) {
+        __stcs(reinterpret_cast<double2*>(p), make_double2(a, b));
+        __stcs(reinterpret_cast<double2*>(p) + 1, make_double2(c, d));
+    }
+};
+
+// Store a tile: forward reads coefficient j of row t from slot src[j];
+// inverse stores the rows as they are.  Four consecutive outputs per
+// thread and 16-byte-aligned vector stores (the tile start is a multiple of
+// 4 elements because TS is a multiple of 4).
 template <class T, int THREADS>
-__device__ __forceinline__ void store_tile(const KArgs& a, const T* buf, long long tile) {
+__device__ __forceinline__ void store_tile(const KArgs& a, const int* src_slot, const T* buf, long long tile) {
     T* dst = reinterpret_cast<T*>(a.y) + tile * (long long)a.ts * a.n;
     const long long rows = min((long long)a.ts, a.batch - tile * (long long)a.ts);
     const int E = (int)rows * a.n;
+    const int E4 = E / 4;
     const int tid = threadIdx.x;
-    if (a.np == a.n) {
-        if constexpr (sizeof(T) == 4) {
-            const int E4 = E / 4;
-            for (int c = tid; c < E4; c += THREADS)
-                __stcs(reinterpret_cast<float4*>(dst) + c, reinterpret_cast<const float4*>(buf)[c]);
-            for (int e = E4 * 4 + tid; e < E; e += THREADS) __stcs(dst + e, buf[e]);
-        } else {
-            const int E2 = E / 2;
-            for (int c = tid; c < E2; c += THREADS)
-                __stcs(reinterpret_cast<double2*>(dst) + c, reinterpret_cast<const double2*>(buf)[c]);
-            for (int e = E2 * 2 + tid; e < E; e += THREADS) __stcs(dst + e, buf[e]);
-        }
-    } else {
-        for (int e = tid; e < E; e += THREADS) {
+    const bool fwd = !a.inverse;
+    for (int c = tid; c < E4; c += THREADS) {
+        T v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = 4 * c + q;
             const int t = row_of(e, a.inv_n);
-            __stcs(dst + e, buf[t * a.np + (e - t * a.n)]);
+            const int j = e - t * a.n;
+            v[q] = buf[t * a.np + (fwd ? src_slot[j] : j)];
         }
+        Vec4Store<T>::st(dst + 4 * c, v[0], v[1], v[2], v[3]);
+    }
+    for (int e = E4 * 4 + tid; e < E; e += THREADS) {
+        const int t = row_of(e, a.inv_n);
+        const int j = e - t * a.n;
+        __stcs(dst + e, buf[t * a.np + (fwd ? src_slot[j] : j)]);
     }
 }
 
-// out[sidx[c]] = sum_r in[gidx[r]] * M[r][c] (c < m) for the RS signals this
-// thread owns; M is BK x BK row-major in shared memory, zero beyond m.
+// In place for the RS signals this thread owns: with v_r = row[idx[r]],
+// row[idx[c]] = sum_r v_r * M[r][c] (c < m).  M is BK x BK row-major in
+// shared memory, zero beyond m.
 template <class T, int BK, int RS, int THREADS>
-__device__ __forceinline__ void leaf_product(const T* in, T* out, int np, const int* gidx, const int* sidx,
-                                             const T* M, int m) {
+__device__ __forceinline__ void leaf_product(T* tile, int np, const int* idx, const T* M, int m) {
     const int tid = threadIdx.x;
     T xr[RS][BK];
 #pragma unroll
     for (int r = 0; r < BK; ++r) {
         if (r < m) {
-            const int g = gidx[r];
+            const int g = idx[r];
 #pragma unroll
-            for (int s = 0; s < RS; ++s) xr[s][r] = in[(tid + s * THREADS) * np + g];
+            for (int s = 0; s < RS; ++s) xr[s][r] = tile[(tid + s * THREADS) * np + g];
         } else {
 #pragma unroll
             for (int s = 0; s < RS; ++s) xr[s][r] = T(0);
@@ -177,65 +203,61 @@ __device__ __forceinline__ void leaf_product(const T* in, T* out, int np, const 
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             if (c0 + j < m) {
-                const int o = sidx[c0 + j];
+                const int o = idx[c0 + j];
 #pragma unroll
-                for (int s = 0; s < RS; ++s) out[(tid + s * THREADS) * np + o] = acc[s][j];
+                for (int s = 0; s < RS; ++s) tile[(tid + s * THREADS) * np + o] = acc[s][j];
             }
         }
     }
 }
 
 template <class T, int RS, int THREADS>
-__device__ __forceinline__ void leaf_dispatch(int bk, const T* in, T* out, int np, const int* gidx,
-                                              const int* sidx, const T* M, int m) {
-    if (bk == 4) leaf_product<T, 4, RS, THREADS>(in, out, np, gidx, sidx, M, m);
-    else if (bk == 8) leaf_product<T, 8, RS, THREADS>(in, out, np, gidx, sidx, M, m);
-    else if (bk == 16) leaf_product<T, 16, RS, THREADS>(in, out, np, gidx, sidx, M, m);
+__device__ __forceinline__ void leaf_dispatch(int bk, T* tile, int np, const int* idx, const T* M, int m) {
+    if (bk == 4) leaf_product<T, 4, RS, THREADS>(tile, np, idx, M, m);
+    else if (bk == 8) leaf_product<T, 8, RS, THREADS>(tile, np, idx, M, m);
+    else if (bk == 16) leaf_product<T, 16, RS, THREADS>(tile, np, idx, M, m);
     else {
         if constexpr (RS <= 2) {
-            if (bk == 24) leaf_product<T, 24, RS, THREADS>(in, out, np, gidx, sidx, M, m);
-            else if (bk == 32) leaf_product<T, 32, RS, THREADS>(in, out, np, gidx, sidx, M, m);
+            if (bk == 24) leaf_product<T, 24, RS, THREADS>(tile, np, idx, M, m);
+            else if (bk == 32) leaf_product<T, 32, RS, THREADS>(tile, np, idx, M, m);
         }
         if constexpr (RS == 1) {
-            if (bk == 48) leaf_product<T, 48, 1, THREADS>(in, out, np, gidx, sidx, M, m);
-            else if (bk == 64) leaf_product<T, 64, 1, THREADS>(in, out, np, gidx, sidx, M, m);
+            if (bk == 48) leaf_product<T, 48, 1, THREADS>(tile, np, idx, M, m);
+            else if (bk == 64) leaf_product<T, 64, 1, THREADS>(tile, np, idx, M, m);
         }
     }
 }
 
-// One tile: stages and leaf products for the RS signals of every thread.
+// One tile in place: stages and leaf products for the RS signals of every
+// thread (forward), or leaf products then stages in reverse (inverse).
 template <class T, int RS, int THREADS>
-__device__ __forceinline__ void compute_tile(const KArgs& a, const int* ints, const T* mats, T* in, T* out) {
+__device__ __forceinline__ void compute_tile(const KArgs& a, const int* ints, const T* mats, T* tile) {
     const int np = a.np, tid = threadIdx.x;
     const int* pairs = ints;
     const int* labels = ints + a.off_labels;
-    const int* outpos = ints + a.off_outpos;
     const int* desc = ints + a.off_desc;
     if (!a.inverse) {
         for (int p = 0; p < a.n_pairs; ++p) {
             const int i = pairs[2 * p], j = pairs[2 * p + 1];
 #pragma unroll
             for (int s = 0; s < RS; ++s) {
-                T* row = in + (tid + s * THREADS) * np;
+                T* row = tile + (tid + s * THREADS) * np;
                 const T u = row[i], v = row[j];
                 row[i] = u + v;
                 row[j] = u - v;
             }
         }
-        for (int k = 0; k < a.n_leaves; ++k) {
-            const int* d = desc + kLeafDesc * k;
-            leaf_dispatch<T, RS, THREADS>(d[1], in, out, np, labels + d[2], outpos + d[2], mats + d[4], d[0]);
-        }
-    } else {
-        for (int k = 0; k < a.n_leaves; ++k) {
-            const int* d = desc + kLeafDesc * k;
-            leaf_dispatch<T, RS, THREADS>(d[1], in, out, np, outpos + d[2], labels + d[2], mats + d[4], d[0]);
-        }
+    }
+    for (int k = 0; k < a.n_leaves; ++k) {
+        const int* d = desc + kLeafDesc * k;
+        leaf_dispatch<T, RS, THREADS>(d[1], tile, np, labels + d[2], mats + d[4], d[0]);
+    }
+    if (a.inverse) {
         for (int p = a.n_pairs - 1; p >= 0; --p) {
             const int i = pairs[2 * p], j = pairs[2 * p + 1];
 #pragma unroll
             for (int s = 0; s < RS; ++s) {
-                T* row = out + (tid + s * THREADS) * np;
+                T* row = tile + (tid + s * THREADS) * np;
                 const T u = row[i], v = row[j];
                 row[i] = u + v;
                 row[j] = u - v;
@@ -247,24 +269,24 @@ __device__ __forceinline__ void compute_tile(const KArgs& a, const int* ints, co
 template <class T, int RS, int THREADS>
 __global__ void __launch_bounds__(THREADS) gft_apply_kernel(KArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    // [this direction's matrices][program ints, padded to 16 B][input tiles][output tile]
+    // [this direction's matrices][program ints, padded to 16 B][nbuf tiles]
     T* mats = reinterpret_cast<T*>(smem_raw);
     int* ints = reinterpret_cast<int*>(smem_raw + sizeof(T) * a.mats_smem);
     const int ints_pad = (a.ints_count + 3) & ~3;
     T* tiles = reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(ints) + sizeof(int) * ints_pad);
     const int tile_elems = a.ts * a.np;
-    T* in0 = tiles;
-    T* in1 = tiles + (a.nbuf == 2 ? tile_elems : 0);
-    T* out = tiles + a.nbuf * tile_elems;
+    T* buf0 = tiles;
+    T* buf1 = tiles + (a.nbuf == 2 ? tile_elems : 0);
     const int tid = threadIdx.x;
     const long long n_tiles = (a.batch + a.ts - 1) / a.ts;
     long long tile = blockIdx.x;
 
-    // start the first tile's copy before loading the program
-    if (tile < n_tiles) issue_tile_load<T, THREADS>(a, in0, tile);
-    cp_async_commit();
+    // program tables first (the inverse load scatters through src)
     for (int i = tid; i < a.ints_count; i += THREADS) ints[i] = a.ints[i];
     __syncthreads();
+    const int* src_slot = ints + a.off_src;
+    if (tile < n_tiles) issue_tile_load<T, THREADS>(a, src_slot, buf0, tile);
+    cp_async_commit();
     {
         const T* gm = reinterpret_cast<const T*>(a.mats);
         const int* desc = ints + a.off_desc;
@@ -277,25 +299,26 @@ __global__ void __launch_bounds__(THREADS) gft_apply_kernel(KArgs a) {
     }
     int cur = 0;
     for (; tile < n_tiles; tile += gridDim.x) {
-        T* in = cur ? in1 : in0;
+        T* buf = cur ? buf1 : buf0;
+        const long long nxt = tile + gridDim.x;
         if (a.nbuf == 2) {
-            const long long nxt = tile + gridDim.x;
-            if (nxt < n_tiles) issue_tile_load<T, THREADS>(a, cur ? in0 : in1, nxt);
+            // the other buffer was released by the barrier that ended the
+            // previous iteration
+            if (nxt < n_tiles) issue_tile_load<T, THREADS>(a, src_slot, cur ? buf0 : buf1, nxt);
             cp_async_commit();
             cp_async_wait1();
         } else {
             cp_async_wait0();
         }
-        __syncthreads();   // tile visible to all; previous output tile fully stored
-        compute_tile<T, RS, THREADS>(a, ints, mats, in, out);
-        __syncthreads();   // output tile complete; input buffer free
-        store_tile<T, THREADS>(a, out, tile);
+        __syncthreads();   // tile landed for every thread
+        compute_tile<T, RS, THREADS>(a, ints, mats, buf);
+        __syncthreads();   // every row computed
+        store_tile<T, THREADS>(a, src_slot, buf, tile);
+        __syncthreads();   // buffer free for the next load
         if (a.nbuf == 2) {
             cur ^= 1;
         } else {
-            const long long nxt = tile + gridDim.x;
-            __syncthreads();
-            if (nxt < n_tiles) issue_tile_load<T, THREADS>(a, in0, nxt);
+            if (nxt < n_tiles) issue_tile_load<T, THREADS>(a, src_slot, buf0, nxt);
             cp_async_commit();
         }
     }
@@ -324,7 +347,7 @@ int rs_limit(int max_bucket) { return max_bucket <= 16 ? 4 : (max_bucket <= 32 ?
 template <class T>
 size_t smem_bytes(const ApplyArgs& A, const Cfg& c) {
     const size_t fixed = sizeof(T) * (size_t)A.mats_smem + sizeof(int) * (size_t)((A.ints_count + 3) & ~3);
-    return fixed + (size_t)(c.nbuf + 1) * c.rs * c.threads * (A.n | 1) * sizeof(T);
+    return fixed + (size_t)c.nbuf * c.rs * c.threads * (A.n | 1) * sizeof(T);
 }
 
 // Configuration: an explicit GFT_APPLY_CFG="rs,threads,nbuf" (tuning), else
@@ -368,7 +391,8 @@ void launch_apply(const ApplyArgs& A, const T* x, T* y, int64_t batch, bool inve
     k.ints_count = A.ints_count;
     k.off_labels = 2 * A.n_pairs + A.n_stages + 1;
     k.off_outpos = k.off_labels + A.n;
-    k.off_desc = k.off_outpos + A.n;
+    k.off_src = k.off_outpos + A.n;
+    k.off_desc = k.off_src + A.n;
     k.mats_smem = A.mats_smem;
     k.ts = c.rs * c.threads;
     k.nbuf = c.nbuf;

@@ -49,7 +49,9 @@ int leaf_bucket(int m);
 constexpr int kMaxCoreLeaf = 64;
 
 // Everything a CUDA-core transform kernel needs, in one device allocation.
-//   ints:  [pairs 2P][stage_off S+1][labels n][out_pos n][leaf desc 5L]
+//   ints:  [pairs 2P][stage_off S+1][labels n][out_pos n][src n][leaf desc 5L]
+//   src[j] = tile slot (node label) that holds coefficient j after the
+//          in-place leaf products
 //   leaf desc = {m, bucket, off (into labels/out_pos), off_u (into mats),
 //                off_s (into the per-direction matrices held in smem)}
 //   mats:  per leaf, the forward matrix M_f (bucket x bucket, row-major,
@@ -89,6 +91,8 @@ struct gft_plan_s {
     cudaStream_t host_streams[2] = {nullptr, nullptr};
     // tensor-core data (built lazily)
     void* tc = nullptr;
+    // plan-specialised kernels (jit.cpp)
+    void* jit = nullptr;
     ~gft_plan_s();
 };
 
@@ -96,7 +100,8 @@ namespace gft {
 
 // plan.cpp
 void analyze(gft_plan_s& p, const double* L, int n_stages, const int32_t* phi);
-void finalize_plan(gft_plan_s& p);           // ordering, signs, device program
+void finalize_host(gft_plan_s& p);           // ordering, signs
+void upload_plan(gft_plan_s& p);             // device program
 void compute_basis(const gft_plan_s& p, double* U);
 void free_device(gft_plan_s& p);
 
@@ -118,6 +123,14 @@ void launch_apply_f64(const ApplyArgs& a, const double* x, double* y, int64_t ba
                       cudaStream_t stream);
 ApplyArgs apply_args(const gft_plan_s& p, bool f64);
 int sm_count();
+
+// jit.cpp: plan-specialised kernels
+bool jit_eligible(const gft_plan_s& p);
+void jit_build(gft_plan_s& p);
+void jit_free(gft_plan_s& p);
+bool jit_launch(gft_plan_s& p, bool f64, const void* x, void* y, int64_t batch, bool inverse, cudaStream_t st);
+void jit_info(const gft_plan_s& p, int* jit, int* tile, int* threads);
+std::string jit_source(const gft_plan_s& p, bool f64);
 
 // tc.cu: leaf products on tcgen05 tensor cores (split precision)
 void launch_tc(gft_plan_s& p, const float* x, float* y, int64_t batch, bool inverse, cudaStream_t st,

@@ -1,0 +1,511 @@
+// Plan-specialised transform kernels, generated at plan creation and
+// compiled with NVRTC for sm_103a.
+//
+// The interpreter kernel (apply.cu) reads stage pairs, node lists and leaf
+// matrices from shared memory and spends most of its instructions on index
+// loads and address arithmetic.  For small graphs (n <= 64) the whole plan
+// fits in straight-line code, so this generator writes one kernel per plan
+// in which every index is a compile-time constant and every leaf-matrix
+// entry is an FMA immediate:
+//   * each thread loads its signal's n values from the shared tile into
+//     registers (vector loads when the row stride allows),
+//   * applies the Haar units as register additions / subtractions,
+//   * computes each coefficient as an FMA chain over its leaf's inputs
+//     (entries that are exactly zero are skipped), and writes the
+//     coefficients back over the row in output order, so the store is a
+//     plain coalesced copy.
+// The tile pipeline (persistent CTAs, cp.async double or single buffering,
+// 16-byte streaming stores) is the same as the interpreter's.  Several
+// launch shapes are compiled into one module and timed at plan creation;
+// the fastest per direction is kept (the autotuner).
+#include <nvrtc.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "gft_internal.h"
+
+namespace gft {
+
+namespace {
+
+constexpr int kSmemLimitJ = 232448;
+
+struct Cand {
+    int rs, threads, nbuf;
+};
+
+// launch shapes compiled and timed for FP32; FP64 uses the first only
+const Cand kCands[] = {{2, 64, 1}, {2, 128, 1}, {1, 128, 1}, {2, 128, 2}};
+
+enum RowMode { kContig = 0, kVec4 = 1, kPad1 = 2 };
+
+std::string lit(double v, bool f64) {
+    char b[64];
+    if (f64) std::snprintf(b, sizeof b, "%a", v);
+    else std::snprintf(b, sizeof b, "%af", (double)(float)v);
+    return b;
+}
+
+const char* kHelpers = R"(
+typedef long long i64;
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+    unsigned a;
+    asm("{ .reg .u64 t; cvta.to.shared.u64 t, %1; cvt.u32.u64 %0, t; }" : "=r"(a) : "l"(p));
+    return a;
+}
+__device__ __forceinline__ void cpa16(void* s, const void* g) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(smem_addr(s)), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cpa8(void* s, const void* g) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" :: "r"(smem_addr(s)), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cpa4(void* s, const void* g) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" :: "r"(smem_addr(s)), "l"(g) : "memory");
+}
+__device__ __forceinline__ void commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void stcs(float* p, float v) { asm volatile("st.global.cs.f32 [%0], %1;" :: "l"(p), "f"(v) : "memory"); }
+__device__ __forceinline__ void stcs(double* p, double v) { asm volatile("st.global.cs.f64 [%0], %1;" :: "l"(p), "d"(v) : "memory"); }
+__device__ __forceinline__ void stcs16(float* p, const float* s) {
+    const float4 v = *reinterpret_cast<const float4*>(s);
+    asm volatile("st.global.cs.v4.f32 [%0], {%1,%2,%3,%4};" :: "l"(p), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w) : "memory");
+}
+__device__ __forceinline__ void stcs16(double* p, const double* s) {
+    const double2 v = *reinterpret_cast<const double2*>(s);
+    asm volatile("st.global.cs.v2.f64 [%0], {%1,%2};" :: "l"(p), "d"(v.x), "d"(v.y) : "memory");
+}
+template <int THREADS, int TS>
+__device__ __forceinline__ void load_tile(const T* __restrict__ x, T* buf, i64 tile, i64 batch) {
+    const T* src = x + tile * (i64)TS * N;
+    const int rows = (int)min((i64)TS, batch - tile * (i64)TS);
+    const int E = rows * N;
+    const int tid = threadIdx.x;
+#if MODE == 0
+    constexpr int PER = 16 / sizeof(T);
+    const int E16 = E / PER;
+    for (int c = tid; c < E16; c += THREADS) cpa16(buf + c * PER, src + c * PER);
+    for (int e = E16 * PER + tid; e < E; e += THREADS) { if (sizeof(T) == 8) cpa8(buf + e, src + e); else cpa4(buf + e, src + e); }
+#elif MODE == 1
+    const int G = E / 4;
+    for (int g = tid; g < G; g += THREADS) { const int t = g / (N / 4), c = g - t * (N / 4); cpa16(buf + t * NP + 4 * c, src + 4 * g); }
+#else
+    for (int e = tid; e < E; e += THREADS) { const int t = e / N, j = e - t * N; if (sizeof(T) == 8) cpa8(buf + t * NP + j, src + e); else cpa4(buf + t * NP + j, src + e); }
+#endif
+}
+template <int THREADS, int TS>
+__device__ __forceinline__ void store_tile(const T* buf, T* __restrict__ y, i64 tile, i64 batch) {
+    T* dst = y + tile * (i64)TS * N;
+    const int rows = (int)min((i64)TS, batch - tile * (i64)TS);
+    const int E = rows * N;
+    const int tid = threadIdx.x;
+#if MODE == 0
+    constexpr int PER = 16 / sizeof(T);
+    const int E16 = E / PER;
+    for (int c = tid; c < E16; c += THREADS) stcs16(dst + c * PER, buf + c * PER);
+    for (int e = E16 * PER + tid; e < E; e += THREADS) stcs(dst + e, buf[e]);
+#elif MODE == 1
+    const int G = E / 4;
+    for (int g = tid; g < G; g += THREADS) { const int t = g / (N / 4), c = g - t * (N / 4); stcs16(dst + 4 * g, buf + t * NP + 4 * c); }
+#else
+    for (int e = tid; e < E; e += THREADS) { const int t = e / N, j = e - t * N; stcs(dst + e, buf[t * NP + j]); }
+#endif
+}
+)";
+
+const char* kKernelTmpl = R"(
+extern "C" __global__ void __launch_bounds__(@THREADS@) @NAME@(const T* __restrict__ x, T* __restrict__ y, i64 batch) {
+    constexpr int THREADS = @THREADS@, RS = @RS@, NBUF = @NBUF@, TS = RS * THREADS;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* tiles = reinterpret_cast<T*>(smem_raw);
+    const int tid = threadIdx.x;
+    const i64 ntiles = (batch + TS - 1) / TS;
+    i64 tile = blockIdx.x;
+    if (tile < ntiles) load_tile<THREADS, TS>(x, tiles, tile, batch);
+    commit();
+    int cur = 0;
+    for (; tile < ntiles; tile += gridDim.x) {
+        T* buf = tiles + (NBUF == 2 ? cur * TS * NP : 0);
+        const i64 nxt = tile + gridDim.x;
+        if (NBUF == 2) {
+            if (nxt < ntiles) load_tile<THREADS, TS>(x, tiles + (cur ^ 1) * TS * NP, nxt, batch);
+            commit();
+            wait1();
+        } else {
+            wait0();
+        }
+        __syncthreads();
+#pragma unroll
+        for (int s = 0; s < RS; ++s) @BODY@(buf + (tid + s * THREADS) * NP);
+        __syncthreads();
+        store_tile<THREADS, TS>(buf, y, tile, batch);
+        __syncthreads();
+        if (NBUF == 2) {
+            cur ^= 1;
+        } else {
+            if (nxt < ntiles) load_tile<THREADS, TS>(x, tiles, nxt, batch);
+            commit();
+        }
+    }
+    wait0();
+}
+)";
+
+std::string replace_all(std::string s, const std::string& a, const std::string& b) {
+    for (size_t pos = s.find(a); pos != std::string::npos; pos = s.find(a, pos + b.size())) s.replace(pos, a.size(), b);
+    return s;
+}
+
+// per-row straight-line code
+std::string gen_bodies(const gft_plan_s& p, bool f64, int mode) {
+    const int n = p.n;
+    const char* T = f64 ? "double" : "float";
+    const char* FMA = f64 ? "fma" : "fmaf";
+    // (leaf, local) for every coefficient position, and the folded matrices
+    std::vector<int> leaf_of(n), local_of(n);
+    {
+        int i = 0;
+        for (size_t k = 0; k < p.leaves.size(); ++k)
+            for (int c = 0; c < p.leaves[k].m(); ++c, ++i) {
+                leaf_of[p.out_pos[i]] = (int)k;
+                local_of[p.out_pos[i]] = c;
+            }
+    }
+    auto Mval = [&](int k, int r, int c) {
+        const Leaf& lf = p.leaves[k];
+        return std::pow(2.0, -0.5 * lf.exps[r]) * lf.V[(size_t)r * lf.m() + c];
+    };
+    auto load_row = [&](std::ostringstream& o, const char* v) {
+        if (mode == kVec4 && !f64) {
+            for (int q = 0; q < n / 4; ++q)
+                o << "    { const float4 t = *reinterpret_cast<const float4*>(row + " << 4 * q << "); " << v << 4 * q
+                  << " = t.x; " << v << 4 * q + 1 << " = t.y; " << v << 4 * q + 2 << " = t.z; " << v << 4 * q + 3
+                  << " = t.w; }\n";
+        } else {
+            for (int i = 0; i < n; ++i) o << "    " << v << i << " = row[" << i << "];\n";
+        }
+    };
+    std::ostringstream o;
+    // ---------------- forward ----------------
+    o << "__device__ __noinline__ void body_fwd(" << T << "* __restrict__ row) {\n    " << T << " ";
+    for (int i = 0; i < n; ++i) o << "v" << i << (i + 1 < n ? ", " : ";\n");
+    load_row(o, "v");
+    for (auto& st : p.stages)
+        for (auto& pr : st)
+            o << "    { const " << T << " a = v" << pr.first << ", b = v" << pr.second << "; v" << pr.first
+              << " = a + b; v" << pr.second << " = a - b; }\n";
+    auto emit_coeff = [&](std::ostringstream& s, int j, const std::string& dst) {
+        const int k = leaf_of[j], c = local_of[j];
+        const Leaf& lf = p.leaves[k];
+        bool first = true;
+        for (int r = 0; r < lf.m(); ++r) {
+            const double u = Mval(k, r, c);
+            const float uf = (float)u;
+            if (f64 ? (u == 0.0) : (uf == 0.0f)) continue;
+            if (first) s << "        " << dst << " = v" << lf.labels[r] << " * " << lit(u, f64) << ";\n";
+            else s << "        " << dst << " = " << FMA << "(v" << lf.labels[r] << ", " << lit(u, f64) << ", " << dst << ");\n";
+            first = false;
+        }
+        if (first) s << "        " << dst << " = 0;\n";
+    };
+    if (mode == kVec4 && !f64) {
+        for (int q = 0; q < n / 4; ++q) {
+            o << "    { float o0, o1, o2, o3;\n";
+            for (int t = 0; t < 4; ++t) emit_coeff(o, 4 * q + t, "o" + std::to_string(t));
+            o << "      *reinterpret_cast<float4*>(row + " << 4 * q << ") = make_float4(o0, o1, o2, o3); }\n";
+        }
+    } else {
+        for (int j = 0; j < n; ++j) {
+            o << "    { " << T << " o;\n";
+            emit_coeff(o, j, "o");
+            o << "      row[" << j << "] = o; }\n";
+        }
+    }
+    o << "}\n";
+    // ---------------- inverse ----------------
+    o << "__device__ __noinline__ void body_inv(" << T << "* __restrict__ row) {\n    " << T << " ";
+    for (int i = 0; i < n; ++i) o << "v" << i << (i + 1 < n ? ", " : ";\n");
+    o << "    " << T << " ";
+    for (int i = 0; i < n; ++i) o << "w" << i << (i + 1 < n ? ", " : ";\n");
+    load_row(o, "v");
+    {
+        int i0 = 0;
+        for (size_t k = 0; k < p.leaves.size(); ++k) {
+            const Leaf& lf = p.leaves[k];
+            const int m = lf.m();
+            for (int r = 0; r < m; ++r) {
+                const std::string dst = "w" + std::to_string(lf.labels[r]);
+                bool first = true;
+                for (int c = 0; c < m; ++c) {
+                    const double u = Mval((int)k, r, c);
+                    if (f64 ? (u == 0.0) : ((float)u == 0.0f)) continue;
+                    const int j = p.out_pos[i0 + c];
+                    if (first) o << "    " << dst << " = v" << j << " * " << lit(u, f64) << ";\n";
+                    else o << "    " << dst << " = " << FMA << "(v" << j << ", " << lit(u, f64) << ", " << dst << ");\n";
+                    first = false;
+                }
+                if (first) o << "    " << dst << " = 0;\n";
+            }
+            i0 += m;
+        }
+    }
+    for (int s = (int)p.stages.size() - 1; s >= 0; --s)
+        for (int q = (int)p.stages[s].size() - 1; q >= 0; --q) {
+            auto& pr = p.stages[s][q];
+            o << "    { const " << T << " a = w" << pr.first << ", b = w" << pr.second << "; w" << pr.first
+              << " = a + b; w" << pr.second << " = a - b; }\n";
+        }
+    if (mode == kVec4 && !f64) {
+        for (int q = 0; q < n / 4; ++q)
+            o << "    *reinterpret_cast<float4*>(row + " << 4 * q << ") = make_float4(w" << 4 * q << ", w" << 4 * q + 1
+              << ", w" << 4 * q + 2 << ", w" << 4 * q + 3 << ");\n";
+    } else {
+        for (int i = 0; i < n; ++i) o << "    row[" << i << "] = w" << i << ";\n";
+    }
+    o << "}\n";
+    return o.str();
+}
+
+struct Layout {
+    int mode, np;
+};
+
+Layout row_layout(int n, bool f64) {
+    if (n & 1) return {kContig, n};
+    if (!f64 && n % 4 == 0) return {kVec4, ((n / 4) & 1) ? n : n + 4};
+    return {kPad1, n + 1};
+}
+
+std::string kernel_name(bool inverse, int ci) { return std::string(inverse ? "gft_jit_inv_" : "gft_jit_fwd_") + std::to_string(ci); }
+
+std::string gen_module(const gft_plan_s& p, bool f64, const Layout& L, std::vector<int>& cand_ids) {
+    std::ostringstream s;
+    s << "#define T " << (f64 ? "double" : "float") << "\n#define N " << p.n << "\n#define NP " << L.np
+      << "\n#define MODE " << L.mode << "\n";
+    s << kHelpers;
+    s << gen_bodies(p, f64, L.mode);
+    const size_t esz = f64 ? 8 : 4;
+    for (int ci = 0; ci < (int)(sizeof(kCands) / sizeof(kCands[0])); ++ci) {
+        const Cand& c = kCands[ci];
+        const size_t smem = (size_t)c.nbuf * c.rs * c.threads * L.np * esz;
+        if (smem > (size_t)kSmemLimitJ) continue;
+        if (f64 && ci > 0) break;
+        cand_ids.push_back(ci);
+        for (int inv = 0; inv < 2; ++inv) {
+            std::string k = kKernelTmpl;
+            k = replace_all(k, "@THREADS@", std::to_string(c.threads));
+            k = replace_all(k, "@RS@", std::to_string(c.rs));
+            k = replace_all(k, "@NBUF@", std::to_string(c.nbuf));
+            k = replace_all(k, "@NAME@", kernel_name(inv, ci));
+            k = replace_all(k, "@BODY@", inv ? "body_inv" : "body_fwd");
+            s << k;
+        }
+    }
+    return s.str();
+}
+
+std::vector<char> nvrtc_compile(const std::string& src) {
+    nvrtcProgram prog;
+    if (nvrtcCreateProgram(&prog, src.c_str(), "gft_plan.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS)
+        fail(GFT_ERR_CUDA, "nvrtcCreateProgram failed");
+    const bool verbose = std::getenv("GFT_JIT_VERBOSE") != nullptr;
+    const char* opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "-default-device", "--fmad=true",
+                          "--ptxas-options=-v"};
+    const nvrtcResult r = nvrtcCompileProgram(prog, verbose ? 5 : 4, opts);
+    if (verbose && r == NVRTC_SUCCESS) {
+        size_t ls = 0;
+        nvrtcGetProgramLogSize(prog, &ls);
+        std::string log(ls, '\0');
+        nvrtcGetProgramLog(prog, &log[0]);
+        std::fprintf(stderr, "%s\n", log.c_str());
+    }
+    if (r != NVRTC_SUCCESS) {
+        size_t ls = 0;
+        nvrtcGetProgramLogSize(prog, &ls);
+        std::string log(ls, '\0');
+        nvrtcGetProgramLog(prog, &log[0]);
+        nvrtcDestroyProgram(&prog);
+        fail(GFT_ERR_CUDA, "NVRTC compile of the plan kernel failed: " + log.substr(0, 2000));
+    }
+    size_t n = 0;
+    nvrtcGetCUBINSize(prog, &n);
+    std::vector<char> bin(n);
+    nvrtcGetCUBIN(prog, bin.data());
+    nvrtcDestroyProgram(&prog);
+    return bin;
+}
+
+// compiled cubins by source text (identical plans share one compile)
+std::mutex g_cache_mu;
+std::map<std::string, std::vector<char>>& cubin_cache() {
+    static std::map<std::string, std::vector<char>> c;
+    return c;
+}
+
+}  // namespace
+
+struct JitDir {
+    cudaKernel_t k = nullptr;
+    int rs = 0, threads = 0, nbuf = 0, per_sm = 0;
+    size_t smem = 0;
+    float us = 0.f;
+};
+
+struct JitPlan {
+    cudaLibrary_t lib32 = nullptr, lib64 = nullptr;
+    JitDir d32[2], d64[2];
+    int np32 = 0, np64 = 0;
+};
+
+bool jit_eligible(const gft_plan_s& p) {
+    if (std::getenv("GFT_DISABLE_JIT")) return false;
+    if (p.flags & GFT_NO_JIT) return false;
+    if (p.n > 64) return false;
+    long long fl = 0;
+    for (auto& lf : p.leaves) fl += (long long)lf.m() * lf.m();
+    return fl <= 2048;
+}
+
+std::string jit_source(const gft_plan_s& p, bool f64) {
+    std::vector<int> ids;
+    return gen_module(p, f64, row_layout(p.n, f64), ids);
+}
+
+static void launch_dir(const JitDir& d, const void* x, void* y, int64_t batch, cudaStream_t st) {
+    const long long ts = (long long)d.rs * d.threads;
+    const long long tiles = (batch + ts - 1) / ts;
+    const long long grid = std::min<long long>(tiles, (long long)d.per_sm * sm_count());
+    long long b = batch;
+    void* args[] = {(void*)&x, (void*)&y, (void*)&b};
+    GFT_CUDA(cudaLaunchKernel((const void*)d.k, dim3((unsigned)grid), dim3(d.threads), args, d.smem, st));
+}
+
+static void build_precision(gft_plan_s& p, JitPlan& J, bool f64) {
+    const Layout L = row_layout(p.n, f64);
+    std::vector<int> ids;
+    const std::string src = gen_module(p, f64, L, ids);
+    std::vector<char> bin;
+    {
+        std::lock_guard<std::mutex> g(g_cache_mu);
+        auto it = cubin_cache().find(src);
+        if (it != cubin_cache().end()) bin = it->second;
+    }
+    if (bin.empty()) {
+        bin = nvrtc_compile(src);
+        std::lock_guard<std::mutex> g(g_cache_mu);
+        cubin_cache()[src] = bin;
+    }
+    cudaLibrary_t lib = nullptr;
+    GFT_CUDA(cudaLibraryLoadData(&lib, bin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0));
+    (f64 ? J.lib64 : J.lib32) = lib;
+    (f64 ? J.np64 : J.np32) = L.np;
+    const size_t esz = f64 ? 8 : 4;
+    // autotune: time every compiled launch shape on a batch larger than L2
+    const int n = p.n;
+    const int64_t tb = std::max<int64_t>(4096, (int64_t)(96ll << 20) / (int64_t)(n * esz));
+    void *dx = nullptr, *dy = nullptr;
+    GFT_CUDA(cudaMalloc(&dx, tb * n * esz));
+    GFT_CUDA(cudaMalloc(&dy, tb * n * esz));
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    try {
+        GFT_CUDA(cudaMemset(dx, 0, tb * n * esz));
+        GFT_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        GFT_CUDA(cudaEventCreate(&e0));
+        GFT_CUDA(cudaEventCreate(&e1));
+        for (int inv = 0; inv < 2; ++inv) {
+            JitDir best;
+            for (int ci : ids) {
+                const Cand& c = kCands[ci];
+                JitDir d;
+                GFT_CUDA(cudaLibraryGetKernel(&d.k, lib, kernel_name(inv, ci).c_str()));
+                d.rs = c.rs;
+                d.threads = c.threads;
+                d.nbuf = c.nbuf;
+                d.smem = (size_t)c.nbuf * c.rs * c.threads * L.np * esz;
+                GFT_CUDA(cudaFuncSetAttribute((const void*)d.k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d.smem));
+                GFT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.per_sm, (const void*)d.k, d.threads, d.smem));
+                if (d.per_sm < 1) continue;
+                launch_dir(d, dx, dy, tb, st);
+                GFT_CUDA(cudaEventRecord(e0, st));
+                for (int r = 0; r < 3; ++r) launch_dir(d, dx, dy, tb, st);
+                GFT_CUDA(cudaEventRecord(e1, st));
+                GFT_CUDA(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                GFT_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                d.us = ms * 1000.f / 3.f;
+                if (!best.k || d.us < best.us) best = d;
+            }
+            if (!best.k) fail(GFT_ERR_UNSUPPORTED, "no plan-specialised launch shape fits");
+            (f64 ? J.d64 : J.d32)[inv] = best;
+        }
+    } catch (...) {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (st) cudaStreamDestroy(st);
+        cudaFree(dx);
+        cudaFree(dy);
+        throw;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(st);
+    cudaFree(dx);
+    cudaFree(dy);
+}
+
+void jit_build(gft_plan_s& p) {
+    if (!jit_eligible(p)) return;
+    JitPlan* J = new JitPlan;
+    try {
+        build_precision(p, *J, false);
+        build_precision(p, *J, true);
+    } catch (...) {
+        if (J->lib32) cudaLibraryUnload(J->lib32);
+        if (J->lib64) cudaLibraryUnload(J->lib64);
+        delete J;
+        throw;
+    }
+    p.jit = J;
+}
+
+void jit_free(gft_plan_s& p) {
+    if (!p.jit) return;
+    JitPlan* J = static_cast<JitPlan*>(p.jit);
+    if (J->lib32) cudaLibraryUnload(J->lib32);
+    if (J->lib64) cudaLibraryUnload(J->lib64);
+    delete J;
+    p.jit = nullptr;
+}
+
+bool jit_launch(gft_plan_s& p, bool f64, const void* x, void* y, int64_t batch, bool inverse, cudaStream_t st) {
+    if (!p.jit || std::getenv("GFT_FORCE_INTERPRETER")) return false;
+    JitPlan* J = static_cast<JitPlan*>(p.jit);
+    const JitDir& d = (f64 ? J->d64 : J->d32)[inverse ? 1 : 0];
+    if (!d.k) return false;
+    if (batch > 0) launch_dir(d, x, y, batch, st);
+    return true;
+}
+
+void jit_info(const gft_plan_s& p, int* jit, int* tile, int* threads) {
+    *jit = 0;
+    *tile = 0;
+    *threads = 0;
+    if (!p.jit) return;
+    const JitPlan* J = static_cast<const JitPlan*>(p.jit);
+    *jit = 1;
+    *tile = J->d32[0].rs * J->d32[0].threads;
+    *threads = J->d32[0].threads;
+}
+
+}  // namespace gft

@@ -228,6 +228,7 @@ void compute_basis(const gft_plan_s& p, double* U) {
 }
 
 void free_device(gft_plan_s& p) {
+    jit_free(p);
     if (p.dev.d_ints) cudaFree(p.dev.d_ints);
     if (p.dev.d_mats32) cudaFree(p.dev.d_mats32);
     if (p.dev.d_mats64) cudaFree(p.dev.d_mats64);
@@ -243,7 +244,7 @@ void free_device(gft_plan_s& p) {
     p.stage_elems = 0;
 }
 
-void finalize_plan(gft_plan_s& p) {
+void finalize_host(gft_plan_s& p) {
     const int n = p.n;
     // ---- output order: ascending eigenvalue, clusters by (leaf, index) ----
     struct Ent { double lam; int leaf, local; };
@@ -293,8 +294,10 @@ void finalize_plan(gft_plan_s& p) {
     }
     p.lam_out.assign(n, 0.0);
     for (int q = 0; q < N; ++q) p.lam_out[p.out_pos[q]] = ent[q].lam;
+}
 
-    // ---- device program ----
+void upload_plan(gft_plan_s& p) {
+    const int n = p.n;
     DevProgram& d = p.dev;
     d.n = n;
     d.n_stages = p.n_stages;
@@ -315,6 +318,15 @@ void finalize_plan(gft_plan_s& p) {
     }
     for (auto& lf : p.leaves) ints.insert(ints.end(), lf.labels.begin(), lf.labels.end());
     ints.insert(ints.end(), p.out_pos.begin(), p.out_pos.end());
+    {
+        // src[j]: the tile slot holding coefficient j once every leaf has
+        // written its outputs over its own input slots (its node labels)
+        std::vector<int> src(n, 0);
+        int i = 0;
+        for (auto& lf : p.leaves)
+            for (int c = 0; c < lf.m(); ++c, ++i) src[p.out_pos[i]] = lf.labels[c];
+        ints.insert(ints.end(), src.begin(), src.end());
+    }
     std::vector<double> mats;
     int off = 0, off_s = 0;
     d.max_bucket = 0;

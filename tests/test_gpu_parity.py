@@ -246,3 +246,24 @@ def test_plan_jacobi_matches_oracle_leaves(env):
         lam = plan.eigenvalues()
         assert np.max(np.abs(lam - ref.lam)) <= 1e-12 * max(1.0, np.abs(ref.lam).max())
         assert plan.info["jacobi_sweeps"] <= 30
+
+
+@pytest.mark.parametrize("g,split", [(W.path(8), False), (W.skeleton25(), True), (W.grid(8), False),
+                                     (W.cycle(12), False), (W.path(9), False), (W.path(6), False),
+                                     (W.grid(8, weights="sym_uniform", seed=3), False)],
+                         ids=lambda v: getattr(v, "name", str(v)))
+def test_specialised_kernel_matches_interpreter(env, g, split):
+    """The plan-specialised (NVRTC) kernel and the table-driven kernel run
+    the same FMA sequence, so their outputs agree bit for bit."""
+    gft, torch = env
+    pj = make_plan(gft, g, split)
+    pi = make_plan(gft, g, split, jit=False)
+    assert pj.info["jit"] == 1 and pi.info["jit"] == 0
+    x = torch.from_numpy(W.signals(4099, g.n, 21)).cuda()
+    assert torch.equal(pj.forward(x), pi.forward(x))
+    assert torch.equal(pj.inverse(x), pi.inverse(x))
+    xd = x.double()
+    assert torch.equal(pj.forward(xd), pi.forward(xd))
+    assert torch.equal(pj.inverse(xd), pi.inverse(xd))
+    src = pj.kernel_source()
+    assert "gft_jit_fwd_0" in src and "body_fwd" in src
