@@ -141,7 +141,8 @@ typedef struct {
     uint32_t flags;
     int64_t fast_mults;     /* multiplies per signal: sum of m_k^2 (Sec. V-G) */
     int64_t fast_adds;      /* adds per signal: 2 per Haar unit + sum m_k(m_k-1) */
-    int32_t jit;            /* 1 if a plan-specialised kernel is in use */
+    int32_t jit;            /* 0: table-driven kernel; 1: plan-specialised kernel with
+                               cp.async tiles; 2: plan-specialised with TMA bulk tiles */
     int32_t tile_signals;   /* FP32 forward launch shape chosen by the autotuner: */
     int32_t threads;        /*   signals per tile and threads per block (0 if none) */
     int32_t reserved;

@@ -41,11 +41,14 @@ namespace {
 constexpr int kSmemLimitJ = 232448;
 
 struct Cand {
-    int rs, threads, nbuf;
+    int rs, threads, nbuf, bulk;
 };
 
-// launch shapes compiled and timed for FP32; FP64 uses the first only
-const Cand kCands[] = {{2, 64, 1}, {2, 128, 1}, {1, 128, 1}, {2, 128, 2}};
+// Launch shapes compiled and timed for FP32 (FP64 uses the first only).
+// bulk = 1: whole tiles move with cp.async.bulk (TMA) and an mbarrier;
+// only for plans whose shared row stride equals n.
+const Cand kCands[] = {{2, 64, 1, 0}, {2, 128, 1, 0}, {1, 128, 1, 0}, {2, 128, 2, 0},
+                       {1, 128, 1, 1}, {1, 128, 2, 1}, {2, 128, 2, 1}, {2, 64, 2, 1}};
 
 enum RowMode { kContig = 0, kVec4 = 1, kPad1 = 2 };
 
@@ -84,6 +87,67 @@ __device__ __forceinline__ void stcs16(float* p, const float* s) {
 __device__ __forceinline__ void stcs16(double* p, const double* s) {
     const double2 v = *reinterpret_cast<const double2*>(s);
     asm volatile("st.global.cs.v2.f64 [%0], {%1,%2};" :: "l"(p), "d"(v.x), "d"(v.y) : "memory");
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* b, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_addr(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* b, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(smem_addr(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(unsigned long long* b, unsigned parity) {
+    unsigned ok;
+    asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                 : "=r"(ok) : "r"(smem_addr(b)), "r"(parity) : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+// bounded wait: gives up after about two seconds
+__device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned parity) {
+    if (mbar_try(b, parity)) return true;
+    const unsigned long long t0 = gtimer();
+    while (!mbar_try(b, parity))
+        if (gtimer() - t0 > 2000000000ull) return false;
+    return true;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* b) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(b)) : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void bulk_s2g(void* dst, const void* src, unsigned bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" :: "l"(dst), "r"(smem_addr(src)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// one thread: whole-tile load (16-byte multiple by TMA, the < 16-byte rest by plain copies)
+template <int TS>
+__device__ __forceinline__ void bulk_load_tile(const T* __restrict__ x, T* buf, i64 tile, i64 batch, unsigned long long* bar) {
+    const T* src = x + tile * (i64)TS * N;
+    const int rows = (int)min((i64)TS, batch - tile * (i64)TS);
+    const unsigned bytes = (unsigned)(rows * N * sizeof(T));
+    const unsigned b16 = bytes & ~15u;
+    mbar_expect_tx(bar, b16);
+    if (b16) bulk_g2s(buf, src, b16, bar);
+    for (unsigned e = b16 / sizeof(T); e < bytes / sizeof(T); ++e) buf[e] = src[e];
+}
+template <int TS>
+__device__ __forceinline__ void bulk_store_tile(const T* buf, T* __restrict__ y, i64 tile, i64 batch) {
+    T* dst = y + tile * (i64)TS * N;
+    const int rows = (int)min((i64)TS, batch - tile * (i64)TS);
+    const unsigned bytes = (unsigned)(rows * N * sizeof(T));
+    const unsigned b16 = bytes & ~15u;
+    if (b16) bulk_s2g(dst, buf, b16);
+    bulk_commit();
+    for (unsigned e = b16 / sizeof(T); e < bytes / sizeof(T); ++e) dst[e] = buf[e];
 }
 template <int THREADS, int TS>
 __device__ __forceinline__ void load_tile(const T* __restrict__ x, T* buf, i64 tile, i64 batch) {
@@ -124,7 +188,7 @@ __device__ __forceinline__ void store_tile(const T* buf, T* __restrict__ y, i64 
 )";
 
 const char* kKernelTmpl = R"(
-extern "C" __global__ void __launch_bounds__(@THREADS@) @NAME@(const T* __restrict__ x, T* __restrict__ y, i64 batch) {
+extern "C" __global__ void __launch_bounds__(@THREADS@) @NAME@(const T* __restrict__ x, T* __restrict__ y, i64 batch, int* err) {
     constexpr int THREADS = @THREADS@, RS = @RS@, NBUF = @NBUF@, TS = RS * THREADS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* tiles = reinterpret_cast<T*>(smem_raw);
@@ -158,6 +222,59 @@ extern "C" __global__ void __launch_bounds__(@THREADS@) @NAME@(const T* __restri
         }
     }
     wait0();
+}
+)";
+
+// Tiles moved by the TMA engine: one thread issues a bulk copy per tile that
+// completes on an mbarrier; after the in-place compute, a bulk store writes
+// the tile back.  Waits are bounded (about 2 s), after which the CTA records
+// GFT_ERR_TIMEOUT in *err, drains its own bulk copies and returns.
+const char* kBulkTmpl = R"(
+extern "C" __global__ void __launch_bounds__(@THREADS@) @NAME@(const T* __restrict__ x, T* __restrict__ y, i64 batch, int* err) {
+    constexpr int THREADS = @THREADS@, RS = @RS@, NBUF = @NBUF@, TS = RS * THREADS;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) unsigned long long mbar[2];
+    T* tiles = reinterpret_cast<T*>(smem_raw);
+    const int tid = threadIdx.x;
+    const i64 ntiles = (batch + TS - 1) / TS;
+    i64 tile = blockIdx.x;
+    if (tid == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    unsigned phase = 0;
+    int cur = 0;
+    bool bad = false;
+    if (tid == 0 && tile < ntiles) bulk_load_tile<TS>(x, tiles, tile, batch, &mbar[0]);
+    for (; tile < ntiles; tile += gridDim.x) {
+        const int b = NBUF == 2 ? cur : 0;
+        T* buf = tiles + b * TS * NP;
+        const i64 nxt = tile + gridDim.x;
+        if (NBUF == 2 && tid == 0 && nxt < ntiles) {
+            bulk_wait_read0();
+            bulk_load_tile<TS>(x, tiles + (cur ^ 1) * TS * NP, nxt, batch, &mbar[cur ^ 1]);
+        }
+        const bool ok = mbar_wait(&mbar[b], (phase >> b) & 1u);
+        phase ^= 1u << b;
+        if (__syncthreads_or(!ok)) { bad = true; break; }
+#pragma unroll
+        for (int s = 0; s < RS; ++s) @BODY@(buf + (tid + s * THREADS) * NP);
+        fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) bulk_store_tile<TS>(buf, y, tile, batch);
+        if (NBUF == 2) {
+            cur ^= 1;
+        } else if (tid == 0 && nxt < ntiles) {
+            bulk_wait_read0();
+            bulk_load_tile<TS>(x, tiles, nxt, batch, &mbar[0]);
+        }
+    }
+    if (tid == 0) {
+        bulk_wait_all();
+        if (bad) atomicExch(err, 8);
+    }
 }
 )";
 
@@ -300,9 +417,10 @@ std::string gen_module(const gft_plan_s& p, bool f64, const Layout& L, std::vect
         const size_t smem = (size_t)c.nbuf * c.rs * c.threads * L.np * esz;
         if (smem > (size_t)kSmemLimitJ) continue;
         if (f64 && ci > 0) break;
+        if (c.bulk && L.np != p.n) continue;
         cand_ids.push_back(ci);
         for (int inv = 0; inv < 2; ++inv) {
-            std::string k = kKernelTmpl;
+            std::string k = c.bulk ? kBulkTmpl : kKernelTmpl;
             k = replace_all(k, "@THREADS@", std::to_string(c.threads));
             k = replace_all(k, "@RS@", std::to_string(c.rs));
             k = replace_all(k, "@NBUF@", std::to_string(c.nbuf));
@@ -356,7 +474,7 @@ std::map<std::string, std::vector<char>>& cubin_cache() {
 
 struct JitDir {
     cudaKernel_t k = nullptr;
-    int rs = 0, threads = 0, nbuf = 0, per_sm = 0;
+    int rs = 0, threads = 0, nbuf = 0, per_sm = 0, bulk = 0;
     size_t smem = 0;
     float us = 0.f;
 };
@@ -381,12 +499,12 @@ std::string jit_source(const gft_plan_s& p, bool f64) {
     return gen_module(p, f64, row_layout(p.n, f64), ids);
 }
 
-static void launch_dir(const JitDir& d, const void* x, void* y, int64_t batch, cudaStream_t st) {
+static void launch_dir(const JitDir& d, const void* x, void* y, int64_t batch, int* err, cudaStream_t st) {
     const long long ts = (long long)d.rs * d.threads;
     const long long tiles = (batch + ts - 1) / ts;
     const long long grid = std::min<long long>(tiles, (long long)d.per_sm * sm_count());
     long long b = batch;
-    void* args[] = {(void*)&x, (void*)&y, (void*)&b};
+    void* args[] = {(void*)&x, (void*)&y, (void*)&b, (void*)&err};
     GFT_CUDA(cudaLaunchKernel((const void*)d.k, dim3((unsigned)grid), dim3(d.threads), args, d.smem, st));
 }
 
@@ -436,9 +554,10 @@ static void build_precision(gft_plan_s& p, JitPlan& J, bool f64) {
                 GFT_CUDA(cudaFuncSetAttribute((const void*)d.k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d.smem));
                 GFT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.per_sm, (const void*)d.k, d.threads, d.smem));
                 if (d.per_sm < 1) continue;
-                launch_dir(d, dx, dy, tb, st);
+                d.bulk = c.bulk;
+                launch_dir(d, dx, dy, tb, p.dev.d_err, st);
                 GFT_CUDA(cudaEventRecord(e0, st));
-                for (int r = 0; r < 3; ++r) launch_dir(d, dx, dy, tb, st);
+                for (int r = 0; r < 3; ++r) launch_dir(d, dx, dy, tb, p.dev.d_err, st);
                 GFT_CUDA(cudaEventRecord(e1, st));
                 GFT_CUDA(cudaEventSynchronize(e1));
                 float ms = 0.f;
@@ -493,7 +612,7 @@ bool jit_launch(gft_plan_s& p, bool f64, const void* x, void* y, int64_t batch, 
     JitPlan* J = static_cast<JitPlan*>(p.jit);
     const JitDir& d = (f64 ? J->d64 : J->d32)[inverse ? 1 : 0];
     if (!d.k) return false;
-    if (batch > 0) launch_dir(d, x, y, batch, st);
+    if (batch > 0) launch_dir(d, x, y, batch, p.dev.d_err, st);
     return true;
 }
 
@@ -503,7 +622,7 @@ void jit_info(const gft_plan_s& p, int* jit, int* tile, int* threads) {
     *threads = 0;
     if (!p.jit) return;
     const JitPlan* J = static_cast<const JitPlan*>(p.jit);
-    *jit = 1;
+    *jit = J->d32[0].bulk ? 2 : 1;
     *tile = J->d32[0].rs * J->d32[0].threads;
     *threads = J->d32[0].threads;
 }

@@ -258,7 +258,7 @@ def test_specialised_kernel_matches_interpreter(env, g, split):
     gft, torch = env
     pj = make_plan(gft, g, split)
     pi = make_plan(gft, g, split, jit=False)
-    assert pj.info["jit"] == 1 and pi.info["jit"] == 0
+    assert pj.info["jit"] in (1, 2) and pi.info["jit"] == 0
     x = torch.from_numpy(W.signals(4099, g.n, 21)).cuda()
     assert torch.equal(pj.forward(x), pi.forward(x))
     assert torch.equal(pj.inverse(x), pi.inverse(x))
