@@ -1,0 +1,98 @@
+"""Mixed batches: one persistent, graph-captured launch over many plans.
+Every plan's output must equal its own single-plan forward bit for bit (the
+batch kernel runs the same FMA sequence), and the single-plan forward is
+pinned to the oracle by test_gpu_parity."""
+import numpy as np
+import pytest
+
+import gft_workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1907_07875_gb300.build import build
+    build()
+    import paper_1907_07875_gb300 as gft
+    return gft, torch
+
+
+def _plans(gft, graphs, split=False):
+    return [gft.Plan(gft.laplacian(g.W, g.s), g.phis, split_components=split, jit=False) for g in graphs]
+
+
+def test_config3_core_kinds_in_one_launch(env):
+    gft, torch = env
+    kinds = [W.config3(coeffs_per_kind=1 << 18)[k] for k in (0, 1, 2, 3, 6, 7)]
+    graphs = [k[0] for k in kinds]
+    batches = [k[1] + 13 for k in kinds]            # ragged tails
+    plans = _plans(gft, graphs)
+    b = gft.Batch(plans, batches)
+    xs = [torch.from_numpy(W.signals(bt, g.n, 100 + i)).cuda() for i, (g, bt) in enumerate(zip(graphs, batches))]
+    ys = [torch.empty_like(x) for x in xs]
+    for rep in range(3):                               # capture, then replays
+        b.forward(xs, ys)
+    torch.cuda.synchronize()
+    for p, x, y in zip(plans, xs, ys):
+        assert torch.equal(y, p.forward(x))
+    for i in range(len(plans)):
+        tile, threads = b.tile(i)
+        assert threads == 128 and tile in (128, 256, 512)
+
+
+def test_pointer_change_reuses_graph(env):
+    gft, torch = env
+    graphs = [W.skeleton25(), W.path(8), W.cycle(12)]
+    plans = _plans(gft, graphs)
+    batches = [1000, 5000, 333]
+    b = gft.Batch(plans, batches)
+    for seed in (1, 2):
+        xs = [torch.from_numpy(W.signals(bt, g.n, seed * 10 + i)).cuda() for i, (g, bt) in enumerate(zip(graphs, batches))]
+        ys = [torch.full_like(x, float("nan")) for x in xs]
+        b.forward(xs, ys)
+        torch.cuda.synchronize()
+        for p, x, y in zip(plans, xs, ys):
+            assert torch.equal(y, p.forward(x))
+
+
+def test_many_small_graphs_and_empty_batches(env):
+    """A sweep-like batch: 120 graphs of 6..64 nodes from every family."""
+    gft, torch = env
+    rng = np.random.default_rng(5)
+    graphs = []
+    for i in range(120):
+        fam = i % 5
+        n = int(rng.integers(6, 65))
+        if fam == 0:
+            graphs.append(W.path(n))
+        elif fam == 1:
+            graphs.append(W.cycle(max(4, n - n % 4)))
+        elif fam == 2:
+            graphs.append(W.grid(max(2, int(np.sqrt(n)))))
+        elif fam == 3:
+            graphs.append(W.skeleton25())
+        else:
+            graphs.append(W.bipartite(max(8, min(64, n - n % 2)), 0.2, seed=int(rng.integers(1 << 30))))
+    plans = _plans(gft, graphs)
+    batches = [int(rng.integers(0, 700)) for _ in graphs]
+    batches[3] = 0
+    b = gft.Batch(plans, batches)
+    xs = [torch.from_numpy(W.signals(max(bt, 1), g.n, i)).cuda()[:bt] for i, (g, bt) in enumerate(zip(graphs, batches))]
+    ys = [torch.empty_like(x) for x in xs]
+    b.forward(xs, ys)
+    torch.cuda.synchronize()
+    for p, x, y in zip(plans, xs, ys):
+        if x.shape[0]:
+            assert torch.equal(y, p.forward(x))
+
+
+def test_batch_rejects_wide_leaves(env):
+    gft, torch = env
+    g = W.grid(32)
+    p = gft.Plan(gft.laplacian(g.W, g.s), g.phis)
+    with pytest.raises(gft.GftError) as e:
+        gft.Batch([p], [10])
+    assert e.value.status == "GFT_ERR_UNSUPPORTED"
