@@ -28,6 +28,7 @@
 #include "apply_core.cuh"
 
 namespace gft {
+using namespace core;
 namespace {
 
 constexpr int kBatchThreads = 128;
