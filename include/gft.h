@@ -259,6 +259,36 @@ gft_status gft_givens_backward(gft_givens_t g, const float* theta, const float* 
                                const float* gy, float* gx, float* gtheta, int64_t batch,
                                gft_stream_t stream);
 
+/*
+ * Allocation-free variant of gft_givens_backward (the paper has no
+ * counterpart: it is an integration aid).  For callers that cannot allocate
+ * device memory once running -- programs whose own pool or fixed budget
+ * owns all device memory, real-time loops that must not wait for or risk a
+ * failed allocation mid-step, and thin C hosts without an allocator.  It
+ * needs no gft_givens_t and calls no cudaMalloc, cudaFree or other
+ * allocating routine.
+ *  pairs     HOST int32 [n_stages][n/2][2], each stage a perfect matching
+ *            (checked; GFT_ERR_INVALID_ARG otherwise), copied every call.
+ *  theta     device [n_stages][n/2]; y (forward output), gy, gx: device
+ *            [batch, n] FP32, 16-byte aligned; gtheta: device [n_stages][n/2],
+ *            overwritten.  Same results as gft_givens_backward (angle sums may
+ *            differ in rounding because the CTA count can differ).
+ * Scratch: a fixed 4 MiB device array compiled into the library (held on
+ * every GPU that loads it until exit) holds the pair table and one row of
+ * n_stages*n/2 partial sums per CTA; the CTA count is capped to fit, and a
+ * network whose pair table plus one row exceeds 4 MiB is rejected with
+ * GFT_ERR_INVALID_ARG (cannot happen within the n and n_stages limits).
+ * Every call rewrites what it reads, so nothing needs clearing between
+ * calls, but all calls share the one array: calls that overlap on the GPU
+ * (different streams, or different host threads) race and must be
+ * serialised by the caller.  The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture.
+ */
+gft_status gft_givens_backward_noalloc(int32_t n, int32_t n_stages, const int32_t* pairs, const float* theta,
+                                       const float* y, const float* gy, float* gx, float* gtheta,
+                                       int64_t batch, gft_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -55,6 +55,7 @@ SIGNATURES = {
     "gft_givens_destroy": (c_status, [C.c_void_p]),
     "gft_givens_forward": (c_status, [C.c_void_p, P, P, P, C.c_int64, P]),
     "gft_givens_backward": (c_status, [C.c_void_p, P, P, P, P, P, C.c_int64, P]),
+    "gft_givens_backward_noalloc": (c_status, [C.c_int32, C.c_int32, P, P, P, P, P, P, C.c_int64, P]),
 }
 
 _lib = None

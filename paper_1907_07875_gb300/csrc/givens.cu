@@ -321,3 +321,116 @@ gft_status gft_givens_backward(gft_givens_t g, const float* theta, const float* 
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free backward pass of the Givens layers.
+//
+// Some callers cannot allocate device memory while they run: programs that
+// hand every byte of the GPU to their own memory pool or a fixed budget,
+// real-time training or serving loops that must neither wait for nor risk a
+// failed allocation in the middle of a step, and hosts that reach this
+// library through a thin C interface with no allocator of their own.
+// gft_givens_backward_noalloc serves them.  It takes the pair table from
+// host memory and everything else from caller-owned device buffers, and
+// keeps its only scratch -- the pair table copy and one row of partial angle
+// sums per CTA -- in a fixed array compiled into this library.  That array
+// (kNoAllocScratchBytes) occupies device memory on every GPU that loads the
+// library until the process exits.  Host code cannot use the array's name
+// as a device address, so its address is looked up once per device with
+// cudaGetSymbolAddress.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace gft {
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = 4u << 20;  // 4 MiB
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+// Device address of the fixed scratch on the current device; the first call
+// on each device performs the lookup.
+void* noalloc_scratch() {
+    int dev = 0;
+    GFT_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoAllocMaxDevices) fail(GFT_ERR_UNSUPPORTED, "device index too large");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            fail(GFT_ERR_CUDA, std::string("cudaGetSymbolAddress of the fixed scratch failed: ") + cudaGetErrorString(e));
+        g_noalloc_addr[dev] = p;
+    }
+    return g_noalloc_addr[dev];
+}
+
+}  // namespace
+}  // namespace gft
+
+extern "C" gft_status gft_givens_backward_noalloc(int32_t n, int32_t n_stages, const int32_t* pairs,
+                                                  const float* theta, const float* y, const float* gy, float* gx,
+                                                  float* gtheta, int64_t batch, gft_stream_t stream) {
+    return guard_g([&] {
+        if (!pairs || !theta || !gtheta) fail(GFT_ERR_INVALID_ARG, "NULL argument");
+        if (n < 2 || n > 1024 || (n & 1)) fail(GFT_ERR_INVALID_ARG, "n must be even, 2..1024");
+        if (n_stages < 1 || n_stages > 64) fail(GFT_ERR_INVALID_ARG, "n_stages must be 1..64");
+        check_io_g(y, gy, batch);
+        check_io_g(gx, gy, batch);
+        const int half = n / 2;
+        bool seen[1024];
+        for (int s = 0; s < n_stages; ++s) {
+            for (int i = 0; i < n; ++i) seen[i] = false;
+            for (int k = 0; k < half; ++k) {
+                const int p = pairs[(size_t)(s * half + k) * 2], q = pairs[(size_t)(s * half + k) * 2 + 1];
+                if (p < 0 || p >= n || q < 0 || q >= n || p == q || seen[p] || seen[q])
+                    fail(GFT_ERR_INVALID_ARG, "stage " + std::to_string(s) + " is not a perfect matching");
+                seen[p] = seen[q] = true;
+            }
+        }
+        const int A = n_stages * half;
+        const size_t pair_bytes = ((size_t)n_stages * n * sizeof(int) + 255) & ~size_t(255);
+        const size_t row_bytes = (size_t)A * sizeof(float);
+        if (pair_bytes + row_bytes > kNoAllocScratchBytes)
+            fail(GFT_ERR_INVALID_ARG, "network needs more than the fixed 4 MiB scratch");
+        const long long rows_cap = (long long)((kNoAllocScratchBytes - pair_bytes) / row_bytes);
+        cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+        unsigned char* scratch = static_cast<unsigned char*>(noalloc_scratch());
+        // the pair table region is rewritten by every call
+        GFT_CUDA(cudaMemcpyAsync(scratch, pairs, (size_t)n_stages * n * sizeof(int), cudaMemcpyHostToDevice, st));
+        if (batch == 0) {
+            GFT_CUDA(cudaMemsetAsync(gtheta, 0, row_bytes, st));
+            return;
+        }
+        GArgs a{};
+        a.pairs = reinterpret_cast<const int*>(scratch);
+        a.theta = theta;
+        a.x = y;
+        a.g = gy;
+        a.y = gx;
+        a.partials = reinterpret_cast<float*>(scratch + pair_bytes);
+        a.batch = batch;
+        a.n = n;
+        a.np = n | 1;
+        a.S = n_stages;
+        a.A = A;
+        a.inv_n = 1.0f / n;
+        const size_t smem = bwd_smem(A, a.np);
+        if (smem > (size_t)kSmemLimitG) fail(GFT_ERR_UNSUPPORTED, "Givens network too large for the backward kernel");
+        GFT_CUDA(cudaFuncSetAttribute(givens_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int per_sm = 0;
+        GFT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, givens_bwd_kernel, kGivThreads, smem));
+        const long long tiles = (batch + kGivThreads - 1) / kGivThreads;
+        // every CTA overwrites its whole partial row, and the reduction reads
+        // only the rows of this call: nothing in the scratch needs clearing
+        const int grid = (int)std::min(std::min<long long>(tiles, (long long)std::max(1, per_sm) * sm_count()), rows_cap);
+        givens_bwd_kernel<<<grid, kGivThreads, smem, st>>>(a);
+        GFT_CUDA(cudaGetLastError());
+        givens_reduce_kernel<<<(A + 127) / 128, 128, 0, st>>>(a.partials, grid, A, gtheta);
+        GFT_CUDA(cudaGetLastError());
+    });
+}
