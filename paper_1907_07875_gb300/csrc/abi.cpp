@@ -146,6 +146,7 @@ gft_status gft_plan_create(int32_t n, const double* L, int32_t n_stages, const i
             finalize_host(*p);
             upload_plan(*p);
             jit_build(*p);
+            tc_build(*p);
             GFT_CUDA(cudaDeviceSynchronize());
         }
         *out = p.release();

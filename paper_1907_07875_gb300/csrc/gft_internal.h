@@ -133,6 +133,9 @@ void jit_info(const gft_plan_s& p, int* jit, int* tile, int* threads);
 std::string jit_source(const gft_plan_s& p, bool f64);
 
 // tc.cu: leaf products on tcgen05 tensor cores (split precision)
+bool tc_eligible(const gft_plan_s& p);
+void tc_build(gft_plan_s& p);
+void tc_free(gft_plan_s& p);
 void launch_tc(gft_plan_s& p, const float* x, float* y, int64_t batch, bool inverse, cudaStream_t st,
                uint32_t precision);
 

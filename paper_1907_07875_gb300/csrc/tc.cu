@@ -1,13 +1,575 @@
-// Tensor-core (tcgen05) leaf products for large leaves: placeholder until the
-// split-precision kernel lands; every call reports GFT_ERR_UNSUPPORTED.
+// Leaf products on the 5th-generation tensor cores (tcgen05, TMEM).
+//
+// For leaves too large for the CUDA-core kernels (m > 64: the 16x16 and
+// 32x32 grids, the 256-cycle, large bipartite graphs) the leaf products
+// y_k = M_k^T v_k (Sec. IV-C, Eq. 13; M_k the folded leaf basis) are dense
+// contractions, run here as GEMMs D[128 x N] = A[128 x K] B[K x N] per tile
+// of 128 signals:
+//   1. tc_gather_kernel: the Haar stages, written as signed sums of the
+//      input entries (each post-stage value is +-x_i1 +- x_i2 ..., one term
+//      per node of its orbit), into a leaf-ordered FP32 scratch V [batch, n];
+//   2. tc_leaf_kernel (persistent, one CTA per SM, 128 threads): for each
+//      leaf and each K chunk of 64, the CTA converts its 128 x 64 block of V
+//      to BF16 (hi, and lo = v - hi for the split precisions) or scaled FP16
+//      hi/lo, writes it and the matching block of B (pre-split on the host,
+//      stored in the smem image order) to shared memory in the canonical
+//      no-swizzle K-major layout (8 x 16-byte core matrices), and one thread
+//      issues tcgen05.mma (M=128, N=leaf width, K=16 per instruction) into
+//      the leaf's TMEM columns: one product for BF16, three (hi*hi + hi*lo +
+//      lo*hi) for the split precisions.  tcgen05.commit arrives on an
+//      mbarrier; every wait is bounded (about 2 s, then GFT_ERR_TIMEOUT).
+//   3. Epilogue: when every leaf of the plan fits the 512 TMEM columns, each
+//      warp reads its 32 rows column by column IN COEFFICIENT ORDER
+//      (tcgen05.ld 32x32b) and writes 32 consecutive coefficients per row,
+//      so the ascending-eigenvalue permutation costs nothing; otherwise the
+//      leaves are processed in groups that fit, each group's D is written to
+//      a leaf-ordered scratch, and tc_permute_kernel produces the output.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
 #include "gft_internal.h"
 
 namespace gft {
+namespace {
+
+constexpr int kTcM = 128;        // signals per tile = MMA M
+constexpr int kTcK = 64;         // K chunk staged per step
+constexpr int kTcThreads = 128;  // 4 warps = 128 TMEM lanes
+constexpr int kTcMaxN = 256;     // widest leaf handled in one MMA
+constexpr int kTcCols = 512;     // TMEM columns allocated per CTA (one CTA per SM)
+
+struct TcLeaf {
+    int m;        // leaf size
+    int npad;     // N padded to a multiple of 16
+    int kchunks;  // ceil(m / 64)
+    int off;      // offset in leaf-concatenated order
+    int tcol;     // TMEM column of this leaf's first output (within its group)
+    int group;
+    long long b_off;  // element offset of the leaf's B image (per precision array)
+};
+
+struct TcArgs {
+    const float* v;          // [batch, n] leaf-ordered post-stage values
+    float* y;                // [batch, n] output (direct mode) or scratch (group mode)
+    const TcLeaf* leaves;
+    const int* colmap;       // direct mode: TMEM column of coefficient j
+    const __nv_bfloat16* bhi;
+    const __nv_bfloat16* blo;
+    const __half* fhi;
+    const __half* flo;
+    long long batch;
+    int n, n_leaves, n_groups, prec, direct;
+    int* err;
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+// shared-memory matrix descriptor, canonical K-major layout without swizzle:
+// start >> 4 in bits 0-13, leading-dimension byte offset (between core
+// matrices adjacent along K) >> 4 in bits 16-29, stride byte offset (between
+// 8-row groups) >> 4 in bits 32-45, descriptor version 1 in bits 46-47,
+// swizzle mode 0 in bits 61-63
+__device__ __forceinline__ unsigned long long smem_desc(unsigned addr, unsigned lbo, unsigned sbo) {
+    unsigned long long d = 0;
+    d |= (unsigned long long)((addr & 0x3FFFFu) >> 4);
+    d |= (unsigned long long)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (unsigned long long)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= 1ull << 46;
+    return d;
+}
+
+// instruction descriptor for kind::f16: FP32 accumulator (bits 4-5 = 1),
+// A and B format (bits 7-9, 10-12: 1 = BF16, 0 = FP16), both K-major,
+// N >> 3 in bits 17-22, M >> 4 in bits 24-28
+__host__ __device__ __forceinline__ unsigned instr_desc(int n, bool bf16) {
+    unsigned d = 0;
+    d |= 1u << 4;
+    if (bf16) d |= (1u << 7) | (1u << 10);
+    d |= (unsigned)((n >> 3) & 0x3F) << 17;
+    d |= (unsigned)((kTcM >> 4) & 0x1F) << 24;
+    return d;
+}
+
+__device__ __forceinline__ void mma_f16(unsigned dt, unsigned long long ad, unsigned long long bd, unsigned id,
+                                        unsigned acc) {
+    asm volatile(
+        "{ .reg .pred p; setp.ne.u32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }\n" ::"r"(dt),
+        "l"(ad), "l"(bd), "r"(id), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mbar_init1(unsigned long long* b) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try1(unsigned long long* b, unsigned parity) {
+    unsigned ok;
+    asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                 : "=r"(ok)
+                 : "r"(smem_u32(b)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ unsigned long long gtimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* b, unsigned parity) {
+    if (mbar_try1(b, parity)) return true;
+    const unsigned long long t0 = gtimer_ns();
+    while (!mbar_try1(b, parity))
+        if (gtimer_ns() - t0 > 2000000000ull) return false;
+    return true;
+}
+
+// one 16-byte row of a core matrix: byte offset of (row, k-group) in a
+// [rows x 64] K-major no-swizzle tile whose 8-row groups are 1024 B apart
+__device__ __forceinline__ unsigned core_off(int row, int kg) {
+    return (unsigned)(((row >> 3) * 8 + kg) * 128 + (row & 7) * 16);
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1) tc_leaf_kernel(TcArgs a) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    // [A hi 16 KB][A lo 16 KB][B hi 32 KB][B lo 32 KB][guard 32 KB]
+    unsigned char* a_hi = sm;
+    unsigned char* a_lo = sm + 16384;
+    unsigned char* b_hi = sm + 32768;
+    unsigned char* b_lo = sm + 65536;
+    __shared__ unsigned s_tmem;
+    __shared__ __align__(8) unsigned long long mbar;
+    __shared__ float s_scale[kTcM];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                     "r"(kTcCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        mbar_init1(&mbar);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const unsigned tmem = s_tmem;
+    unsigned phase = 0;
+    bool bad = false;
+    const bool split = a.prec != GFT_PREC_BF16;
+    const bool fp16 = a.prec == GFT_PREC_FP16X3;
+    const long long n_tiles = (a.batch + kTcM - 1) / kTcM;
+    for (long long tile = blockIdx.x; tile < n_tiles && !bad; tile += gridDim.x) {
+        const long long r0 = tile * kTcM;
+        if (fp16) {
+            // one power-of-two scale per signal (row), shared by every leaf,
+            // so the FP16 hi/lo parts keep their precision at any magnitude
+            const long long row = r0 + tid;
+            float mx = 0.f;
+            if (row < a.batch)
+                for (int c = 0; c < a.n; ++c) mx = fmaxf(mx, fabsf(a.v[row * a.n + c]));
+            s_scale[tid] = mx > 0.f ? exp2f(ceilf(log2f(mx))) : 1.f;
+            __syncthreads();
+        }
+        for (int g = 0; g < a.n_groups && !bad; ++g) {
+            for (int k = 0; k < a.n_leaves && !bad; ++k) {
+                const TcLeaf L = a.leaves[k];
+                if (L.group != g) continue;
+                const unsigned id = instr_desc(L.npad, !fp16);
+                for (int kc = 0; kc < L.kchunks && !bad; ++kc) {
+                    // ---- A: 128 rows x 64 K, hi/lo ----
+                    for (int gi = tid; gi < kTcM * 8; gi += kTcThreads) {
+                        const int row = gi & (kTcM - 1), kg = gi >> 7;
+                        const long long grow = r0 + row;
+                        float v[8];
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            const int c = kc * kTcK + kg * 8 + e;
+                            v[e] = (grow < a.batch && c < L.m) ? a.v[grow * a.n + L.off + c] : 0.f;
+                        }
+                        unsigned hi[4], lo[4];
+                        if (fp16) {
+                            const float inv = 1.f / s_scale[row];
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                const float x0 = v[2 * e] * inv, x1 = v[2 * e + 1] * inv;
+                                const __half h0 = __float2half_rn(x0), h1 = __float2half_rn(x1);
+                                const __half l0 = __float2half_rn(x0 - __half2float(h0));
+                                const __half l1 = __float2half_rn(x1 - __half2float(h1));
+                                hi[e] = (unsigned)__half_as_ushort(h0) | ((unsigned)__half_as_ushort(h1) << 16);
+                                lo[e] = (unsigned)__half_as_ushort(l0) | ((unsigned)__half_as_ushort(l1) << 16);
+                            }
+                        } else {
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                const __nv_bfloat16 h0 = __float2bfloat16_rn(v[2 * e]);
+                                const __nv_bfloat16 h1 = __float2bfloat16_rn(v[2 * e + 1]);
+                                const __nv_bfloat16 l0 = __float2bfloat16_rn(v[2 * e] - __bfloat162float(h0));
+                                const __nv_bfloat16 l1 = __float2bfloat16_rn(v[2 * e + 1] - __bfloat162float(h1));
+                                hi[e] = (unsigned)__bfloat16_as_ushort(h0) | ((unsigned)__bfloat16_as_ushort(h1) << 16);
+                                lo[e] = (unsigned)__bfloat16_as_ushort(l0) | ((unsigned)__bfloat16_as_ushort(l1) << 16);
+                            }
+                        }
+                        const unsigned o = core_off(row, kg);
+                        *reinterpret_cast<uint4*>(a_hi + o) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+                        if (split) *reinterpret_cast<uint4*>(a_lo + o) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+                    }
+                    // ---- B: npad rows x 64 K, image copied as stored ----
+                    {
+                        const size_t img = (size_t)L.npad * kTcK;  // elements per chunk
+                        const uint4* sh = fp16 ? reinterpret_cast<const uint4*>(a.fhi + L.b_off + kc * img)
+                                               : reinterpret_cast<const uint4*>(a.bhi + L.b_off + kc * img);
+                        const uint4* sl = fp16 ? reinterpret_cast<const uint4*>(a.flo + L.b_off + kc * img)
+                                               : reinterpret_cast<const uint4*>(a.blo + L.b_off + kc * img);
+                        const int n16 = (int)(img * 2 / 16);
+                        for (int i = tid; i < n16; i += kTcThreads) {
+                            reinterpret_cast<uint4*>(b_hi)[i] = sh[i];
+                            if (split) reinterpret_cast<uint4*>(b_lo)[i] = sl[i];
+                        }
+                    }
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    __syncthreads();
+                    if (tid == 0) {
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                        const unsigned dt = tmem + (unsigned)L.tcol;
+#pragma unroll
+                        for (int ks = 0; ks < kTcK / 16; ++ks) {
+                            if (kc * kTcK + ks * 16 >= ((L.m + 15) & ~15)) break;
+                            const unsigned koff = ks * 256u;
+                            const unsigned long long ah = smem_desc(smem_u32(a_hi) + koff, 128, 1024);
+                            const unsigned long long bh = smem_desc(smem_u32(b_hi) + koff, 128, 1024);
+                            const unsigned acc0 = (kc | ks) ? 1u : 0u;
+                            mma_f16(dt, ah, bh, id, acc0);
+                            if (split) {
+                                const unsigned long long al = smem_desc(smem_u32(a_lo) + koff, 128, 1024);
+                                const unsigned long long bl = smem_desc(smem_u32(b_lo) + koff, 128, 1024);
+                                mma_f16(dt, ah, bl, id, 1u);
+                                mma_f16(dt, al, bh, id, 1u);
+                            }
+                        }
+                        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                         smem_u32(&mbar))
+                                     : "memory");
+                    }
+                    const bool ok = mbar_wait_bounded(&mbar, phase);
+                    phase ^= 1u;
+                    if (__syncthreads_or(!ok)) bad = true;
+                }
+            }
+            if (bad) break;
+            // ---- epilogue: TMEM -> registers -> global ----
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const long long row = r0 + warp * 32 + lane;
+            const unsigned lane_base = (unsigned)(warp * 32) << 16;
+            if (a.direct) {
+                for (int j0 = 0; j0 < a.n; j0 += 32) {
+                    float r[32];
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) {
+                        const int j = min(j0 + q, a.n - 1);
+                        const unsigned col = (unsigned)a.colmap[j];
+                        unsigned u;
+                        asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];"
+                                     : "=r"(u)
+                                     : "r"(tmem + lane_base + col)
+                                     : "memory");
+                        r[q] = __uint_as_float(u);
+                    }
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    if (row < a.batch) {
+                        float* dst = a.y + row * a.n + j0;
+                        const int cnt = min(32, a.n - j0);
+                        const float sc = fp16 ? s_scale[warp * 32 + lane] : 1.f;
+                        if (cnt == 32 && (a.n & 3) == 0) {
+#pragma unroll
+                            for (int q = 0; q < 32; q += 4)
+                                __stcs(reinterpret_cast<float4*>(dst + q),
+                                       make_float4(r[q] * sc, r[q + 1] * sc, r[q + 2] * sc, r[q + 3] * sc));
+                        } else {
+                            for (int q = 0; q < cnt; ++q) __stcs(dst + q, r[q] * sc);
+                        }
+                    }
+                }
+            } else {
+                for (int k = 0; k < a.n_leaves; ++k) {
+                    const TcLeaf L = a.leaves[k];
+                    if (L.group != g) continue;
+                    for (int c0 = 0; c0 < L.m; c0 += 32) {
+                        float r[32];
+#pragma unroll
+                        for (int q = 0; q < 32; ++q) {
+                            const unsigned col = (unsigned)(L.tcol + min(c0 + q, L.npad - 1));
+                            unsigned u;
+                            asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];"
+                                         : "=r"(u)
+                                         : "r"(tmem + lane_base + col)
+                                         : "memory");
+                            r[q] = __uint_as_float(u);
+                        }
+                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                        if (row < a.batch) {
+                            float* dst = a.y + row * a.n + L.off + c0;
+                            const int cnt = min(32, L.m - c0);
+                            const float sc = fp16 ? s_scale[warp * 32 + lane] : 1.f;
+                            for (int q = 0; q < cnt; ++q) dst[q] = r[q] * sc;
+                        }
+                    }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncthreads();
+        }
+    }
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols) : "memory");
+    }
+    if (bad && tid == 0) atomicExch(a.err, (int)GFT_ERR_TIMEOUT);
+}
+
+// post-stage values in leaf order: v[t][j] = sum_q sign_q x[t][src_q]
+__global__ void tc_gather_kernel(const float* __restrict__ x, float* __restrict__ v, long long batch, int n,
+                                 const int* __restrict__ term_off, const int* __restrict__ term_src,
+                                 const float* __restrict__ term_sign) {
+    const long long total = batch * n;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long t = e / n;
+        const int j = (int)(e - t * n);
+        const float* row = x + t * n;
+        float s = 0.f;
+        for (int q = term_off[j]; q < term_off[j + 1]; ++q) s += term_sign[q] * __ldg(row + term_src[q]);
+        v[e] = s;
+    }
+}
+
+// group mode: y[t][j] = z[t][srcmap[j]] (z leaf ordered)
+__global__ void tc_permute_kernel(const float* __restrict__ z, float* __restrict__ y, long long batch, int n,
+                                  const int* __restrict__ srcmap) {
+    const long long total = batch * n;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long t = e / n;
+        const int j = (int)(e - t * n);
+        __stcs(y + e, z[t * n + srcmap[j]]);
+    }
+}
+
+struct TcPlan {
+    int n = 0, n_leaves = 0, n_groups = 0, direct = 0;
+    TcLeaf* d_leaves = nullptr;
+    int* d_colmap = nullptr;
+    int* d_srcmap = nullptr;
+    int* d_term_off = nullptr;
+    int* d_term_src = nullptr;
+    float* d_term_sign = nullptr;
+    __nv_bfloat16* d_bhi = nullptr;
+    __nv_bfloat16* d_blo = nullptr;
+    __half* d_fhi = nullptr;
+    __half* d_flo = nullptr;
+    float* d_v = nullptr;
+    float* d_z = nullptr;
+    size_t rows_cap = 0;
+    ~TcPlan() {
+        for (void* p : {(void*)d_leaves, (void*)d_colmap, (void*)d_srcmap, (void*)d_term_off, (void*)d_term_src,
+                        (void*)d_term_sign, (void*)d_bhi, (void*)d_blo, (void*)d_fhi, (void*)d_flo, (void*)d_v,
+                        (void*)d_z})
+            if (p) cudaFree(p);
+    }
+};
+
+template <class T>
+T* upload(const std::vector<T>& v) {
+    T* d = nullptr;
+    GFT_CUDA(cudaMalloc(&d, sizeof(T) * std::max<size_t>(1, v.size())));
+    if (!v.empty()) GFT_CUDA(cudaMemcpy(d, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice));
+    return d;
+}
+
+uint16_t bf16_bits(float f) {
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    const uint32_t r = ((u >> 16) & 1u) + 0x7FFFu;  // round to nearest even
+    return (uint16_t)((u + r) >> 16);
+}
+float bf16_val(uint16_t b) {
+    const uint32_t u = (uint32_t)b << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
+}  // namespace
+
+bool tc_eligible(const gft_plan_s& p) {
+    for (auto& lf : p.leaves)
+        if (lf.m() > kTcMaxN) return false;
+    return p.n >= 2;
+}
+
+// host preparation: leaves, TMEM column groups, coefficient map, stage
+// terms, and the pre-split B images (BF16 hi/lo and FP16 hi/lo)
+void tc_build(gft_plan_s& p) {
+    if (!tc_eligible(p)) return;
+    TcPlan* T = new TcPlan;
+    try {
+        const int n = p.n;
+        T->n = n;
+        T->n_leaves = (int)p.leaves.size();
+        std::vector<TcLeaf> L;
+        int off = 0, cols = 0, group = 0;
+        long long boff = 0;
+        for (auto& lf : p.leaves) {
+            TcLeaf t{};
+            t.m = lf.m();
+            t.npad = std::max(16, (t.m + 15) & ~15);
+            t.kchunks = (t.m + kTcK - 1) / kTcK;
+            t.off = off;
+            if (cols + t.npad > kTcCols) {
+                ++group;
+                cols = 0;
+            }
+            t.tcol = cols;
+            t.group = group;
+            cols += t.npad;
+            t.b_off = boff;
+            boff += (long long)t.kchunks * t.npad * kTcK;
+            off += t.m;
+            L.push_back(t);
+        }
+        T->n_groups = group + 1;
+        T->direct = T->n_groups == 1 ? 1 : 0;
+        // coefficient maps
+        std::vector<int> colmap(n), srcmap(n);
+        {
+            int i = 0;
+            for (size_t k = 0; k < p.leaves.size(); ++k)
+                for (int c = 0; c < p.leaves[k].m(); ++c, ++i) {
+                    colmap[p.out_pos[i]] = L[k].tcol + c;
+                    srcmap[p.out_pos[i]] = i;
+                }
+        }
+        // stage terms: post-stage value at label l as signed sum of inputs
+        std::vector<std::vector<std::pair<int, float>>> comb(n);
+        for (int l = 0; l < n; ++l) comb[l] = {{l, 1.f}};
+        for (auto& st : p.stages)
+            for (auto& pr : st) {
+                auto a = comb[pr.first], b = comb[pr.second];
+                std::vector<std::pair<int, float>> u = a, w = a;
+                for (auto& t : b) u.push_back(t);
+                for (auto& t : b) w.push_back({t.first, -t.second});
+                comb[pr.first] = u;
+                comb[pr.second] = w;
+            }
+        std::vector<int> toff(1, 0), tsrc;
+        std::vector<float> tsign;
+        for (auto& lf : p.leaves)
+            for (int lab : lf.labels) {
+                for (auto& t : comb[lab]) {
+                    tsrc.push_back(t.first);
+                    tsign.push_back(t.second);
+                }
+                toff.push_back((int)tsrc.size());
+            }
+        // B images: for each leaf and K chunk, npad rows (outputs c) x 64 K
+        // (inputs r) in the smem core-matrix order; B[c][r] = M_k[r][c]
+        std::vector<uint16_t> bhi(boff, 0), blo(boff, 0), fhi(boff, 0), flo(boff, 0);
+        for (size_t k = 0; k < p.leaves.size(); ++k) {
+            const Leaf& lf = p.leaves[k];
+            const TcLeaf& t = L[k];
+            const int m = lf.m();
+            for (int kc = 0; kc < t.kchunks; ++kc)
+                for (int c = 0; c < t.npad; ++c)
+                    for (int kk = 0; kk < kTcK; ++kk) {
+                        const int r = kc * kTcK + kk;
+                        double val = 0.0;
+                        if (r < m && c < m) val = std::pow(2.0, -0.5 * lf.exps[r]) * lf.V[(size_t)r * m + c];
+                        const size_t o = (size_t)t.b_off + (size_t)kc * t.npad * kTcK +
+                                         (size_t)(((c >> 3) * 8 + (kk >> 3)) * 64 + (c & 7) * 8 + (kk & 7));
+                        const float f = (float)val;
+                        const uint16_t h = bf16_bits(f);
+                        bhi[o] = h;
+                        blo[o] = bf16_bits((float)(val - (double)bf16_val(h)));
+                        const __half fh = __float2half_rn(f);
+                        const __half fl = __float2half_rn((float)(val - (double)__half2float(fh)));
+                        fhi[o] = __half_as_ushort(fh);
+                        flo[o] = __half_as_ushort(fl);
+                    }
+        }
+        T->d_leaves = upload(L);
+        T->d_colmap = upload(colmap);
+        T->d_srcmap = upload(srcmap);
+        T->d_term_off = upload(toff);
+        T->d_term_src = upload(tsrc);
+        T->d_term_sign = upload(tsign);
+        T->d_bhi = reinterpret_cast<__nv_bfloat16*>(upload(bhi));
+        T->d_blo = reinterpret_cast<__nv_bfloat16*>(upload(blo));
+        T->d_fhi = reinterpret_cast<__half*>(upload(fhi));
+        T->d_flo = reinterpret_cast<__half*>(upload(flo));
+    } catch (...) {
+        delete T;
+        throw;
+    }
+    p.tc = T;
+}
+
+void tc_free(gft_plan_s& p) {
+    delete static_cast<TcPlan*>(p.tc);
+    p.tc = nullptr;
+}
 
 void launch_tc(gft_plan_s& p, const float* x, float* y, int64_t batch, bool inverse, cudaStream_t st,
                uint32_t precision) {
-    (void)p; (void)x; (void)y; (void)batch; (void)inverse; (void)st; (void)precision;
-    fail(GFT_ERR_UNSUPPORTED, "tensor-core precisions are not available in this build");
+    if (inverse) fail(GFT_ERR_UNSUPPORTED, "tensor-core precisions are implemented for the forward transform");
+    if (!p.tc) fail(GFT_ERR_UNSUPPORTED, "tensor-core path needs every leaf to have at most 256 nodes");
+    if (x == y) fail(GFT_ERR_UNSUPPORTED, "tensor-core path does not run in place");
+    TcPlan* T = static_cast<TcPlan*>(p.tc);
+    const int n = p.n;
+    if ((size_t)batch > T->rows_cap) {
+        if (T->d_v) cudaFree(T->d_v);
+        if (T->d_z) cudaFree(T->d_z);
+        T->d_v = T->d_z = nullptr;
+        T->rows_cap = 0;
+        GFT_CUDA(cudaMalloc(&T->d_v, sizeof(float) * (size_t)batch * n));
+        if (!T->direct) GFT_CUDA(cudaMalloc(&T->d_z, sizeof(float) * (size_t)batch * n));
+        T->rows_cap = (size_t)batch;
+    }
+    const int sms = sm_count();
+    tc_gather_kernel<<<sms * 8, 256, 0, st>>>(x, T->d_v, batch, n, T->d_term_off, T->d_term_src, T->d_term_sign);
+    GFT_CUDA(cudaGetLastError());
+    TcArgs a{};
+    a.v = T->d_v;
+    a.y = T->direct ? y : T->d_z;
+    a.leaves = T->d_leaves;
+    a.colmap = T->d_colmap;
+    a.bhi = T->d_bhi;
+    a.blo = T->d_blo;
+    a.fhi = T->d_fhi;
+    a.flo = T->d_flo;
+    a.batch = batch;
+    a.n = n;
+    a.n_leaves = T->n_leaves;
+    a.n_groups = T->n_groups;
+    a.prec = (int)precision;
+    a.direct = T->direct;
+    a.err = p.dev.d_err;
+    const size_t smem = 131072;  // A hi/lo 32 KB + B hi/lo 64 KB + 32 KB guard
+    GFT_CUDA(cudaFuncSetAttribute(tc_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const long long tiles = (batch + kTcM - 1) / kTcM;
+    const int grid = (int)std::min<long long>(tiles, sms);
+    tc_leaf_kernel<<<grid, kTcThreads, smem, st>>>(a);
+    GFT_CUDA(cudaGetLastError());
+    if (!T->direct) {
+        tc_permute_kernel<<<sms * 8, 256, 0, st>>>(T->d_z, y, batch, n, T->d_srcmap);
+        GFT_CUDA(cudaGetLastError());
+    }
 }
 
 }  // namespace gft
