@@ -56,14 +56,18 @@ def _kernel_hash():
 
 
 def _traffic_from_profile(kernel_hash):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "apply_skeleton25_traffic.json")
+    """DRAM bytes per launch from the committed ncu summary of the forward
+    kernel, if it was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "skeleton25_fwd_2e20.md")
+    vals = {}
     try:
         with open(path) as fh:
-            d = json.load(fh)
-        if d.get("kernel_hash") == kernel_hash:
-            return d.get("dram_bytes_per_launch_full")
+            for line in fh:
+                if ":" in line and line.strip().startswith("- "):
+                    k, v = line.strip()[2:].split(":", 1)
+                    vals[k.strip()] = v.strip().strip("`")
+        if vals.get("kernel_hash") == kernel_hash:
+            return int(vals["dram_bytes_per_launch"])
     except Exception:
         pass
     return None
@@ -169,6 +173,81 @@ def run_reference(args, rank, world):
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def _timed(torch, fn, reps=10):
+    for _ in range(3):
+        fn()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps / 1e3
+
+
+def extras(torch, gft, dev):
+    """Context numbers after the timed region: the grid/cycle kinds in every
+    precision against the dense GEMM, the mixed batch in one launch, and the
+    learned surrogate against the exact dense GFT.  Errors are relative L2
+    against the plan's FP64 basis applied in FP64 on the GPU."""
+    out = {}
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    kinds = {}
+    for k, (g, batch, seed) in enumerate(W.config3()):
+        plan = gft.Plan(gft.laplacian(g.W, g.s), g.phis)
+        x = torch.from_numpy(W.signals(batch, g.n, seed)).to(dev)
+        y = torch.empty_like(x)
+        U = torch.from_numpy(plan.basis()).to(dev)
+        ref = x[:2048].double() @ U
+        row = {"n": g.n, "signals": batch}
+        coeffs = batch * g.n
+        for prec in ("fp32", "bf16", "bf16x3", "fp16x3"):
+            try:
+                t = _timed(torch, lambda: plan.forward(x, out=y, precision=prec))
+                yy = plan.forward(x[:2048].contiguous(), precision=prec).double()
+                err = float(torch.linalg.norm(yy - ref) / torch.linalg.norm(ref))
+                row[prec] = {"gcoeffs_s": round(coeffs / t / 1e9, 1), "err_vs_fp64": float(f"{err:.2e}")}
+            except gft.GftError:
+                row[prec] = "unsupported"
+        Uf = U.float()
+        t = _timed(torch, lambda: torch.matmul(x, Uf, out=y))
+        row["dense_fp32_gcoeffs_s"] = round(coeffs / t / 1e9, 1)
+        xb, Ub = x.bfloat16(), Uf.bfloat16()
+        t = _timed(torch, lambda: torch.matmul(xb, Ub))
+        row["dense_bf16_gcoeffs_s"] = round(coeffs / t / 1e9, 1)
+        kinds[g.name] = row
+    out["config3_kinds"] = kinds
+    # mixed batch of the CUDA-core kinds (grid 8/16, cycle 64/256) in one launch
+    sel = [W.config3()[k] for k in (0, 1, 2, 3, 6, 7)]
+    plans = [gft.Plan(gft.laplacian(g.W, g.s), g.phis, jit=False) for g, _, _ in sel]
+    xs = [torch.from_numpy(W.signals(b, g.n, s)).to(dev) for g, b, s in sel]
+    ys = [torch.empty_like(v) for v in xs]
+    bat = gft.Batch(plans, [b for _, b, _ in sel])
+    t = _timed(torch, lambda: bat.forward(xs, ys))
+    tot = sum(b * g.n for g, b, _ in sel)
+    out["mixed_batch_6kinds"] = {"gcoeffs_s": round(tot / t / 1e9, 1), "coeffs": tot, "launches": 1,
+                                 "kernel": "gft_batch_kernel (CUDA graph replay)"}
+    # learned Givens surrogate vs the exact dense GFT (nearly symmetric path, n=16)
+    from paper_1907_07875_gb300.learned import LearnedGFT, delta
+    g = W.near_symmetric_path(16, 0.05, seed=1)
+    exact = gft.Plan(gft.laplacian(g.W, g.s), [])
+    model = LearnedGFT(16, device=dev)
+    model.train(exact.basis(), steps=1500, lr=0.05)
+    d = delta(model.matrix(), exact.basis())
+    x = torch.from_numpy(W.signals(1 << 20, 16, 5)).to(dev)
+    y = torch.empty_like(x)
+    t_l = _timed(torch, lambda: model.forward(x, out=y))
+    t_e = _timed(torch, lambda: exact.forward(x, out=y))
+    out["learned_c4_path16_eps0.05"] = {"delta_vs_exact": round(d, 4),
+                                        "learned_gcoeffs_s": round((1 << 24) / t_l / 1e9, 1),
+                                        "exact_dense_gcoeffs_s": round((1 << 24) / t_e / 1e9, 1)}
+    torch.backends.cuda.matmul.allow_tf32 = prev
+    return out
 
 
 def run_ours(args, rank, world, local_rank):
@@ -326,6 +405,8 @@ def run_ours(args, rank, world, local_rank):
         "kernel_hash": khash,
         "cpu_baseline": cpu,
     }
+    if not args.no_extras and world == 1:
+        line["extras"] = extras(torch, gft, dev)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -338,6 +419,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the context measurements")
     ap.add_argument("--profile", action="store_true",
                     help="forward steps only, 2 buffer sets (for ncu captures)")
     args = ap.parse_args()
