@@ -253,6 +253,7 @@ def extras(torch, gft, dev):
 def run_ours(args, rank, world, local_rank):
     import torch
     import paper_1907_07875_gb300 as gft
+    from paper_1907_07875_gb300 import sharding
     from paper_1907_07875_gb300.build import build
     dist = None
     if world > 1:
@@ -270,7 +271,7 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.current_stream()
     # rotating input/output sets, together larger than L2, so every step reads
     # its input from HBM
-    x_host = W.signals(batch, n, seed + 7919 * rank)
+    x_host = W.signals(batch, n, sharding.rank_seed(seed, rank))
     nbytes = batch * n * 4
     nsets = 2 if args.profile else max(2, -(-4 * L2_BYTES // (2 * nbytes)))
     xs = [torch.from_numpy(x_host).to(dev) for _ in range(nsets)]
@@ -326,10 +327,7 @@ def run_ours(args, rank, world, local_rank):
             print(json.dumps({"profile_run": True, "ms_per_step": total_ms / args.steps,
                               "config": {"workload": WORKLOAD, "sets": nsets}}), flush=True)
         return
-    if dist is not None:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = sharding.max_over_ranks(total_ms, dist, dev)
     ms_per_step = total_ms / args.steps
     coeffs_per_step = batch * n
     value = coeffs_per_step * world / (total_ms / 1e3) * args.steps

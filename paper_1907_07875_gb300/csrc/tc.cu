@@ -5,19 +5,21 @@
 // y_k = M_k^T v_k (Sec. IV-C, Eq. 13; M_k the folded leaf basis) are dense
 // contractions, run here as GEMMs D[128 x N] = A[128 x K] B[K x N] per tile
 // of 128 signals:
-//   1. tc_gather_kernel: the Haar stages, written as signed sums of the
-//      input entries (each post-stage value is +-x_i1 +- x_i2 ..., one term
-//      per node of its orbit), into a leaf-ordered FP32 scratch V [batch, n];
-//   2. tc_leaf_kernel (persistent, one CTA per SM, 128 threads): for each
-//      leaf and each K chunk of 64, the CTA converts its 128 x 64 block of V
-//      to BF16 (hi, and lo = v - hi for the split precisions) or scaled FP16
-//      hi/lo, writes it and the matching block of B (pre-split on the host,
-//      stored in the smem image order) to shared memory in the canonical
-//      no-swizzle K-major layout (8 x 16-byte core matrices), and one thread
-//      issues tcgen05.mma (M=128, N=leaf width, K=16 per instruction) into
-//      the leaf's TMEM columns: one product for BF16, three (hi*hi + hi*lo +
-//      lo*hi) for the split precisions.  tcgen05.commit arrives on an
-//      mbarrier; every wait is bounded (about 2 s, then GFT_ERR_TIMEOUT).
+//   1. tc_pack_kernel: the Haar stages, written as signed sums of the input
+//      entries (each post-stage value is +-x_i1 +- x_i2 ..., one term per
+//      node of its orbit), converted to BF16 (hi, and lo = v - hi for the
+//      split precisions) or per-signal scaled FP16 hi/lo, and written as
+//      ready-made shared-memory images: per tile of 128 signals and per item
+//      (leaf, K chunk of 64), a 128 x 64 block in the canonical no-swizzle
+//      K-major layout (8 x 16-byte core matrices), hi then lo;
+//   2. tc_leaf_kernel (persistent, one CTA per SM): one thread bulk-loads
+//      (TMA) the A image and the leaf's pre-split B image of each item into
+//      a two-deep ring of shared-memory buffers, issues tcgen05.mma (M=128,
+//      N=leaf width, K=16 per instruction) into the leaf's TMEM columns --
+//      one product for BF16, three (hi*hi + hi*lo + lo*hi) for the split
+//      precisions -- and commits to mbarriers; loads of the next items
+//      overlap the MMAs and the epilogue.  Every wait is bounded (about 2 s,
+//      then GFT_ERR_TIMEOUT, drain, TMEM freed).
 //   3. Epilogue: when every leaf of the plan fits the 512 TMEM columns, each
 //      warp reads its 32 rows column by column IN COEFFICIENT ORDER
 //      (tcgen05.ld 32x32b) and writes 32 consecutive coefficients per row,
@@ -54,7 +56,6 @@ struct TcLeaf {
 };
 
 struct TcArgs {
-    const float* v;          // [batch, n] leaf-ordered post-stage values
     float* y;                // [batch, n] output (direct mode) or scratch (group mode)
     const TcLeaf* leaves;
     const int* colmap;       // direct mode: TMEM column of coefficient j
@@ -136,16 +137,38 @@ __device__ __forceinline__ unsigned core_off(int row, int kg) {
     return (unsigned)(((row >> 3) * 8 + kg) * 128 + (row & 7) * 16);
 }
 
-__global__ void __launch_bounds__(kTcThreads, 1) tc_leaf_kernel(TcArgs a) {
+__device__ __forceinline__ void mbar_expect(unsigned long long* b, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* b) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(b))
+                 : "memory");
+}
+
+// Work item = (leaf, K chunk); items of a tile run in leaf order.
+struct TcItem {
+    int leaf, kc;
+};
+
+// Persistent tensor-core kernel.  Thread 0 drives a two-deep ring of
+// shared-memory buffers: it bulk-loads the A image (128 x 64, hi then lo,
+// written by tc_pack_kernel) and the B image of item i into buffer i % 2,
+// waits for the load, issues the item's MMAs, commits them to the buffer's
+// MMA barrier, and before reusing the buffer for item i + 2 waits for those
+// MMAs to finish reading it.  After a tile's last MMA of a leaf group all
+// four warps read TMEM (lane = signal) and write the coefficients.
+__global__ void __launch_bounds__(kTcThreads, 1) tc_leaf_kernel(TcArgs a, const TcItem* __restrict__ items,
+                                                               int n_items, const unsigned char* __restrict__ aimg,
+                                                               const float* __restrict__ scale) {
     extern __shared__ __align__(1024) unsigned char sm[];
-    // [A hi 16 KB][A lo 16 KB][B hi 32 KB][B lo 32 KB][guard 32 KB]
-    unsigned char* a_hi = sm;
-    unsigned char* a_lo = sm + 16384;
-    unsigned char* b_hi = sm + 32768;
-    unsigned char* b_lo = sm + 65536;
+    // buffer s (96 KB): [A hi 16 KB][A lo 16 KB][B hi 32 KB][B lo 32 KB]
     __shared__ unsigned s_tmem;
-    __shared__ __align__(8) unsigned long long mbar;
-    __shared__ float s_scale[kTcM];
+    __shared__ __align__(8) unsigned long long bar_load[2];
+    __shared__ __align__(8) unsigned long long bar_mma[2];
+    __shared__ __align__(8) unsigned long long bar_done;
+    __shared__ int s_bad;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
@@ -154,171 +177,159 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_leaf_kernel(TcArgs a) {
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        mbar_init1(&mbar);
+        mbar_init1(&bar_load[0]);
+        mbar_init1(&bar_load[1]);
+        mbar_init1(&bar_mma[0]);
+        mbar_init1(&bar_mma[1]);
+        mbar_init1(&bar_done);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_bad = 0;
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const unsigned tmem = s_tmem;
-    unsigned phase = 0;
-    bool bad = false;
     const bool split = a.prec != GFT_PREC_BF16;
     const bool fp16 = a.prec == GFT_PREC_FP16X3;
+    const unsigned a_bytes = split ? 32768u : 16384u;
     const long long n_tiles = (a.batch + kTcM - 1) / kTcM;
-    for (long long tile = blockIdx.x; tile < n_tiles && !bad; tile += gridDim.x) {
-        const long long r0 = tile * kTcM;
-        if (fp16) {
-            // one power-of-two scale per signal (row), shared by every leaf,
-            // so the FP16 hi/lo parts keep their precision at any magnitude
-            const long long row = r0 + tid;
-            float mx = 0.f;
-            if (row < a.batch)
-                for (int c = 0; c < a.n; ++c) mx = fmaxf(mx, fabsf(a.v[row * a.n + c]));
-            s_scale[tid] = mx > 0.f ? exp2f(ceilf(log2f(mx))) : 1.f;
-            __syncthreads();
+    // thread 0's ring state (items counted over the whole CTA lifetime)
+    unsigned ph_load[2] = {0, 0}, ph_mma[2] = {0, 0}, ph_done = 0;
+    long long issued = 0, consumed = 0;  // global item counters of this CTA
+    bool pending_mma[2] = {false, false};
+    auto buf = [&](int s) { return sm + s * 98304; };
+    // item q of this CTA's sequence -> (tile, item index)
+    const long long my_tiles = n_tiles > blockIdx.x ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const long long total = my_tiles * n_items;
+    auto issue = [&](long long q) {
+        const int s = (int)(q & 1);
+        const long long tile = blockIdx.x + (q / n_items) * (long long)gridDim.x;
+        const TcItem it = items[q % n_items];
+        const TcLeaf L = a.leaves[it.leaf];
+        if (pending_mma[s]) {  // MMAs of item q-2 still read this buffer
+            if (!mbar_wait_bounded(&bar_mma[s], ph_mma[s])) s_bad = 1;
+            ph_mma[s] ^= 1u;
+            pending_mma[s] = false;
         }
-        for (int g = 0; g < a.n_groups && !bad; ++g) {
-            for (int k = 0; k < a.n_leaves && !bad; ++k) {
-                const TcLeaf L = a.leaves[k];
-                if (L.group != g) continue;
-                const unsigned id = instr_desc(L.npad, !fp16);
-                for (int kc = 0; kc < L.kchunks && !bad; ++kc) {
-                    // ---- A: 128 rows x 64 K, hi/lo ----
-                    for (int gi = tid; gi < kTcM * 8; gi += kTcThreads) {
-                        const int row = gi & (kTcM - 1), kg = gi >> 7;
-                        const long long grow = r0 + row;
-                        float v[8];
-#pragma unroll
-                        for (int e = 0; e < 8; ++e) {
-                            const int c = kc * kTcK + kg * 8 + e;
-                            v[e] = (grow < a.batch && c < L.m) ? a.v[grow * a.n + L.off + c] : 0.f;
-                        }
-                        unsigned hi[4], lo[4];
-                        if (fp16) {
-                            const float inv = 1.f / s_scale[row];
-#pragma unroll
-                            for (int e = 0; e < 4; ++e) {
-                                const float x0 = v[2 * e] * inv, x1 = v[2 * e + 1] * inv;
-                                const __half h0 = __float2half_rn(x0), h1 = __float2half_rn(x1);
-                                const __half l0 = __float2half_rn(x0 - __half2float(h0));
-                                const __half l1 = __float2half_rn(x1 - __half2float(h1));
-                                hi[e] = (unsigned)__half_as_ushort(h0) | ((unsigned)__half_as_ushort(h1) << 16);
-                                lo[e] = (unsigned)__half_as_ushort(l0) | ((unsigned)__half_as_ushort(l1) << 16);
-                            }
-                        } else {
-#pragma unroll
-                            for (int e = 0; e < 4; ++e) {
-                                const __nv_bfloat16 h0 = __float2bfloat16_rn(v[2 * e]);
-                                const __nv_bfloat16 h1 = __float2bfloat16_rn(v[2 * e + 1]);
-                                const __nv_bfloat16 l0 = __float2bfloat16_rn(v[2 * e] - __bfloat162float(h0));
-                                const __nv_bfloat16 l1 = __float2bfloat16_rn(v[2 * e + 1] - __bfloat162float(h1));
-                                hi[e] = (unsigned)__bfloat16_as_ushort(h0) | ((unsigned)__bfloat16_as_ushort(h1) << 16);
-                                lo[e] = (unsigned)__bfloat16_as_ushort(l0) | ((unsigned)__bfloat16_as_ushort(l1) << 16);
-                            }
-                        }
-                        const unsigned o = core_off(row, kg);
-                        *reinterpret_cast<uint4*>(a_hi + o) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-                        if (split) *reinterpret_cast<uint4*>(a_lo + o) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-                    }
-                    // ---- B: npad rows x 64 K, image copied as stored ----
-                    {
-                        const size_t img = (size_t)L.npad * kTcK;  // elements per chunk
-                        const uint4* sh = fp16 ? reinterpret_cast<const uint4*>(a.fhi + L.b_off + kc * img)
-                                               : reinterpret_cast<const uint4*>(a.bhi + L.b_off + kc * img);
-                        const uint4* sl = fp16 ? reinterpret_cast<const uint4*>(a.flo + L.b_off + kc * img)
-                                               : reinterpret_cast<const uint4*>(a.blo + L.b_off + kc * img);
-                        const int n16 = (int)(img * 2 / 16);
-                        for (int i = tid; i < n16; i += kTcThreads) {
-                            reinterpret_cast<uint4*>(b_hi)[i] = sh[i];
-                            if (split) reinterpret_cast<uint4*>(b_lo)[i] = sl[i];
+        const size_t img = (size_t)L.npad * kTcK;
+        const unsigned b_bytes = (unsigned)(img * 2);
+        mbar_expect(&bar_load[s], a_bytes + (split ? 2 * b_bytes : b_bytes));
+        const unsigned char* asrc = aimg + ((size_t)tile * n_items + (size_t)(q % n_items)) * 32768u;
+        bulk_load(buf(s), asrc, a_bytes, &bar_load[s]);
+        const unsigned char* bh = fp16 ? reinterpret_cast<const unsigned char*>(a.fhi + L.b_off + it.kc * img)
+                                       : reinterpret_cast<const unsigned char*>(a.bhi + L.b_off + it.kc * img);
+        bulk_load(buf(s) + 32768, bh, b_bytes, &bar_load[s]);
+        if (split) {
+            const unsigned char* bl = fp16 ? reinterpret_cast<const unsigned char*>(a.flo + L.b_off + it.kc * img)
+                                           : reinterpret_cast<const unsigned char*>(a.blo + L.b_off + it.kc * img);
+            bulk_load(buf(s) + 65536, bl, b_bytes, &bar_load[s]);
+        }
+    };
+    if (tid == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        for (; issued < total && issued < 2; ++issued) issue(issued);
+    }
+    for (long long t = 0; t < my_tiles; ++t) {
+        const long long tile = blockIdx.x + t * (long long)gridDim.x;
+        const long long r0 = tile * kTcM;
+        for (int g = 0; g < a.n_groups; ++g) {
+            if (tid == 0) {
+                // consume every item of this group
+                while (consumed < total && consumed < (t + 1) * n_items) {
+                    const TcItem it = items[consumed % n_items];
+                    const TcLeaf L = a.leaves[it.leaf];
+                    if (L.group != g) break;
+                    const int s = (int)(consumed & 1);
+                    if (!mbar_wait_bounded(&bar_load[s], ph_load[s])) s_bad = 1;
+                    ph_load[s] ^= 1u;
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const unsigned id = instr_desc(L.npad, !fp16);
+                    const unsigned dt = tmem + (unsigned)L.tcol;
+                    const unsigned base = smem_u32(buf(s));
+                    for (int ks = 0; ks < kTcK / 16; ++ks) {
+                        if (it.kc * kTcK + ks * 16 >= ((L.m + 15) & ~15)) break;
+                        const unsigned koff = ks * 256u;
+                        const unsigned long long ah = smem_desc(base + koff, 128, 1024);
+                        const unsigned long long bh = smem_desc(base + 32768 + koff, 128, 1024);
+                        mma_f16(dt, ah, bh, id, (it.kc | ks) ? 1u : 0u);
+                        if (split) {
+                            mma_f16(dt, ah, smem_desc(base + 65536 + koff, 128, 1024), id, 1u);
+                            mma_f16(dt, smem_desc(base + 16384 + koff, 128, 1024), bh, id, 1u);
                         }
                     }
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    __syncthreads();
-                    if (tid == 0) {
-                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                        const unsigned dt = tmem + (unsigned)L.tcol;
-#pragma unroll
-                        for (int ks = 0; ks < kTcK / 16; ++ks) {
-                            if (kc * kTcK + ks * 16 >= ((L.m + 15) & ~15)) break;
-                            const unsigned koff = ks * 256u;
-                            const unsigned long long ah = smem_desc(smem_u32(a_hi) + koff, 128, 1024);
-                            const unsigned long long bh = smem_desc(smem_u32(b_hi) + koff, 128, 1024);
-                            const unsigned acc0 = (kc | ks) ? 1u : 0u;
-                            mma_f16(dt, ah, bh, id, acc0);
-                            if (split) {
-                                const unsigned long long al = smem_desc(smem_u32(a_lo) + koff, 128, 1024);
-                                const unsigned long long bl = smem_desc(smem_u32(b_lo) + koff, 128, 1024);
-                                mma_f16(dt, ah, bl, id, 1u);
-                                mma_f16(dt, al, bh, id, 1u);
-                            }
-                        }
-                        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                                         smem_u32(&mbar))
-                                     : "memory");
-                    }
-                    const bool ok = mbar_wait_bounded(&mbar, phase);
-                    phase ^= 1u;
-                    if (__syncthreads_or(!ok)) bad = true;
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                     smem_u32(&bar_mma[s]))
+                                 : "memory");
+                    pending_mma[s] = true;
+                    ++consumed;
+                    if (issued < total && issued < consumed + 2) issue(issued++);
                 }
+                // all MMAs of the group: arrive on bar_done once they finish
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 smem_u32(&bar_done))
+                             : "memory");
             }
-            if (bad) break;
-            // ---- epilogue: TMEM -> registers -> global ----
+            // everyone waits for the group's MMAs (bounded)
+            const bool ok = mbar_wait_bounded(&bar_done, ph_done);
+            ph_done ^= 1u;
+            if (__syncthreads_or(!ok || s_bad)) {
+                if (tid == 0) atomicExch(a.err, (int)GFT_ERR_TIMEOUT);
+                goto teardown;
+            }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const long long row = r0 + warp * 32 + lane;
-            const unsigned lane_base = (unsigned)(warp * 32) << 16;
-            if (a.direct) {
-                for (int j0 = 0; j0 < a.n; j0 += 32) {
-                    float r[32];
-#pragma unroll
-                    for (int q = 0; q < 32; ++q) {
-                        const int j = min(j0 + q, a.n - 1);
-                        const unsigned col = (unsigned)a.colmap[j];
-                        unsigned u;
-                        asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];"
-                                     : "=r"(u)
-                                     : "r"(tmem + lane_base + col)
-                                     : "memory");
-                        r[q] = __uint_as_float(u);
-                    }
-                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                    if (row < a.batch) {
-                        float* dst = a.y + row * a.n + j0;
-                        const int cnt = min(32, a.n - j0);
-                        const float sc = fp16 ? s_scale[warp * 32 + lane] : 1.f;
-                        if (cnt == 32 && (a.n & 3) == 0) {
-#pragma unroll
-                            for (int q = 0; q < 32; q += 4)
-                                __stcs(reinterpret_cast<float4*>(dst + q),
-                                       make_float4(r[q] * sc, r[q + 1] * sc, r[q + 2] * sc, r[q + 3] * sc));
-                        } else {
-                            for (int q = 0; q < cnt; ++q) __stcs(dst + q, r[q] * sc);
-                        }
-                    }
-                }
-            } else {
-                for (int k = 0; k < a.n_leaves; ++k) {
-                    const TcLeaf L = a.leaves[k];
-                    if (L.group != g) continue;
-                    for (int c0 = 0; c0 < L.m; c0 += 32) {
+            {
+                const long long row = r0 + warp * 32 + lane;
+                const unsigned lane_base = (unsigned)(warp * 32) << 16;
+                const float sc = fp16 ? (row < a.batch ? scale[row] : 1.f) : 1.f;
+                if (a.direct) {
+                    for (int j0 = 0; j0 < a.n; j0 += 32) {
                         float r[32];
 #pragma unroll
                         for (int q = 0; q < 32; ++q) {
-                            const unsigned col = (unsigned)(L.tcol + min(c0 + q, L.npad - 1));
+                            const int j = min(j0 + q, a.n - 1);
                             unsigned u;
                             asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];"
                                          : "=r"(u)
-                                         : "r"(tmem + lane_base + col)
+                                         : "r"(tmem + lane_base + (unsigned)a.colmap[j])
                                          : "memory");
                             r[q] = __uint_as_float(u);
                         }
                         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                         if (row < a.batch) {
-                            float* dst = a.y + row * a.n + L.off + c0;
-                            const int cnt = min(32, L.m - c0);
-                            const float sc = fp16 ? s_scale[warp * 32 + lane] : 1.f;
-                            for (int q = 0; q < cnt; ++q) dst[q] = r[q] * sc;
+                            float* dst = a.y + row * a.n + j0;
+                            const int cnt = min(32, a.n - j0);
+                            if (cnt == 32 && (a.n & 3) == 0) {
+#pragma unroll
+                                for (int q = 0; q < 32; q += 4)
+                                    __stcs(reinterpret_cast<float4*>(dst + q),
+                                           make_float4(r[q] * sc, r[q + 1] * sc, r[q + 2] * sc, r[q + 3] * sc));
+                            } else {
+                                for (int q = 0; q < cnt; ++q) __stcs(dst + q, r[q] * sc);
+                            }
+                        }
+                    }
+                } else {
+                    for (int k = 0; k < a.n_leaves; ++k) {
+                        const TcLeaf L = a.leaves[k];
+                        if (L.group != g) continue;
+                        for (int c0 = 0; c0 < L.m; c0 += 32) {
+                            float r[32];
+#pragma unroll
+                            for (int q = 0; q < 32; ++q) {
+                                const unsigned col = (unsigned)(L.tcol + min(c0 + q, L.npad - 1));
+                                unsigned u;
+                                asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];"
+                                             : "=r"(u)
+                                             : "r"(tmem + lane_base + col)
+                                             : "memory");
+                                r[q] = __uint_as_float(u);
+                            }
+                            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                            if (row < a.batch) {
+                                float* dst = a.y + row * a.n + L.off + c0;
+                                const int cnt = min(32, L.m - c0);
+                                for (int q = 0; q < cnt; ++q) dst[q] = r[q] * sc;
+                            }
                         }
                     }
                 }
@@ -327,26 +338,110 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_leaf_kernel(TcArgs a) {
             __syncthreads();
         }
     }
+teardown:
+    __syncthreads();
+    if (tid == 0) {
+        // drain: wait (bounded) for MMAs still reading shared memory
+        for (int s = 0; s < 2; ++s)
+            if (pending_mma[s]) mbar_wait_bounded(&bar_mma[s], ph_mma[s]);
+    }
     __syncthreads();
     if (warp == 0) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols) : "memory");
     }
-    if (bad && tid == 0) atomicExch(a.err, (int)GFT_ERR_TIMEOUT);
 }
 
-// post-stage values in leaf order: v[t][j] = sum_q sign_q x[t][src_q]
-__global__ void tc_gather_kernel(const float* __restrict__ x, float* __restrict__ v, long long batch, int n,
-                                 const int* __restrict__ term_off, const int* __restrict__ term_src,
-                                 const float* __restrict__ term_sign) {
-    const long long total = batch * n;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x) {
-        const long long t = e / n;
-        const int j = (int)(e - t * n);
-        const float* row = x + t * n;
-        float s = 0.f;
-        for (int q = term_off[j]; q < term_off[j + 1]; ++q) s += term_sign[q] * __ldg(row + term_src[q]);
-        v[e] = s;
+// A images: for tile, item (leaf, K chunk), 128 rows x 64 K as BF16 (or
+// scaled FP16) hi then lo in the core-matrix order; row values are the
+// post-stage signal entries (signed sums of inputs).  A block handles one
+// slice of `rows` signals of one tile: it stages those rows of x (odd row
+// stride) and the term tables in shared memory, then writes the slice's
+// rows of every item image, consecutive threads on consecutive signals.
+__global__ void __launch_bounds__(256) tc_pack_kernel(const float* __restrict__ x, unsigned char* __restrict__ aimg,
+                                                      long long batch, int n, const TcLeaf* __restrict__ leaves,
+                                                      const TcItem* __restrict__ items, int n_items,
+                                                      const int* __restrict__ term_off,
+                                                      const int* __restrict__ term_src,
+                                                      const float* __restrict__ term_sign, int n_terms,
+                                                      const float* __restrict__ scale, int prec, int rows) {
+    extern __shared__ __align__(16) float sx[];
+    const int np = n | 1;
+    int* s_off = reinterpret_cast<int*>(sx + (size_t)rows * np);
+    int* s_src = s_off + n + 1;
+    float* s_sign = reinterpret_cast<float*>(s_src + n_terms);
+    const int tid = threadIdx.x;
+    const int slices = kTcM / rows;
+    const long long tile = blockIdx.x / slices;
+    const int slice = (int)(blockIdx.x - tile * slices);
+    const long long row0 = tile * kTcM + (long long)slice * rows;
+    for (int i = tid; i <= n; i += blockDim.x) s_off[i] = term_off[i];
+    for (int i = tid; i < n_terms; i += blockDim.x) {
+        s_src[i] = term_src[i];
+        s_sign[i] = term_sign[i];
+    }
+    for (int e = tid; e < rows * n; e += blockDim.x) {
+        const int r = e / n, c = e - r * n;
+        const long long g = row0 + r;
+        sx[r * np + c] = g < batch ? x[g * n + c] : 0.f;
+    }
+    __syncthreads();
+    const bool fp16 = prec == GFT_PREC_FP16X3, split = prec != GFT_PREC_BF16;
+    const int work = n_items * rows * 8;
+    for (int w = tid; w < work; w += blockDim.x) {
+        const int item = w / (rows * 8);
+        const int rem = w - item * rows * 8;
+        const int kg = rem / rows, r = rem - kg * rows;
+        const TcItem it = items[item];
+        const TcLeaf L = leaves[it.leaf];
+        const long long grow = row0 + r;
+        const float inv = (fp16 && grow < batch) ? 1.f / scale[grow] : 1.f;
+        const float* xr = sx + r * np;
+        float v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int c = it.kc * kTcK + kg * 8 + q;
+            float acc = 0.f;
+            if (c < L.m) {
+                const int j = L.off + c;
+                for (int u = s_off[j]; u < s_off[j + 1]; ++u) acc += s_sign[u] * xr[s_src[u]];
+            }
+            v[q] = acc * inv;
+        }
+        unsigned hi[4], lo[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (fp16) {
+                const __half h0 = __float2half_rn(v[2 * q]), h1 = __float2half_rn(v[2 * q + 1]);
+                const __half l0 = __float2half_rn(v[2 * q] - __half2float(h0));
+                const __half l1 = __float2half_rn(v[2 * q + 1] - __half2float(h1));
+                hi[q] = (unsigned)__half_as_ushort(h0) | ((unsigned)__half_as_ushort(h1) << 16);
+                lo[q] = (unsigned)__half_as_ushort(l0) | ((unsigned)__half_as_ushort(l1) << 16);
+            } else {
+                const __nv_bfloat16 h0 = __float2bfloat16_rn(v[2 * q]), h1 = __float2bfloat16_rn(v[2 * q + 1]);
+                const __nv_bfloat16 l0 = __float2bfloat16_rn(v[2 * q] - __bfloat162float(h0));
+                const __nv_bfloat16 l1 = __float2bfloat16_rn(v[2 * q + 1] - __bfloat162float(h1));
+                hi[q] = (unsigned)__bfloat16_as_ushort(h0) | ((unsigned)__bfloat16_as_ushort(h1) << 16);
+                lo[q] = (unsigned)__bfloat16_as_ushort(l0) | ((unsigned)__bfloat16_as_ushort(l1) << 16);
+            }
+        }
+        unsigned char* dst =
+            aimg + ((size_t)tile * n_items + item) * 32768u + core_off(slice * rows + r, kg);
+        __stcg(reinterpret_cast<uint4*>(dst), make_uint4(hi[0], hi[1], hi[2], hi[3]));
+        if (split) __stcg(reinterpret_cast<uint4*>(dst + 16384), make_uint4(lo[0], lo[1], lo[2], lo[3]));
+    }
+}
+
+// FP16 split: one power-of-two scale per signal bounding its post-stage
+// values (|v| <= 2^S max|x|), so hi and lo keep their precision
+__global__ void tc_scale_kernel(const float* __restrict__ x, float* __restrict__ scale, long long batch, int n,
+                                int n_stages) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (long long r = blockIdx.x * (long long)(blockDim.x >> 5) + warp; r < batch;
+         r += (long long)gridDim.x * (blockDim.x >> 5)) {
+        float m = 0.f;
+        for (int j = lane; j < n; j += 32) m = fmaxf(m, fabsf(x[r * n + j]));
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) scale[r] = m > 0.f ? exp2f(ceilf(log2f(m)) + (float)n_stages) : 1.f;
     }
 }
 
@@ -363,8 +458,9 @@ __global__ void tc_permute_kernel(const float* __restrict__ z, float* __restrict
 }
 
 struct TcPlan {
-    int n = 0, n_leaves = 0, n_groups = 0, direct = 0;
+    int n = 0, n_leaves = 0, n_groups = 0, direct = 0, n_items = 0, n_stages = 0, n_terms = 0;
     TcLeaf* d_leaves = nullptr;
+    TcItem* d_items = nullptr;
     int* d_colmap = nullptr;
     int* d_srcmap = nullptr;
     int* d_term_off = nullptr;
@@ -374,13 +470,14 @@ struct TcPlan {
     __nv_bfloat16* d_blo = nullptr;
     __half* d_fhi = nullptr;
     __half* d_flo = nullptr;
-    float* d_v = nullptr;
-    float* d_z = nullptr;
+    unsigned char* d_aimg = nullptr;   // A images, [tiles][items] x 32 KB
+    float* d_scale = nullptr;          // per-signal FP16 scale
+    float* d_z = nullptr;              // leaf-ordered output (several TMEM groups)
     size_t rows_cap = 0;
     ~TcPlan() {
-        for (void* p : {(void*)d_leaves, (void*)d_colmap, (void*)d_srcmap, (void*)d_term_off, (void*)d_term_src,
-                        (void*)d_term_sign, (void*)d_bhi, (void*)d_blo, (void*)d_fhi, (void*)d_flo, (void*)d_v,
-                        (void*)d_z})
+        for (void* p : {(void*)d_leaves, (void*)d_items, (void*)d_colmap, (void*)d_srcmap, (void*)d_term_off,
+                        (void*)d_term_src, (void*)d_term_sign, (void*)d_bhi, (void*)d_blo, (void*)d_fhi,
+                        (void*)d_flo, (void*)d_aimg, (void*)d_scale, (void*)d_z})
             if (p) cudaFree(p);
     }
 };
@@ -503,9 +600,16 @@ void tc_build(gft_plan_s& p) {
                         flo[o] = __half_as_ushort(fl);
                     }
         }
+        std::vector<TcItem> items;
+        for (size_t k = 0; k < L.size(); ++k)
+            for (int kc = 0; kc < L[k].kchunks; ++kc) items.push_back({(int)k, kc});
+        T->n_items = (int)items.size();
+        T->n_stages = p.n_stages;
+        T->d_items = upload(items);
         T->d_leaves = upload(L);
         T->d_colmap = upload(colmap);
         T->d_srcmap = upload(srcmap);
+        T->n_terms = (int)tsrc.size();
         T->d_term_off = upload(toff);
         T->d_term_src = upload(tsrc);
         T->d_term_sign = upload(tsign);
@@ -532,20 +636,41 @@ void launch_tc(gft_plan_s& p, const float* x, float* y, int64_t batch, bool inve
     if (x == y) fail(GFT_ERR_UNSUPPORTED, "tensor-core path does not run in place");
     TcPlan* T = static_cast<TcPlan*>(p.tc);
     const int n = p.n;
+    const long long n_tiles = (batch + kTcM - 1) / kTcM;
     if ((size_t)batch > T->rows_cap) {
-        if (T->d_v) cudaFree(T->d_v);
-        if (T->d_z) cudaFree(T->d_z);
-        T->d_v = T->d_z = nullptr;
+        for (void** q : {(void**)&T->d_aimg, (void**)&T->d_scale, (void**)&T->d_z})
+            if (*q) {
+                cudaFree(*q);
+                *q = nullptr;
+            }
         T->rows_cap = 0;
-        GFT_CUDA(cudaMalloc(&T->d_v, sizeof(float) * (size_t)batch * n));
+        const long long tiles_cap = (batch + kTcM - 1) / kTcM;
+        GFT_CUDA(cudaMalloc(&T->d_aimg, (size_t)tiles_cap * T->n_items * 32768u));
+        GFT_CUDA(cudaMalloc(&T->d_scale, sizeof(float) * (size_t)batch));
         if (!T->direct) GFT_CUDA(cudaMalloc(&T->d_z, sizeof(float) * (size_t)batch * n));
         T->rows_cap = (size_t)batch;
     }
     const int sms = sm_count();
-    tc_gather_kernel<<<sms * 8, 256, 0, st>>>(x, T->d_v, batch, n, T->d_term_off, T->d_term_src, T->d_term_sign);
-    GFT_CUDA(cudaGetLastError());
+    if (precision == GFT_PREC_FP16X3) {
+        tc_scale_kernel<<<sms * 4, 256, 0, st>>>(x, T->d_scale, batch, n, T->n_stages);
+        GFT_CUDA(cudaGetLastError());
+    }
+    {
+        // signal rows per pack block: a power of two with the rows' x in <= 96 KB
+        int rows = kTcM;
+        while (rows > 1 && (size_t)rows * (n | 1) * sizeof(float) > 98304) rows >>= 1;
+        const size_t smem = (size_t)rows * (n | 1) * sizeof(float) + sizeof(int) * (n + 1) +
+                            (sizeof(int) + sizeof(float)) * (size_t)T->n_terms;
+        if (smem > 232448) fail(GFT_ERR_UNSUPPORTED, "tensor-core pack stage does not fit in shared memory");
+        GFT_CUDA(cudaFuncSetAttribute(tc_pack_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        const long long blocks = n_tiles * (kTcM / rows);
+        tc_pack_kernel<<<(unsigned)blocks, 256, smem, st>>>(x, T->d_aimg, batch, n, T->d_leaves, T->d_items,
+                                                            T->n_items, T->d_term_off, T->d_term_src,
+                                                            T->d_term_sign, T->n_terms, T->d_scale,
+                                                            (int)precision, rows);
+        GFT_CUDA(cudaGetLastError());
+    }
     TcArgs a{};
-    a.v = T->d_v;
     a.y = T->direct ? y : T->d_z;
     a.leaves = T->d_leaves;
     a.colmap = T->d_colmap;
@@ -560,11 +685,10 @@ void launch_tc(gft_plan_s& p, const float* x, float* y, int64_t batch, bool inve
     a.prec = (int)precision;
     a.direct = T->direct;
     a.err = p.dev.d_err;
-    const size_t smem = 131072;  // A hi/lo 32 KB + B hi/lo 64 KB + 32 KB guard
+    const size_t smem = 2 * 98304;  // two ring buffers of 96 KB
     GFT_CUDA(cudaFuncSetAttribute(tc_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const long long tiles = (batch + kTcM - 1) / kTcM;
-    const int grid = (int)std::min<long long>(tiles, sms);
-    tc_leaf_kernel<<<grid, kTcThreads, smem, st>>>(a);
+    const int grid = (int)std::min<long long>(n_tiles, sms);
+    tc_leaf_kernel<<<grid, kTcThreads, smem, st>>>(a, T->d_items, T->n_items, T->d_aimg, T->d_scale);
     GFT_CUDA(cudaGetLastError());
     if (!T->direct) {
         tc_permute_kernel<<<sms * 8, 256, 0, st>>>(T->d_z, y, batch, n, T->d_srcmap);
