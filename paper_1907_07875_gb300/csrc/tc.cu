@@ -150,24 +150,35 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned b
 // Work item = (leaf, K chunk); items of a tile run in leaf order.
 struct TcItem {
     int leaf, kc;
+    int bres;   // byte offset of this item's B image among the resident images (hi set)
 };
 
-// Persistent tensor-core kernel.  Thread 0 drives a two-deep ring of
-// shared-memory buffers: it bulk-loads the A image (128 x 64, hi then lo,
-// written by tc_pack_kernel) and the B image of item i into buffer i % 2,
-// waits for the load, issues the item's MMAs, commits them to the buffer's
-// MMA barrier, and before reusing the buffer for item i + 2 waits for those
-// MMAs to finish reading it.  After a tile's last MMA of a leaf group all
-// four warps read TMEM (lane = signal) and write the coefficients.
+// Persistent tensor-core kernel.  Thread 0 drives a ring of shared-memory
+// buffers: it bulk-loads (TMA) the A image of item q (written by
+// tc_pack_kernel) -- and, unless every B image is resident, the item's B
+// images -- into buffer q % nbuf, waits for the load, issues the item's MMAs,
+// commits them to the buffer's MMA barrier, and before reusing the buffer
+// waits for those MMAs to finish reading it.  When all B images fit in
+// 96 KB they are loaded once per CTA and the ring holds four A images;
+// otherwise two A+B buffers.  After the MMAs of a tile's leaf group all four
+// warps read TMEM (lane = signal) and write the coefficients.
+struct TcRing {
+    int resident;       // B images resident in shared memory
+    int nbuf;           // ring depth
+    unsigned bufsz;     // bytes per ring buffer
+    unsigned res_off;   // byte offset of the resident B region
+    unsigned total_b;   // bytes of all hi B images (lo images follow)
+};
+
 __global__ void __launch_bounds__(kTcThreads, 1) tc_leaf_kernel(TcArgs a, const TcItem* __restrict__ items,
                                                                int n_items, const unsigned char* __restrict__ aimg,
-                                                               const float* __restrict__ scale) {
+                                                               const float* __restrict__ scale, TcRing ring) {
     extern __shared__ __align__(1024) unsigned char sm[];
-    // buffer s (96 KB): [A hi 16 KB][A lo 16 KB][B hi 32 KB][B lo 32 KB]
     __shared__ unsigned s_tmem;
-    __shared__ __align__(8) unsigned long long bar_load[2];
-    __shared__ __align__(8) unsigned long long bar_mma[2];
+    __shared__ __align__(8) unsigned long long bar_load[4];
+    __shared__ __align__(8) unsigned long long bar_mma[4];
     __shared__ __align__(8) unsigned long long bar_done;
+    __shared__ __align__(8) unsigned long long bar_b;
     __shared__ int s_bad;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (warp == 0) {
@@ -177,11 +188,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_leaf_kernel(TcArgs a, const 
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        mbar_init1(&bar_load[0]);
-        mbar_init1(&bar_load[1]);
-        mbar_init1(&bar_mma[0]);
-        mbar_init1(&bar_mma[1]);
+        for (int i = 0; i < 4; ++i) {
+            mbar_init1(&bar_load[i]);
+            mbar_init1(&bar_mma[i]);
+        }
         mbar_init1(&bar_done);
+        mbar_init1(&bar_b);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_bad = 0;
     }
@@ -193,68 +205,78 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_leaf_kernel(TcArgs a, const 
     const bool fp16 = a.prec == GFT_PREC_FP16X3;
     const unsigned a_bytes = split ? 32768u : 16384u;
     const long long n_tiles = (a.batch + kTcM - 1) / kTcM;
-    // thread 0's ring state (items counted over the whole CTA lifetime)
-    unsigned ph_load[2] = {0, 0}, ph_mma[2] = {0, 0}, ph_done = 0;
-    long long issued = 0, consumed = 0;  // global item counters of this CTA
-    bool pending_mma[2] = {false, false};
-    auto buf = [&](int s) { return sm + s * 98304; };
-    // item q of this CTA's sequence -> (tile, item index)
+    unsigned ph_load[4] = {0, 0, 0, 0}, ph_mma[4] = {0, 0, 0, 0}, ph_done = 0;
+    long long issued = 0, consumed = 0;
+    bool pending_mma[4] = {false, false, false, false};
     const long long my_tiles = n_tiles > blockIdx.x ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     const long long total = my_tiles * n_items;
+    unsigned char* res = sm + ring.res_off;
+    auto bsrc = [&](const TcLeaf& L, const TcItem& it, bool lo) {
+        const size_t img = (size_t)L.npad * kTcK;
+        if (fp16) return reinterpret_cast<const unsigned char*>((lo ? a.flo : a.fhi) + L.b_off + it.kc * img);
+        return reinterpret_cast<const unsigned char*>((lo ? a.blo : a.bhi) + L.b_off + it.kc * img);
+    };
     auto issue = [&](long long q) {
-        const int s = (int)(q & 1);
+        const int s = (int)(q % ring.nbuf);
         const long long tile = blockIdx.x + (q / n_items) * (long long)gridDim.x;
         const TcItem it = items[q % n_items];
         const TcLeaf L = a.leaves[it.leaf];
-        if (pending_mma[s]) {  // MMAs of item q-2 still read this buffer
+        if (pending_mma[s]) {  // MMAs of item q - nbuf still read this buffer
             if (!mbar_wait_bounded(&bar_mma[s], ph_mma[s])) s_bad = 1;
             ph_mma[s] ^= 1u;
             pending_mma[s] = false;
         }
-        const size_t img = (size_t)L.npad * kTcK;
-        const unsigned b_bytes = (unsigned)(img * 2);
-        mbar_expect(&bar_load[s], a_bytes + (split ? 2 * b_bytes : b_bytes));
-        const unsigned char* asrc = aimg + ((size_t)tile * n_items + (size_t)(q % n_items)) * 32768u;
-        bulk_load(buf(s), asrc, a_bytes, &bar_load[s]);
-        const unsigned char* bh = fp16 ? reinterpret_cast<const unsigned char*>(a.fhi + L.b_off + it.kc * img)
-                                       : reinterpret_cast<const unsigned char*>(a.bhi + L.b_off + it.kc * img);
-        bulk_load(buf(s) + 32768, bh, b_bytes, &bar_load[s]);
-        if (split) {
-            const unsigned char* bl = fp16 ? reinterpret_cast<const unsigned char*>(a.flo + L.b_off + it.kc * img)
-                                           : reinterpret_cast<const unsigned char*>(a.blo + L.b_off + it.kc * img);
-            bulk_load(buf(s) + 65536, bl, b_bytes, &bar_load[s]);
+        unsigned char* b = sm + (size_t)s * ring.bufsz;
+        const unsigned b_bytes = (unsigned)L.npad * kTcK * 2u;
+        mbar_expect(&bar_load[s], a_bytes + (ring.resident ? 0u : (split ? 2 * b_bytes : b_bytes)));
+        bulk_load(b, aimg + ((size_t)tile * n_items + (size_t)(q % n_items)) * 32768u, a_bytes, &bar_load[s]);
+        if (!ring.resident) {
+            bulk_load(b + 32768, bsrc(L, it, false), b_bytes, &bar_load[s]);
+            if (split) bulk_load(b + 65536, bsrc(L, it, true), b_bytes, &bar_load[s]);
         }
     };
     if (tid == 0) {
+        if (ring.resident && total > 0) {
+            mbar_expect(&bar_b, split ? 2 * ring.total_b : ring.total_b);
+            for (int i = 0; i < n_items; ++i) {
+                const TcItem it = items[i];
+                const TcLeaf L = a.leaves[it.leaf];
+                const unsigned b_bytes = (unsigned)L.npad * kTcK * 2u;
+                bulk_load(res + it.bres, bsrc(L, it, false), b_bytes, &bar_b);
+                if (split) bulk_load(res + ring.total_b + it.bres, bsrc(L, it, true), b_bytes, &bar_b);
+            }
+            if (!mbar_wait_bounded(&bar_b, 0)) s_bad = 1;
+        }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        for (; issued < total && issued < 2; ++issued) issue(issued);
+        for (; issued < total && issued < ring.nbuf; ++issued) issue(issued);
     }
     for (long long t = 0; t < my_tiles; ++t) {
         const long long tile = blockIdx.x + t * (long long)gridDim.x;
         const long long r0 = tile * kTcM;
         for (int g = 0; g < a.n_groups; ++g) {
             if (tid == 0) {
-                // consume every item of this group
                 while (consumed < total && consumed < (t + 1) * n_items) {
                     const TcItem it = items[consumed % n_items];
                     const TcLeaf L = a.leaves[it.leaf];
                     if (L.group != g) break;
-                    const int s = (int)(consumed & 1);
+                    const int s = (int)(consumed % ring.nbuf);
                     if (!mbar_wait_bounded(&bar_load[s], ph_load[s])) s_bad = 1;
                     ph_load[s] ^= 1u;
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const unsigned id = instr_desc(L.npad, !fp16);
                     const unsigned dt = tmem + (unsigned)L.tcol;
-                    const unsigned base = smem_u32(buf(s));
+                    const unsigned abase = smem_u32(sm + (size_t)s * ring.bufsz);
+                    const unsigned bhi = ring.resident ? smem_u32(res + it.bres) : abase + 32768u;
+                    const unsigned blo = ring.resident ? smem_u32(res + ring.total_b + it.bres) : abase + 65536u;
                     for (int ks = 0; ks < kTcK / 16; ++ks) {
                         if (it.kc * kTcK + ks * 16 >= ((L.m + 15) & ~15)) break;
                         const unsigned koff = ks * 256u;
-                        const unsigned long long ah = smem_desc(base + koff, 128, 1024);
-                        const unsigned long long bh = smem_desc(base + 32768 + koff, 128, 1024);
+                        const unsigned long long ah = smem_desc(abase + koff, 128, 1024);
+                        const unsigned long long bh = smem_desc(bhi + koff, 128, 1024);
                         mma_f16(dt, ah, bh, id, (it.kc | ks) ? 1u : 0u);
                         if (split) {
-                            mma_f16(dt, ah, smem_desc(base + 65536 + koff, 128, 1024), id, 1u);
-                            mma_f16(dt, smem_desc(base + 16384 + koff, 128, 1024), bh, id, 1u);
+                            mma_f16(dt, ah, smem_desc(blo + koff, 128, 1024), id, 1u);
+                            mma_f16(dt, smem_desc(abase + 16384u + koff, 128, 1024), bh, id, 1u);
                         }
                     }
                     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -262,14 +284,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_leaf_kernel(TcArgs a, const 
                                  : "memory");
                     pending_mma[s] = true;
                     ++consumed;
-                    if (issued < total && issued < consumed + 2) issue(issued++);
+                    if (issued < total && issued < consumed + ring.nbuf) issue(issued++);
                 }
-                // all MMAs of the group: arrive on bar_done once they finish
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                                  smem_u32(&bar_done))
                              : "memory");
             }
-            // everyone waits for the group's MMAs (bounded)
             const bool ok = mbar_wait_bounded(&bar_done, ph_done);
             ph_done ^= 1u;
             if (__syncthreads_or(!ok || s_bad)) {
@@ -341,8 +361,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_leaf_kernel(TcArgs a, const 
 teardown:
     __syncthreads();
     if (tid == 0) {
-        // drain: wait (bounded) for MMAs still reading shared memory
-        for (int s = 0; s < 2; ++s)
+        for (int s = 0; s < 4; ++s)
             if (pending_mma[s]) mbar_wait_bounded(&bar_mma[s], ph_mma[s]);
     }
     __syncthreads();
@@ -352,82 +371,81 @@ teardown:
 }
 
 // A images: for tile, item (leaf, K chunk), 128 rows x 64 K as BF16 (or
-// scaled FP16) hi then lo in the core-matrix order; row values are the
-// post-stage signal entries (signed sums of inputs).  A block handles one
-// slice of `rows` signals of one tile: it stages those rows of x (odd row
-// stride) and the term tables in shared memory, then writes the slice's
-// rows of every item image, consecutive threads on consecutive signals.
-__global__ void __launch_bounds__(256) tc_pack_kernel(const float* __restrict__ x, unsigned char* __restrict__ aimg,
-                                                      long long batch, int n, const TcLeaf* __restrict__ leaves,
-                                                      const TcItem* __restrict__ items, int n_items,
-                                                      const int* __restrict__ term_off,
-                                                      const int* __restrict__ term_src,
-                                                      const float* __restrict__ term_sign, int n_terms,
-                                                      const float* __restrict__ scale, int prec, int rows) {
+// scaled FP16) hi then lo in the core-matrix order.  One warp per signal:
+// a coalesced read of the row into a per-warp shared buffer, the Haar units
+// of every stage applied in place (a+b, a-b; the 1/sqrt2 factors are folded
+// into B), then each lane forms 16-byte core-matrix rows (8 consecutive K of
+// one item) by reading the leaf's node slots.  Persistent blocks, tables in
+// shared memory.
+constexpr int kPackWarps = 8;
+__global__ void __launch_bounds__(kPackWarps * 32) tc_pack_kernel(
+    const float* __restrict__ x, unsigned char* __restrict__ aimg, long long batch, int n,
+    const TcLeaf* __restrict__ leaves, const TcItem* __restrict__ items, int n_items,
+    const int* __restrict__ pairs, int n_pairs, const int* __restrict__ stage_off, int n_stages,
+    const int* __restrict__ labels, const float* __restrict__ scale, int prec) {
     extern __shared__ __align__(16) float sx[];
-    const int np = n | 1;
-    int* s_off = reinterpret_cast<int*>(sx + (size_t)rows * np);
-    int* s_src = s_off + n + 1;
-    float* s_sign = reinterpret_cast<float*>(s_src + n_terms);
-    const int tid = threadIdx.x;
-    const int slices = kTcM / rows;
-    const long long tile = blockIdx.x / slices;
-    const int slice = (int)(blockIdx.x - tile * slices);
-    const long long row0 = tile * kTcM + (long long)slice * rows;
-    for (int i = tid; i <= n; i += blockDim.x) s_off[i] = term_off[i];
-    for (int i = tid; i < n_terms; i += blockDim.x) {
-        s_src[i] = term_src[i];
-        s_sign[i] = term_sign[i];
-    }
-    for (int e = tid; e < rows * n; e += blockDim.x) {
-        const int r = e / n, c = e - r * n;
-        const long long g = row0 + r;
-        sx[r * np + c] = g < batch ? x[g * n + c] : 0.f;
-    }
+    int* s_pairs = reinterpret_cast<int*>(sx + (size_t)kPackWarps * n);
+    int* s_soff = s_pairs + 2 * n_pairs;
+    int* s_lab = s_soff + n_stages + 1;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int i = tid; i < 2 * n_pairs; i += blockDim.x) s_pairs[i] = pairs[i];
+    for (int i = tid; i <= n_stages; i += blockDim.x) s_soff[i] = stage_off[i];
+    for (int i = tid; i < n; i += blockDim.x) s_lab[i] = labels[i];
     __syncthreads();
     const bool fp16 = prec == GFT_PREC_FP16X3, split = prec != GFT_PREC_BF16;
-    const int work = n_items * rows * 8;
-    for (int w = tid; w < work; w += blockDim.x) {
-        const int item = w / (rows * 8);
-        const int rem = w - item * rows * 8;
-        const int kg = rem / rows, r = rem - kg * rows;
-        const TcItem it = items[item];
-        const TcLeaf L = leaves[it.leaf];
-        const long long grow = row0 + r;
-        const float inv = (fp16 && grow < batch) ? 1.f / scale[grow] : 1.f;
-        const float* xr = sx + r * np;
-        float v[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int c = it.kc * kTcK + kg * 8 + q;
-            float acc = 0.f;
-            if (c < L.m) {
-                const int j = L.off + c;
-                for (int u = s_off[j]; u < s_off[j + 1]; ++u) acc += s_sign[u] * xr[s_src[u]];
+    const long long n_tiles = (batch + kTcM - 1) / kTcM;
+    const long long rows_total = n_tiles * kTcM;   // padded rows are packed as zeros
+    float* xr = sx + warp * n;
+    const int segs = n_items * 8;
+    for (long long row = blockIdx.x * (long long)kPackWarps + warp; row < rows_total;
+         row += (long long)gridDim.x * kPackWarps) {
+        const bool live = row < batch;
+        for (int c = lane; c < n; c += 32) xr[c] = live ? __ldcs(x + row * n + c) : 0.f;
+        __syncwarp();
+        for (int s = 0; s < n_stages; ++s) {
+            for (int q = s_soff[s] + lane; q < s_soff[s + 1]; q += 32) {
+                const int i = s_pairs[2 * q], j = s_pairs[2 * q + 1];
+                const float u = xr[i], w = xr[j];
+                xr[i] = u + w;
+                xr[j] = u - w;
             }
-            v[q] = acc * inv;
+            __syncwarp();
         }
-        unsigned hi[4], lo[4];
+        const float inv = (fp16 && live) ? 1.f / scale[row] : 1.f;
+        const long long tile = row / kTcM;
+        const int r = (int)(row - tile * kTcM);
+        for (int sg = lane; sg < segs; sg += 32) {
+            const int item = sg >> 3, kg = sg & 7;
+            const TcItem it = items[item];
+            const TcLeaf L = leaves[it.leaf];
+            float v[8];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            if (fp16) {
-                const __half h0 = __float2half_rn(v[2 * q]), h1 = __float2half_rn(v[2 * q + 1]);
-                const __half l0 = __float2half_rn(v[2 * q] - __half2float(h0));
-                const __half l1 = __float2half_rn(v[2 * q + 1] - __half2float(h1));
-                hi[q] = (unsigned)__half_as_ushort(h0) | ((unsigned)__half_as_ushort(h1) << 16);
-                lo[q] = (unsigned)__half_as_ushort(l0) | ((unsigned)__half_as_ushort(l1) << 16);
-            } else {
-                const __nv_bfloat16 h0 = __float2bfloat16_rn(v[2 * q]), h1 = __float2bfloat16_rn(v[2 * q + 1]);
-                const __nv_bfloat16 l0 = __float2bfloat16_rn(v[2 * q] - __bfloat162float(h0));
-                const __nv_bfloat16 l1 = __float2bfloat16_rn(v[2 * q + 1] - __bfloat162float(h1));
-                hi[q] = (unsigned)__bfloat16_as_ushort(h0) | ((unsigned)__bfloat16_as_ushort(h1) << 16);
-                lo[q] = (unsigned)__bfloat16_as_ushort(l0) | ((unsigned)__bfloat16_as_ushort(l1) << 16);
+            for (int q = 0; q < 8; ++q) {
+                const int c = it.kc * kTcK + kg * 8 + q;
+                v[q] = c < L.m ? xr[s_lab[L.off + c]] * inv : 0.f;
             }
+            unsigned hi[4], lo[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (fp16) {
+                    const __half h0 = __float2half_rn(v[2 * q]), h1 = __float2half_rn(v[2 * q + 1]);
+                    const __half l0 = __float2half_rn(v[2 * q] - __half2float(h0));
+                    const __half l1 = __float2half_rn(v[2 * q + 1] - __half2float(h1));
+                    hi[q] = (unsigned)__half_as_ushort(h0) | ((unsigned)__half_as_ushort(h1) << 16);
+                    lo[q] = (unsigned)__half_as_ushort(l0) | ((unsigned)__half_as_ushort(l1) << 16);
+                } else {
+                    const __nv_bfloat16 h0 = __float2bfloat16_rn(v[2 * q]), h1 = __float2bfloat16_rn(v[2 * q + 1]);
+                    const __nv_bfloat16 l0 = __float2bfloat16_rn(v[2 * q] - __bfloat162float(h0));
+                    const __nv_bfloat16 l1 = __float2bfloat16_rn(v[2 * q + 1] - __bfloat162float(h1));
+                    hi[q] = (unsigned)__bfloat16_as_ushort(h0) | ((unsigned)__bfloat16_as_ushort(h1) << 16);
+                    lo[q] = (unsigned)__bfloat16_as_ushort(l0) | ((unsigned)__bfloat16_as_ushort(l1) << 16);
+                }
+            }
+            unsigned char* dst = aimg + ((size_t)tile * n_items + item) * 32768u + core_off(r, kg);
+            __stcg(reinterpret_cast<uint4*>(dst), make_uint4(hi[0], hi[1], hi[2], hi[3]));
+            if (split) __stcg(reinterpret_cast<uint4*>(dst + 16384), make_uint4(lo[0], lo[1], lo[2], lo[3]));
         }
-        unsigned char* dst =
-            aimg + ((size_t)tile * n_items + item) * 32768u + core_off(slice * rows + r, kg);
-        __stcg(reinterpret_cast<uint4*>(dst), make_uint4(hi[0], hi[1], hi[2], hi[3]));
-        if (split) __stcg(reinterpret_cast<uint4*>(dst + 16384), make_uint4(lo[0], lo[1], lo[2], lo[3]));
+        __syncwarp();
     }
 }
 
@@ -459,6 +477,7 @@ __global__ void tc_permute_kernel(const float* __restrict__ z, float* __restrict
 
 struct TcPlan {
     int n = 0, n_leaves = 0, n_groups = 0, direct = 0, n_items = 0, n_stages = 0, n_terms = 0;
+    unsigned total_b = 0;   // bytes of all hi B images
     TcLeaf* d_leaves = nullptr;
     TcItem* d_items = nullptr;
     int* d_colmap = nullptr;
@@ -601,8 +620,13 @@ void tc_build(gft_plan_s& p) {
                     }
         }
         std::vector<TcItem> items;
+        unsigned bres = 0;
         for (size_t k = 0; k < L.size(); ++k)
-            for (int kc = 0; kc < L[k].kchunks; ++kc) items.push_back({(int)k, kc});
+            for (int kc = 0; kc < L[k].kchunks; ++kc) {
+                items.push_back({(int)k, kc, (int)bres});
+                bres += (unsigned)L[k].npad * kTcK * 2u;
+            }
+        T->total_b = bres;
         T->n_items = (int)items.size();
         T->n_stages = p.n_stages;
         T->d_items = upload(items);
@@ -656,18 +680,22 @@ void launch_tc(gft_plan_s& p, const float* x, float* y, int64_t batch, bool inve
         GFT_CUDA(cudaGetLastError());
     }
     {
-        // signal rows per pack block: a power of two with the rows' x in <= 96 KB
-        int rows = kTcM;
-        while (rows > 1 && (size_t)rows * (n | 1) * sizeof(float) > 98304) rows >>= 1;
-        const size_t smem = (size_t)rows * (n | 1) * sizeof(float) + sizeof(int) * (n + 1) +
-                            (sizeof(int) + sizeof(float)) * (size_t)T->n_terms;
+        const DevProgram& d = p.dev;
+        const size_t smem = sizeof(float) * (size_t)kPackWarps * n +
+                            sizeof(int) * (size_t)(2 * d.n_pairs + d.n_stages + 1 + n);
         if (smem > 232448) fail(GFT_ERR_UNSUPPORTED, "tensor-core pack stage does not fit in shared memory");
         GFT_CUDA(cudaFuncSetAttribute(tc_pack_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        const long long blocks = n_tiles * (kTcM / rows);
-        tc_pack_kernel<<<(unsigned)blocks, 256, smem, st>>>(x, T->d_aimg, batch, n, T->d_leaves, T->d_items,
-                                                            T->n_items, T->d_term_off, T->d_term_src,
-                                                            T->d_term_sign, T->n_terms, T->d_scale,
-                                                            (int)precision, rows);
+        int per_sm = 0;
+        GFT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc_pack_kernel, kPackWarps * 32, smem));
+        const long long need = (n_tiles * kTcM + kPackWarps - 1) / kPackWarps;
+        const long long blocks = std::min<long long>(need, (long long)std::max(1, per_sm) * sms);
+        // program tables: [pairs 2P][stage offsets S+1][labels n] at the start of the plan's ints
+        const int* pairs = d.d_ints;
+        const int* soff = d.d_ints + 2 * d.n_pairs;
+        const int* labels = d.d_ints + 2 * d.n_pairs + d.n_stages + 1;
+        tc_pack_kernel<<<(unsigned)blocks, kPackWarps * 32, smem, st>>>(
+            x, T->d_aimg, batch, n, T->d_leaves, T->d_items, T->n_items, pairs, d.n_pairs, soff, d.n_stages,
+            labels, T->d_scale, (int)precision);
         GFT_CUDA(cudaGetLastError());
     }
     TcArgs a{};
@@ -685,10 +713,26 @@ void launch_tc(gft_plan_s& p, const float* x, float* y, int64_t batch, bool inve
     a.prec = (int)precision;
     a.direct = T->direct;
     a.err = p.dev.d_err;
-    const size_t smem = 2 * 98304;  // two ring buffers of 96 KB
+    TcRing ring{};
+    const bool split = precision != GFT_PREC_BF16;
+    const unsigned res_bytes = T->total_b * (split ? 2u : 1u);
+    if (res_bytes <= 98304u) {
+        ring.resident = 1;
+        ring.nbuf = 4;
+        ring.bufsz = 32768u;
+        ring.res_off = 4u * 32768u;
+        ring.total_b = T->total_b;
+    } else {
+        ring.resident = 0;
+        ring.nbuf = 2;
+        ring.bufsz = 98304u;
+        ring.res_off = 0;
+        ring.total_b = T->total_b;
+    }
+    const size_t smem = ring.resident ? (size_t)ring.res_off + res_bytes : 2u * 98304u;
     GFT_CUDA(cudaFuncSetAttribute(tc_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int grid = (int)std::min<long long>(n_tiles, sms);
-    tc_leaf_kernel<<<grid, kTcThreads, smem, st>>>(a, T->d_items, T->n_items, T->d_aimg, T->d_scale);
+    tc_leaf_kernel<<<grid, kTcThreads, smem, st>>>(a, T->d_items, T->n_items, T->d_aimg, T->d_scale, ring);
     GFT_CUDA(cudaGetLastError());
     if (!T->direct) {
         tc_permute_kernel<<<sms * 8, 256, 0, st>>>(T->d_z, y, batch, n, T->d_srcmap);
