@@ -168,7 +168,10 @@ struct TcRing {
     unsigned bufsz;     // bytes per ring buffer
     unsigned res_off;   // byte offset of the resident B region
     unsigned total_b;   // bytes of all hi B images (lo images follow)
+    unsigned meta_off;  // byte offset of [items][leaves][colmap][epilogue staging]
 };
+
+constexpr int kStageLd = 33;   // epilogue staging row stride (floats): conflict-free
 
 __global__ void __launch_bounds__(kTcThreads, 1) tc_leaf_kernel(TcArgs a, const TcItem* __restrict__ items,
                                                                int n_items, const unsigned char* __restrict__ aimg,
@@ -181,6 +184,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_leaf_kernel(TcArgs a, const 
     __shared__ __align__(8) unsigned long long bar_b;
     __shared__ int s_bad;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // per-CTA copies of the item list, leaf table and coefficient map
+    // layout (every part 16-byte aligned): items, leaves, colmap, staging
+    unsigned char* meta = sm + ring.meta_off;
+    TcItem* s_items = reinterpret_cast<TcItem*>(meta);
+    const size_t items_bytes = (sizeof(TcItem) * n_items + 15) & ~size_t(15);
+    TcLeaf* s_leaves = reinterpret_cast<TcLeaf*>(meta + items_bytes);
+    const size_t leaves_bytes = (sizeof(TcLeaf) * a.n_leaves + 15) & ~size_t(15);
+    int* s_colmap = reinterpret_cast<int*>(meta + items_bytes + leaves_bytes);
+    float* s_stage = reinterpret_cast<float*>(s_colmap + ((a.n + 3) & ~3));
+    for (int i = tid; i < n_items; i += blockDim.x) s_items[i] = items[i];
+    for (int i = tid; i < a.n_leaves; i += blockDim.x) s_leaves[i] = a.leaves[i];
+    if (a.direct)
+        for (int i = tid; i < a.n; i += blockDim.x) s_colmap[i] = a.colmap[i];
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
                      "r"(kTcCols)
@@ -219,8 +235,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_leaf_kernel(TcArgs a, const 
     auto issue = [&](long long q) {
         const int s = (int)(q % ring.nbuf);
         const long long tile = blockIdx.x + (q / n_items) * (long long)gridDim.x;
-        const TcItem it = items[q % n_items];
-        const TcLeaf L = a.leaves[it.leaf];
+        const TcItem it = s_items[q % n_items];
+        const TcLeaf L = s_leaves[it.leaf];
         if (pending_mma[s]) {  // MMAs of item q - nbuf still read this buffer
             if (!mbar_wait_bounded(&bar_mma[s], ph_mma[s])) s_bad = 1;
             ph_mma[s] ^= 1u;
@@ -239,8 +255,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_leaf_kernel(TcArgs a, const 
         if (ring.resident && total > 0) {
             mbar_expect(&bar_b, split ? 2 * ring.total_b : ring.total_b);
             for (int i = 0; i < n_items; ++i) {
-                const TcItem it = items[i];
-                const TcLeaf L = a.leaves[it.leaf];
+                const TcItem it = s_items[i];
+                const TcLeaf L = s_leaves[it.leaf];
                 const unsigned b_bytes = (unsigned)L.npad * kTcK * 2u;
                 bulk_load(res + it.bres, bsrc(L, it, false), b_bytes, &bar_b);
                 if (split) bulk_load(res + ring.total_b + it.bres, bsrc(L, it, true), b_bytes, &bar_b);
@@ -256,8 +272,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_leaf_kernel(TcArgs a, const 
         for (int g = 0; g < a.n_groups; ++g) {
             if (tid == 0) {
                 while (consumed < total && consumed < (t + 1) * n_items) {
-                    const TcItem it = items[consumed % n_items];
-                    const TcLeaf L = a.leaves[it.leaf];
+                    const TcItem it = s_items[consumed % n_items];
+                    const TcLeaf L = s_leaves[it.leaf];
                     if (L.group != g) break;
                     const int s = (int)(consumed % ring.nbuf);
                     if (!mbar_wait_bounded(&bar_load[s], ph_load[s])) s_bad = 1;
@@ -302,35 +318,35 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_leaf_kernel(TcArgs a, const 
                 const unsigned lane_base = (unsigned)(warp * 32) << 16;
                 const float sc = fp16 ? (row < a.batch ? scale[row] : 1.f) : 1.f;
                 if (a.direct) {
+                    float* stg = s_stage + warp * 32 * kStageLd;
                     for (int j0 = 0; j0 < a.n; j0 += 32) {
+                        int cm[32];
+#pragma unroll
+                        for (int q = 0; q < 32; ++q) cm[q] = s_colmap[min(j0 + q, a.n - 1)];
                         float r[32];
 #pragma unroll
                         for (int q = 0; q < 32; ++q) {
-                            const int j = min(j0 + q, a.n - 1);
                             unsigned u;
                             asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];"
                                          : "=r"(u)
-                                         : "r"(tmem + lane_base + (unsigned)a.colmap[j])
-                                         : "memory");
+                                         : "r"(tmem + lane_base + (unsigned)cm[q]));
                             r[q] = __uint_as_float(u);
                         }
                         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                        if (row < a.batch) {
-                            float* dst = a.y + row * a.n + j0;
-                            const int cnt = min(32, a.n - j0);
-                            if (cnt == 32 && (a.n & 3) == 0) {
+                        // transpose through shared memory: lane = row -> lane = column
 #pragma unroll
-                                for (int q = 0; q < 32; q += 4)
-                                    __stcs(reinterpret_cast<float4*>(dst + q),
-                                           make_float4(r[q] * sc, r[q + 1] * sc, r[q + 2] * sc, r[q + 3] * sc));
-                            } else {
-                                for (int q = 0; q < cnt; ++q) __stcs(dst + q, r[q] * sc);
-                            }
+                        for (int q = 0; q < 32; ++q) stg[lane * kStageLd + q] = r[q] * sc;
+                        __syncwarp();
+                        const int cnt = min(32, a.n - j0);
+                        for (int rr = 0; rr < 32; ++rr) {
+                            const long long grow = r0 + warp * 32 + rr;
+                            if (grow < a.batch && lane < cnt) __stcs(a.y + grow * a.n + j0 + lane, stg[rr * kStageLd + lane]);
                         }
+                        __syncwarp();
                     }
                 } else {
                     for (int k = 0; k < a.n_leaves; ++k) {
-                        const TcLeaf L = a.leaves[k];
+                        const TcLeaf L = s_leaves[k];
                         if (L.group != g) continue;
                         for (int c0 = 0; c0 < L.m; c0 += 32) {
                             float r[32];
@@ -716,20 +732,26 @@ void launch_tc(gft_plan_s& p, const float* x, float* y, int64_t batch, bool inve
     TcRing ring{};
     const bool split = precision != GFT_PREC_BF16;
     const unsigned res_bytes = T->total_b * (split ? 2u : 1u);
-    if (res_bytes <= 98304u) {
-        ring.resident = 1;
+    const size_t meta = ((sizeof(TcItem) * T->n_items + 15) & ~size_t(15)) +
+                        ((sizeof(TcLeaf) * T->n_leaves + 15) & ~size_t(15)) + sizeof(int) * ((n + 3) & ~3) +
+                        sizeof(float) * (size_t)kTcM * kStageLd;
+    const size_t limit = 232448 - 2048;   // leave room for static shared memory
+    ring.total_b = T->total_b;
+    if (4u * 32768u + (size_t)res_bytes + meta <= limit) {
+        ring.resident = 1;   // all B images once per CTA, four A buffers
         ring.nbuf = 4;
         ring.bufsz = 32768u;
         ring.res_off = 4u * 32768u;
-        ring.total_b = T->total_b;
     } else {
-        ring.resident = 0;
+        ring.resident = 0;   // two buffers holding A and the item's B images
         ring.nbuf = 2;
         ring.bufsz = 98304u;
         ring.res_off = 0;
-        ring.total_b = T->total_b;
     }
-    const size_t smem = ring.resident ? (size_t)ring.res_off + res_bytes : 2u * 98304u;
+    const size_t ring_bytes = ring.resident ? (size_t)ring.res_off + res_bytes : 2u * 98304u;
+    ring.meta_off = (unsigned)((ring_bytes + 15) & ~size_t(15));
+    const size_t smem = ring.meta_off + meta;
+    if (smem > limit) fail(GFT_ERR_UNSUPPORTED, "tensor-core kernel does not fit in shared memory");
     GFT_CUDA(cudaFuncSetAttribute(tc_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int grid = (int)std::min<long long>(n_tiles, sms);
     tc_leaf_kernel<<<grid, kTcThreads, smem, st>>>(a, T->d_items, T->n_items, T->d_aimg, T->d_scale, ring);
