@@ -197,10 +197,13 @@ gft_status gft_plan_inverse_f64(gft_plan_t plan, const double* y, double* x, int
 
 /*
  * Forward transform of a HOST batch: x_host, y_host are host [batch, n] FP32
- * (pinned memory gives full copy bandwidth).  The plan streams the batch
- * through its own device staging buffers in chunks, overlapping the
- * host-to-device copy, the transform and the device-to-host copy, and
- * returns when y_host is complete.
+ * (pinned memory gives full copy bandwidth).  When both buffers are pinned
+ * and mapped into the device address space (cudaHostAlloc / cudaHostRegister,
+ * e.g. torch's pin_memory) and FP32 is requested, the transform kernel reads
+ * and writes them directly over the host link with no copies; otherwise the
+ * plan streams the batch through its own device staging buffers in chunks,
+ * overlapping the host-to-device copy, the transform and the device-to-host
+ * copy.  Returns when y_host is complete.
  */
 gft_status gft_plan_forward_host(gft_plan_t plan, const float* x_host, float* y_host,
                                  int64_t batch, uint32_t precision);

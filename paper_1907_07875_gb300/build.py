@@ -73,7 +73,7 @@ def build(force: bool = False, extra_flags=None) -> str:
             os.path.getmtime(o) > os.path.getmtime(LIB_PATH) for o in objs):
         tmp = LIB_PATH + ".tmp"
         cuda_lib = os.path.join(os.path.dirname(os.path.dirname(nvcc())), "lib64")
-        cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-L", cuda_lib, "-lnvrtc",
+        cmd = [nvcc(), *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs, "-L", cuda_lib, "-lnvrtc",
                "-Xlinker", "-rpath," + cuda_lib]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:

@@ -318,44 +318,78 @@ gft_status gft_plan_forward_host(gft_plan_t p, const float* x_host, float* y_hos
         if (!x_host || !y_host) fail(GFT_ERR_INVALID_ARG, "NULL host pointer");
         check_precision(p, precision);
         const int n = p->n;
-        // chunks of about 4 Mi coefficients, two in flight on two streams
-        int64_t chunk = std::max<int64_t>(1, (int64_t)(4 << 20) / n);
-        chunk = (chunk + 3) & ~int64_t(3);
+        constexpr int NB = gft_plan_s::kHostStreams;
+        for (int b = 0; b < NB; ++b)
+            if (!p->host_streams[b]) GFT_CUDA(cudaStreamCreateWithFlags(&p->host_streams[b], cudaStreamNonBlocking));
+        // Pinned, device-mapped host buffers: the transform kernel reads and
+        // writes host memory directly (no copy engines, no staging).
+        if (precision == GFT_PREC_FP32) {
+            cudaPointerAttributes ax{}, ay{};
+            const bool qx = cudaPointerGetAttributes(&ax, x_host) == cudaSuccess;
+            const bool qy = cudaPointerGetAttributes(&ay, y_host) == cudaSuccess;
+            cudaGetLastError();
+            if (qx && qy && ax.type == cudaMemoryTypeHost && ay.type == cudaMemoryTypeHost && ax.devicePointer &&
+                ay.devicePointer && !((reinterpret_cast<uintptr_t>(ax.devicePointer) |
+                                       reinterpret_cast<uintptr_t>(ay.devicePointer)) & 15u)) {
+                const float* xd = static_cast<const float*>(ax.devicePointer);
+                float* yd = static_cast<float*>(ay.devicePointer);
+                cudaStream_t st = p->host_streams[1];
+                if (!jit_launch_plain(*p, xd, yd, batch, st)) launch_apply_f32(apply_args(*p, false), xd, yd, batch, false, st);
+                GFT_CUDA(cudaStreamSynchronize(st));
+                p->last_stream = nullptr;
+                return;
+            }
+        }
+        // Otherwise chunks (a quarter of the batch, 16..64 MB) flow through a
+        // ring of NB device buffer pairs.  Uploads, transforms and downloads
+        // run on three streams chained by events, so the host-to-device copy
+        // of a chunk overlaps the device-to-host copy of an earlier one.
+        const int64_t row_bytes = (int64_t)n * sizeof(float);
+        int64_t chunk = std::min<int64_t>(std::max<int64_t>((batch + 3) / 4, (16ll << 20) / row_bytes),
+                                          (64ll << 20) / row_bytes);
+        chunk = std::max<int64_t>(4, (chunk + 3) & ~int64_t(3));
         const size_t elems = (size_t)chunk * n;
         if (p->stage_elems < elems) {
-            for (int b = 0; b < 2; ++b) {
+            for (int b = 0; b < NB; ++b) {
                 if (p->d_stage[b]) cudaFree(p->d_stage[b]);
                 if (p->d_stage_out[b]) cudaFree(p->d_stage_out[b]);
                 p->d_stage[b] = p->d_stage_out[b] = nullptr;
             }
             p->stage_elems = 0;
-            for (int b = 0; b < 2; ++b) {
+            for (int b = 0; b < NB; ++b) {
                 GFT_CUDA(cudaMalloc(&p->d_stage[b], elems * sizeof(float)));
                 GFT_CUDA(cudaMalloc(&p->d_stage_out[b], elems * sizeof(float)));
             }
             p->stage_elems = elems;
         }
-        for (int b = 0; b < 2; ++b)
-            if (!p->host_streams[b]) GFT_CUDA(cudaStreamCreateWithFlags(&p->host_streams[b], cudaStreamNonBlocking));
+        for (int b = 0; b < NB; ++b) {
+            for (cudaEvent_t* e : {&p->ev_up[b], &p->ev_k[b], &p->ev_down[b]})
+                if (!*e) GFT_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+        }
+        cudaStream_t s_up = p->host_streams[0], s_k = p->host_streams[1], s_down = p->host_streams[2];
         int64_t done = 0;
-        int which = 0;
-        while (done < batch) {
+        for (int64_t i = 0; done < batch; ++i) {
+            const int b = (int)(i % NB);
             const int64_t rows = std::min(chunk, batch - done);
             const size_t bytes = (size_t)rows * n * sizeof(float);
-            cudaStream_t st = p->host_streams[which];
-            GFT_CUDA(cudaMemcpyAsync(p->d_stage[which], x_host + (size_t)done * n, bytes, cudaMemcpyHostToDevice, st));
+            if (i >= NB) GFT_CUDA(cudaStreamWaitEvent(s_up, p->ev_k[b], 0));      // input buffer free
+            GFT_CUDA(cudaMemcpyAsync(p->d_stage[b], x_host + (size_t)done * n, bytes, cudaMemcpyHostToDevice, s_up));
+            GFT_CUDA(cudaEventRecord(p->ev_up[b], s_up));
+            GFT_CUDA(cudaStreamWaitEvent(s_k, p->ev_up[b], 0));
+            if (i >= NB) GFT_CUDA(cudaStreamWaitEvent(s_k, p->ev_down[b], 0));   // output buffer free
             if (precision == GFT_PREC_FP32) {
-                if (!jit_launch(*p, false, p->d_stage[which], p->d_stage_out[which], rows, false, st))
-                    launch_apply_f32(apply_args(*p, false), p->d_stage[which], p->d_stage_out[which], rows, false, st);
+                if (!jit_launch(*p, false, p->d_stage[b], p->d_stage_out[b], rows, false, s_k))
+                    launch_apply_f32(apply_args(*p, false), p->d_stage[b], p->d_stage_out[b], rows, false, s_k);
+            } else {
+                launch_tc(*p, p->d_stage[b], p->d_stage_out[b], rows, false, s_k, precision);
             }
-            else
-                launch_tc(*p, p->d_stage[which], p->d_stage_out[which], rows, false, st, precision);
-            GFT_CUDA(cudaMemcpyAsync(y_host + (size_t)done * n, p->d_stage_out[which], bytes, cudaMemcpyDeviceToHost, st));
+            GFT_CUDA(cudaEventRecord(p->ev_k[b], s_k));
+            GFT_CUDA(cudaStreamWaitEvent(s_down, p->ev_k[b], 0));
+            GFT_CUDA(cudaMemcpyAsync(y_host + (size_t)done * n, p->d_stage_out[b], bytes, cudaMemcpyDeviceToHost, s_down));
+            GFT_CUDA(cudaEventRecord(p->ev_down[b], s_down));
             done += rows;
-            which ^= 1;
         }
-        GFT_CUDA(cudaStreamSynchronize(p->host_streams[0]));
-        GFT_CUDA(cudaStreamSynchronize(p->host_streams[1]));
+        for (int b = 0; b < NB; ++b) GFT_CUDA(cudaStreamSynchronize(p->host_streams[b]));
         p->last_stream = nullptr;
     });
 }

@@ -84,11 +84,13 @@ struct gft_plan_s {
     gft::DevProgram dev;
     cudaStream_t last_stream = nullptr;
     int device = 0;
-    // host-batch staging (gft_plan_forward_host)
-    float* d_stage[2] = {nullptr, nullptr};
-    float* d_stage_out[2] = {nullptr, nullptr};
+    // host-batch staging (gft_plan_forward_host): one in/out buffer pair per stream
+    static constexpr int kHostStreams = 3;
+    float* d_stage[kHostStreams] = {};
+    float* d_stage_out[kHostStreams] = {};
     size_t stage_elems = 0;
-    cudaStream_t host_streams[2] = {nullptr, nullptr};
+    cudaStream_t host_streams[kHostStreams] = {};   // upload, compute, download
+    cudaEvent_t ev_up[kHostStreams] = {}, ev_k[kHostStreams] = {}, ev_down[kHostStreams] = {};
     // tensor-core data (built lazily)
     void* tc = nullptr;
     // plan-specialised kernels (jit.cpp)
@@ -130,6 +132,7 @@ void jit_build(gft_plan_s& p);
 void jit_free(gft_plan_s& p);
 bool jit_launch(gft_plan_s& p, bool f64, const void* x, void* y, int64_t batch, bool inverse, cudaStream_t st);
 void jit_info(const gft_plan_s& p, int* jit, int* tile, int* threads);
+bool jit_launch_plain(gft_plan_s& p, const float* x, float* y, int64_t batch, cudaStream_t st);
 std::string jit_source(const gft_plan_s& p, bool f64);
 
 // tc.cu: leaf products on tcgen05 tensor cores (split precision)

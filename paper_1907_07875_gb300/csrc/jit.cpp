@@ -482,6 +482,7 @@ struct JitDir {
 struct JitPlan {
     cudaLibrary_t lib32 = nullptr, lib64 = nullptr;
     JitDir d32[2], d64[2];
+    JitDir d32_plain[2];   // fastest shape without TMA bulk tiles (zero-copy host buffers)
     int np32 = 0, np64 = 0;
 };
 
@@ -564,6 +565,7 @@ static void build_precision(gft_plan_s& p, JitPlan& J, bool f64) {
                 GFT_CUDA(cudaEventElapsedTime(&ms, e0, e1));
                 d.us = ms * 1000.f / 3.f;
                 if (!best.k || d.us < best.us) best = d;
+                if (!f64 && !c.bulk && (!J.d32_plain[inv].k || d.us < J.d32_plain[inv].us)) J.d32_plain[inv] = d;
             }
             if (!best.k) fail(GFT_ERR_UNSUPPORTED, "no plan-specialised launch shape fits");
             (f64 ? J.d64 : J.d32)[inv] = best;
@@ -611,6 +613,15 @@ bool jit_launch(gft_plan_s& p, bool f64, const void* x, void* y, int64_t batch, 
     if (!p.jit || std::getenv("GFT_FORCE_INTERPRETER")) return false;
     JitPlan* J = static_cast<JitPlan*>(p.jit);
     const JitDir& d = (f64 ? J->d64 : J->d32)[inverse ? 1 : 0];
+    if (!d.k) return false;
+    if (batch > 0) launch_dir(d, x, y, batch, p.dev.d_err, st);
+    return true;
+}
+
+bool jit_launch_plain(gft_plan_s& p, const float* x, float* y, int64_t batch, cudaStream_t st) {
+    if (!p.jit || std::getenv("GFT_FORCE_INTERPRETER")) return false;
+    JitPlan* J = static_cast<JitPlan*>(p.jit);
+    const JitDir& d = J->d32_plain[0];
     if (!d.k) return false;
     if (batch > 0) launch_dir(d, x, y, batch, p.dev.d_err, st);
     return true;

@@ -235,10 +235,15 @@ void free_device(gft_plan_s& p) {
     if (p.dev.d_mats64) cudaFree(p.dev.d_mats64);
     if (p.dev.d_err) cudaFree(p.dev.d_err);
     p.dev = DevProgram{};
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < gft_plan_s::kHostStreams; ++b) {
         if (p.d_stage[b]) cudaFree(p.d_stage[b]);
         if (p.d_stage_out[b]) cudaFree(p.d_stage_out[b]);
         if (p.host_streams[b]) cudaStreamDestroy(p.host_streams[b]);
+        for (cudaEvent_t* e : {&p.ev_up[b], &p.ev_k[b], &p.ev_down[b]})
+            if (*e) {
+                cudaEventDestroy(*e);
+                *e = nullptr;
+            }
         p.d_stage[b] = p.d_stage_out[b] = nullptr;
         p.host_streams[b] = nullptr;
     }

@@ -232,9 +232,14 @@ def test_forward_host_matches_device(env):
     g = W.skeleton25()
     plan = make_plan(gft, g, True)
     x = W.signals(300001, 25, 9)
-    y_host = plan.forward_host(torch.from_numpy(x).pin_memory()).numpy()
     y_dev = plan.forward(torch.from_numpy(x).cuda()).cpu().numpy()
-    assert np.array_equal(y_host, y_dev)
+    # pinned, device-mapped buffers: the kernel reads and writes host memory
+    y_pinned = plan.forward_host(torch.from_numpy(x).pin_memory(), out=torch.empty(300001, 25).pin_memory()).numpy()
+    assert np.array_equal(y_pinned, y_dev)
+    # pageable buffers: chunked copies through device staging
+    y_pageable = plan.forward_host(torch.from_numpy(x.copy())).numpy()
+    assert np.array_equal(y_pageable, y_dev)
+    assert plan.device_error() == 0
 
 
 def test_plan_jacobi_matches_oracle_leaves(env):
