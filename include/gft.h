@@ -63,6 +63,10 @@ typedef enum {
 #define GFT_ORDER_BLOCK      0x2u  /* coefficients in leaf order instead of ascending eigenvalue */
 #define GFT_ANALYZE_ONLY     0x4u  /* host-side decomposition only: no device, no bases */
 #define GFT_NO_JIT           0x8u  /* never build plan-specialised kernels (interpreter only) */
+#define GFT_KERNEL_TABLE     0x10u /* CUDA-core transforms: the table-driven kernel wherever
+                                      it fits (leaves of at most 64 nodes) */
+#define GFT_KERNEL_WIDE      0x20u /* CUDA-core transforms: the wide-leaf kernel whenever the
+                                      plan has a leaf of more than 32 nodes */
 
 /* transform precision (plan forward / inverse) */
 #define GFT_PREC_FP32    0u  /* CUDA-core FP32 FMA, FP32 accumulation */
@@ -105,7 +109,8 @@ gft_status gft_laplacian_from_weights(int32_t n, const double* W, const double* 
  *            block, the pair member that comes first in the block's order
  *            goes to X, its partner to Y; G+ lists X then the fixed points Z,
  *            G- lists the partners of X in X's order.
- *  flags     GFT_SPLIT_COMPONENTS | GFT_ORDER_BLOCK | GFT_ANALYZE_ONLY.
+ *  flags     GFT_SPLIT_COMPONENTS | GFT_ORDER_BLOCK | GFT_ANALYZE_ONLY | GFT_NO_JIT |
+ *            GFT_KERNEL_TABLE | GFT_KERNEL_WIDE (the last two are exclusive).
  *  out       receives the plan (owned by the caller; free with
  *            gft_plan_destroy).  Unchanged on error.
  * Unless GFT_ANALYZE_ONLY is set, the leaf Laplacians are eigendecomposed on
@@ -115,7 +120,11 @@ gft_status gft_laplacian_from_weights(int32_t n, const double* W, const double* 
  * call also generates a kernel specialised to this plan (indices and
  * folded leaf matrices as constants), compiles it with NVRTC for sm_103a,
  * and times several launch shapes on a scratch batch to keep the fastest;
- * transforms then use it, otherwise the table-driven kernel.  Eigenvector signs: the first
+ * transforms then use it.  Otherwise, when some leaf has more than 32 nodes
+ * (up to 512), a wide-leaf kernel computes each tile's leaf products as a
+ * register-blocked GEMM of the whole CTA; for leaves of at most 64 nodes the
+ * call times it against the table-driven kernel and keeps the faster
+ * (GFT_KERNEL_TABLE / GFT_KERNEL_WIDE force one).  Eigenvector signs: the first
  * entry of largest magnitude (within 1e-9 relative) of every full-length
  * basis vector is made positive.  Output order: ascending eigenvalue;
  * eigenvalues within 1e-9*max(1,|lambda|max) of a neighbour form a cluster
@@ -145,7 +154,7 @@ typedef struct {
                                cp.async tiles; 2: plan-specialised with TMA bulk tiles */
     int32_t tile_signals;   /* FP32 forward launch shape chosen by the autotuner: */
     int32_t threads;        /*   signals per tile and threads per block (0 if none) */
-    int32_t reserved;
+    int32_t wide;           /* 1 if FP32 CUDA-core transforms use the wide-leaf kernel */
 } gft_plan_info_t;
 
 gft_status gft_plan_get_info(gft_plan_t plan, gft_plan_info_t* info);

@@ -24,6 +24,8 @@ SPLIT_COMPONENTS = 0x1
 ORDER_BLOCK = 0x2
 ANALYZE_ONLY = 0x4
 NO_JIT = 0x8
+KERNEL_TABLE = 0x10
+KERNEL_WIDE = 0x20
 PRECISIONS = {"fp32": 0, "bf16": 1, "bf16x3": 2, "fp16x3": 3}
 
 STATUS = {0: "GFT_OK", 1: "GFT_ERR_INVALID_ARG", 2: "GFT_ERR_NOT_INVOLUTION", 3: "GFT_ERR_NOT_SYMMETRIC",
@@ -85,7 +87,8 @@ class Plan:
     """A fast-GFT plan for one graph (gft_plan_create)."""
 
     def __init__(self, L, phis: Optional[Sequence] = None, *, split_components: bool = False,
-                 order_block: bool = False, analyze_only: bool = False, jit: bool = True):
+                 order_block: bool = False, analyze_only: bool = False, jit: bool = True,
+                 kernel: str = "auto"):
         L = _as_f64(L)
         n = L.shape[0]
         if L.shape != (n, n):
@@ -94,7 +97,8 @@ class Plan:
         ph = (np.ascontiguousarray(np.stack([np.asarray(p, dtype=np.int32) for p in phis]))
               if phis else None)
         flags = ((SPLIT_COMPONENTS if split_components else 0) | (ORDER_BLOCK if order_block else 0)
-                 | (ANALYZE_ONLY if analyze_only else 0) | (0 if jit else NO_JIT))
+                 | (ANALYZE_ONLY if analyze_only else 0) | (0 if jit else NO_JIT)
+                 | {"auto": 0, "table": KERNEL_TABLE, "wide": KERNEL_WIDE}[kernel])
         h = C.c_void_p()
         self._h = None
         _check(lib().gft_plan_create(n, _ptr(L), len(phis), _ptr(ph), flags, C.byref(h)))
@@ -336,4 +340,5 @@ def givens_apply(x, theta, net: Givens):
 
 
 __all__ = ["Plan", "Batch", "Givens", "givens_apply", "laplacian", "GftError", "lib",
-           "SPLIT_COMPONENTS", "ORDER_BLOCK", "ANALYZE_ONLY", "NO_JIT", "PRECISIONS"]
+           "SPLIT_COMPONENTS", "ORDER_BLOCK", "ANALYZE_ONLY", "NO_JIT", "KERNEL_TABLE",
+           "KERNEL_WIDE", "PRECISIONS"]

@@ -17,7 +17,7 @@ class PlanInfo(C.Structure):
                 ("n_pairs", C.c_int32), ("max_leaf", C.c_int32), ("has_device", C.c_int32),
                 ("jacobi_sweeps", C.c_int32), ("flags", C.c_uint32),
                 ("fast_mults", C.c_int64), ("fast_adds", C.c_int64), ("jit", C.c_int32),
-                ("tile_signals", C.c_int32), ("threads", C.c_int32), ("reserved", C.c_int32)]
+                ("tile_signals", C.c_int32), ("threads", C.c_int32), ("wide", C.c_int32)]
 
 
 P = C.c_void_p

@@ -126,8 +126,11 @@ gft_status gft_plan_create(int32_t n, const double* L, int32_t n_stages, const i
         if (!L) fail(GFT_ERR_INVALID_ARG, "L is NULL");
         if (n_stages < 0 || n_stages > 16) fail(GFT_ERR_INVALID_ARG, "n_stages must be in [0, 16]");
         if (n_stages > 0 && !phi) fail(GFT_ERR_INVALID_ARG, "phi is NULL");
-        if (flags & ~(GFT_SPLIT_COMPONENTS | GFT_ORDER_BLOCK | GFT_ANALYZE_ONLY | GFT_NO_JIT))
+        if (flags & ~(GFT_SPLIT_COMPONENTS | GFT_ORDER_BLOCK | GFT_ANALYZE_ONLY | GFT_NO_JIT | GFT_KERNEL_TABLE |
+                      GFT_KERNEL_WIDE))
             fail(GFT_ERR_INVALID_ARG, "unknown flag");
+        if ((flags & GFT_KERNEL_TABLE) && (flags & GFT_KERNEL_WIDE))
+            fail(GFT_ERR_INVALID_ARG, "GFT_KERNEL_TABLE and GFT_KERNEL_WIDE are exclusive");
         std::unique_ptr<gft_plan_s> p(new gft_plan_s);
         p->n = n;
         p->flags = flags;
@@ -147,6 +150,7 @@ gft_status gft_plan_create(int32_t n, const double* L, int32_t n_stages, const i
             upload_plan(*p);
             jit_build(*p);
             tc_build(*p);
+            wide_build(*p);
             GFT_CUDA(cudaDeviceSynchronize());
         }
         *out = p.release();
@@ -177,6 +181,7 @@ gft_status gft_plan_get_info(gft_plan_t p, gft_plan_info_t* info) {
         r.has_device = p->has_device ? 1 : 0;
         r.flags = p->flags;
         jit_info(*p, &r.jit, &r.tile_signals, &r.threads);
+        r.wide = (!r.jit && wide_ready(*p, false)) ? 1 : 0;
         *info = r;
     });
 }
@@ -246,6 +251,19 @@ gft_status gft_plan_basis(gft_plan_t p, double* U) {
     });
 }
 
+// CUDA-core transform: the plan-specialised kernel if the plan has one, the
+// wide-leaf kernel for leaves over 32 nodes, else the table-driven kernel.
+static void core_f32(gft_plan_s& p, const float* x, float* y, int64_t batch, bool inverse, cudaStream_t st) {
+    if (jit_launch(p, false, x, y, batch, inverse, st)) return;
+    if (wide_ready(p, false)) return launch_wide_f32(p, x, y, batch, inverse, st);
+    launch_apply_f32(apply_args(p, false), x, y, batch, inverse, st);
+}
+static void core_f64(gft_plan_s& p, const double* x, double* y, int64_t batch, bool inverse, cudaStream_t st) {
+    if (jit_launch(p, true, x, y, batch, inverse, st)) return;
+    if (wide_ready(p, true)) return launch_wide_f64(p, x, y, batch, inverse, st);
+    launch_apply_f64(apply_args(p, true), x, y, batch, inverse, st);
+}
+
 static void check_precision(gft_plan_s* p, uint32_t precision) {
     if (precision > GFT_PREC_FP16X3) fail(GFT_ERR_INVALID_ARG, "unknown precision");
     (void)p;
@@ -261,8 +279,7 @@ gft_status gft_plan_forward(gft_plan_t p, const float* x, float* y, int64_t batc
         p->last_stream = st;
         if (batch == 0) return;
         if (precision == GFT_PREC_FP32) {
-            if (!jit_launch(*p, false, x, y, batch, false, st))
-                launch_apply_f32(apply_args(*p, false), x, y, batch, false, st);
+            core_f32(*p, x, y, batch, false, st);
         } else {
             launch_tc(*p, x, y, batch, false, st, precision);
         }
@@ -279,8 +296,7 @@ gft_status gft_plan_inverse(gft_plan_t p, const float* y, float* x, int64_t batc
         p->last_stream = st;
         if (batch == 0) return;
         if (precision == GFT_PREC_FP32) {
-            if (!jit_launch(*p, false, y, x, batch, true, st))
-                launch_apply_f32(apply_args(*p, false), y, x, batch, true, st);
+            core_f32(*p, y, x, batch, true, st);
         } else {
             launch_tc(*p, y, x, batch, true, st, precision);
         }
@@ -293,8 +309,7 @@ gft_status gft_plan_forward_f64(gft_plan_t p, const double* x, double* y, int64_
         check_io(x, y, batch);
         cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
         p->last_stream = st;
-        if (!jit_launch(*p, true, x, y, batch, false, st))
-            launch_apply_f64(apply_args(*p, true), x, y, batch, false, st);
+        core_f64(*p, x, y, batch, false, st);
     });
 }
 
@@ -304,8 +319,7 @@ gft_status gft_plan_inverse_f64(gft_plan_t p, const double* y, double* x, int64_
         check_io(y, x, batch);
         cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
         p->last_stream = st;
-        if (!jit_launch(*p, true, y, x, batch, true, st))
-            launch_apply_f64(apply_args(*p, true), y, x, batch, true, st);
+        core_f64(*p, y, x, batch, true, st);
     });
 }
 
@@ -334,7 +348,7 @@ gft_status gft_plan_forward_host(gft_plan_t p, const float* x_host, float* y_hos
                 const float* xd = static_cast<const float*>(ax.devicePointer);
                 float* yd = static_cast<float*>(ay.devicePointer);
                 cudaStream_t st = p->host_streams[1];
-                if (!jit_launch_plain(*p, xd, yd, batch, st)) launch_apply_f32(apply_args(*p, false), xd, yd, batch, false, st);
+                if (!jit_launch_plain(*p, xd, yd, batch, st)) core_f32(*p, xd, yd, batch, false, st);
                 GFT_CUDA(cudaStreamSynchronize(st));
                 p->last_stream = nullptr;
                 return;
@@ -378,8 +392,7 @@ gft_status gft_plan_forward_host(gft_plan_t p, const float* x_host, float* y_hos
             GFT_CUDA(cudaStreamWaitEvent(s_k, p->ev_up[b], 0));
             if (i >= NB) GFT_CUDA(cudaStreamWaitEvent(s_k, p->ev_down[b], 0));   // output buffer free
             if (precision == GFT_PREC_FP32) {
-                if (!jit_launch(*p, false, p->d_stage[b], p->d_stage_out[b], rows, false, s_k))
-                    launch_apply_f32(apply_args(*p, false), p->d_stage[b], p->d_stage_out[b], rows, false, s_k);
+                core_f32(*p, p->d_stage[b], p->d_stage_out[b], rows, false, s_k);
             } else {
                 launch_tc(*p, p->d_stage[b], p->d_stage_out[b], rows, false, s_k, precision);
             }

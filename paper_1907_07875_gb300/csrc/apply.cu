@@ -189,7 +189,23 @@ void launch_apply(const ApplyArgs& A, const T* x, T* y, int64_t batch, bool inve
     GFT_CUDA(cudaGetLastError());
 }
 
+template <class T>
+bool supported(const ApplyArgs& A) {
+    if (A.max_bucket == 0) return false;
+    const int rmax = rs_limit(A.max_bucket);
+    const Cfg pref[] = {{2, 128, 2}, {1, 256, 2}, {2, 64, 2}, {1, 128, 2}, {1, 64, 2},
+                        {2, 128, 1}, {1, 128, 1}, {1, 64, 1}};
+    for (const Cfg& c : pref) {
+        if (c.rs > rmax) continue;
+        if (sizeof(T) == 8 && c.threads == 256) continue;
+        if (smem_bytes<T>(A, c) <= (size_t)kSmemLimit) return true;
+    }
+    return false;
+}
+
 }  // namespace
+
+bool apply_supported(const ApplyArgs& a, bool f64) { return f64 ? supported<double>(a) : supported<float>(a); }
 
 int sm_count() {
     static int cached = 0;

@@ -95,6 +95,8 @@ struct gft_plan_s {
     void* tc = nullptr;
     // plan-specialised kernels (jit.cpp)
     void* jit = nullptr;
+    // wide-leaf CUDA-core kernel data (wide.cu)
+    void* wide = nullptr;
     ~gft_plan_s();
 };
 
@@ -124,6 +126,7 @@ void launch_apply_f32(const ApplyArgs& a, const float* x, float* y, int64_t batc
 void launch_apply_f64(const ApplyArgs& a, const double* x, double* y, int64_t batch, bool inverse,
                       cudaStream_t stream);
 ApplyArgs apply_args(const gft_plan_s& p, bool f64);
+bool apply_supported(const ApplyArgs& a, bool f64);   // the table-driven kernel fits this plan
 int sm_count();
 
 // jit.cpp: plan-specialised kernels
@@ -134,6 +137,14 @@ bool jit_launch(gft_plan_s& p, bool f64, const void* x, void* y, int64_t batch, 
 void jit_info(const gft_plan_s& p, int* jit, int* tile, int* threads);
 bool jit_launch_plain(gft_plan_s& p, const float* x, float* y, int64_t batch, cudaStream_t st);
 std::string jit_source(const gft_plan_s& p, bool f64);
+
+// wide.cu: CUDA-core kernel for leaves wider than 32 nodes (up to 512)
+bool wide_eligible(const gft_plan_s& p);
+void wide_build(gft_plan_s& p);
+void wide_free(gft_plan_s& p);
+bool wide_ready(const gft_plan_s& p, bool f64);
+void launch_wide_f32(gft_plan_s& p, const float* x, float* y, int64_t batch, bool inverse, cudaStream_t st);
+void launch_wide_f64(gft_plan_s& p, const double* x, double* y, int64_t batch, bool inverse, cudaStream_t st);
 
 // tc.cu: leaf products on tcgen05 tensor cores (split precision)
 bool tc_eligible(const gft_plan_s& p);

@@ -1,0 +1,573 @@
+// CUDA-core transform kernel for plans with WIDE leaves (more than 32 nodes),
+// FP32 and FP64, forward and inverse.
+//
+// The table-driven kernel (apply.cu) gives every thread whole signals: a
+// thread gathers a leaf's m inputs into registers and computes all m
+// outputs, so its registers and its shared-memory tile grow with m and the
+// SM runs few warps once leaves reach 64 nodes.  Here the leaf products of
+// a tile are instead computed like a small GEMM by the whole CTA:
+//
+//   Y_k[TS x m] = V_k[TS x m] * M_k[m x m]        (forward, Eq. 13 per leaf)
+//
+// with V_k the tile's post-stage values at the leaf's node slots.  Each
+// thread owns an RS x OC register block (RS signals x OC consecutive
+// outputs); a warp is LR x LC threads (LR signal groups, LC = P/OC output
+// groups, P = leaf width rounded up to a power of two), so a warp covers
+// RS*LR signals and all P output columns, and the 4 warps of the CTA cover
+// the tile's TS signals.  Per input r, a thread reads RS tile values
+// (broadcast within its signal group) and OC matrix entries (vector loads
+// of one matrix row, consecutive across the warp), then issues RS*OC FMAs.
+// The leaf matrix streams from global memory (L2-resident) through two
+// shared-memory chunk buffers with cp.async, so leaves of any width up to
+// 512 work with a fixed shared-memory budget.  (RS, OC) is chosen per leaf
+// on the host for the fewest shared-memory wavefronts per FMA.
+//
+// Per tile: load (16-byte cp.async when rows allow, otherwise 4/8-byte),
+// Haar stages with the CTA's threads spread over the pairs of one stage at a
+// time (Sec. III: one addition and one subtraction per unit, the 1/sqrt2
+// factors folded into M_k), leaf products in place (a leaf's outputs
+// overwrite its own input slots once every warp has finished reading them),
+// then the permuted store (coefficients in ascending-eigenvalue order).  The
+// inverse loads through the permutation, runs the leaves with M_k^T and then
+// the stages in reverse order (B_phi is its own inverse).
+//
+// Shared-memory row stride: np = n rounded up to 4 (mod 32) floats (2 mod
+// 16 doubles), which keeps rows 16-byte aligned and puts the rows read by
+// the LR signal groups of a warp in different banks.
+#include <algorithm>
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <vector>
+
+#include "apply_core.cuh"
+
+namespace gft {
+using namespace core;
+namespace {
+
+constexpr int kWThreads = 128;
+constexpr int kWSmemLimit = 232448;
+constexpr int kWDesc = 8;   // per leaf: m, P, lab_off, f_off, i_off, variant, lc, kc_rows
+
+struct WArgs {
+    const void* x;
+    void* y;
+    const int* ints;       // plan program (pairs, stage offsets, labels, out_pos, src, ...)
+    const int* wdesc;      // per-leaf descriptors, kWDesc ints each
+    const void* mats;      // per leaf: M_f (m x P) then M_i (m x P), zero padded columns
+    long long batch;
+    int n, np, ts, nbuf, n_pairs, n_stages, n_leaves;
+    int off_labels, off_src;
+    int chunk_elems;       // elements of one matrix chunk buffer
+    int inverse;
+    float inv_n;
+};
+
+template <class T, int OC>
+__device__ __forceinline__ void load_row(const T* p, T (&w)[OC]) {
+    if constexpr (sizeof(T) == 4 && OC % 4 == 0) {
+#pragma unroll
+        for (int q = 0; q < OC / 4; ++q) {
+            const float4 v = reinterpret_cast<const float4*>(p)[q];
+            w[4 * q] = v.x;
+            w[4 * q + 1] = v.y;
+            w[4 * q + 2] = v.z;
+            w[4 * q + 3] = v.w;
+        }
+    } else if constexpr (sizeof(T) == 4 && OC == 2) {
+        const float2 v = *reinterpret_cast<const float2*>(p);
+        w[0] = v.x;
+        w[1] = v.y;
+    } else if constexpr (sizeof(T) == 8 && OC % 2 == 0) {
+#pragma unroll
+        for (int q = 0; q < OC / 2; ++q) {
+            const double2 v = reinterpret_cast<const double2*>(p)[q];
+            w[2 * q] = v.x;
+            w[2 * q + 1] = v.y;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < OC; ++q) w[q] = p[q];
+    }
+}
+
+// rows x P elements of a leaf matrix (contiguous) -> shared memory, 16-byte
+// copies (P * sizeof(T) is a multiple of 16 and chunks start 16-byte aligned)
+template <class T>
+__device__ __forceinline__ void load_chunk(T* dst, const T* src, int elems) {
+    constexpr int PER = 16 / sizeof(T);
+    for (int c = threadIdx.x; c < elems / PER; c += kWThreads) cp_async16(dst + c * PER, src + c * PER);
+}
+
+// One leaf's product over the tile, in place.  M points at the leaf's
+// m x P matrix for this direction.
+template <class T, int RS, int OC>
+__device__ __forceinline__ void wide_leaf(T* tile, int np, int ts, const int* lab, const T* __restrict__ M, int m,
+                                          int P, int lc, int kc_rows, T* mbuf, int chunk_elems) {
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int lr_cnt = 32 / lc;
+    const int lr = lane / lc;
+    const int c0 = (lane - lr * lc) * OC;
+    const int sbase = warp * RS * lr_cnt + lr;
+    int rowoff[RS];
+#pragma unroll
+    for (int i = 0; i < RS; ++i) rowoff[i] = min(sbase + i * lr_cnt, ts - 1) * np;   // clamp: never outside the tile
+    T acc[RS][OC];
+#pragma unroll
+    for (int i = 0; i < RS; ++i)
+#pragma unroll
+        for (int j = 0; j < OC; ++j) acc[i][j] = T(0);
+    const int nch = (m + kc_rows - 1) / kc_rows;
+    const int celems = kc_rows * P;
+    load_chunk(mbuf, M, min(kc_rows, m) * P);
+    cp_async_commit();
+    for (int kc = 0; kc < nch; ++kc) {
+        if (kc + 1 < nch) {
+            const int r0n = (kc + 1) * kc_rows;
+            load_chunk(mbuf + ((kc + 1) & 1) * chunk_elems, M + (size_t)r0n * P, min(kc_rows, m - r0n) * P);
+        }
+        cp_async_commit();
+        cp_async_wait1();
+        __syncthreads();   // chunk kc visible to every thread
+        const T* Mc = mbuf + (kc & 1) * chunk_elems + c0;
+        const int r0 = kc * kc_rows, rn = min(kc_rows, m - r0);
+#pragma unroll 4
+        for (int r = 0; r < rn; ++r) {
+            const int g = lab[r0 + r];
+            T v[RS];
+#pragma unroll
+            for (int i = 0; i < RS; ++i) v[i] = tile[rowoff[i] + g];
+            T w[OC];
+            load_row<T, OC>(Mc + r * P, w);
+#pragma unroll
+            for (int i = 0; i < RS; ++i)
+#pragma unroll
+                for (int j = 0; j < OC; ++j) acc[i][j] = fma(v[i], w[j], acc[i][j]);
+        }
+        __syncthreads();   // every thread done with chunk kc's buffer and (last chunk) with V_k
+    }
+#pragma unroll
+    for (int i = 0; i < RS; ++i) {
+        if (sbase + i * lr_cnt < ts) {
+#pragma unroll
+            for (int j = 0; j < OC; ++j)
+                if (c0 + j < m) tile[rowoff[i] + lab[c0 + j]] = acc[i][j];
+        }
+    }
+    (void)celems;
+}
+
+// variant code = log2(RS) * 5 + log2(OC), RS in {1,2,4,8}, OC in {1,...,16}
+template <class T>
+__device__ __forceinline__ void wide_leaf_dispatch(int code, T* tile, int np, int ts, const int* lab, const T* M,
+                                                   int m, int P, int lc, int kc, T* mbuf, int ce) {
+#define GFT_W(R, O, C)                                                              \
+    case C:                                                                        \
+        if constexpr (sizeof(T) == 4 || R * O <= 32)                               \
+            wide_leaf<T, R, O>(tile, np, ts, lab, M, m, P, lc, kc, mbuf, ce);      \
+        break;
+    switch (code) {
+        GFT_W(1, 1, 0) GFT_W(1, 2, 1) GFT_W(1, 4, 2) GFT_W(1, 8, 3) GFT_W(1, 16, 4)
+        GFT_W(2, 1, 5) GFT_W(2, 2, 6) GFT_W(2, 4, 7) GFT_W(2, 8, 8) GFT_W(2, 16, 9)
+        GFT_W(4, 1, 10) GFT_W(4, 2, 11) GFT_W(4, 4, 12) GFT_W(4, 8, 13) GFT_W(4, 16, 14)
+        GFT_W(8, 1, 15) GFT_W(8, 2, 16) GFT_W(8, 4, 17) GFT_W(8, 8, 18)
+        default: break;
+    }
+#undef GFT_W
+}
+
+template <class T>
+__device__ __forceinline__ void wide_stage(T* tile, int np, int ts, const int* pairs, int p0, int P) {
+    const int total = ts * P;
+    for (int idx = threadIdx.x; idx < total; idx += kWThreads) {
+        const int t = idx / P;
+        const int q = p0 + idx - t * P;
+        T* row = tile + t * np;
+        const int i = pairs[2 * q], j = pairs[2 * q + 1];
+        const T u = row[i], v = row[j];
+        row[i] = u + v;
+        row[j] = u - v;
+    }
+}
+
+template <class T>
+__device__ __forceinline__ void wide_load(const WArgs& a, const int* src_slot, T* buf, long long tile) {
+    constexpr int PER = 16 / sizeof(T);
+    const long long rows = min((long long)a.ts, a.batch - tile * (long long)a.ts);
+    const T* src = reinterpret_cast<const T*>(a.x) + tile * (long long)a.ts * a.n;
+    if (!a.inverse && a.n % PER == 0) {
+        const int per_row = a.n / PER;
+        const int total = (int)rows * per_row;
+        for (int c = threadIdx.x; c < total; c += kWThreads) {
+            const int t = c / per_row;
+            const int k = c - t * per_row;
+            cp_async16(buf + t * a.np + k * PER, src + (long long)c * PER);
+        }
+    } else {
+        const int E = (int)rows * a.n;
+        for (int e = threadIdx.x; e < E; e += kWThreads) {
+            const int t = row_of(e, a.inv_n);
+            const int j = e - t * a.n;
+            cp_async_elem(buf + t * a.np + (a.inverse ? src_slot[j] : j), src + e);
+        }
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(kWThreads) gft_wide_kernel(WArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    // [nbuf tiles][2 matrix chunks][pairs 2P][stage_off S+1][labels n][src n][leaf desc]
+    T* tiles = reinterpret_cast<T*>(smem_raw);
+    const int tile_elems = a.ts * a.np;
+    T* mbuf = tiles + a.nbuf * tile_elems;
+    int* s_pairs = reinterpret_cast<int*>(mbuf + 2 * a.chunk_elems);
+    int* s_soff = s_pairs + 2 * a.n_pairs;
+    int* s_lab = s_soff + a.n_stages + 1;
+    int* s_src = s_lab + a.n;
+    int* s_desc = s_src + a.n;
+    const int tid = threadIdx.x;
+    for (int i = tid; i < 2 * a.n_pairs + a.n_stages + 1; i += kWThreads) s_pairs[i] = a.ints[i];
+    for (int i = tid; i < a.n; i += kWThreads) {
+        s_lab[i] = a.ints[a.off_labels + i];
+        s_src[i] = a.ints[a.off_src + i];
+    }
+    for (int i = tid; i < kWDesc * a.n_leaves; i += kWThreads) s_desc[i] = a.wdesc[i];
+    __syncthreads();
+    const T* mats = reinterpret_cast<const T*>(a.mats);
+    const long long n_tiles = (a.batch + a.ts - 1) / a.ts;
+    KArgs ka{};
+    ka.y = a.y;
+    ka.batch = a.batch;
+    ka.n = a.n;
+    ka.np = a.np;
+    ka.ts = a.ts;
+    ka.inverse = a.inverse;
+    ka.inv_n = a.inv_n;
+    long long tile = blockIdx.x;
+    if (tile < n_tiles) wide_load<T>(a, s_src, tiles, tile);
+    cp_async_commit();
+    int cur = 0;
+    for (; tile < n_tiles; tile += gridDim.x) {
+        T* buf = tiles + cur * tile_elems;
+        const long long nxt = tile + gridDim.x;
+        if (a.nbuf == 2) {
+            if (nxt < n_tiles) wide_load<T>(a, s_src, tiles + (cur ^ 1) * tile_elems, nxt);
+            cp_async_commit();
+            cp_async_wait1();
+        } else {
+            cp_async_wait0();
+        }
+        __syncthreads();   // tile landed
+        if (!a.inverse) {
+            for (int s = 0; s < a.n_stages; ++s) {
+                wide_stage(buf, a.np, a.ts, s_pairs, s_soff[s], s_soff[s + 1] - s_soff[s]);
+                __syncthreads();
+            }
+        }
+        for (int k = 0; k < a.n_leaves; ++k) {
+            const int* d = s_desc + kWDesc * k;
+            const T* M = mats + (a.inverse ? d[4] : d[3]);
+            wide_leaf_dispatch<T>(d[5], buf, a.np, a.ts, s_lab + d[2], M, d[0], d[1], d[6], d[7], mbuf,
+                                  a.chunk_elems);
+        }
+        __syncthreads();   // every leaf's outputs written
+        if (a.inverse) {
+            for (int s = a.n_stages - 1; s >= 0; --s) {
+                wide_stage(buf, a.np, a.ts, s_pairs, s_soff[s], s_soff[s + 1] - s_soff[s]);
+                __syncthreads();
+            }
+        }
+        store_tile<T, kWThreads>(ka, s_src, buf, tile);
+        __syncthreads();   // buffer free
+        if (a.nbuf == 2) {
+            cur ^= 1;
+        } else {
+            if (nxt < n_tiles) wide_load<T>(a, s_src, tiles, nxt);
+            cp_async_commit();
+        }
+    }
+    cp_async_wait0();
+}
+
+int pow2_at_least(int v) {
+    int p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+int ilog2(int v) {
+    int l = 0;
+    while ((1 << l) < v) ++l;
+    return l;
+}
+
+int row_stride(int n, size_t esz) {
+    // float: np = 4 (mod 32); double: np = 2 (mod 16)
+    const int mod = esz == 4 ? 32 : 16, want = esz == 4 ? 4 : 2;
+    return n + ((want - n % mod) % mod + mod) % mod;
+}
+
+struct WVariant {
+    int rs, oc, lc;
+};
+
+// (RS, OC) for a leaf of padded width P in a tile of TS signals; rs = 0 if none
+WVariant pick_variant(int P, int ts, size_t esz) {
+    const int max_acc = esz == 4 ? 64 : 32;
+    const int target = ts * P / 128;
+    if (target < 1) return P <= 32 ? WVariant{1, 1, P} : WVariant{0, 0, 0};
+    if (target > max_acc) return {0, 0, 0};
+    const int vw = 16 / (int)esz;
+    WVariant best{0, 0, 0};
+    double best_ratio = -1.0;
+    for (int rs = 1; rs <= 8; rs <<= 1) {
+        if (target % rs) continue;
+        const int oc = target / rs;
+        if (oc > 16 || oc > P || (rs == 8 && oc == 16)) continue;
+        const int lc = P / oc;
+        if (lc < 1 || lc > 32) continue;
+        const int vloads = std::max(1, oc / vw);
+        const double m_wave = vloads * std::max(1.0, lc * (double)std::min(oc, vw) * esz / 128.0);
+        const double ratio = (double)(rs * oc) / (rs + m_wave);
+        if (ratio > best_ratio) {
+            best_ratio = ratio;
+            best = {rs, oc, lc};
+        }
+    }
+    return best;
+}
+
+struct WidePlan {
+    struct Cfg {
+        int ts = 0, nbuf = 1, chunk_elems = 0;
+        size_t smem = 0;
+        int* d_desc = nullptr;
+        bool use = false;          // chosen over the table-driven kernel
+    } cfg[2];                      // FP32, FP64
+    float* d_m32 = nullptr;
+    double* d_m64 = nullptr;
+    ~WidePlan() {
+        for (auto& c : cfg)
+            if (c.d_desc) cudaFree(c.d_desc);
+        if (d_m32) cudaFree(d_m32);
+        if (d_m64) cudaFree(d_m64);
+    }
+};
+
+}  // namespace
+
+template <class T>
+static void launch_wide_t(gft_plan_s& p, const T* x, T* y, int64_t batch, bool inverse, cudaStream_t st);
+static void wide_tune(gft_plan_s& p);
+
+bool wide_eligible(const gft_plan_s& p) {
+    int mx = 0;
+    for (auto& lf : p.leaves) mx = std::max(mx, lf.m());
+    return p.n >= 4 && mx > 32 && mx <= 512;
+}
+
+// Host preparation: pow2-padded forward / inverse leaf matrices (FP32 and
+// FP64) and, per precision, the tile size and per-leaf variants.
+void wide_build(gft_plan_s& p) {
+    if (!wide_eligible(p)) return;
+    WidePlan* W = new WidePlan;
+    try {
+        const int n = p.n;
+        std::vector<double> mats;
+        std::vector<int> Ps, lab_off, f_off, i_off;
+        int lo = 0;
+        for (auto& lf : p.leaves) {
+            const int m = lf.m(), P = std::max(4, pow2_at_least(m));
+            Ps.push_back(P);
+            lab_off.push_back(lo);
+            lo += m;
+            f_off.push_back((int)mats.size());
+            std::vector<double> Mf((size_t)m * P, 0.0), Mi((size_t)m * P, 0.0);
+            for (int r = 0; r < m; ++r) {
+                const double sc = std::pow(2.0, -0.5 * lf.exps[r]);
+                for (int c = 0; c < m; ++c) {
+                    const double v = sc * lf.V[(size_t)r * m + c];
+                    Mf[(size_t)r * P + c] = v;   // forward: y_c = sum_r v_r Mf[r][c]
+                    Mi[(size_t)c * P + r] = v;   // inverse: x_r = sum_c y_c Mi[c][r]
+                }
+            }
+            mats.insert(mats.end(), Mf.begin(), Mf.end());
+            i_off.push_back((int)mats.size());
+            mats.insert(mats.end(), Mi.begin(), Mi.end());
+        }
+        const int ints_smem = 2 * p.dev.n_pairs + p.dev.n_stages + 1 + 2 * n + kWDesc * (int)p.leaves.size();
+        for (int prec = 0; prec < 2; ++prec) {
+            const size_t esz = prec == 0 ? 4 : 8;
+            const int np = row_stride(n, esz);
+            int maxP = 4;
+            for (int P : Ps) maxP = std::max(maxP, P);
+            WidePlan::Cfg& c = W->cfg[prec];
+            // largest power-of-two tile (64 down to 4) whose leaves all have a
+            // variant and whose buffers fit; two tile buffers when they fit
+            // in about half of the SM (two CTAs per SM) or when the tile is small
+            for (int ts = 64; ts >= 4; ts >>= 1) {
+                bool ok = true;
+                int chunk = 0;
+                std::vector<int> desc;
+                for (size_t k = 0; k < p.leaves.size() && ok; ++k) {
+                    const int m = p.leaves[k].m(), P = Ps[k];
+                    const WVariant v = pick_variant(P, ts, esz);
+                    if (!v.rs) {
+                        ok = false;
+                        break;
+                    }
+                    int kc = std::max(4, (int)(16384 / (P * esz)));
+                    kc = std::min(kc, m);
+                    chunk = std::max(chunk, kc * P);
+                    desc.insert(desc.end(), {m, P, lab_off[k], f_off[k], i_off[k],
+                                             ilog2(v.rs) * 5 + ilog2(v.oc), v.lc, kc});
+                }
+                if (!ok) continue;
+                const size_t fixed = esz * 2 * (size_t)chunk + sizeof(int) * (size_t)((ints_smem + 3) & ~3);
+                const size_t tile = esz * (size_t)ts * np;
+                int nbuf = 0;
+                if (fixed + 2 * tile <= (size_t)kWSmemLimit / 2 - 1024) nbuf = 2;
+                else if (fixed + tile <= (size_t)kWSmemLimit) nbuf = 1;
+                if (!nbuf) continue;
+                if (const char* e = std::getenv("GFT_WIDE_TS")) {
+                    const int want = std::atoi(e);
+                    if (want && want != ts) continue;
+                }
+                c.ts = ts;
+                c.nbuf = nbuf;
+                c.chunk_elems = chunk;
+                c.smem = fixed + nbuf * tile;
+                GFT_CUDA(cudaMalloc(&c.d_desc, sizeof(int) * desc.size()));
+                GFT_CUDA(cudaMemcpy(c.d_desc, desc.data(), sizeof(int) * desc.size(), cudaMemcpyHostToDevice));
+                break;
+            }
+        }
+        std::vector<float> m32(mats.begin(), mats.end());
+        GFT_CUDA(cudaMalloc(&W->d_m32, sizeof(float) * m32.size()));
+        GFT_CUDA(cudaMemcpy(W->d_m32, m32.data(), sizeof(float) * m32.size(), cudaMemcpyHostToDevice));
+        GFT_CUDA(cudaMalloc(&W->d_m64, sizeof(double) * mats.size()));
+        GFT_CUDA(cudaMemcpy(W->d_m64, mats.data(), sizeof(double) * mats.size(), cudaMemcpyHostToDevice));
+    } catch (...) {
+        delete W;
+        throw;
+    }
+    p.wide = W;
+    // Choose between this kernel and the table-driven one (which handles
+    // leaves up to 64 nodes) by timing both on a scratch batch.
+    // GFT_KERNEL_TABLE keeps the table-driven kernel wherever it fits.
+    bool tune = false;
+    for (int prec = 0; prec < 2; ++prec) {
+        WidePlan::Cfg& c = W->cfg[prec];
+        const bool table_ok = apply_supported(apply_args(p, prec == 1), prec == 1);
+        c.use = c.ts > 0 && (!table_ok || !(p.flags & GFT_KERNEL_TABLE));
+        tune |= c.use && table_ok && !(p.flags & GFT_KERNEL_WIDE);
+    }
+    if (tune) wide_tune(p);
+}
+
+void wide_free(gft_plan_s& p) {
+    delete static_cast<WidePlan*>(p.wide);
+    p.wide = nullptr;
+}
+
+bool wide_ready(const gft_plan_s& p, bool f64) {
+    const WidePlan* W = static_cast<const WidePlan*>(p.wide);
+    return W && W->cfg[f64 ? 1 : 0].use;
+}
+
+// Time the wide and the table-driven FP32 / FP64 forward kernels on a
+// scratch batch of zeros (no data-dependent work) and keep the faster.
+static void wide_tune(gft_plan_s& p) {
+    WidePlan* W = static_cast<WidePlan*>(p.wide);
+    const int n = p.n;
+    const int64_t tb = std::max<int64_t>(4096, (int64_t)(32 << 20) / (8 * n));
+    void* dx = nullptr;
+    void* dy = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaStream_t st = nullptr;
+    auto cleanup = [&] {
+        if (dx) cudaFree(dx);
+        if (dy) cudaFree(dy);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (st) cudaStreamDestroy(st);
+    };
+    try {
+        GFT_CUDA(cudaMalloc(&dx, (size_t)tb * n * 8));
+        GFT_CUDA(cudaMalloc(&dy, (size_t)tb * n * 8));
+        GFT_CUDA(cudaMemset(dx, 0, (size_t)tb * n * 8));
+        GFT_CUDA(cudaEventCreate(&e0));
+        GFT_CUDA(cudaEventCreate(&e1));
+        GFT_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        for (int prec = 0; prec < 2; ++prec) {
+            if (!W->cfg[prec].use || !apply_supported(apply_args(p, prec == 1), prec == 1)) continue;
+            float best[2] = {1e30f, 1e30f};
+            for (int rep = 0; rep < 3; ++rep)
+                for (int which = 0; which < 2; ++which) {
+                    GFT_CUDA(cudaEventRecord(e0, st));
+                    if (prec == 0) {
+                        if (which) launch_wide_t<float>(p, (const float*)dx, (float*)dy, tb, false, st);
+                        else launch_apply_f32(apply_args(p, false), (const float*)dx, (float*)dy, tb, false, st);
+                    } else {
+                        if (which) launch_wide_t<double>(p, (const double*)dx, (double*)dy, tb, false, st);
+                        else launch_apply_f64(apply_args(p, true), (const double*)dx, (double*)dy, tb, false, st);
+                    }
+                    GFT_CUDA(cudaEventRecord(e1, st));
+                    GFT_CUDA(cudaEventSynchronize(e1));
+                    float ms = 0.f;
+                    GFT_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                    best[which] = std::min(best[which], ms);
+                }
+            W->cfg[prec].use = best[1] < best[0];
+        }
+    } catch (...) {
+        cleanup();
+        throw;
+    }
+    cleanup();
+}
+
+template <class T>
+static void launch_wide_t(gft_plan_s& p, const T* x, T* y, int64_t batch, bool inverse, cudaStream_t st) {
+    WidePlan* W = static_cast<WidePlan*>(p.wide);
+    const int prec = sizeof(T) == 8 ? 1 : 0;
+    const auto& c = W->cfg[prec];
+    if (!c.ts) fail(GFT_ERR_UNSUPPORTED, "no wide-leaf kernel configuration fits this plan");
+    WArgs a{};
+    a.x = x;
+    a.y = y;
+    a.ints = p.dev.d_ints;
+    a.wdesc = c.d_desc;
+    a.mats = prec ? (const void*)W->d_m64 : (const void*)W->d_m32;
+    a.batch = batch;
+    a.n = p.n;
+    a.np = row_stride(p.n, sizeof(T));
+    a.ts = c.ts;
+    a.nbuf = c.nbuf;
+    a.n_pairs = p.dev.n_pairs;
+    a.n_stages = p.dev.n_stages;
+    a.n_leaves = p.dev.n_leaves;
+    a.off_labels = 2 * p.dev.n_pairs + p.dev.n_stages + 1;
+    a.off_src = a.off_labels + 2 * p.n;
+    a.chunk_elems = c.chunk_elems;
+    a.inverse = inverse ? 1 : 0;
+    a.inv_n = 1.0f / (float)p.n;
+    auto fn = gft_wide_kernel<T>;
+    GFT_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem));
+    int per_sm = 0;
+    GFT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kWThreads, c.smem));
+    if (per_sm < 1) fail(GFT_ERR_UNSUPPORTED, "wide-leaf kernel does not fit on an SM");
+    const long long n_tiles = (batch + c.ts - 1) / c.ts;
+    const long long grid = std::min<long long>(n_tiles, (long long)per_sm * sm_count());
+    fn<<<(unsigned)grid, kWThreads, c.smem, st>>>(a);
+    GFT_CUDA(cudaGetLastError());
+}
+
+void launch_wide_f32(gft_plan_s& p, const float* x, float* y, int64_t batch, bool inverse, cudaStream_t st) {
+    launch_wide_t<float>(p, x, y, batch, inverse, st);
+}
+void launch_wide_f64(gft_plan_s& p, const double* x, double* y, int64_t batch, bool inverse, cudaStream_t st) {
+    launch_wide_t<double>(p, x, y, batch, inverse, st);
+}
+
+}  // namespace gft

@@ -158,17 +158,6 @@ def test_config3_core_kinds_full(env, kind):
     assert rel_l2(y[idx], y_ref) <= FP32_TOL
 
 
-def test_grid32_needs_tensor_cores_on_fp32_kernel(env):
-    gft, torch = env
-    g, batch, seed = W.config3()[4]
-    plan = make_plan(gft, g, False)
-    x = torch.zeros(64, g.n, device="cuda")
-    try:
-        plan.forward(x)
-    except gft.GftError as e:
-        assert e.status == "GFT_ERR_UNSUPPORTED"
-
-
 @pytest.mark.parametrize("n", [16, 32, 64])
 def test_dense_plans_no_stages(env, n):
     """Zero stages = the dense GFT (one leaf of n nodes), as used for the
