@@ -227,22 +227,36 @@ gft_status gft_device_error(gft_plan_t plan, int32_t* code);
 
 /*
  * Mixed batch: many plans, each with its own batch of signals, transformed
- * forward by ONE persistent kernel launch over a work list of (plan, tile)
- * items, captured in a CUDA graph on first use and replayed afterwards.
- *  plans[n_plans]  plans created with device bases (all FP32 CUDA-core
- *                  capable); the batch does not own them, and they must
- *                  outlive it.
+ * forward by one CUDA-graph launch, captured on first use and replayed.
+ * Plans are routed by leaf width:
+ *   - leaves of at most 64 nodes (unless the plan prefers the wide-leaf
+ *     kernel): ONE persistent table-driven kernel over a work list of
+ *     (plan, tile) items, with per-plan tile shapes timed at creation;
+ *   - leaves of 33..512 nodes: ONE persistent wide-leaf kernel over the
+ *     (plan, tile) items of those plans;
+ *   - with a tensor-core precision, plans with a leaf of 64 or more nodes
+ *     (at most 256): each plan's tensor-core kernels.
+ * The groups run on forked streams inside the graph and join at its end.
+ *  plans[n_plans]  plans created with device bases; the batch does not own
+ *                  them, and they must outlive it.  A plan may appear more
+ *                  than once (its entries then run one after another).
  *  batches[n_plans] signals per plan.
+ *  flags           precision of the tensor-core leaves: GFT_PREC_FP32 (0:
+ *                  CUDA cores only), GFT_PREC_BF16, GFT_PREC_BF16X3,
+ *                  GFT_PREC_FP16X3.
  * gft_batch_forward: x[i], y[i] device pointers to [batches[i], n_i] FP32
- * (host arrays of n_plans pointers).  A replay with the same pointers reuses
- * the captured graph; new pointers trigger a new capture.
+ * (host arrays of n_plans pointers); x[i] != y[i] for tensor-core entries.
+ * A replay with the same pointers reuses the captured graph; new pointers
+ * are written to the kernels' device descriptors (and trigger a new capture
+ * when the batch has tensor-core entries).
  */
 gft_status gft_batch_create(int32_t n_plans, const gft_plan_t* plans, const int64_t* batches,
                             uint32_t flags, gft_batch_t* out);
 gft_status gft_batch_forward(gft_batch_t batch, const float* const* x, float* const* y,
                              gft_stream_t stream);
-/* Tile configuration chosen by the autotuner for plan i: signals per tile
- * and threads per block (0 if not tuned yet). */
+/* Tile configuration chosen by the autotuner for plan i of the table-driven
+ * group: signals per tile and threads per block (0 for entries routed to
+ * the wide-leaf or tensor-core kernels). */
 gft_status gft_batch_get_tile(gft_batch_t batch, int32_t i, int32_t* tile, int32_t* threads);
 gft_status gft_batch_destroy(gft_batch_t batch);
 

@@ -226,15 +226,18 @@ class Plan:
 
 
 class Batch:
-    """Many plans transformed by one persistent, graph-captured launch."""
+    """Many plans transformed by one graph-captured launch (gft_batch_create):
+    persistent kernels over (plan, tile) work lists, plus the tensor-core
+    kernels of wide plans when a tensor-core precision is asked for."""
 
-    def __init__(self, plans: Sequence[Plan], batches: Sequence[int]):
+    def __init__(self, plans: Sequence[Plan], batches: Sequence[int], precision: str = "fp32"):
         self.plans = list(plans)
         arr = (C.c_void_p * len(plans))(*[p.handle for p in plans])
         b = np.ascontiguousarray(np.asarray(batches, dtype=np.int64))
         h = C.c_void_p()
         self._h = None
-        _check(lib().gft_batch_create(len(plans), C.cast(arr, C.c_void_p), _ptr(b), 0, C.byref(h)))
+        _check(lib().gft_batch_create(len(plans), C.cast(arr, C.c_void_p), _ptr(b), PRECISIONS[precision],
+                                      C.byref(h)))
         self._h = h
         self.batches = b
 

@@ -21,6 +21,7 @@
 // only rewrites the per-plan descriptors in device memory; the captured graph
 // is reused.
 #include <algorithm>
+#include <map>
 #include <memory>
 #include <numeric>
 #include <vector>
@@ -32,6 +33,7 @@ using namespace core;
 namespace {
 
 constexpr int kBatchThreads = 128;
+constexpr int kTcMinLeaf = 64;   // leaves this wide go to the tensor cores in a tensor-core batch
 constexpr int kBatchSmemLimit = 232448;
 
 struct BatchPlanDev {
@@ -135,7 +137,23 @@ int rs_cap(int max_bucket) { return max_bucket <= 16 ? 4 : (max_bucket <= 32 ? 2
 using namespace gft;
 
 struct gft_batch_s {
-    std::vector<gft_plan_s*> plans;        // user order
+    // routing of the caller's plans: 0 = table-driven batch kernel, 1 = wide-leaf
+    // batch kernel, 2 = tensor-core sequence; idx = position within its group
+    uint32_t precision = GFT_PREC_FP32;
+    std::vector<int> kind, idx;
+    std::vector<int64_t> user_batch;
+    std::vector<int> table_users, wide_users, tc_users;
+    std::vector<gft_plan_s*> tc_plans;
+    std::vector<int64_t> tc_batches;
+    std::vector<int> tc_stream;            // stream slot of each tensor-core entry
+    std::vector<std::unique_ptr<gft::TcScratch>> tc_scratch;   // one per distinct tensor-core plan
+    std::vector<int> tc_scr;               // scratch index of each tensor-core entry
+    void* wide = nullptr;
+    static constexpr int kTcStreams = 4;
+    cudaStream_t side[1 + kTcStreams] = {};
+    cudaEvent_t ev_fork = nullptr, ev_join[1 + kTcStreams] = {};
+    // table-driven group
+    std::vector<gft_plan_s*> plans;        // table-driven group, group order
     std::vector<int64_t> batches;
     std::vector<int> order;                // descriptor slot -> user index
     std::vector<int> rs;                   // per user index
@@ -151,6 +169,12 @@ struct gft_batch_s {
     cudaGraphExec_t exec = nullptr;
     std::vector<const void*> last_x, last_y;
     ~gft_batch_s() {
+        if (wide) gft::wide_batch_free(wide);
+        for (auto& st : side)
+            if (st) cudaStreamDestroy(st);
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        for (auto& e : ev_join)
+            if (e) cudaEventDestroy(e);
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
         if (cap_stream) cudaStreamDestroy(cap_stream);
@@ -333,24 +357,68 @@ gft_status gft_batch_create(int32_t n_plans, const gft_plan_t* plans, const int6
                             gft_batch_t* out) {
     return guard_b([&] {
         if (!out || !plans || !batches || n_plans < 1) fail(GFT_ERR_INVALID_ARG, "bad arguments");
-        if (flags != 0) fail(GFT_ERR_INVALID_ARG, "unknown flag");
+        if (flags > GFT_PREC_FP16X3) fail(GFT_ERR_INVALID_ARG, "unknown flag");
         std::unique_ptr<gft_batch_s> b(new gft_batch_s);
+        b->precision = flags;
+        std::vector<gft_plan_s*> wide_plans;
+        std::vector<int64_t> wide_batches;
+        std::map<gft_plan_s*, int> tc_slot;
         for (int i = 0; i < n_plans; ++i) {
             gft_plan_s* p = plans[i];
             if (!p) fail(GFT_ERR_INVALID_ARG, "NULL plan");
             if (!p->has_device) fail(GFT_ERR_NO_DEVICE, "plan without device data");
-            if (p->dev.max_bucket == 0)
-                fail(GFT_ERR_UNSUPPORTED, "plan " + std::to_string(i) + " has a leaf wider than 64 nodes");
             if (batches[i] < 0) fail(GFT_ERR_INVALID_ARG, "negative batch");
-            b->plans.push_back(p);
-            b->batches.push_back(batches[i]);
+            int max_leaf = 0;
+            for (auto& lf : p->leaves) max_leaf = std::max(max_leaf, lf.m());
+            int kind;
+            if (b->precision != GFT_PREC_FP32 && p->tc && max_leaf >= kTcMinLeaf) kind = 2;
+            else if (p->dev.max_bucket != 0 && !(wide_configured(*p) && wide_ready(*p, false))) kind = 0;
+            else if (wide_configured(*p)) kind = 1;
+            else fail(GFT_ERR_UNSUPPORTED, "plan " + std::to_string(i) + " has a leaf wider than 512 nodes");
+            b->kind.push_back(kind);
+            b->user_batch.push_back(batches[i]);
+            if (kind == 0) {
+                b->idx.push_back((int)b->plans.size());
+                b->table_users.push_back(i);
+                b->plans.push_back(p);
+                b->batches.push_back(batches[i]);
+            } else if (kind == 1) {
+                b->idx.push_back((int)wide_plans.size());
+                b->wide_users.push_back(i);
+                wide_plans.push_back(p);
+                wide_batches.push_back(batches[i]);
+            } else {
+                b->idx.push_back((int)b->tc_plans.size());
+                b->tc_users.push_back(i);
+                b->tc_plans.push_back(p);
+                b->tc_batches.push_back(batches[i]);
+                // entries of one plan share one scratch: same stream, in order
+                auto it = tc_slot.find(p);
+                int scr;
+                if (it == tc_slot.end()) {
+                    scr = (int)b->tc_scratch.size();
+                    tc_slot[p] = scr;
+                    b->tc_scratch.emplace_back(new TcScratch);
+                } else {
+                    scr = it->second;
+                }
+                b->tc_scr.push_back(scr);
+                b->tc_stream.push_back(scr % gft_batch_s::kTcStreams);
+                tc_reserve(*p, *b->tc_scratch[scr], batches[i]);
+            }
         }
-        GFT_CUDA(cudaMalloc(&b->d_desc, sizeof(BatchPlanDev) * n_plans));
+        GFT_CUDA(cudaMalloc(&b->d_desc, sizeof(BatchPlanDev) * std::max<size_t>(1, b->plans.size())));
         GFT_CUDA(cudaMalloc(&b->d_counter, sizeof(unsigned long long)));
-        autotune(*b);
-        layout(*b);
-        configure(*b);
+        if (!b->plans.empty()) {
+            autotune(*b);
+            layout(*b);
+            configure(*b);
+        }
+        if (!wide_plans.empty()) b->wide = wide_batch_create(wide_plans, wide_batches);
         GFT_CUDA(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+        for (auto& st : b->side) GFT_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        GFT_CUDA(cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming));
+        for (auto& e : b->ev_join) GFT_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         *out = b.release();
     });
 }
@@ -358,27 +426,69 @@ gft_status gft_batch_create(int32_t n_plans, const gft_plan_t* plans, const int6
 gft_status gft_batch_forward(gft_batch_t b, const float* const* x, float* const* y, gft_stream_t stream) {
     return guard_b([&] {
         if (!b || !x || !y) fail(GFT_ERR_INVALID_ARG, "NULL argument");
-        const int k = (int)b->plans.size();
+        const int k = (int)b->kind.size();
         for (int i = 0; i < k; ++i) {
-            if (b->batches[i] == 0) continue;
+            if (b->user_batch[i] == 0) continue;
             if (!x[i] || !y[i]) fail(GFT_ERR_INVALID_ARG, "NULL signal pointer");
             if ((reinterpret_cast<uintptr_t>(x[i]) | reinterpret_cast<uintptr_t>(y[i])) & 15u)
                 fail(GFT_ERR_MISALIGNED, "signal pointers must be 16-byte aligned");
+            if (b->kind[i] == 2 && x[i] == y[i]) fail(GFT_ERR_UNSUPPORTED, "tensor-core entries do not run in place");
         }
         cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
         const bool same = b->last_x.size() == (size_t)k &&
                           std::equal(x, x + k, b->last_x.begin()) &&
                           std::equal(y, y + k, b->last_y.begin(), [](float* a, const void* c) { return a == c; });
         if (!same) {
-            upload_desc(*b, x, y, st);
+            // table-driven and wide groups read their pointers from device
+            // descriptors; tensor-core launches carry them as arguments, so
+            // a batch with tensor-core entries is captured again
+            std::vector<const float*> tx, wx;
+            std::vector<float*> ty, wy;
+            for (int i : b->table_users) {
+                tx.push_back(x[i]);
+                ty.push_back(y[i]);
+            }
+            for (int i : b->wide_users) {
+                wx.push_back(x[i]);
+                wy.push_back(y[i]);
+            }
+            if (!b->plans.empty()) upload_desc(*b, tx.data(), ty.data(), st);
+            if (b->wide) wide_batch_upload(b->wide, wx, wy, st);
+            if (!b->tc_users.empty() && b->exec) {
+                cudaGraphExecDestroy(b->exec);
+                cudaGraphDestroy(b->graph);
+                b->exec = nullptr;
+                b->graph = nullptr;
+            }
             b->last_x.assign(x, x + k);
             b->last_y.assign(y, y + k);
         }
         if (!b->exec) {
-            // capture once on a private stream: counter reset + persistent kernel
+            // capture once on a private stream; the groups run on forked
+            // streams and join before the graph ends
             GFT_CUDA(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
             try {
-                launch_batch(*b, b->cap_stream);
+                cudaStream_t cs = b->cap_stream;
+                GFT_CUDA(cudaEventRecord(b->ev_fork, cs));
+                bool used[1 + gft_batch_s::kTcStreams] = {};
+                auto fork = [&](int s) {
+                    if (!used[s]) GFT_CUDA(cudaStreamWaitEvent(b->side[s], b->ev_fork, 0));
+                    used[s] = true;
+                    return b->side[s];
+                };
+                if (b->wide) wide_batch_launch(b->wide, fork(0));
+                for (size_t j = 0; j < b->tc_plans.size(); ++j) {
+                    if (b->tc_batches[j] == 0) continue;
+                    const int u = b->tc_users[j];
+                    launch_tc(*b->tc_plans[j], x[u], y[u], b->tc_batches[j], false, fork(1 + b->tc_stream[j]),
+                              b->precision, b->tc_scratch[b->tc_scr[j]].get());
+                }
+                if (!b->plans.empty()) launch_batch(*b, cs);
+                for (int s = 0; s <= gft_batch_s::kTcStreams; ++s)
+                    if (used[s]) {
+                        GFT_CUDA(cudaEventRecord(b->ev_join[s], b->side[s]));
+                        GFT_CUDA(cudaStreamWaitEvent(cs, b->ev_join[s], 0));
+                    }
             } catch (...) {
                 cudaGraph_t g = nullptr;
                 cudaStreamEndCapture(b->cap_stream, &g);
@@ -395,9 +505,13 @@ gft_status gft_batch_forward(gft_batch_t b, const float* const* x, float* const*
 gft_status gft_batch_get_tile(gft_batch_t b, int32_t i, int32_t* tile, int32_t* threads) {
     return guard_b([&] {
         if (!b || !tile || !threads) fail(GFT_ERR_INVALID_ARG, "NULL argument");
-        if (i < 0 || i >= (int32_t)b->plans.size()) fail(GFT_ERR_INVALID_ARG, "index out of range");
-        *tile = b->rs[i] * kBatchThreads;
-        *threads = kBatchThreads;
+        if (i < 0 || i >= (int32_t)b->kind.size()) fail(GFT_ERR_INVALID_ARG, "index out of range");
+        *tile = 0;
+        *threads = 0;
+        if (b->kind[i] == 0) {
+            *tile = b->rs[b->idx[i]] * kBatchThreads;
+            *threads = kBatchThreads;
+        }
     });
 }
 

@@ -145,12 +145,30 @@ void wide_free(gft_plan_s& p);
 bool wide_ready(const gft_plan_s& p, bool f64);
 void launch_wide_f32(gft_plan_s& p, const float* x, float* y, int64_t batch, bool inverse, cudaStream_t st);
 void launch_wide_f64(gft_plan_s& p, const double* x, double* y, int64_t batch, bool inverse, cudaStream_t st);
+bool wide_configured(const gft_plan_s& p);    // an FP32 wide-leaf configuration exists
+// mixed batches of wide-leaf plans: one persistent FP32 forward launch
+void* wide_batch_create(const std::vector<gft_plan_s*>& plans, const std::vector<int64_t>& batches);
+void wide_batch_upload(void* wb, const std::vector<const float*>& x, const std::vector<float*>& y, cudaStream_t st);
+void wide_batch_launch(void* wb, cudaStream_t st);
+void wide_batch_free(void* wb);
 
 // tc.cu: leaf products on tcgen05 tensor cores (split precision)
 bool tc_eligible(const gft_plan_s& p);
 void tc_build(gft_plan_s& p);
 void tc_free(gft_plan_s& p);
+// Device scratch of the tensor-core path: a plan holds one for its own
+// transforms; a mixed batch holds one per tensor-core plan so that its
+// captured graph never sees the plan's scratch move.
+struct TcScratch {
+    unsigned char* d_aimg = nullptr;   // A images, [tiles][items] x 32 KB
+    float* d_scale = nullptr;          // per-signal FP16 scale
+    float* d_z = nullptr;              // leaf-ordered output (several TMEM groups)
+    size_t rows_cap = 0;
+    void release();
+    ~TcScratch() { release(); }
+};
+void tc_reserve(const gft_plan_s& p, TcScratch& s, int64_t batch);
 void launch_tc(gft_plan_s& p, const float* x, float* y, int64_t batch, bool inverse, cudaStream_t st,
-               uint32_t precision);
+               uint32_t precision, TcScratch* scratch = nullptr);
 
 }  // namespace gft

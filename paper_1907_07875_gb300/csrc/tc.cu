@@ -505,14 +505,11 @@ struct TcPlan {
     __nv_bfloat16* d_blo = nullptr;
     __half* d_fhi = nullptr;
     __half* d_flo = nullptr;
-    unsigned char* d_aimg = nullptr;   // A images, [tiles][items] x 32 KB
-    float* d_scale = nullptr;          // per-signal FP16 scale
-    float* d_z = nullptr;              // leaf-ordered output (several TMEM groups)
-    size_t rows_cap = 0;
+    TcScratch own;                     // the plan's scratch for its own transforms
     ~TcPlan() {
         for (void* p : {(void*)d_leaves, (void*)d_items, (void*)d_colmap, (void*)d_srcmap, (void*)d_term_off,
                         (void*)d_term_src, (void*)d_term_sign, (void*)d_bhi, (void*)d_blo, (void*)d_fhi,
-                        (void*)d_flo, (void*)d_aimg, (void*)d_scale, (void*)d_z})
+                        (void*)d_flo})
             if (p) cudaFree(p);
     }
 };
@@ -669,30 +666,42 @@ void tc_free(gft_plan_s& p) {
     p.tc = nullptr;
 }
 
+// Scratch for batches of up to `batch` signals (A images, FP16 scales,
+// leaf-ordered output in group mode); grows only.  Reserved before a launch
+// that is captured in a CUDA graph, where allocation is not possible.
+void tc_reserve(const gft_plan_s& p, TcScratch& S, int64_t batch) {
+    const TcPlan* T = static_cast<const TcPlan*>(p.tc);
+    if (!T || (size_t)batch <= S.rows_cap) return;
+    S.release();
+    const long long tiles_cap = (batch + kTcM - 1) / kTcM;
+    GFT_CUDA(cudaMalloc(&S.d_aimg, (size_t)tiles_cap * T->n_items * 32768u));
+    GFT_CUDA(cudaMalloc(&S.d_scale, sizeof(float) * (size_t)batch));
+    if (!T->direct) GFT_CUDA(cudaMalloc(&S.d_z, sizeof(float) * (size_t)batch * p.n));
+    S.rows_cap = (size_t)batch;
+}
+
+void TcScratch::release() {
+    for (void** q : {(void**)&d_aimg, (void**)&d_scale, (void**)&d_z})
+        if (*q) {
+            cudaFree(*q);
+            *q = nullptr;
+        }
+    rows_cap = 0;
+}
+
 void launch_tc(gft_plan_s& p, const float* x, float* y, int64_t batch, bool inverse, cudaStream_t st,
-               uint32_t precision) {
+               uint32_t precision, TcScratch* scratch) {
     if (inverse) fail(GFT_ERR_UNSUPPORTED, "tensor-core precisions are implemented for the forward transform");
     if (!p.tc) fail(GFT_ERR_UNSUPPORTED, "tensor-core path needs every leaf to have at most 256 nodes");
     if (x == y) fail(GFT_ERR_UNSUPPORTED, "tensor-core path does not run in place");
     TcPlan* T = static_cast<TcPlan*>(p.tc);
     const int n = p.n;
     const long long n_tiles = (batch + kTcM - 1) / kTcM;
-    if ((size_t)batch > T->rows_cap) {
-        for (void** q : {(void**)&T->d_aimg, (void**)&T->d_scale, (void**)&T->d_z})
-            if (*q) {
-                cudaFree(*q);
-                *q = nullptr;
-            }
-        T->rows_cap = 0;
-        const long long tiles_cap = (batch + kTcM - 1) / kTcM;
-        GFT_CUDA(cudaMalloc(&T->d_aimg, (size_t)tiles_cap * T->n_items * 32768u));
-        GFT_CUDA(cudaMalloc(&T->d_scale, sizeof(float) * (size_t)batch));
-        if (!T->direct) GFT_CUDA(cudaMalloc(&T->d_z, sizeof(float) * (size_t)batch * n));
-        T->rows_cap = (size_t)batch;
-    }
+    TcScratch& S = scratch ? *scratch : T->own;
+    tc_reserve(p, S, batch);
     const int sms = sm_count();
     if (precision == GFT_PREC_FP16X3) {
-        tc_scale_kernel<<<sms * 4, 256, 0, st>>>(x, T->d_scale, batch, n, T->n_stages);
+        tc_scale_kernel<<<sms * 4, 256, 0, st>>>(x, S.d_scale, batch, n, T->n_stages);
         GFT_CUDA(cudaGetLastError());
     }
     {
@@ -710,12 +719,12 @@ void launch_tc(gft_plan_s& p, const float* x, float* y, int64_t batch, bool inve
         const int* soff = d.d_ints + 2 * d.n_pairs;
         const int* labels = d.d_ints + 2 * d.n_pairs + d.n_stages + 1;
         tc_pack_kernel<<<(unsigned)blocks, kPackWarps * 32, smem, st>>>(
-            x, T->d_aimg, batch, n, T->d_leaves, T->d_items, T->n_items, pairs, d.n_pairs, soff, d.n_stages,
-            labels, T->d_scale, (int)precision);
+            x, S.d_aimg, batch, n, T->d_leaves, T->d_items, T->n_items, pairs, d.n_pairs, soff, d.n_stages,
+            labels, S.d_scale, (int)precision);
         GFT_CUDA(cudaGetLastError());
     }
     TcArgs a{};
-    a.y = T->direct ? y : T->d_z;
+    a.y = T->direct ? y : S.d_z;
     a.leaves = T->d_leaves;
     a.colmap = T->d_colmap;
     a.bhi = T->d_bhi;
@@ -754,10 +763,10 @@ void launch_tc(gft_plan_s& p, const float* x, float* y, int64_t batch, bool inve
     if (smem > limit) fail(GFT_ERR_UNSUPPORTED, "tensor-core kernel does not fit in shared memory");
     GFT_CUDA(cudaFuncSetAttribute(tc_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int grid = (int)std::min<long long>(n_tiles, sms);
-    tc_leaf_kernel<<<grid, kTcThreads, smem, st>>>(a, T->d_items, T->n_items, T->d_aimg, T->d_scale, ring);
+    tc_leaf_kernel<<<grid, kTcThreads, smem, st>>>(a, T->d_items, T->n_items, S.d_aimg, S.d_scale, ring);
     GFT_CUDA(cudaGetLastError());
     if (!T->direct) {
-        tc_permute_kernel<<<sms * 8, 256, 0, st>>>(T->d_z, y, batch, n, T->d_srcmap);
+        tc_permute_kernel<<<sms * 8, 256, 0, st>>>(S.d_z, y, batch, n, T->d_srcmap);
         GFT_CUDA(cudaGetLastError());
     }
 }

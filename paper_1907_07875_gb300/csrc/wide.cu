@@ -38,6 +38,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstdlib>
+#include <memory>
 #include <vector>
 
 #include "apply_core.cuh"
@@ -101,14 +102,21 @@ __device__ __forceinline__ void load_chunk(T* dst, const T* src, int elems) {
 }
 
 // One leaf's product over the tile, in place.  M points at the leaf's
-// m x P matrix for this direction.
+// m x P matrix for this direction.  A thread's OC output columns are
+// interleaved in groups of VW (one vector load each): columns
+// VW*(lcol + LC*q) + e, q < OC/VW, e < VW, so that each vector load of a
+// matrix row is contiguous across the LC lanes of a signal group (no bank
+// conflicts).  The next row's operands are loaded before the current row's
+// FMAs are issued.
 template <class T, int RS, int OC>
 __device__ __forceinline__ void wide_leaf(T* tile, int np, int ts, const int* lab, const T* __restrict__ M, int m,
                                           int P, int lc, int kc_rows, T* mbuf, int chunk_elems) {
+    constexpr int VW = (sizeof(T) == 4 ? 4 : 2) < OC ? (sizeof(T) == 4 ? 4 : 2) : OC;   // elements per vector load
+    constexpr int NV = OC / VW;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int lr_cnt = 32 / lc;
     const int lr = lane / lc;
-    const int c0 = (lane - lr * lc) * OC;
+    const int lcol = lane - lr * lc;
     const int sbase = warp * RS * lr_cnt + lr;
     int rowoff[RS];
 #pragma unroll
@@ -119,7 +127,6 @@ __device__ __forceinline__ void wide_leaf(T* tile, int np, int ts, const int* la
 #pragma unroll
         for (int j = 0; j < OC; ++j) acc[i][j] = T(0);
     const int nch = (m + kc_rows - 1) / kc_rows;
-    const int celems = kc_rows * P;
     load_chunk(mbuf, M, min(kc_rows, m) * P);
     cp_async_commit();
     for (int kc = 0; kc < nch; ++kc) {
@@ -130,20 +137,34 @@ __device__ __forceinline__ void wide_leaf(T* tile, int np, int ts, const int* la
         cp_async_commit();
         cp_async_wait1();
         __syncthreads();   // chunk kc visible to every thread
-        const T* Mc = mbuf + (kc & 1) * chunk_elems + c0;
+        const T* Mc = mbuf + (kc & 1) * chunk_elems + VW * lcol;
         const int r0 = kc * kc_rows, rn = min(kc_rows, m - r0);
-#pragma unroll 4
-        for (int r = 0; r < rn; ++r) {
-            const int g = lab[r0 + r];
-            T v[RS];
+        const int* lab_c = lab + r0;
+        T v[RS], w[OC];
+        {
+            const int g = lab_c[0];
 #pragma unroll
             for (int i = 0; i < RS; ++i) v[i] = tile[rowoff[i] + g];
-            T w[OC];
-            load_row<T, OC>(Mc + r * P, w);
+#pragma unroll
+            for (int q = 0; q < NV; ++q) load_row<T, VW>(Mc + q * VW * lc, *reinterpret_cast<T(*)[VW]>(w + q * VW));
+        }
+        for (int r = 0; r < rn; ++r) {
+            T vn[RS], wn[OC];
+            const int rr = min(r + 1, rn - 1);   // the last prefetch re-reads row rn-1 (in bounds)
+            const int g = lab_c[rr];
+#pragma unroll
+            for (int i = 0; i < RS; ++i) vn[i] = tile[rowoff[i] + g];
+#pragma unroll
+            for (int q = 0; q < NV; ++q)
+                load_row<T, VW>(Mc + rr * P + q * VW * lc, *reinterpret_cast<T(*)[VW]>(wn + q * VW));
 #pragma unroll
             for (int i = 0; i < RS; ++i)
 #pragma unroll
                 for (int j = 0; j < OC; ++j) acc[i][j] = fma(v[i], w[j], acc[i][j]);
+#pragma unroll
+            for (int i = 0; i < RS; ++i) v[i] = vn[i];
+#pragma unroll
+            for (int j = 0; j < OC; ++j) w[j] = wn[j];
         }
         __syncthreads();   // every thread done with chunk kc's buffer and (last chunk) with V_k
     }
@@ -151,11 +172,14 @@ __device__ __forceinline__ void wide_leaf(T* tile, int np, int ts, const int* la
     for (int i = 0; i < RS; ++i) {
         if (sbase + i * lr_cnt < ts) {
 #pragma unroll
-            for (int j = 0; j < OC; ++j)
-                if (c0 + j < m) tile[rowoff[i] + lab[c0 + j]] = acc[i][j];
+            for (int q = 0; q < NV; ++q)
+#pragma unroll
+                for (int e = 0; e < VW; ++e) {
+                    const int c = VW * (lcol + lc * q) + e;
+                    if (c < m) tile[rowoff[i] + lab[c]] = acc[i][q * VW + e];
+                }
         }
     }
-    (void)celems;
 }
 
 // variant code = log2(RS) * 5 + log2(OC), RS in {1,2,4,8}, OC in {1,...,16}
@@ -214,28 +238,56 @@ __device__ __forceinline__ void wide_load(const WArgs& a, const int* src_slot, T
     }
 }
 
-template <class T>
-__global__ void __launch_bounds__(kWThreads) gft_wide_kernel(WArgs a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    // [nbuf tiles][2 matrix chunks][pairs 2P][stage_off S+1][labels n][src n][leaf desc]
-    T* tiles = reinterpret_cast<T*>(smem_raw);
-    const int tile_elems = a.ts * a.np;
-    T* mbuf = tiles + a.nbuf * tile_elems;
-    int* s_pairs = reinterpret_cast<int*>(mbuf + 2 * a.chunk_elems);
-    int* s_soff = s_pairs + 2 * a.n_pairs;
-    int* s_lab = s_soff + a.n_stages + 1;
+// Tables of one plan in shared memory:
+// [pairs 2P][stage_off S+1][labels n][src n][leaf desc kWDesc*L]
+__device__ __forceinline__ int wide_ints(const WArgs& a) {
+    return 2 * a.n_pairs + a.n_stages + 1 + 2 * a.n + kWDesc * a.n_leaves;
+}
+__device__ __forceinline__ void wide_load_tables(const WArgs& a, int* s_ints) {
+    const int head = 2 * a.n_pairs + a.n_stages + 1;
+    int* s_lab = s_ints + head;
     int* s_src = s_lab + a.n;
     int* s_desc = s_src + a.n;
-    const int tid = threadIdx.x;
-    for (int i = tid; i < 2 * a.n_pairs + a.n_stages + 1; i += kWThreads) s_pairs[i] = a.ints[i];
-    for (int i = tid; i < a.n; i += kWThreads) {
+    for (int i = threadIdx.x; i < head; i += kWThreads) s_ints[i] = a.ints[i];
+    for (int i = threadIdx.x; i < a.n; i += kWThreads) {
         s_lab[i] = a.ints[a.off_labels + i];
         s_src[i] = a.ints[a.off_src + i];
     }
-    for (int i = tid; i < kWDesc * a.n_leaves; i += kWThreads) s_desc[i] = a.wdesc[i];
-    __syncthreads();
+    for (int i = threadIdx.x; i < kWDesc * a.n_leaves; i += kWThreads) s_desc[i] = a.wdesc[i];
+}
+
+// Stages and leaf products of one tile already in shared memory (forward:
+// stages then leaves; inverse: leaves then stages in reverse).  Ends with a
+// barrier, so the tile is ready for the store.
+template <class T>
+__device__ __forceinline__ void wide_compute(const WArgs& a, T* buf, T* mbuf, const int* s_ints) {
+    const int* s_pairs = s_ints;
+    const int* s_soff = s_pairs + 2 * a.n_pairs;
+    const int* s_lab = s_soff + a.n_stages + 1;
+    const int* s_desc = s_lab + 2 * a.n;
     const T* mats = reinterpret_cast<const T*>(a.mats);
-    const long long n_tiles = (a.batch + a.ts - 1) / a.ts;
+    if (!a.inverse) {
+        for (int s = 0; s < a.n_stages; ++s) {
+            wide_stage(buf, a.np, a.ts, s_pairs, s_soff[s], s_soff[s + 1] - s_soff[s]);
+            __syncthreads();
+        }
+    }
+    for (int k = 0; k < a.n_leaves; ++k) {
+        const int* d = s_desc + kWDesc * k;
+        const T* M = mats + (a.inverse ? d[4] : d[3]);
+        wide_leaf_dispatch<T>(d[5], buf, a.np, a.ts, s_lab + d[2], M, d[0], d[1], d[6], d[7], mbuf, a.chunk_elems);
+    }
+    __syncthreads();   // every leaf's outputs written
+    if (a.inverse) {
+        for (int s = a.n_stages - 1; s >= 0; --s) {
+            wide_stage(buf, a.np, a.ts, s_pairs, s_soff[s], s_soff[s + 1] - s_soff[s]);
+            __syncthreads();
+        }
+    }
+}
+
+template <class T>
+__device__ __forceinline__ KArgs wide_store_args(const WArgs& a) {
     KArgs ka{};
     ka.y = a.y;
     ka.batch = a.batch;
@@ -244,6 +296,22 @@ __global__ void __launch_bounds__(kWThreads) gft_wide_kernel(WArgs a) {
     ka.ts = a.ts;
     ka.inverse = a.inverse;
     ka.inv_n = a.inv_n;
+    return ka;
+}
+
+template <class T>
+__global__ void __launch_bounds__(kWThreads) gft_wide_kernel(WArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    // [nbuf tiles][2 matrix chunks][tables]
+    T* tiles = reinterpret_cast<T*>(smem_raw);
+    const int tile_elems = a.ts * a.np;
+    T* mbuf = tiles + a.nbuf * tile_elems;
+    int* s_ints = reinterpret_cast<int*>(mbuf + 2 * a.chunk_elems);
+    const int* s_src = s_ints + 2 * a.n_pairs + a.n_stages + 1 + a.n;
+    wide_load_tables(a, s_ints);
+    __syncthreads();
+    const long long n_tiles = (a.batch + a.ts - 1) / a.ts;
+    const KArgs ka = wide_store_args<T>(a);
     long long tile = blockIdx.x;
     if (tile < n_tiles) wide_load<T>(a, s_src, tiles, tile);
     cp_async_commit();
@@ -259,25 +327,7 @@ __global__ void __launch_bounds__(kWThreads) gft_wide_kernel(WArgs a) {
             cp_async_wait0();
         }
         __syncthreads();   // tile landed
-        if (!a.inverse) {
-            for (int s = 0; s < a.n_stages; ++s) {
-                wide_stage(buf, a.np, a.ts, s_pairs, s_soff[s], s_soff[s + 1] - s_soff[s]);
-                __syncthreads();
-            }
-        }
-        for (int k = 0; k < a.n_leaves; ++k) {
-            const int* d = s_desc + kWDesc * k;
-            const T* M = mats + (a.inverse ? d[4] : d[3]);
-            wide_leaf_dispatch<T>(d[5], buf, a.np, a.ts, s_lab + d[2], M, d[0], d[1], d[6], d[7], mbuf,
-                                  a.chunk_elems);
-        }
-        __syncthreads();   // every leaf's outputs written
-        if (a.inverse) {
-            for (int s = a.n_stages - 1; s >= 0; --s) {
-                wide_stage(buf, a.np, a.ts, s_pairs, s_soff[s], s_soff[s + 1] - s_soff[s]);
-                __syncthreads();
-            }
-        }
+        wide_compute<T>(a, buf, mbuf, s_ints);
         store_tile<T, kWThreads>(ka, s_src, buf, tile);
         __syncthreads();   // buffer free
         if (a.nbuf == 2) {
@@ -288,6 +338,65 @@ __global__ void __launch_bounds__(kWThreads) gft_wide_kernel(WArgs a) {
         }
     }
     cp_async_wait0();
+}
+
+// Mixed batches: one persistent launch over (plan, tile) items of many
+// wide-leaf plans (FP32 forward).  Every CTA takes the next item from a
+// device counter, finds its plan by binary search over the plans' first item
+// indices, reloads the plan's tables into shared memory when the plan
+// changes, and runs the single-plan tile code.
+struct WBatchPlan {
+    WArgs a;
+    long long item0;
+};
+
+__global__ void __launch_bounds__(kWThreads) gft_wide_batch_kernel(const WBatchPlan* __restrict__ plans, int n_plans,
+                                                                   long long total_items,
+                                                                   unsigned long long* counter, int tile_cap,
+                                                                   int chunk_cap) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* buf = reinterpret_cast<float*>(smem_raw);
+    float* mbuf = buf + tile_cap;
+    int* s_ints = reinterpret_cast<int*>(mbuf + 2 * chunk_cap);
+    __shared__ long long s_item;
+    __shared__ int s_plan;
+    int loaded = -1;
+    while (true) {
+        if (threadIdx.x == 0) {
+            const long long it = (long long)atomicAdd(counter, 1ull);
+            int p = 0;
+            if (it < total_items) {
+                int lo = 0, hi = n_plans - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (plans[mid].item0 <= it) lo = mid;
+                    else hi = mid - 1;
+                }
+                p = lo;
+            }
+            s_item = it;
+            s_plan = p;
+        }
+        __syncthreads();
+        const long long it = s_item;
+        const int p = s_plan;
+        if (it >= total_items) break;
+        const WArgs a = plans[p].a;
+        if (p != loaded) {
+            wide_load_tables(a, s_ints);
+            __syncthreads();
+            loaded = p;
+        }
+        const int* s_src = s_ints + 2 * a.n_pairs + a.n_stages + 1 + a.n;
+        const long long tile = it - plans[p].item0;
+        wide_load<float>(a, s_src, buf, tile);
+        cp_async_commit();
+        cp_async_wait0();
+        __syncthreads();
+        wide_compute<float>(a, buf, mbuf, s_ints);
+        store_tile<float, kWThreads>(wide_store_args<float>(a), s_src, buf, tile);
+        __syncthreads();   // tile buffer and s_item free
+    }
 }
 
 int pow2_at_least(int v) {
@@ -470,6 +579,11 @@ void wide_free(gft_plan_s& p) {
     p.wide = nullptr;
 }
 
+bool wide_configured(const gft_plan_s& p) {
+    const WidePlan* W = static_cast<const WidePlan*>(p.wide);
+    return W && W->cfg[0].ts > 0;
+}
+
 bool wide_ready(const gft_plan_s& p, bool f64) {
     const WidePlan* W = static_cast<const WidePlan*>(p.wide);
     return W && W->cfg[f64 ? 1 : 0].use;
@@ -562,6 +676,103 @@ static void launch_wide_t(gft_plan_s& p, const T* x, T* y, int64_t batch, bool i
     fn<<<(unsigned)grid, kWThreads, c.smem, st>>>(a);
     GFT_CUDA(cudaGetLastError());
 }
+
+// ---------------------------------------------------------------------------
+// mixed batches of wide-leaf plans (FP32 forward)
+// ---------------------------------------------------------------------------
+namespace {
+struct WideBatch {
+    std::vector<WBatchPlan> desc;   // slot order (decreasing cost per item)
+    std::vector<int> order;         // slot -> index in the caller's list
+    WBatchPlan* d_desc = nullptr;
+    unsigned long long* d_counter = nullptr;
+    long long total_items = 0;
+    int tile_cap = 0, chunk_cap = 0;
+    size_t smem = 0;
+    int grid = 0;
+    ~WideBatch() {
+        if (d_desc) cudaFree(d_desc);
+        if (d_counter) cudaFree(d_counter);
+    }
+};
+}  // namespace
+
+void* wide_batch_create(const std::vector<gft_plan_s*>& plans, const std::vector<int64_t>& batches) {
+    std::unique_ptr<WideBatch> B(new WideBatch);
+    const int k = (int)plans.size();
+    std::vector<WBatchPlan> d(k);
+    std::vector<double> cost(k);
+    int ints_cap = 0;
+    for (int i = 0; i < k; ++i) {
+        gft_plan_s& p = *plans[i];
+        WidePlan* W = static_cast<WidePlan*>(p.wide);
+        if (!W || !W->cfg[0].ts) fail(GFT_ERR_UNSUPPORTED, "plan has no wide-leaf kernel configuration");
+        const auto& c = W->cfg[0];
+        WArgs& a = d[i].a;
+        a = WArgs{};
+        a.ints = p.dev.d_ints;
+        a.wdesc = c.d_desc;
+        a.mats = W->d_m32;
+        a.batch = batches[i];
+        a.n = p.n;
+        a.np = row_stride(p.n, 4);
+        a.ts = c.ts;
+        a.nbuf = 1;
+        a.n_pairs = p.dev.n_pairs;
+        a.n_stages = p.dev.n_stages;
+        a.n_leaves = p.dev.n_leaves;
+        a.off_labels = 2 * p.dev.n_pairs + p.dev.n_stages + 1;
+        a.off_src = a.off_labels + 2 * p.n;
+        a.chunk_elems = c.chunk_elems;
+        a.inverse = 0;
+        a.inv_n = 1.0f / (float)p.n;
+        double fl = 0;
+        for (auto& lf : p.leaves) fl += (double)lf.m() * lf.m();
+        cost[i] = (fl + 8.0 * p.n) * c.ts;
+        B->tile_cap = std::max(B->tile_cap, c.ts * a.np);
+        B->chunk_cap = std::max(B->chunk_cap, c.chunk_elems);
+        ints_cap = std::max(ints_cap, 2 * a.n_pairs + a.n_stages + 1 + 2 * a.n + kWDesc * a.n_leaves);
+    }
+    B->order.resize(k);
+    for (int i = 0; i < k; ++i) B->order[i] = i;
+    std::stable_sort(B->order.begin(), B->order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    for (int slot = 0; slot < k; ++slot) {
+        WBatchPlan e = d[B->order[slot]];
+        e.item0 = B->total_items;
+        B->total_items += (e.a.batch + e.a.ts - 1) / e.a.ts;
+        B->desc.push_back(e);
+    }
+    B->smem = sizeof(float) * ((size_t)B->tile_cap + 2 * (size_t)B->chunk_cap) + sizeof(int) * (size_t)ints_cap;
+    if (B->smem > (size_t)kWSmemLimit) fail(GFT_ERR_UNSUPPORTED, "mixed batch of wide plans needs too much shared memory");
+    GFT_CUDA(cudaMalloc(&B->d_desc, sizeof(WBatchPlan) * std::max(1, k)));
+    GFT_CUDA(cudaMalloc(&B->d_counter, sizeof(unsigned long long)));
+    GFT_CUDA(cudaFuncSetAttribute(gft_wide_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B->smem));
+    int per_sm = 0;
+    GFT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gft_wide_batch_kernel, kWThreads, B->smem));
+    if (per_sm < 1) fail(GFT_ERR_UNSUPPORTED, "wide mixed-batch kernel does not fit on an SM");
+    B->grid = per_sm * sm_count();
+    return B.release();
+}
+
+void wide_batch_upload(void* h, const std::vector<const float*>& x, const std::vector<float*>& y, cudaStream_t st) {
+    WideBatch* B = static_cast<WideBatch*>(h);
+    for (size_t slot = 0; slot < B->desc.size(); ++slot) {
+        B->desc[slot].a.x = x[B->order[slot]];
+        B->desc[slot].a.y = y[B->order[slot]];
+    }
+    GFT_CUDA(cudaMemcpyAsync(B->d_desc, B->desc.data(), sizeof(WBatchPlan) * B->desc.size(), cudaMemcpyHostToDevice, st));
+}
+
+void wide_batch_launch(void* h, cudaStream_t st) {
+    WideBatch* B = static_cast<WideBatch*>(h);
+    GFT_CUDA(cudaMemsetAsync(B->d_counter, 0, sizeof(unsigned long long), st));
+    if (B->total_items == 0) return;
+    gft_wide_batch_kernel<<<B->grid, kWThreads, B->smem, st>>>(B->d_desc, (int)B->desc.size(), B->total_items,
+                                                             B->d_counter, B->tile_cap, B->chunk_cap);
+    GFT_CUDA(cudaGetLastError());
+}
+
+void wide_batch_free(void* h) { delete static_cast<WideBatch*>(h); }
 
 void launch_wide_f32(gft_plan_s& p, const float* x, float* y, int64_t batch, bool inverse, cudaStream_t st) {
     launch_wide_t<float>(p, x, y, batch, inverse, st);

@@ -91,10 +91,61 @@ def test_many_small_graphs_and_empty_batches(env):
             assert torch.equal(y, p.forward(x))
 
 
-def test_batch_rejects_wide_leaves(env):
+def test_batch_rejects_leaves_over_512(env):
     gft, torch = env
-    g = W.grid(32)
+    g = W.path(1100)                                   # two leaves of 550 nodes
     p = gft.Plan(gft.laplacian(g.W, g.s), g.phis)
     with pytest.raises(gft.GftError) as e:
         gft.Batch([p], [10])
     assert e.value.status == "GFT_ERR_UNSUPPORTED"
+
+
+def _config3_plans(gft, coeffs):
+    kinds = W.config3(coeffs_per_kind=coeffs)
+    graphs = [k[0] for k in kinds]
+    batches = [k[1] + 5 for k in kinds]                # ragged tails
+    plans = [gft.Plan(gft.laplacian(g.W, g.s), g.phis) for g in graphs]
+    return graphs, batches, plans
+
+
+def test_config3_all_kinds_fp32_one_graph(env):
+    """All eight grid / cycle kinds of the mixed workload, grid32 (leaves of
+    256) included, in one graph launch: table-driven and wide-leaf groups.
+    Every output equals its plan's own forward bit for bit (same kernel code
+    and tile shape), which the single-plan tests pin to the oracle."""
+    gft, torch = env
+    graphs, batches, plans = _config3_plans(gft, 1 << 18)
+    b = gft.Batch(plans, batches)
+    xs = [torch.from_numpy(W.signals(bt, g.n, 60 + i)).cuda() for i, (g, bt) in enumerate(zip(graphs, batches))]
+    ys = [torch.full_like(x, float("nan")) for x in xs]
+    for _ in range(2):
+        b.forward(xs, ys)
+    torch.cuda.synchronize()
+    for p, x, y in zip(plans, xs, ys):
+        assert torch.equal(y, p.forward(x))
+    assert any(p.info["wide"] for p in plans)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "bf16x3", "fp16x3"])
+def test_config3_tensor_core_precisions_one_graph(env, prec):
+    """The mixed workload in a tensor-core precision: grids 16/32 and the
+    256-cycle (leaves of 64 and 256) on the tensor cores, the rest on CUDA
+    cores, in one graph launch; a plan appears twice (its two entries share
+    its scratch and run in order).  Outputs equal the single-plan forwards
+    in the same precision bit for bit; new pointers re-capture the graph."""
+    gft, torch = env
+    graphs, batches, plans = _config3_plans(gft, 1 << 17)
+    graphs.append(graphs[2])
+    plans.append(plans[2])
+    batches.append(300)
+    b = gft.Batch(plans, batches, precision=prec)
+    for rep in range(2):
+        xs = [torch.from_numpy(W.signals(bt, g.n, 90 + 7 * rep + i)).cuda()
+              for i, (g, bt) in enumerate(zip(graphs, batches))]
+        ys = [torch.full_like(x, float("nan")) for x in xs]
+        b.forward(xs, ys)
+        b.forward(xs, ys)
+        torch.cuda.synchronize()
+        for p, x, y in zip(plans, xs, ys):
+            tc = p.info["max_leaf"] >= 64
+            assert torch.equal(y, p.forward(x, precision=prec if tc else "fp32"))
