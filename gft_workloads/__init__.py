@@ -27,7 +27,8 @@ __all__ = [
     "star", "complete", "near_symmetric_path", "near_symmetric_grid",
     "planted_symmetric", "reversal", "cycle_second_reflection", "grid_lr",
     "grid_ud", "grid_diag", "grid_antidiag", "grid_centro", "involution_count",
-    "all_involutions", "config1", "config2", "config3", "config4", "config5",
+    "all_involutions", "config1", "config2", "config3", "config4", "config5", "config5_specs",
+    "make_graph",
 ]
 
 
@@ -357,27 +358,52 @@ def config4():
     return out
 
 
-def config5(n_graphs: int = 10000, total_coeffs: int = 1 << 28, seed: int = 2005):
-    """Size sweep: graphs of sizes 8..1024 (log-uniform per family) from the
-    path, cycle, grid, skeleton and bipartite families; returns
-    (graph, batch, signal_seed) with ceil(total/(n_graphs*n)) signals each."""
+def config5_specs(n_graphs: int = 10000, total_coeffs: int = 1 << 28, seed: int = 2005):
+    """Size sweep recipe without building the graphs: graphs of sizes 8..1024
+    (log-uniform per family) from the path, cycle, grid, skeleton and
+    bipartite families.  Returns (family, n, graph_seed, batch, signal_seed)
+    tuples with ceil(total / (n_graphs * n)) signals each; graph_seed is
+    None for the deterministic families.  ``make_graph`` builds one."""
     rng = np.random.default_rng(seed)
     fams = ("path", "cycle", "grid", "skeleton", "bipartite")
     out = []
     for gi in range(n_graphs):
         fam = fams[gi % len(fams)]
         n = int(round(np.exp(rng.uniform(np.log(8), np.log(1024)))))
+        gseed = None
         if fam == "path":
-            g = path(max(n, 2))
+            n = max(n, 2)
         elif fam == "cycle":
-            g = cycle(max(4, n - n % 4))
+            n = max(4, n - n % 4)
         elif fam == "grid":
             N = max(2, int(round(np.sqrt(n))))
-            g = grid(N)
+            n = N * N
         elif fam == "skeleton":
-            g = skeleton25()
+            n = 25
         else:
-            g = bipartite(max(8, n - n % 2), seed=int(rng.integers(1 << 31)))
-        b = -(-total_coeffs // (n_graphs * g.n))
-        out.append((g, b, 1005 * 100000 + gi))
+            n = max(8, n - n % 2)
+            gseed = int(rng.integers(1 << 31))
+        b = -(-total_coeffs // (n_graphs * n))
+        out.append((fam, n, gseed, b, 1005 * 100000 + gi))
     return out
+
+
+def make_graph(family: str, n: int, graph_seed: Optional[int] = None) -> Graph:
+    if family == "path":
+        return path(n)
+    if family == "cycle":
+        return cycle(n)
+    if family == "grid":
+        N = int(round(np.sqrt(n)))
+        return grid(N)
+    if family == "skeleton":
+        return skeleton25()
+    if family == "bipartite":
+        return bipartite(n, seed=graph_seed)
+    raise ValueError(family)
+
+
+def config5(n_graphs: int = 10000, total_coeffs: int = 1 << 28, seed: int = 2005):
+    """The size sweep as (graph, batch, signal_seed) triples (builds every
+    graph: use ``config5_specs`` for the full 10^4-graph recipe)."""
+    return [(make_graph(f, n, gs), b, ss) for f, n, gs, b, ss in config5_specs(n_graphs, total_coeffs, seed)]

@@ -120,7 +120,9 @@ gft_status gft_laplacian_from_weights(int32_t n, const double* W, const double* 
  * call also generates a kernel specialised to this plan (indices and
  * folded leaf matrices as constants), compiles it with NVRTC for sm_103a,
  * and times several launch shapes on a scratch batch to keep the fastest;
- * transforms then use it.  Otherwise, when some leaf has more than 32 nodes
+ * transforms then use it.  The tensor-core data (pre-split leaf bases) is
+ * built on the first tensor-core transform; make that first call outside
+ * any stream capture.  Otherwise, when some leaf has more than 32 nodes
  * (up to 512), a wide-leaf kernel computes each tile's leaf products as a
  * register-blocked GEMM of the whole CTA; for leaves of at most 64 nodes the
  * call times it against the table-driven kernel and keeps the faster
@@ -134,6 +136,20 @@ gft_status gft_laplacian_from_weights(int32_t n, const double* W, const double* 
  */
 gft_status gft_plan_create(int32_t n, const double* L, int32_t n_stages, const int32_t* phi,
                            uint32_t flags, gft_plan_t* out);
+
+/*
+ * Build `count` plans at once (same meaning per plan as gft_plan_create):
+ * n[i], L[i] (host pointers), n_stages[i], phi[i] (host pointer, NULL when
+ * n_stages[i] = 0; phi itself may be NULL when every n_stages[i] = 0).  The
+ * graphs are decomposed on the host and the leaves of ALL of them are
+ * eigendecomposed in one batched FP64 Jacobi solve on the device (leaves
+ * grouped by size; the largest on their own stream), which is what makes
+ * building thousands of plans practical.  All or nothing: on any error no
+ * plan is returned and out is unchanged.  out[count] receives the plans.
+ */
+gft_status gft_plan_create_many(int32_t count, const int32_t* n, const double* const* L,
+                                const int32_t* n_stages, const int32_t* const* phi, uint32_t flags,
+                                gft_plan_t* out);
 
 /* Free a plan and its device memory (NULL is accepted).  The caller must
  * make sure no transform using the plan is still running. */

@@ -105,6 +105,13 @@ class Plan:
         self._h = h
         self.n = n
 
+    @classmethod
+    def _wrap(cls, handle, n):
+        obj = cls.__new__(cls)
+        obj._h = handle
+        obj.n = n
+        return obj
+
     # -- lifetime ------------------------------------------------------------
     def close(self):
         if getattr(self, "_h", None):
@@ -223,6 +230,27 @@ class Plan:
         v = C.c_int32(0)
         _check(lib().gft_device_error(self._h, C.byref(v)))
         return v.value
+
+
+def plans_from_laplacians(Ls, phis_list, *, split_components: bool = False, order_block: bool = False,
+                          analyze_only: bool = False, jit: bool = True, kernel: str = "auto"):
+    """Many plans at once (gft_plan_create_many): every graph's leaves are
+    eigendecomposed in one batched Jacobi solve on the device."""
+    k = len(Ls)
+    Ls = [_as_f64(L) for L in Ls]
+    phs = [(np.ascontiguousarray(np.stack([np.asarray(p, dtype=np.int32) for p in ph])) if len(ph) else None)
+           for ph in phis_list]
+    ns = np.array([L.shape[0] for L in Ls], dtype=np.int32)
+    st = np.array([len(ph) for ph in phis_list], dtype=np.int32)
+    Lp = (C.c_void_p * k)(*[L.ctypes.data for L in Ls])
+    Pp = (C.c_void_p * k)(*[(p.ctypes.data if p is not None else None) for p in phs])
+    flags = ((SPLIT_COMPONENTS if split_components else 0) | (ORDER_BLOCK if order_block else 0)
+             | (ANALYZE_ONLY if analyze_only else 0) | (0 if jit else NO_JIT)
+             | {"auto": 0, "table": KERNEL_TABLE, "wide": KERNEL_WIDE}[kernel])
+    out = (C.c_void_p * k)()
+    _check(lib().gft_plan_create_many(k, _ptr(ns), C.cast(Lp, C.c_void_p), _ptr(st), C.cast(Pp, C.c_void_p),
+                                      flags, C.cast(out, C.c_void_p)))
+    return [Plan._wrap(C.c_void_p(out[i]), int(ns[i])) for i in range(k)]
 
 
 class Batch:
@@ -344,4 +372,4 @@ def givens_apply(x, theta, net: Givens):
 
 __all__ = ["Plan", "Batch", "Givens", "givens_apply", "laplacian", "GftError", "lib",
            "SPLIT_COMPONENTS", "ORDER_BLOCK", "ANALYZE_ONLY", "NO_JIT", "KERNEL_TABLE",
-           "KERNEL_WIDE", "PRECISIONS"]
+           "KERNEL_WIDE", "PRECISIONS", "plans_from_laplacians"]

@@ -32,6 +32,7 @@ SIGNATURES = {
     "gft_version": (C.c_int32, []),
     "gft_laplacian_from_weights": (c_status, [C.c_int32, P, P, P]),
     "gft_plan_create": (c_status, [C.c_int32, P, C.c_int32, P, C.c_uint32, C.POINTER(c_plan)]),
+    "gft_plan_create_many": (c_status, [C.c_int32, P, P, P, P, C.c_uint32, P]),
     "gft_plan_destroy": (c_status, [c_plan]),
     "gft_plan_get_info": (c_status, [c_plan, C.POINTER(PlanInfo)]),
     "gft_plan_get_stage_pairs": (c_status, [c_plan, C.c_int32, P, I32P]),

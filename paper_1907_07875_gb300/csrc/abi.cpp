@@ -8,6 +8,7 @@
 #include <memory>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "gft_internal.h"
 
@@ -118,42 +119,92 @@ gft_status gft_laplacian_from_weights(int32_t n, const double* W, const double* 
     });
 }
 
+}  // extern "C"
+
+namespace gft {
+namespace {
+
+void check_create_args(int32_t n, const double* L, int32_t n_stages, const int32_t* phi, uint32_t flags) {
+    if (n < 1 || n > 4096) fail(GFT_ERR_INVALID_ARG, "n must be in [1, 4096]");
+    if (!L) fail(GFT_ERR_INVALID_ARG, "L is NULL");
+    if (n_stages < 0 || n_stages > 16) fail(GFT_ERR_INVALID_ARG, "n_stages must be in [0, 16]");
+    if (n_stages > 0 && !phi) fail(GFT_ERR_INVALID_ARG, "phi is NULL");
+    if (flags & ~(GFT_SPLIT_COMPONENTS | GFT_ORDER_BLOCK | GFT_ANALYZE_ONLY | GFT_NO_JIT | GFT_KERNEL_TABLE |
+                  GFT_KERNEL_WIDE))
+        fail(GFT_ERR_INVALID_ARG, "unknown flag");
+    if ((flags & GFT_KERNEL_TABLE) && (flags & GFT_KERNEL_WIDE))
+        fail(GFT_ERR_INVALID_ARG, "GFT_KERNEL_TABLE and GFT_KERNEL_WIDE are exclusive");
+}
+
+// Decompose every graph on the host, eigendecompose all their leaves in one
+// batched Jacobi solve on the device, then finish and upload each plan.
+void create_plans(int32_t count, const int32_t* ns, const double* const* Ls, const int32_t* n_stages,
+                  const int32_t* const* phis, uint32_t flags, gft_plan_t* out) {
+    for (int i = 0; i < count; ++i)
+        check_create_args(ns[i], Ls[i], n_stages[i], phis ? phis[i] : nullptr, flags);
+    std::vector<std::unique_ptr<gft_plan_s>> made;
+    for (int i = 0; i < count; ++i) {
+        std::unique_ptr<gft_plan_s> p(new gft_plan_s);
+        p->n = ns[i];
+        p->flags = flags;
+        analyze(*p, Ls[i], n_stages[i], phis ? phis[i] : nullptr);
+        made.push_back(std::move(p));
+    }
+    if (!(flags & GFT_ANALYZE_ONLY)) {
+        int dev = 0;
+        GFT_CUDA(cudaGetDevice(&dev));
+        std::vector<Leaf*> all;
+        for (auto& p : made) {
+            p->device = dev;
+            for (auto& lf : p->leaves) all.push_back(&lf);
+        }
+        cudaStream_t st = nullptr;
+        GFT_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        try {
+            jacobi_leaf_ptrs(all, st);
+        } catch (...) {
+            cudaStreamDestroy(st);
+            throw;
+        }
+        GFT_CUDA(cudaStreamDestroy(st));
+        for (auto& p : made) {
+            finalize_host(*p);
+            upload_plan(*p);
+            jit_build(*p);
+            wide_build(*p);
+        }
+        GFT_CUDA(cudaDeviceSynchronize());
+    }
+    for (int i = 0; i < count; ++i) out[i] = made[i].release();
+}
+
+}  // namespace
+}  // namespace gft
+
+extern "C" {
+
 gft_status gft_plan_create(int32_t n, const double* L, int32_t n_stages, const int32_t* phi,
                            uint32_t flags, gft_plan_t* out) {
     return guard([&] {
         if (!out) fail(GFT_ERR_INVALID_ARG, "out is NULL");
-        if (n < 1 || n > 4096) fail(GFT_ERR_INVALID_ARG, "n must be in [1, 4096]");
-        if (!L) fail(GFT_ERR_INVALID_ARG, "L is NULL");
-        if (n_stages < 0 || n_stages > 16) fail(GFT_ERR_INVALID_ARG, "n_stages must be in [0, 16]");
-        if (n_stages > 0 && !phi) fail(GFT_ERR_INVALID_ARG, "phi is NULL");
-        if (flags & ~(GFT_SPLIT_COMPONENTS | GFT_ORDER_BLOCK | GFT_ANALYZE_ONLY | GFT_NO_JIT | GFT_KERNEL_TABLE |
-                      GFT_KERNEL_WIDE))
-            fail(GFT_ERR_INVALID_ARG, "unknown flag");
-        if ((flags & GFT_KERNEL_TABLE) && (flags & GFT_KERNEL_WIDE))
-            fail(GFT_ERR_INVALID_ARG, "GFT_KERNEL_TABLE and GFT_KERNEL_WIDE are exclusive");
-        std::unique_ptr<gft_plan_s> p(new gft_plan_s);
-        p->n = n;
-        p->flags = flags;
-        analyze(*p, L, n_stages, phi);
-        if (!(flags & GFT_ANALYZE_ONLY)) {
-            GFT_CUDA(cudaGetDevice(&p->device));
-            cudaStream_t st = nullptr;
-            GFT_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
-            try {
-                jacobi_leaves(p->leaves, st);
-            } catch (...) {
-                cudaStreamDestroy(st);
-                throw;
-            }
-            GFT_CUDA(cudaStreamDestroy(st));
-            finalize_host(*p);
-            upload_plan(*p);
-            jit_build(*p);
-            tc_build(*p);
-            wide_build(*p);
-            GFT_CUDA(cudaDeviceSynchronize());
-        }
-        *out = p.release();
+        const int32_t* phis[1] = {phi};
+        create_plans(1, &n, &L, &n_stages, phis, flags, out);
+    });
+}
+
+gft_status gft_plan_create_many(int32_t count, const int32_t* n, const double* const* L,
+                                const int32_t* n_stages, const int32_t* const* phi, uint32_t flags,
+                                gft_plan_t* out) {
+    return guard([&] {
+        if (!out || !n || !L || !n_stages) fail(GFT_ERR_INVALID_ARG, "NULL argument");
+        if (count < 0) fail(GFT_ERR_INVALID_ARG, "count < 0");
+        if (count == 0) return;
+        bool any_stage = false;
+        for (int i = 0; i < count; ++i) any_stage |= n_stages[i] > 0;
+        if (any_stage && !phi) fail(GFT_ERR_INVALID_ARG, "phi is NULL");
+        std::vector<gft_plan_t> tmp(count, nullptr);
+        create_plans(count, n, L, n_stages, phi, flags, tmp.data());
+        std::copy(tmp.begin(), tmp.end(), out);
     });
 }
 

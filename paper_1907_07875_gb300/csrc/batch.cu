@@ -371,7 +371,7 @@ gft_status gft_batch_create(int32_t n_plans, const gft_plan_t* plans, const int6
             int max_leaf = 0;
             for (auto& lf : p->leaves) max_leaf = std::max(max_leaf, lf.m());
             int kind;
-            if (b->precision != GFT_PREC_FP32 && p->tc && max_leaf >= kTcMinLeaf) kind = 2;
+            if (b->precision != GFT_PREC_FP32 && tc_eligible(*p) && max_leaf >= kTcMinLeaf) kind = 2;
             else if (p->dev.max_bucket != 0 && !(wide_configured(*p) && wide_ready(*p, false))) kind = 0;
             else if (wide_configured(*p)) kind = 1;
             else fail(GFT_ERR_UNSUPPORTED, "plan " + std::to_string(i) + " has a leaf wider than 512 nodes");

@@ -111,6 +111,7 @@ void free_device(gft_plan_s& p);
 
 // jacobi.cu: eigendecompose every leaf on the current device (FP64).
 void jacobi_leaves(std::vector<Leaf>& leaves, cudaStream_t stream);
+void jacobi_leaf_ptrs(const std::vector<Leaf*>& leaves, cudaStream_t stream);   // leaves of many plans
 
 // apply.cu
 struct ApplyArgs {
@@ -167,7 +168,7 @@ struct TcScratch {
     void release();
     ~TcScratch() { release(); }
 };
-void tc_reserve(const gft_plan_s& p, TcScratch& s, int64_t batch);
+void tc_reserve(gft_plan_s& p, TcScratch& s, int64_t batch);   // builds the tensor-core data on first use
 void launch_tc(gft_plan_s& p, const float* x, float* y, int64_t batch, bool inverse, cudaStream_t st,
                uint32_t precision, TcScratch* scratch = nullptr);
 

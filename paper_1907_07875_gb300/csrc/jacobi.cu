@@ -14,6 +14,7 @@
 // scratch copy.  Plan build only: nothing here is on the transform path.
 #include <algorithm>
 #include <cmath>
+#include <memory>
 #include <numeric>
 #include <vector>
 
@@ -212,74 +213,122 @@ struct DevBuf {
     }
     DevBuf(const DevBuf&) = delete;
     DevBuf& operator=(const DevBuf&) = delete;
+    DevBuf(DevBuf&& o) noexcept : p(o.p) { o.p = nullptr; }
+    DevBuf& operator=(DevBuf&& o) noexcept {
+        if (this != &o) {
+            if (p) cudaFree(p);
+            p = o.p;
+            o.p = nullptr;
+        }
+        return *this;
+    }
 };
 
 }  // namespace
 
-void jacobi_leaves(std::vector<Leaf>& leaves, cudaStream_t stream) {
-    // group the leaves: 1x1 on the host, small in shared memory, large in global
-    std::vector<int> small, large;
+// Every leaf of every plan in one batched solve: 1x1 leaves on the host,
+// the others grouped by size (shared-memory kernel for m <= 16, 32, 64,
+// 110, so each launch sizes its shared memory to its own largest leaf; the
+// global-memory kernel above) -- the large group on its own stream, so it
+// overlaps the small ones.
+void jacobi_leaf_ptrs(const std::vector<Leaf*>& leaves, cudaStream_t stream) {
+    std::vector<std::vector<int>> groups(5);
+    const int lim[4] = {16, 32, 64, kSmemMaxM};
     for (size_t k = 0; k < leaves.size(); ++k) {
-        Leaf& lf = leaves[k];
+        Leaf& lf = *leaves[k];
         const int m = lf.m();
         if (m == 1) {
             lf.lam = {lf.L[0]};
             lf.V = {1.0};
             lf.sweeps = 0;
-        } else if (m <= kSmemMaxM) {
-            small.push_back((int)k);
-        } else {
-            large.push_back((int)k);
+            continue;
         }
+        int g = 4;
+        for (int b = 0; b < 4; ++b)
+            if (m <= lim[b]) {
+                g = b;
+                break;
+            }
+        groups[g].push_back((int)k);
     }
-    auto run = [&](const std::vector<int>& ids, bool in_smem) {
-        if (ids.empty()) return;
+    struct Run {
+        std::vector<int> ids;
         std::vector<JacobiJob> jobs;
-        long long total = 0;
-        int maxm = 0;
-        for (int k : ids) {
-            const int m = leaves[k].m();
-            jobs.push_back({m, in_smem ? (m | 1) : m, total});
-            total += (long long)m * m;
-            maxm = std::max(maxm, m);
+        std::vector<double> hA, hV;
+        std::vector<int> hS, hOk;
+        DevBuf<double> dA, dV;
+        DevBuf<JacobiJob> dJ;
+        DevBuf<int> dS, dOk;
+    };
+    cudaStream_t big = nullptr;
+    GFT_CUDA(cudaStreamCreateWithFlags(&big, cudaStreamNonBlocking));
+    std::vector<std::unique_ptr<Run>> runs;
+    try {
+        for (int g = 4; g >= 0; --g) {   // large leaves first: they take longest
+            if (groups[g].empty()) continue;
+            const bool in_smem = g < 4;
+            cudaStream_t st = in_smem ? stream : big;
+            std::unique_ptr<Run> R(new Run);
+            R->ids = groups[g];
+            long long total = 0;
+            int maxm = 0;
+            for (int k : R->ids) {
+                const int m = leaves[k]->m();
+                R->jobs.push_back({m, in_smem ? (m | 1) : m, total});
+                total += (long long)m * m;
+                maxm = std::max(maxm, m);
+            }
+            R->hA.resize((size_t)total);
+            for (size_t j = 0; j < R->ids.size(); ++j) {
+                const Leaf& lf = *leaves[R->ids[j]];
+                std::copy(lf.L.begin(), lf.L.end(), R->hA.begin() + R->jobs[j].off);
+            }
+            const int B = (int)R->ids.size();
+            R->dA = DevBuf<double>(total);
+            R->dV = DevBuf<double>(total);
+            R->dJ = DevBuf<JacobiJob>(B);
+            R->dS = DevBuf<int>(B);
+            R->dOk = DevBuf<int>(B);
+            GFT_CUDA(cudaMemcpyAsync(R->dA.p, R->hA.data(), sizeof(double) * total, cudaMemcpyHostToDevice, st));
+            GFT_CUDA(cudaMemcpyAsync(R->dJ.p, R->jobs.data(), sizeof(JacobiJob) * B, cudaMemcpyHostToDevice, st));
+            const size_t aux = sizeof(double) * ((maxm + 1) + 32) + sizeof(int) * (maxm + 1);
+            if (in_smem) {
+                const int ld = maxm | 1;
+                const size_t smem = sizeof(double) * 2 * (size_t)maxm * ld + aux;
+                GFT_CUDA(cudaFuncSetAttribute(jacobi_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+                const int threads = maxm <= 32 ? 128 : 256;
+                jacobi_smem_kernel<<<B, threads, smem, st>>>(R->dJ.p, R->dA.p, R->dV.p, R->dS.p, R->dOk.p);
+            } else {
+                jacobi_global_kernel<<<B, 1024, aux, st>>>(R->dJ.p, R->dA.p, R->dV.p, R->dS.p, R->dOk.p);
+            }
+            GFT_CUDA(cudaGetLastError());
+            R->hV.resize((size_t)total);
+            R->hS.resize(B);
+            R->hOk.resize(B);
+            GFT_CUDA(cudaMemcpyAsync(R->hA.data(), R->dA.p, sizeof(double) * total, cudaMemcpyDeviceToHost, st));
+            GFT_CUDA(cudaMemcpyAsync(R->hV.data(), R->dV.p, sizeof(double) * total, cudaMemcpyDeviceToHost, st));
+            GFT_CUDA(cudaMemcpyAsync(R->hS.data(), R->dS.p, sizeof(int) * B, cudaMemcpyDeviceToHost, st));
+            GFT_CUDA(cudaMemcpyAsync(R->hOk.data(), R->dOk.p, sizeof(int) * B, cudaMemcpyDeviceToHost, st));
+            runs.push_back(std::move(R));
         }
-        std::vector<double> hA((size_t)total);
-        for (size_t j = 0; j < ids.size(); ++j) {
-            const Leaf& lf = leaves[ids[j]];
-            std::copy(lf.L.begin(), lf.L.end(), hA.begin() + jobs[j].off);
-        }
-        const int B = (int)ids.size();
-        DevBuf<double> dA(total), dV(total);
-        DevBuf<JacobiJob> dJ(B);
-        DevBuf<int> dS(B), dOk(B);
-        GFT_CUDA(cudaMemcpyAsync(dA.p, hA.data(), sizeof(double) * total, cudaMemcpyHostToDevice, stream));
-        GFT_CUDA(cudaMemcpyAsync(dJ.p, jobs.data(), sizeof(JacobiJob) * B, cudaMemcpyHostToDevice, stream));
-        const size_t aux = sizeof(double) * ((maxm + 1) + 32) + sizeof(int) * (maxm + 1);
-        if (in_smem) {
-            const int ld = maxm | 1;
-            const size_t smem = sizeof(double) * 2 * (size_t)maxm * ld + aux;
-            GFT_CUDA(cudaFuncSetAttribute(jacobi_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            const int threads = maxm <= 32 ? 128 : 256;
-            jacobi_smem_kernel<<<B, threads, smem, stream>>>(dJ.p, dA.p, dV.p, dS.p, dOk.p);
-        } else {
-            jacobi_global_kernel<<<B, 1024, aux, stream>>>(dJ.p, dA.p, dV.p, dS.p, dOk.p);
-        }
-        GFT_CUDA(cudaGetLastError());
-        std::vector<double> hV((size_t)total);
-        std::vector<int> hS(B), hOk(B);
-        GFT_CUDA(cudaMemcpyAsync(hA.data(), dA.p, sizeof(double) * total, cudaMemcpyDeviceToHost, stream));
-        GFT_CUDA(cudaMemcpyAsync(hV.data(), dV.p, sizeof(double) * total, cudaMemcpyDeviceToHost, stream));
-        GFT_CUDA(cudaMemcpyAsync(hS.data(), dS.p, sizeof(int) * B, cudaMemcpyDeviceToHost, stream));
-        GFT_CUDA(cudaMemcpyAsync(hOk.data(), dOk.p, sizeof(int) * B, cudaMemcpyDeviceToHost, stream));
         GFT_CUDA(cudaStreamSynchronize(stream));
-        for (size_t j = 0; j < ids.size(); ++j) {
-            Leaf& lf = leaves[ids[j]];
+        GFT_CUDA(cudaStreamSynchronize(big));
+    } catch (...) {
+        cudaStreamSynchronize(stream);
+        cudaStreamSynchronize(big);
+        cudaStreamDestroy(big);
+        throw;
+    }
+    GFT_CUDA(cudaStreamDestroy(big));
+    for (auto& R : runs) {
+        for (size_t j = 0; j < R->ids.size(); ++j) {
+            Leaf& lf = *leaves[R->ids[j]];
             const int m = lf.m();
-            if (!hOk[j])
+            if (!R->hOk[j])
                 fail(GFT_ERR_NO_CONVERGENCE, "Jacobi did not converge for leaf '" + lf.tag + "' (m=" +
                                                  std::to_string(m) + ")");
-            const double* A = hA.data() + jobs[j].off;
-            const double* V = hV.data() + jobs[j].off;
+            const double* A = R->hA.data() + R->jobs[j].off;
+            const double* V = R->hV.data() + R->jobs[j].off;
             std::vector<int> ord(m);
             std::iota(ord.begin(), ord.end(), 0);
             std::stable_sort(ord.begin(), ord.end(),
@@ -290,11 +339,15 @@ void jacobi_leaves(std::vector<Leaf>& leaves, cudaStream_t stream) {
                 lf.lam[c] = A[(size_t)ord[c] * m + ord[c]];
                 for (int r = 0; r < m; ++r) lf.V[(size_t)r * m + c] = V[(size_t)r * m + ord[c]];
             }
-            lf.sweeps = hS[j];
+            lf.sweeps = R->hS[j];
         }
-    };
-    run(small, true);
-    run(large, false);
+    }
+}
+
+void jacobi_leaves(std::vector<Leaf>& leaves, cudaStream_t stream) {
+    std::vector<Leaf*> ptrs;
+    for (auto& lf : leaves) ptrs.push_back(&lf);
+    jacobi_leaf_ptrs(ptrs, stream);
 }
 
 }  // namespace gft

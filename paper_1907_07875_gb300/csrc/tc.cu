@@ -669,7 +669,8 @@ void tc_free(gft_plan_s& p) {
 // Scratch for batches of up to `batch` signals (A images, FP16 scales,
 // leaf-ordered output in group mode); grows only.  Reserved before a launch
 // that is captured in a CUDA graph, where allocation is not possible.
-void tc_reserve(const gft_plan_s& p, TcScratch& S, int64_t batch) {
+void tc_reserve(gft_plan_s& p, TcScratch& S, int64_t batch) {
+    if (!p.tc && tc_eligible(p)) tc_build(p);
     const TcPlan* T = static_cast<const TcPlan*>(p.tc);
     if (!T || (size_t)batch <= S.rows_cap) return;
     S.release();
@@ -692,6 +693,7 @@ void TcScratch::release() {
 void launch_tc(gft_plan_s& p, const float* x, float* y, int64_t batch, bool inverse, cudaStream_t st,
                uint32_t precision, TcScratch* scratch) {
     if (inverse) fail(GFT_ERR_UNSUPPORTED, "tensor-core precisions are implemented for the forward transform");
+    if (!p.tc && tc_eligible(p)) tc_build(p);   // built on first use
     if (!p.tc) fail(GFT_ERR_UNSUPPORTED, "tensor-core path needs every leaf to have at most 256 nodes");
     if (x == y) fail(GFT_ERR_UNSUPPORTED, "tensor-core path does not run in place");
     TcPlan* T = static_cast<TcPlan*>(p.tc);

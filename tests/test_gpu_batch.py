@@ -149,3 +149,49 @@ def test_config3_tensor_core_precisions_one_graph(env, prec):
         for p, x, y in zip(plans, xs, ys):
             tc = p.info["max_leaf"] >= 64
             assert torch.equal(y, p.forward(x, precision=prec if tc else "fp32"))
+
+
+def test_create_many_matches_single_plans(env):
+    """Plans built together (one batched Jacobi solve over all leaves, grouped
+    by size) agree with plans built one at a time: same structure and output
+    map, eigenvalues within 1e-12, eigenspace projectors within 1e-10."""
+    from _helpers import projector_distance
+    gft, torch = env
+    graphs = [W.path(9), W.cycle(64), W.grid(8, weights="sym_uniform", seed=4), W.skeleton25(),
+              W.bipartite(300, 0.1, seed=6), W.path(600), W.grid(12), W.cycle(8), W.bipartite(40, 0.3, seed=8)]
+    many = gft.plans_from_laplacians([gft.laplacian(g.W, g.s) for g in graphs], [g.phis for g in graphs])
+    for g, pm in zip(graphs, many):
+        ps = gft.Plan(gft.laplacian(g.W, g.s), g.phis)
+        assert pm.leaves() == ps.leaves()
+        assert pm.output_map().tolist() == ps.output_map().tolist()
+        lam = ps.eigenvalues()
+        assert np.max(np.abs(pm.eigenvalues() - lam)) <= 1e-12 * max(1.0, np.abs(lam).max())
+        assert projector_distance(pm.basis(), ps.basis(), lam) <= 1e-10
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_size_sweep_sample_one_graph(env, prec):
+    """A 400-graph slice of the size sweep (families path, cycle, grid,
+    skeleton, bipartite; sizes 8..1024; 2^22 coefficients), plans built in
+    one call and shared between identical graphs, transformed in one graph
+    launch; every output equals its plan's own forward bit for bit."""
+    gft, torch = env
+    specs = W.config5_specs(n_graphs=400, total_coeffs=1 << 22)
+    keys, graphs = {}, []
+    for fam, n, gs, b, ss in specs:
+        if (fam, n, gs) not in keys:
+            keys[(fam, n, gs)] = len(graphs)
+            graphs.append(W.make_graph(fam, n, gs))
+    plans = gft.plans_from_laplacians([gft.laplacian(g.W, g.s) for g in graphs], [g.phis for g in graphs],
+                                      jit=False)
+    entry_plans = [plans[keys[(f, n, gs)]] for f, n, gs, b, ss in specs]
+    batches = [b for f, n, gs, b, ss in specs]
+    bt = gft.Batch(entry_plans, batches, precision=prec)
+    xs = [torch.from_numpy(W.signals(b, n, ss % 100000)).cuda() for f, n, gs, b, ss in specs]
+    ys = [torch.empty_like(x) for x in xs]
+    bt.forward(xs, ys)
+    torch.cuda.synchronize()
+    for p, x, y in zip(entry_plans, xs, ys):
+        mx = p.info["max_leaf"]
+        tc = prec != "fp32" and 64 <= mx <= 256
+        assert torch.equal(y, p.forward(x, precision=prec if tc else "fp32"))

@@ -124,3 +124,22 @@ def test_analyze_only_plan_refuses_device_calls(gft):
         with pytest.raises(gft.GftError) as e:
             call()
         assert e.value.status == "GFT_ERR_NO_DEVICE"
+
+
+def test_create_many_analysis_matches_single_and_is_all_or_nothing(gft):
+    """gft_plan_create_many decomposes each graph exactly as gft_plan_create
+    does (bit-exact stage pairs and leaves against the oracle); one bad graph
+    fails the whole call with that graph's status."""
+    graphs = [W.path(9), W.cycle(12), W.grid(5, 4), W.skeleton25(), W.bipartite(16, 0.3, seed=2)]
+    Ls = [ograph.laplacian(g.W, g.s) for g in graphs]
+    plans = gft.plans_from_laplacians(Ls, [g.phis for g in graphs], analyze_only=True)
+    for g, L, plan in zip(graphs, Ls, plans):
+        ref = ogft.decompose(L, g.phis)
+        assert plan.leaves() == [b.labels for b in ref.leaves]
+        for s, pairs in enumerate(ref.stages):
+            assert plan.stage_pairs(s).tolist() == [list(p) for p in pairs]
+    bad = [list(range(6))[::-1], [1, 2, 0, 3, 4, 5]]
+    p6 = ograph.laplacian(W.path(6).W, W.path(6).s)
+    with pytest.raises(gft.GftError) as e:
+        gft.plans_from_laplacians([p6, p6], [[bad[0]], [bad[1]]], analyze_only=True)
+    assert e.value.status == "GFT_ERR_NOT_INVOLUTION"
