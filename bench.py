@@ -47,12 +47,10 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-def _kernel_hash():
-    h = hashlib.sha256()
-    for f in ("apply.cu", "jit.cpp", "gft_internal.h"):
-        with open(os.path.join(ROOT, "paper_1907_07875_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
-    return h.hexdigest()[:16]
+def _kernel_hash(plan):
+    """Hash of the CUDA source of the plan-specialised kernel module that the
+    timed step launches (the text NVRTC compiles)."""
+    return hashlib.sha256(plan.kernel_source().encode()).hexdigest()[:16]
 
 
 def _traffic_from_profile(kernel_hash):
@@ -189,28 +187,55 @@ def _timed(torch, fn, reps=10):
     return a.elapsed_time(b) / reps / 1e3
 
 
+def _rel(a, b):
+    return float((a - b).norm() / b.norm())
+
+
 def extras(torch, gft, dev):
-    """Context numbers after the timed region: the grid/cycle kinds in every
-    precision against the dense GEMM, the mixed batch in one launch, and the
-    learned surrogate against the exact dense GFT.  Errors are relative L2
-    against the plan's FP64 basis applied in FP64 on the GPU."""
+    """Context numbers after the timed region (each kernel timed with CUDA
+    events, 3 warm-up + 10 timed launches, inputs larger than L2 unless
+    stated).  Errors are relative L2 against the plan's FP64 basis applied in
+    FP64 on the GPU to the first 2048 signals."""
     out = {}
     prev = torch.backends.cuda.matmul.allow_tf32
     torch.backends.cuda.matmul.allow_tf32 = False
+    # ---- config 1: path N=8, FP64 and FP32, 4096 signals (launch-bound) and 2^26 coefficients
+    (g, batch, seed), = W.config1()
+    plan = gft.Plan(gft.laplacian(g.W, g.s), g.phis)
+    U = torch.from_numpy(plan.basis()).to(dev)
+    c1 = {}
+    for nb, tag in ((batch, "4096_signals"), ((1 << 26) // 8, "2^26_coeffs")):
+        x = torch.from_numpy(W.signals(nb, 8, seed)).to(dev)
+        ref = x[:2048].double() @ U
+        row = {}
+        for dt, xx in (("fp32", x), ("fp64", x.double())):
+            y = torch.empty_like(xx)
+            t = _timed(torch, lambda: plan.forward(xx, out=y))
+            row[dt] = {"gcoeffs_s": round(nb * 8 / t / 1e9, 2),
+                       "err_vs_fp64": float(f"{_rel(plan.forward(xx[:2048].contiguous()).double(), ref):.2e}")}
+        yd = torch.empty_like(x)
+        t = _timed(torch, lambda: torch.matmul(x, U.float(), out=yd))
+        row["dense_fp32_gcoeffs_s"] = round(nb * 8 / t / 1e9, 2)
+        c1[tag] = row
+    c1["note"] = "4096 signals = 128 KiB: launch-bound and L2-resident"
+    out["config1_path8"] = c1
+    # ---- config 3 kinds alone, 2^26 coefficients each (256 MiB in: > L2)
     kinds = {}
-    for k, (g, batch, seed) in enumerate(W.config3()):
+    for k, (g, _, seed) in enumerate(W.config3()):
+        batch = (1 << 26) // g.n
         plan = gft.Plan(gft.laplacian(g.W, g.s), g.phis)
         x = torch.from_numpy(W.signals(batch, g.n, seed)).to(dev)
         y = torch.empty_like(x)
         U = torch.from_numpy(plan.basis()).to(dev)
         ref = x[:2048].double() @ U
-        row = {"n": g.n, "signals": batch}
+        inf = plan.info
+        row = {"n": g.n, "signals": batch, "max_leaf": inf["max_leaf"],
+               "fp32_kernel": "plan-specialised" if inf["jit"] else ("wide-leaf" if inf["wide"] else "table-driven")}
         coeffs = batch * g.n
         for prec in ("fp32", "bf16", "bf16x3", "fp16x3"):
             try:
                 t = _timed(torch, lambda: plan.forward(x, out=y, precision=prec))
-                yy = plan.forward(x[:2048].contiguous(), precision=prec).double()
-                err = float(torch.linalg.norm(yy - ref) / torch.linalg.norm(ref))
+                err = _rel(plan.forward(x[:2048].contiguous(), precision=prec).double(), ref)
                 row[prec] = {"gcoeffs_s": round(coeffs / t / 1e9, 1), "err_vs_fp64": float(f"{err:.2e}")}
             except gft.GftError:
                 row[prec] = "unsupported"
@@ -221,31 +246,132 @@ def extras(torch, gft, dev):
         t = _timed(torch, lambda: torch.matmul(xb, Ub))
         row["dense_bf16_gcoeffs_s"] = round(coeffs / t / 1e9, 1)
         kinds[g.name] = row
-    out["config3_kinds"] = kinds
-    # mixed batch of the CUDA-core kinds (grid 8/16, cycle 64/256) in one launch
-    sel = [W.config3()[k] for k in (0, 1, 2, 3, 6, 7)]
-    plans = [gft.Plan(gft.laplacian(g.W, g.s), g.phis, jit=False) for g, _, _ in sel]
+        del x, y, U
+    out["config3_kinds_2^26"] = kinds
+    # ---- config 3 as specified: eight kinds x 2^23 coefficients in ONE graph launch
+    sel = W.config3()
+    plans = [gft.Plan(gft.laplacian(g.W, g.s), g.phis) for g, _, _ in sel]
     xs = [torch.from_numpy(W.signals(b, g.n, s)).to(dev) for g, b, s in sel]
     ys = [torch.empty_like(v) for v in xs]
-    bat = gft.Batch(plans, [b for _, b, _ in sel])
-    t = _timed(torch, lambda: bat.forward(xs, ys))
     tot = sum(b * g.n for g, b, _ in sel)
-    out["mixed_batch_6kinds"] = {"gcoeffs_s": round(tot / t / 1e9, 1), "coeffs": tot, "launches": 1,
-                                 "kernel": "gft_batch_kernel (CUDA graph replay)"}
-    # learned Givens surrogate vs the exact dense GFT (nearly symmetric path, n=16)
+    mixed = {"coeffs": tot, "graph_launches_per_step": 1}
+    for prec in ("fp32", "bf16", "bf16x3"):
+        bat = gft.Batch(plans, [b for _, b, _ in sel], precision=prec)
+        t = _timed(torch, lambda: bat.forward(xs, ys))
+        mixed[prec] = {"gcoeffs_s": round(tot / t / 1e9, 1), "ms": round(t * 1e3, 3)}
+        del bat
+    out["config3_mixed_one_graph"] = mixed
+    del xs, ys, plans
+    # ---- config 4: learned Givens surrogates on the nine nearly symmetric graphs
+    out["config4_learned"] = learned_extras(torch, gft, dev)
+    torch.backends.cuda.matmul.allow_tf32 = prev
+    return out
+
+
+def learned_extras(torch, gft, dev, steps=1500):
+    """Per nearly symmetric graph: the surrogate trained on the GPU against
+    the exact basis, its sign-normalised error delta (Sec. VI-B) before and
+    after training, the error of the method without it (the exact butterfly
+    of the graph with its weights symmetrised under the involutions), and
+    coefficients/s of the surrogate, the exact dense GFT and that butterfly
+    on 2^24 coefficients."""
     from paper_1907_07875_gb300.learned import LearnedGFT, delta
-    g = W.near_symmetric_path(16, 0.05, seed=1)
-    exact = gft.Plan(gft.laplacian(g.W, g.s), [])
-    model = LearnedGFT(16, device=dev)
-    model.train(exact.basis(), steps=1500, lr=0.05)
-    d = delta(model.matrix(), exact.basis())
-    x = torch.from_numpy(W.signals(1 << 20, 16, 5)).to(dev)
-    y = torch.empty_like(x)
-    t_l = _timed(torch, lambda: model.forward(x, out=y))
-    t_e = _timed(torch, lambda: exact.forward(x, out=y))
-    out["learned_c4_path16_eps0.05"] = {"delta_vs_exact": round(d, 4),
-                                        "learned_gcoeffs_s": round((1 << 24) / t_l / 1e9, 1),
-                                        "exact_dense_gcoeffs_s": round((1 << 24) / t_e / 1e9, 1)}
+    res = {}
+    for g in W.config4():
+        n = g.n
+        phis = [W.grid_lr(int(round(n ** 0.5))), W.grid_ud(int(round(n ** 0.5)))] if "grid" in g.name \
+            else [W.reversal(n)]
+        Ws = g.W.copy()
+        for _ in range(2):
+            for ph in phis:
+                Ws = 0.5 * (Ws + Ws[np.ix_(ph, ph)])
+        exact = gft.Plan(gft.laplacian(g.W, g.s), [])
+        sym = gft.Plan(gft.laplacian(Ws, g.s), phis)
+        U = exact.basis()
+        model = LearnedGFT(n, device=dev)
+        d0 = delta(model.matrix(), U)
+        model.train(U, steps=steps, lr=0.05)
+        d1 = delta(model.matrix(), U)
+        nb = (1 << 24) // n
+        x = torch.from_numpy(W.signals(nb, n, 5)).to(dev)
+        y = torch.empty_like(x)
+        t_l = _timed(torch, lambda: model.forward(x, out=y))
+        t_e = _timed(torch, lambda: exact.forward(x, out=y))
+        t_s = _timed(torch, lambda: sym.forward(x, out=y))
+        res[g.name] = {"delta_untrained": round(d0, 4), "delta_learned": round(d1, 4),
+                       "delta_symmetrised_butterfly": round(delta(sym.basis(), U), 4),
+                       "learned_gcoeffs_s": round((1 << 24) / t_l / 1e9, 1),
+                       "exact_dense_gcoeffs_s": round((1 << 24) / t_e / 1e9, 1),
+                       "symmetrised_butterfly_gcoeffs_s": round((1 << 24) / t_s / 1e9, 1)}
+    return res
+
+
+def sweep(torch, gft, dev, precisions=("fp32", "bf16x3"), n_graphs=10000, total=1 << 28, reps=5):
+    """Config-5 size sweep: 10^4 graphs (path, cycle, grid, skeleton,
+    bipartite; n = 8..1024 log-uniform), 2^28 FP32 coefficients, in one graph
+    launch per precision; plans built in one batched call, identical graphs
+    share a plan.  Dense baseline: torch.bmm of each size class against its
+    graphs' FP32 bases (TF32 off)."""
+    import collections
+    t0 = time.perf_counter()
+    specs = W.config5_specs(n_graphs=n_graphs, total_coeffs=total)
+    keys, graphs = {}, []
+    for fam, n, gs, b, ss in specs:
+        if (fam, n, gs) not in keys:
+            keys[(fam, n, gs)] = len(graphs)
+            graphs.append((fam, n, gs))
+    Ls, phis = [], []
+    for fam, n, gs in graphs:
+        g = W.make_graph(fam, n, gs)
+        Ls.append(gft.laplacian(g.W, g.s))
+        phis.append(g.phis)
+    t1 = time.perf_counter()
+    plans = gft.plans_from_laplacians(Ls, phis, jit=False)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    del Ls
+    entry = [keys[(f, n, gs)] for f, n, gs, b, ss in specs]
+    batches = [b for f, n, gs, b, ss in specs]
+    ns = [n for f, n, gs, b, ss in specs]
+    # one input and one output buffer; entry views start 16-byte aligned
+    offs, o = [], 0
+    for b, n in zip(batches, ns):
+        offs.append(o)
+        o += (b * n + 3) & ~3
+    X = torch.randn(o, device=dev)
+    Y = torch.empty(o, device=dev)
+    xs = [X[a:a + b * n].view(b, n) for a, b, n in zip(offs, batches, ns)]
+    ys = [Y[a:a + b * n].view(b, n) for a, b, n in zip(offs, batches, ns)]
+    coeffs = sum(b * n for b, n in zip(batches, ns))
+    out = {"graphs": len(specs), "distinct_plans": len(graphs), "coeffs": coeffs,
+           "build_graphs_s": round(t1 - t0, 1), "build_plans_s": round(t2 - t1, 1)}
+    for prec in precisions:
+        t3 = time.perf_counter()
+        bt = gft.Batch([plans[i] for i in entry], batches, precision=prec)
+        bt.forward(xs, ys)
+        torch.cuda.synchronize()
+        t4 = time.perf_counter()
+        t = _timed(torch, lambda: bt.forward(xs, ys), reps=reps)
+        out[prec] = {"gcoeffs_s": round(coeffs / t / 1e9, 1), "ms": round(t * 1e3, 2),
+                     "batch_create_s": round(t4 - t3, 1)}
+        del bt
+    # dense baseline: grouped by size
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    by_n = collections.defaultdict(list)
+    for j, n in enumerate(ns):
+        by_n[n].append(j)
+    groups, basis = [], {}
+    for n, js in by_n.items():
+        for j in js:
+            if entry[j] not in basis:
+                basis[entry[j]] = torch.from_numpy(plans[entry[j]].basis()).float().to(dev)
+        U = torch.stack([basis[entry[j]] for j in js])
+        Xg = torch.stack([xs[j] for j in js])
+        groups.append((Xg, U, torch.empty_like(Xg)))
+    t = _timed(torch, lambda: [torch.bmm(a, u, out=c) for a, u, c in groups], reps=reps)
+    out["dense_bmm_fp32"] = {"gcoeffs_s": round(coeffs / t / 1e9, 1), "ms": round(t * 1e3, 2),
+                             "size_classes": len(groups)}
     torch.backends.cuda.matmul.allow_tf32 = prev
     return out
 
@@ -324,7 +450,10 @@ def run_ours(args, rank, world, local_rank):
     launch_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     if args.profile:
         if rank == 0:
+            inf = plan.info
             print(json.dumps({"profile_run": True, "ms_per_step": total_ms / args.steps,
+                              "kernel_hash": _kernel_hash(plan), "tile_signals": inf["tile_signals"],
+                              "threads": inf["threads"], "jit": inf["jit"],
                               "config": {"workload": WORKLOAD, "sets": nsets}}), flush=True)
         return
     total_ms = sharding.max_over_ranks(total_ms, dist, dev)
@@ -337,7 +466,7 @@ def run_ours(args, rank, world, local_rank):
     alg_bytes = 8 * coeffs_per_step          # FP32 read + write per coefficient
     peak, peak_kind = _peaks()
     achieved = alg_bytes / avg_launch_s / 1e9
-    khash = _kernel_hash()
+    khash = _kernel_hash(plan)
     traffic = _traffic_from_profile(khash)
 
     # inverse and the dense GEMM on the same data (context)
@@ -405,6 +534,8 @@ def run_ours(args, rank, world, local_rank):
     }
     if not args.no_extras and world == 1:
         line["extras"] = extras(torch, gft, dev)
+        if not args.no_sweep:
+            line["extras"]["config5_sweep"] = sweep(torch, gft, dev)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -418,6 +549,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the context measurements")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the 10^4-graph size sweep in the extras")
     ap.add_argument("--profile", action="store_true",
                     help="forward steps only, 2 buffer sets (for ncu captures)")
     args = ap.parse_args()
