@@ -24,6 +24,7 @@
 
 struct gft_givens_s {
     int n = 0, S = 0;
+    int xor_log2 = 0;              // > 0: butterfly wiring (stage t pairs i, i ^ 2^(t mod log2 n)), n <= 64
     int* d_pairs = nullptr;        // S * n/2 * 2
     float* d_partials = nullptr;   // grid * S * n/2 (scratch for the backward pass)
     int partial_rows = 0;
@@ -96,12 +97,89 @@ __global__ void __launch_bounds__(kGivThreads) givens_fwd_kernel(GArgs a) {
                 const int p = pr[2 * i], q = pr[2 * i + 1];
                 const float c = cs[2 * i], s = cs[2 * i + 1];
                 const float xp = r[p], xq = r[q];
-                r[p] = c * xp - s * xq;
-                r[q] = s * xp + c * xq;
+                r[p] = fmaf(c, xp, -s * xq);
+                r[q] = fmaf(s, xp, c * xq);
             }
         }
         __syncthreads();
         store_rows(tile, a.y + tl * kGivThreads * a.n, rows, a.n, a.np, a.inv_n);
+    }
+}
+
+// Forward pass for the butterfly wiring (the surrogate's default): stage t
+// pairs i with i ^ 2^(t mod log2 N) in ascending order of the lower index,
+// so every index is a compile-time constant once the log2 N stages of a
+// round are unrolled.  Each thread keeps its signal in registers; per
+// rotation it reads one (cos, sin) pair (a shared-memory broadcast) and
+// issues two multiplies and two FMAs -- the same arithmetic, in the same
+// order, as the general kernel.  Tiles of 128 signals move with 16-byte
+// cp.async copies into rows of stride N + 4 floats (16-byte aligned, and the
+// 16-byte row reads of consecutive lanes hit distinct banks).
+template <int N>
+__global__ void __launch_bounds__(kGivThreads) givens_fwd_xor_kernel(GArgs a) {
+    constexpr int LG = N == 4 ? 2 : N == 8 ? 3 : N == 16 ? 4 : N == 32 ? 5 : 6;
+    constexpr int H = N / 2;
+    constexpr int NP = N + 4;
+    extern __shared__ __align__(16) unsigned char sm[];
+    float2* cs = reinterpret_cast<float2*>(sm);                                    // A
+    float* tile = reinterpret_cast<float*>(sm + ((sizeof(float2) * a.A + 15) & ~size_t(15)));   // 128 x NP
+    for (int i = threadIdx.x; i < a.A; i += blockDim.x) {
+        float sn, c;
+        sincosf(a.theta[i], &sn, &c);
+        cs[i] = make_float2(c, sn);
+    }
+    const long long n_tiles = (a.batch + kGivThreads - 1) / kGivThreads;
+    for (long long tl = blockIdx.x; tl < n_tiles; tl += gridDim.x) {
+        const int rows = (int)min((long long)kGivThreads, a.batch - tl * kGivThreads);
+        const float* src = a.x + tl * kGivThreads * N;
+        __syncthreads();   // previous tile stored, angles written
+        for (int c = threadIdx.x; c < rows * (N / 4); c += kGivThreads) {
+            const int t = c / (N / 4), k = c - t * (N / 4);
+            const unsigned d = (unsigned)__cvta_generic_to_shared(tile + t * NP + 4 * k);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src + 4 * c) : "memory");
+        }
+        asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+        __syncthreads();
+        if ((int)threadIdx.x < rows) {
+            float* row = tile + threadIdx.x * NP;
+            float r[N];
+#pragma unroll
+            for (int q = 0; q < N / 4; ++q) {
+                const float4 v = reinterpret_cast<const float4*>(row)[q];
+                r[4 * q] = v.x;
+                r[4 * q + 1] = v.y;
+                r[4 * q + 2] = v.z;
+                r[4 * q + 3] = v.w;
+            }
+            for (int s0 = 0; s0 < a.S; s0 += LG) {
+#pragma unroll
+                for (int b = 0; b < LG; ++b) {
+                    if (s0 + b < a.S) {
+                        const float2* st = cs + (s0 + b) * H;
+                        constexpr int dummy = 0;
+                        (void)dummy;
+#pragma unroll
+                        for (int k = 0; k < H; ++k) {
+                            const int lo = ((k >> b) << (b + 1)) | (k & ((1 << b) - 1));
+                            const int hi = lo | (1 << b);
+                            const float2 w = st[k];
+                            const float xp = r[lo], xq = r[hi];
+                            r[lo] = fmaf(w.x, xp, -w.y * xq);
+                            r[hi] = fmaf(w.y, xp, w.x * xq);
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < N / 4; ++q)
+                reinterpret_cast<float4*>(row)[q] = make_float4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
+        }
+        __syncthreads();
+        float* dst = a.y + tl * kGivThreads * N;
+        for (int c = threadIdx.x; c < rows * (N / 4); c += kGivThreads) {
+            const int t = c / (N / 4), k = c - t * (N / 4);
+            __stcs(reinterpret_cast<float4*>(dst) + c, *reinterpret_cast<const float4*>(tile + t * NP + 4 * k));
+        }
     }
 }
 
@@ -185,6 +263,28 @@ void check_io_g(const void* a, const void* b, int64_t batch) {
 // exported through abi_givens below
 void givens_forward(gft_givens_s& g, const float* theta, const float* x, float* y, int64_t batch, cudaStream_t st) {
     if (batch == 0) return;
+    if (g.xor_log2) {
+        GArgs a{};
+        a.theta = theta;
+        a.x = x;
+        a.y = y;
+        a.batch = batch;
+        a.n = g.n;
+        a.S = g.S;
+        a.A = g.S * g.n / 2;
+        void (*fn)(GArgs) = g.n == 4 ? givens_fwd_xor_kernel<4> : g.n == 8 ? givens_fwd_xor_kernel<8>
+                          : g.n == 16 ? givens_fwd_xor_kernel<16> : g.n == 32 ? givens_fwd_xor_kernel<32>
+                          : givens_fwd_xor_kernel<64>;
+        const size_t smem = ((sizeof(float2) * a.A + 15) & ~size_t(15)) + sizeof(float) * kGivThreads * (g.n + 4);
+        GFT_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int per_sm = 0;
+        GFT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kGivThreads, smem));
+        const long long tiles = (batch + kGivThreads - 1) / kGivThreads;
+        const long long grid = std::min<long long>(tiles, (long long)std::max(1, per_sm) * sm_count());
+        fn<<<(unsigned)grid, kGivThreads, smem, st>>>(a);
+        GFT_CUDA(cudaGetLastError());
+        return;
+    }
     GArgs a{};
     a.pairs = g.d_pairs;
     a.theta = theta;
@@ -290,6 +390,19 @@ gft_status gft_givens_create(int32_t n, int32_t n_stages, const int32_t* pairs, 
         std::unique_ptr<gft_givens_s> g(new gft_givens_s);
         g->n = n;
         g->S = n_stages;
+        int lg = 0;
+        while ((1 << lg) < n) ++lg;
+        if ((1 << lg) == n && n >= 4 && n <= 64) {
+            bool ok = true;
+            for (int s = 0; s < n_stages && ok; ++s) {
+                const int b = s % lg;
+                for (int k = 0; k < half && ok; ++k) {
+                    const int lo = ((k >> b) << (b + 1)) | (k & ((1 << b) - 1));
+                    ok = pairs[(size_t)(s * half + k) * 2] == lo && pairs[(size_t)(s * half + k) * 2 + 1] == (lo | (1 << b));
+                }
+            }
+            if (ok) g->xor_log2 = lg;
+        }
         const size_t cnt = (size_t)n_stages * half * 2;
         GFT_CUDA(cudaMalloc(&g->d_pairs, sizeof(int) * cnt));
         GFT_CUDA(cudaMemcpy(g->d_pairs, pairs, sizeof(int) * cnt, cudaMemcpyHostToDevice));

@@ -106,3 +106,28 @@ def test_training_gains_over_untrained_surrogate(env):
     eps_err = metrics.epsilon(model.matrix(), U, x.cpu().numpy())
     exact = plan.forward(x).cpu().numpy()
     assert np.isfinite(eps_err) and exact.shape == (4096, 16)
+
+
+@pytest.mark.parametrize("n", [8, 32, 64])
+def test_butterfly_kernel_equals_general_kernel(env, n):
+    """The butterfly wiring runs a register-resident kernel; listing the same
+    pairs of each stage in another order (angles permuted with them) sends
+    the network through the general kernel.  Rotations of one stage are
+    disjoint, so both must give the same bits; a random wiring (general
+    kernel only) is checked against the oracle."""
+    gft, torch = env
+    S = 2 * int(math.log2(n))
+    pairs = ogiv.xor_pairs(n, S)
+    rng = np.random.default_rng(n)
+    theta = rng.uniform(-math.pi, math.pi, (S, n // 2))
+    perm = np.stack([rng.permutation(n // 2) for _ in range(S)])
+    pairs_p = np.stack([pairs[s][perm[s]] for s in range(S)])
+    theta_p = np.stack([theta[s][perm[s]] for s in range(S)])
+    x = torch.from_numpy(W.signals(4099, n, 3)).cuda()
+    y_fast = gft.Givens(n, pairs).forward(torch.from_numpy(theta).float().cuda(), x)
+    y_gen = gft.Givens(n, pairs_p).forward(torch.from_numpy(theta_p).float().cuda(), x)
+    assert torch.equal(y_fast, y_gen)
+    wiring = np.stack([rng.permutation(n).reshape(n // 2, 2) for _ in range(S)]).astype(np.int32)
+    y_rand = gft.Givens(n, wiring).forward(torch.from_numpy(theta).float().cuda(), x).cpu().numpy()
+    th32 = theta.astype(np.float32).astype(np.float64)
+    assert rel_l2(y_rand, ogiv.forward(x.cpu().numpy().astype(np.float64), wiring, th32)) <= 2e-6
