@@ -9,31 +9,32 @@
 //
 //   Y_k[TS x m] = V_k[TS x m] * M_k[m x m]        (forward, Eq. 13 per leaf)
 //
-// with V_k the tile's post-stage values at the leaf's node slots.  Each
-// thread owns an RS x OC register block (RS signals x OC consecutive
-// outputs); a warp is LR x LC threads (LR signal groups, LC = P/OC output
-// groups, P = leaf width rounded up to a power of two), so a warp covers
-// RS*LR signals and all P output columns, and the 4 warps of the CTA cover
-// the tile's TS signals.  Per input r, a thread reads RS tile values
-// (broadcast within its signal group) and OC matrix entries (vector loads
-// of one matrix row, consecutive across the warp), then issues RS*OC FMAs.
-// The leaf matrix streams from global memory (L2-resident) through two
-// shared-memory chunk buffers with cp.async, so leaves of any width up to
-// 512 work with a fixed shared-memory budget.  (RS, OC) is chosen per leaf
-// on the host for the fewest shared-memory wavefronts per FMA.
+// with V_k the tile's post-stage values at the leaf's node slots.
 //
-// Per tile: load (16-byte cp.async when rows allow, otherwise 4/8-byte),
-// Haar stages with the CTA's threads spread over the pairs of one stage at a
-// time (Sec. III: one addition and one subtraction per unit, the 1/sqrt2
-// factors folded into M_k), leaf products in place (a leaf's outputs
-// overwrite its own input slots once every warp has finished reading them),
-// then the permuted store (coefficients in ascending-eigenvalue order).  The
-// inverse loads through the permutation, runs the leaves with M_k^T and then
-// the stages in reverse order (B_phi is its own inverse).
-//
-// Shared-memory row stride: np = n rounded up to 4 (mod 32) floats (2 mod
-// 16 doubles), which keeps rows 16-byte aligned and puts the rows read by
-// the LR signal groups of a warp in different banks.
+// The tile is kept TRANSPOSED in shared memory, node-major: T[slot][signal]
+// with a signal stride TSP (TS rounded up so rows are 16-byte aligned and
+// sit 4 banks apart).  Then
+//   * a Haar unit (x_i, x_j) -> (x_i + x_j, x_i - x_j) (Sec. III; the
+//     1/sqrt2 factors are folded into M_k) is two 16-byte row loads and two
+//     stores for four signals,
+//   * the GEMM reads RS consecutive signals of one slot with vector loads
+//     (a broadcast within a signal group) and OC entries of one matrix row
+//     with vector loads (consecutive across the group's lanes), then issues
+//     RS*OC FMAs -- about one shared-memory wavefront per 4-10 FMA
+//     instructions, so the FMA pipe, not shared memory, is the limit,
+//   * a leaf's outputs overwrite its own input slots (16-byte stores) once
+//     every warp has finished reading them.
+// Each thread owns an RS x OC register block; a warp is LR x LC threads
+// (LC = P / OC output groups, P = leaf width rounded up to a power of two,
+// LR = 32 / LC signal groups); the 4 warps cover TS = 4 * RS * LR signals.
+// (RS, OC) is chosen per leaf on the host.  The leaf matrix streams from
+// global memory (L2-resident) through two shared-memory chunk buffers with
+// cp.async.  The tile itself arrives with 4-byte cp.async copies that
+// transpose on the fly (a warp copies an 8-node x 4-signal block: one
+// sector per signal row in global memory, 32 distinct banks in shared
+// memory); the permuted store gathers four coefficients per thread and
+// writes them with one 16-byte store.  The inverse loads through the
+// permutation, runs the leaves with M_k^T and then the stages in reverse.
 #include <algorithm>
 #include <cstdint>
 #include <cstdio>
@@ -58,38 +59,55 @@ struct WArgs {
     const int* wdesc;      // per-leaf descriptors, kWDesc ints each
     const void* mats;      // per leaf: M_f (m x P) then M_i (m x P), zero padded columns
     long long batch;
-    int n, np, ts, nbuf, n_pairs, n_stages, n_leaves;
+    int n, tsp, ts, nbuf, n_pairs, n_stages, n_leaves;
     int off_labels, off_src;
     int chunk_elems;       // elements of one matrix chunk buffer
     int inverse;
-    float inv_n;
 };
 
-template <class T, int OC>
-__device__ __forceinline__ void load_row(const T* p, T (&w)[OC]) {
-    if constexpr (sizeof(T) == 4 && OC % 4 == 0) {
+// W consecutive elements of shared memory into registers (vector loads)
+template <class T, int W>
+__device__ __forceinline__ void lds_vec(const T* p, T* w) {
+    if constexpr (sizeof(T) == 4 && W % 4 == 0) {
 #pragma unroll
-        for (int q = 0; q < OC / 4; ++q) {
+        for (int q = 0; q < W / 4; ++q) {
             const float4 v = reinterpret_cast<const float4*>(p)[q];
             w[4 * q] = v.x;
             w[4 * q + 1] = v.y;
             w[4 * q + 2] = v.z;
             w[4 * q + 3] = v.w;
         }
-    } else if constexpr (sizeof(T) == 4 && OC == 2) {
+    } else if constexpr (sizeof(T) == 4 && W == 2) {
         const float2 v = *reinterpret_cast<const float2*>(p);
         w[0] = v.x;
         w[1] = v.y;
-    } else if constexpr (sizeof(T) == 8 && OC % 2 == 0) {
+    } else if constexpr (sizeof(T) == 8 && W % 2 == 0) {
 #pragma unroll
-        for (int q = 0; q < OC / 2; ++q) {
+        for (int q = 0; q < W / 2; ++q) {
             const double2 v = reinterpret_cast<const double2*>(p)[q];
             w[2 * q] = v.x;
             w[2 * q + 1] = v.y;
         }
     } else {
 #pragma unroll
-        for (int q = 0; q < OC; ++q) w[q] = p[q];
+        for (int q = 0; q < W; ++q) w[q] = p[q];
+    }
+}
+
+template <class T, int W>
+__device__ __forceinline__ void sts_vec(T* p, const T* w) {
+    if constexpr (sizeof(T) == 4 && W % 4 == 0) {
+#pragma unroll
+        for (int q = 0; q < W / 4; ++q)
+            reinterpret_cast<float4*>(p)[q] = make_float4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+    } else if constexpr (sizeof(T) == 4 && W == 2) {
+        *reinterpret_cast<float2*>(p) = make_float2(w[0], w[1]);
+    } else if constexpr (sizeof(T) == 8 && W % 2 == 0) {
+#pragma unroll
+        for (int q = 0; q < W / 2; ++q) reinterpret_cast<double2*>(p)[q] = make_double2(w[2 * q], w[2 * q + 1]);
+    } else {
+#pragma unroll
+        for (int q = 0; q < W; ++q) p[q] = w[q];
     }
 }
 
@@ -102,25 +120,24 @@ __device__ __forceinline__ void load_chunk(T* dst, const T* src, int elems) {
 }
 
 // One leaf's product over the tile, in place.  M points at the leaf's
-// m x P matrix for this direction.  A thread's OC output columns are
-// interleaved in groups of VW (one vector load each): columns
-// VW*(lcol + LC*q) + e, q < OC/VW, e < VW, so that each vector load of a
-// matrix row is contiguous across the LC lanes of a signal group (no bank
-// conflicts).  The next row's operands are loaded before the current row's
-// FMAs are issued.
+// m x P matrix for this direction.  Thread (lr, lcol) of its warp owns the
+// RS signals s0 .. s0+RS-1 and the OC output columns VW*(lcol + LC*q) + e
+// (q < OC/VW, e < VW): every vector load of a matrix row is contiguous
+// across the LC lanes of a signal group.  The next row's operands are
+// loaded before the current row's FMAs are issued.
 template <class T, int RS, int OC>
-__device__ __forceinline__ void wide_leaf(T* tile, int np, int ts, const int* lab, const T* __restrict__ M, int m,
+__device__ __forceinline__ void wide_leaf(T* tile, int tsp, int ts, const int* lab, const T* __restrict__ M, int m,
                                           int P, int lc, int kc_rows, T* mbuf, int chunk_elems) {
-    constexpr int VW = (sizeof(T) == 4 ? 4 : 2) < OC ? (sizeof(T) == 4 ? 4 : 2) : OC;   // elements per vector load
+    constexpr int VE = 16 / sizeof(T);                   // elements per 16-byte vector
+    constexpr int VW = OC < VE ? OC : VE;                 // matrix vector width
     constexpr int NV = OC / VW;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int lr_cnt = 32 / lc;
     const int lr = lane / lc;
     const int lcol = lane - lr * lc;
-    const int sbase = warp * RS * lr_cnt + lr;
-    int rowoff[RS];
-#pragma unroll
-    for (int i = 0; i < RS; ++i) rowoff[i] = min(sbase + i * lr_cnt, ts - 1) * np;   // clamp: never outside the tile
+    const int s0 = (warp * lr_cnt + lr) * RS;
+    const bool live = s0 < ts;                            // tiles smaller than the CTA's cover
+    const int sv = live ? s0 : 0;                          // reads stay inside the tile
     T acc[RS][OC];
 #pragma unroll
     for (int i = 0; i < RS; ++i)
@@ -140,56 +157,62 @@ __device__ __forceinline__ void wide_leaf(T* tile, int np, int ts, const int* la
         const T* Mc = mbuf + (kc & 1) * chunk_elems + VW * lcol;
         const int r0 = kc * kc_rows, rn = min(kc_rows, m - r0);
         const int* lab_c = lab + r0;
-        T v[RS], w[OC];
-        {
-            const int g = lab_c[0];
+        // two register sets used in turn: the loads of row r+1 go to one set
+        // while the FMAs of row r read the other (no register copies)
+        T v0[RS], w0[OC], v1[RS], w1[OC];
+        lds_vec<T, RS>(tile + lab_c[0] * tsp + sv, v0);
 #pragma unroll
-            for (int i = 0; i < RS; ++i) v[i] = tile[rowoff[i] + g];
+        for (int q = 0; q < NV; ++q) lds_vec<T, VW>(Mc + q * VW * lc, w0 + q * VW);
+        int r = 0;
+        for (; r + 1 < rn; r += 2) {
+            lds_vec<T, RS>(tile + lab_c[r + 1] * tsp + sv, v1);
 #pragma unroll
-            for (int q = 0; q < NV; ++q) load_row<T, VW>(Mc + q * VW * lc, *reinterpret_cast<T(*)[VW]>(w + q * VW));
-        }
-        for (int r = 0; r < rn; ++r) {
-            T vn[RS], wn[OC];
-            const int rr = min(r + 1, rn - 1);   // the last prefetch re-reads row rn-1 (in bounds)
-            const int g = lab_c[rr];
-#pragma unroll
-            for (int i = 0; i < RS; ++i) vn[i] = tile[rowoff[i] + g];
-#pragma unroll
-            for (int q = 0; q < NV; ++q)
-                load_row<T, VW>(Mc + rr * P + q * VW * lc, *reinterpret_cast<T(*)[VW]>(wn + q * VW));
+            for (int q = 0; q < NV; ++q) lds_vec<T, VW>(Mc + (r + 1) * P + q * VW * lc, w1 + q * VW);
 #pragma unroll
             for (int i = 0; i < RS; ++i)
 #pragma unroll
-                for (int j = 0; j < OC; ++j) acc[i][j] = fma(v[i], w[j], acc[i][j]);
+                for (int j = 0; j < OC; ++j) acc[i][j] = fma(v0[i], w0[j], acc[i][j]);
+            const int r2 = min(r + 2, rn - 1);   // past the end: re-reads row rn-1 (in bounds, unused)
+            lds_vec<T, RS>(tile + lab_c[r2] * tsp + sv, v0);
 #pragma unroll
-            for (int i = 0; i < RS; ++i) v[i] = vn[i];
+            for (int q = 0; q < NV; ++q) lds_vec<T, VW>(Mc + r2 * P + q * VW * lc, w0 + q * VW);
 #pragma unroll
-            for (int j = 0; j < OC; ++j) w[j] = wn[j];
+            for (int i = 0; i < RS; ++i)
+#pragma unroll
+                for (int j = 0; j < OC; ++j) acc[i][j] = fma(v1[i], w1[j], acc[i][j]);
+        }
+        if (r < rn) {   // odd row count: the last row is in set 0
+#pragma unroll
+            for (int i = 0; i < RS; ++i)
+#pragma unroll
+                for (int j = 0; j < OC; ++j) acc[i][j] = fma(v0[i], w0[j], acc[i][j]);
         }
         __syncthreads();   // every thread done with chunk kc's buffer and (last chunk) with V_k
     }
+    if (live) {
 #pragma unroll
-    for (int i = 0; i < RS; ++i) {
-        if (sbase + i * lr_cnt < ts) {
+        for (int q = 0; q < NV; ++q)
 #pragma unroll
-            for (int q = 0; q < NV; ++q)
+            for (int e = 0; e < VW; ++e) {
+                const int c = VW * (lcol + lc * q) + e;
+                if (c < m) {
+                    T col[RS];
 #pragma unroll
-                for (int e = 0; e < VW; ++e) {
-                    const int c = VW * (lcol + lc * q) + e;
-                    if (c < m) tile[rowoff[i] + lab[c]] = acc[i][q * VW + e];
+                    for (int i = 0; i < RS; ++i) col[i] = acc[i][q * VW + e];
+                    sts_vec<T, RS>(tile + lab[c] * tsp + s0, col);
                 }
-        }
+            }
     }
 }
 
 // variant code = log2(RS) * 5 + log2(OC), RS in {1,2,4,8}, OC in {1,...,16}
 template <class T>
-__device__ __forceinline__ void wide_leaf_dispatch(int code, T* tile, int np, int ts, const int* lab, const T* M,
+__device__ __forceinline__ void wide_leaf_dispatch(int code, T* tile, int tsp, int ts, const int* lab, const T* M,
                                                    int m, int P, int lc, int kc, T* mbuf, int ce) {
 #define GFT_W(R, O, C)                                                              \
     case C:                                                                        \
         if constexpr (sizeof(T) == 4 || R * O <= 32)                               \
-            wide_leaf<T, R, O>(tile, np, ts, lab, M, m, P, lc, kc, mbuf, ce);      \
+            wide_leaf<T, R, O>(tile, tsp, ts, lab, M, m, P, lc, kc, mbuf, ce);     \
         break;
     switch (code) {
         GFT_W(1, 1, 0) GFT_W(1, 2, 1) GFT_W(1, 4, 2) GFT_W(1, 8, 3) GFT_W(1, 16, 4)
@@ -201,48 +224,76 @@ __device__ __forceinline__ void wide_leaf_dispatch(int code, T* tile, int np, in
 #undef GFT_W
 }
 
+// One stage of Haar units on the transposed tile: thread -> (pair, 4 or 2
+// consecutive signals), 16-byte row loads and stores.
 template <class T>
-__device__ __forceinline__ void wide_stage(T* tile, int np, int ts, const int* pairs, int p0, int P) {
-    const int total = ts * P;
+__device__ __forceinline__ void wide_stage(T* tile, int tsp, int ts, const int* pairs, int p0, int P) {
+    constexpr int VE = 16 / sizeof(T);
+    const int groups = ts / VE;
+    const int total = P * groups;
     for (int idx = threadIdx.x; idx < total; idx += kWThreads) {
-        const int t = idx / P;
-        const int q = p0 + idx - t * P;
-        T* row = tile + t * np;
-        const int i = pairs[2 * q], j = pairs[2 * q + 1];
-        const T u = row[i], v = row[j];
-        row[i] = u + v;
-        row[j] = u - v;
+        const int q = idx / groups;
+        const int sg = idx - q * groups;
+        const int i = pairs[2 * (p0 + q)], j = pairs[2 * (p0 + q) + 1];
+        T u[VE], v[VE], a[VE], b[VE];
+        lds_vec<T, VE>(tile + i * tsp + VE * sg, u);
+        lds_vec<T, VE>(tile + j * tsp + VE * sg, v);
+#pragma unroll
+        for (int e = 0; e < VE; ++e) {
+            a[e] = u[e] + v[e];
+            b[e] = u[e] - v[e];
+        }
+        sts_vec<T, VE>(tile + i * tsp + VE * sg, a);
+        sts_vec<T, VE>(tile + j * tsp + VE * sg, b);
     }
 }
 
+// Tile load, transposing: element (signal s, node j) -> T[slot(j)][s] with
+// slot(j) = j (forward) or src[j] (inverse: coefficient j belongs to slot
+// src[j]).  A warp moves an 8-node x 4-signal block per step.
 template <class T>
 __device__ __forceinline__ void wide_load(const WArgs& a, const int* src_slot, T* buf, long long tile) {
-    constexpr int PER = 16 / sizeof(T);
-    const long long rows = min((long long)a.ts, a.batch - tile * (long long)a.ts);
+    const int rows = (int)min((long long)a.ts, a.batch - tile * (long long)a.ts);
     const T* src = reinterpret_cast<const T*>(a.x) + tile * (long long)a.ts * a.n;
-    if (!a.inverse && a.n % PER == 0) {
-        const int per_row = a.n / PER;
-        const int total = (int)rows * per_row;
-        for (int c = threadIdx.x; c < total; c += kWThreads) {
-            const int t = c / per_row;
-            const int k = c - t * per_row;
-            cp_async16(buf + t * a.np + k * PER, src + (long long)c * PER);
+    const int jb = (a.n + 7) >> 3, sb = (rows + 3) >> 2;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int jl = lane & 7, sl = lane >> 3;
+    for (int blk = warp; blk < jb * sb; blk += kWThreads / 32) {
+        const int bs = blk / jb;
+        const int j = (blk - bs * jb) * 8 + jl, s = bs * 4 + sl;
+        if (j < a.n && s < rows) cp_async_elem(buf + (a.inverse ? src_slot[j] : j) * a.tsp + s, src + (long long)s * a.n + j);
+    }
+}
+
+// Tile store: forward y[s][j] = T[src[j]][s]; inverse x[s][j] = T[j][s].
+// Four consecutive outputs per thread, one 16-byte (two for FP64) store.
+template <class T>
+__device__ __forceinline__ void wide_store(const WArgs& a, const int* src_slot, const T* buf, long long tile) {
+    const long long rows = min((long long)a.ts, a.batch - tile * (long long)a.ts);
+    T* dst = reinterpret_cast<T*>(a.y) + tile * (long long)a.ts * a.n;
+    const int E = (int)rows * a.n;
+    const bool fwd = !a.inverse;
+    if (a.n % 4 == 0) {
+        const int per_row = a.n / 4;
+        for (int c = threadIdx.x; c < E / 4; c += kWThreads) {
+            const int s = c / per_row;
+            const int j = 4 * (c - s * per_row);
+            T v[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v[q] = buf[(fwd ? src_slot[j + q] : j + q) * a.tsp + s];
+            Vec4Store<T>::st(dst + 4 * (long long)c, v[0], v[1], v[2], v[3]);
         }
     } else {
-        const int E = (int)rows * a.n;
         for (int e = threadIdx.x; e < E; e += kWThreads) {
-            const int t = row_of(e, a.inv_n);
-            const int j = e - t * a.n;
-            cp_async_elem(buf + t * a.np + (a.inverse ? src_slot[j] : j), src + e);
+            const int s = e / a.n;
+            const int j = e - s * a.n;
+            __stcs(dst + e, buf[(fwd ? src_slot[j] : j) * a.tsp + s]);
         }
     }
 }
 
 // Tables of one plan in shared memory:
 // [pairs 2P][stage_off S+1][labels n][src n][leaf desc kWDesc*L]
-__device__ __forceinline__ int wide_ints(const WArgs& a) {
-    return 2 * a.n_pairs + a.n_stages + 1 + 2 * a.n + kWDesc * a.n_leaves;
-}
 __device__ __forceinline__ void wide_load_tables(const WArgs& a, int* s_ints) {
     const int head = 2 * a.n_pairs + a.n_stages + 1;
     int* s_lab = s_ints + head;
@@ -268,50 +319,36 @@ __device__ __forceinline__ void wide_compute(const WArgs& a, T* buf, T* mbuf, co
     const T* mats = reinterpret_cast<const T*>(a.mats);
     if (!a.inverse) {
         for (int s = 0; s < a.n_stages; ++s) {
-            wide_stage(buf, a.np, a.ts, s_pairs, s_soff[s], s_soff[s + 1] - s_soff[s]);
+            wide_stage(buf, a.tsp, a.ts, s_pairs, s_soff[s], s_soff[s + 1] - s_soff[s]);
             __syncthreads();
         }
     }
     for (int k = 0; k < a.n_leaves; ++k) {
         const int* d = s_desc + kWDesc * k;
         const T* M = mats + (a.inverse ? d[4] : d[3]);
-        wide_leaf_dispatch<T>(d[5], buf, a.np, a.ts, s_lab + d[2], M, d[0], d[1], d[6], d[7], mbuf, a.chunk_elems);
+        wide_leaf_dispatch<T>(d[5], buf, a.tsp, a.ts, s_lab + d[2], M, d[0], d[1], d[6], d[7], mbuf, a.chunk_elems);
     }
     __syncthreads();   // every leaf's outputs written
     if (a.inverse) {
         for (int s = a.n_stages - 1; s >= 0; --s) {
-            wide_stage(buf, a.np, a.ts, s_pairs, s_soff[s], s_soff[s + 1] - s_soff[s]);
+            wide_stage(buf, a.tsp, a.ts, s_pairs, s_soff[s], s_soff[s + 1] - s_soff[s]);
             __syncthreads();
         }
     }
 }
 
 template <class T>
-__device__ __forceinline__ KArgs wide_store_args(const WArgs& a) {
-    KArgs ka{};
-    ka.y = a.y;
-    ka.batch = a.batch;
-    ka.n = a.n;
-    ka.np = a.np;
-    ka.ts = a.ts;
-    ka.inverse = a.inverse;
-    ka.inv_n = a.inv_n;
-    return ka;
-}
-
-template <class T>
-__global__ void __launch_bounds__(kWThreads) gft_wide_kernel(WArgs a) {
+__global__ void __launch_bounds__(kWThreads, 2) gft_wide_kernel(WArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     // [nbuf tiles][2 matrix chunks][tables]
     T* tiles = reinterpret_cast<T*>(smem_raw);
-    const int tile_elems = a.ts * a.np;
+    const int tile_elems = a.n * a.tsp;
     T* mbuf = tiles + a.nbuf * tile_elems;
     int* s_ints = reinterpret_cast<int*>(mbuf + 2 * a.chunk_elems);
     const int* s_src = s_ints + 2 * a.n_pairs + a.n_stages + 1 + a.n;
     wide_load_tables(a, s_ints);
     __syncthreads();
     const long long n_tiles = (a.batch + a.ts - 1) / a.ts;
-    const KArgs ka = wide_store_args<T>(a);
     long long tile = blockIdx.x;
     if (tile < n_tiles) wide_load<T>(a, s_src, tiles, tile);
     cp_async_commit();
@@ -328,7 +365,7 @@ __global__ void __launch_bounds__(kWThreads) gft_wide_kernel(WArgs a) {
         }
         __syncthreads();   // tile landed
         wide_compute<T>(a, buf, mbuf, s_ints);
-        store_tile<T, kWThreads>(ka, s_src, buf, tile);
+        wide_store<T>(a, s_src, buf, tile);
         __syncthreads();   // buffer free
         if (a.nbuf == 2) {
             cur ^= 1;
@@ -350,7 +387,7 @@ struct WBatchPlan {
     long long item0;
 };
 
-__global__ void __launch_bounds__(kWThreads) gft_wide_batch_kernel(const WBatchPlan* __restrict__ plans, int n_plans,
+__global__ void __launch_bounds__(kWThreads, 2) gft_wide_batch_kernel(const WBatchPlan* __restrict__ plans, int n_plans,
                                                                    long long total_items,
                                                                    unsigned long long* counter, int tile_cap,
                                                                    int chunk_cap) {
@@ -394,7 +431,7 @@ __global__ void __launch_bounds__(kWThreads) gft_wide_batch_kernel(const WBatchP
         cp_async_wait0();
         __syncthreads();
         wide_compute<float>(a, buf, mbuf, s_ints);
-        store_tile<float, kWThreads>(wide_store_args<float>(a), s_src, buf, tile);
+        wide_store<float>(a, s_src, buf, tile);
         __syncthreads();   // tile buffer and s_item free
     }
 }
@@ -410,10 +447,12 @@ int ilog2(int v) {
     return l;
 }
 
-int row_stride(int n, size_t esz) {
-    // float: np = 4 (mod 32); double: np = 2 (mod 16)
-    const int mod = esz == 4 ? 32 : 16, want = esz == 4 ? 4 : 2;
-    return n + ((want - n % mod) % mod + mod) % mod;
+// Signal stride of the transposed tile: a multiple of the 16-byte vector
+// (rows stay aligned) that is 4 (mod 8) floats, so the 8-node x 4-signal
+// blocks of the tile load hit 32 distinct banks; FP64: 2 (mod 4).
+int signal_stride(int ts, size_t esz) {
+    if (esz == 4) return ts % 8 == 0 ? ts + 4 : ts + 8;
+    return ts % 4 == 0 ? ts + 2 : ts + 4;
 }
 
 struct WVariant {
@@ -437,7 +476,8 @@ WVariant pick_variant(int P, int ts, size_t esz) {
         if (lc < 1 || lc > 32) continue;
         const int vloads = std::max(1, oc / vw);
         const double m_wave = vloads * std::max(1.0, lc * (double)std::min(oc, vw) * esz / 128.0);
-        const double ratio = (double)(rs * oc) / (rs + m_wave);
+        const double v_wave = std::max(1, rs / vw);   // broadcast within a signal group
+        const double ratio = (double)(rs * oc) / (v_wave + m_wave);
         if (ratio > best_ratio) {
             best_ratio = ratio;
             best = {rs, oc, lc};
@@ -507,7 +547,6 @@ void wide_build(gft_plan_s& p) {
         const int ints_smem = 2 * p.dev.n_pairs + p.dev.n_stages + 1 + 2 * n + kWDesc * (int)p.leaves.size();
         for (int prec = 0; prec < 2; ++prec) {
             const size_t esz = prec == 0 ? 4 : 8;
-            const int np = row_stride(n, esz);
             int maxP = 4;
             for (int P : Ps) maxP = std::max(maxP, P);
             WidePlan::Cfg& c = W->cfg[prec];
@@ -533,7 +572,7 @@ void wide_build(gft_plan_s& p) {
                 }
                 if (!ok) continue;
                 const size_t fixed = esz * 2 * (size_t)chunk + sizeof(int) * (size_t)((ints_smem + 3) & ~3);
-                const size_t tile = esz * (size_t)ts * np;
+                const size_t tile = esz * (size_t)n * signal_stride(ts, esz);
                 int nbuf = 0;
                 if (fixed + 2 * tile <= (size_t)kWSmemLimit / 2 - 1024) nbuf = 2;
                 else if (fixed + tile <= (size_t)kWSmemLimit) nbuf = 1;
@@ -655,7 +694,7 @@ static void launch_wide_t(gft_plan_s& p, const T* x, T* y, int64_t batch, bool i
     a.mats = prec ? (const void*)W->d_m64 : (const void*)W->d_m32;
     a.batch = batch;
     a.n = p.n;
-    a.np = row_stride(p.n, sizeof(T));
+    a.tsp = signal_stride(c.ts, sizeof(T));
     a.ts = c.ts;
     a.nbuf = c.nbuf;
     a.n_pairs = p.dev.n_pairs;
@@ -665,7 +704,6 @@ static void launch_wide_t(gft_plan_s& p, const T* x, T* y, int64_t batch, bool i
     a.off_src = a.off_labels + 2 * p.n;
     a.chunk_elems = c.chunk_elems;
     a.inverse = inverse ? 1 : 0;
-    a.inv_n = 1.0f / (float)p.n;
     auto fn = gft_wide_kernel<T>;
     GFT_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem));
     int per_sm = 0;
@@ -715,7 +753,7 @@ void* wide_batch_create(const std::vector<gft_plan_s*>& plans, const std::vector
         a.mats = W->d_m32;
         a.batch = batches[i];
         a.n = p.n;
-        a.np = row_stride(p.n, 4);
+        a.tsp = signal_stride(c.ts, 4);
         a.ts = c.ts;
         a.nbuf = 1;
         a.n_pairs = p.dev.n_pairs;
@@ -725,11 +763,10 @@ void* wide_batch_create(const std::vector<gft_plan_s*>& plans, const std::vector
         a.off_src = a.off_labels + 2 * p.n;
         a.chunk_elems = c.chunk_elems;
         a.inverse = 0;
-        a.inv_n = 1.0f / (float)p.n;
         double fl = 0;
         for (auto& lf : p.leaves) fl += (double)lf.m() * lf.m();
         cost[i] = (fl + 8.0 * p.n) * c.ts;
-        B->tile_cap = std::max(B->tile_cap, c.ts * a.np);
+        B->tile_cap = std::max(B->tile_cap, p.n * a.tsp);
         B->chunk_cap = std::max(B->chunk_cap, c.chunk_elems);
         ints_cap = std::max(ints_cap, 2 * a.n_pairs + a.n_stages + 1 + 2 * a.n + kWDesc * a.n_leaves);
     }
