@@ -5,13 +5,13 @@
 // y_k = M_k^T v_k (Sec. IV-C, Eq. 13; M_k the folded leaf basis) are dense
 // contractions, run here as GEMMs D[128 x N] = A[128 x K] B[K x N] per tile
 // of 128 signals:
-//   1. tc_pack_kernel: the Haar stages, written as signed sums of the input
-//      entries (each post-stage value is +-x_i1 +- x_i2 ..., one term per
-//      node of its orbit), converted to BF16 (hi, and lo = v - hi for the
-//      split precisions) or per-signal scaled FP16 hi/lo, and written as
-//      ready-made shared-memory images: per tile of 128 signals and per item
-//      (leaf, K chunk of 64), a 128 x 64 block in the canonical no-swizzle
-//      K-major layout (8 x 16-byte core matrices), hi then lo;
+//   1. tc_pack8_kernel: eight signals per warp step, staged in shared
+//      memory by cp.async; the Haar stages in place; each post-stage value
+//      converted to BF16 (hi, and lo = v - hi for the split precisions) or
+//      per-signal scaled FP16 hi/lo, and written as ready-made shared-memory
+//      images: per tile of 128 signals and per item (leaf, K chunk of 64), a
+//      128 x 64 block in the canonical no-swizzle K-major layout (8 x 16-byte
+//      core matrices), hi then lo, with 512-byte coalesced stores;
 //   2. tc_leaf_kernel (persistent, one CTA per SM): one thread bulk-loads
 //      (TMA) the A image and the leaf's pre-split B image of each item into
 //      a two-deep ring of shared-memory buffers, issues tcgen05.mma (M=128,
@@ -155,7 +155,7 @@ struct TcItem {
 
 // Persistent tensor-core kernel.  Thread 0 drives a ring of shared-memory
 // buffers: it bulk-loads (TMA) the A image of item q (written by
-// tc_pack_kernel) -- and, unless every B image is resident, the item's B
+// tc_pack8_kernel) -- and, unless every B image is resident, the item's B
 // images -- into buffer q % nbuf, waits for the load, issues the item's MMAs,
 // commits them to the buffer's MMA barrier, and before reusing the buffer
 // waits for those MMAs to finish reading it.  When all B images fit in
@@ -386,97 +386,141 @@ teardown:
     }
 }
 
-// A images: for tile, item (leaf, K chunk), 128 rows x 64 K as BF16 (or
-// scaled FP16) hi then lo in the core-matrix order.  One warp per signal:
-// a coalesced read of the row into a per-warp shared buffer, the Haar units
-// of every stage applied in place (a+b, a-b; the 1/sqrt2 factors are folded
-// into B), then each lane forms 16-byte core-matrix rows (8 consecutive K of
-// one item) by reading the leaf's node slots.  Persistent blocks, tables in
-// shared memory.
-constexpr int kPackWarps = 8;
-__global__ void __launch_bounds__(kPackWarps * 32) tc_pack_kernel(
-    const float* __restrict__ x, unsigned char* __restrict__ aimg, long long batch, int n,
-    const TcLeaf* __restrict__ leaves, const TcItem* __restrict__ items, int n_items,
-    const int* __restrict__ pairs, int n_pairs, const int* __restrict__ stage_off, int n_stages,
-    const int* __restrict__ labels, const float* __restrict__ scale, int prec) {
-    extern __shared__ __align__(16) float sx[];
-    int* s_pairs = reinterpret_cast<int*>(sx + (size_t)kPackWarps * n);
-    int* s_soff = s_pairs + 2 * n_pairs;
-    int* s_lab = s_soff + n_stages + 1;
+// A images, eight signals per warp step.  A warp owns a group of 8
+// consecutive signals (one 8-row block of the core-matrix layout): the rows
+// arrive in a per-warp shared buffer (row stride n + 4) by 16-byte cp.async
+// copies, the next group's copies overlapping this group's work; the Haar
+// units of every stage run in place; for FP16 the warp also computes each
+// signal's power-of-two scale (written to `scale`).  Lane (r, sub) then
+// forms 16-byte core-matrix rows for K groups kg = sub, sub + 4, ...: the 32
+// lanes of a store instruction cover 4 K groups x 8 rows = 512 contiguous
+// bytes of the image, hi and lo.  gather[item * 64 + k] is the slot whose
+// value feeds K index k of the item (-1: zero padding).
+constexpr int kPack8Warps = 4;
+__global__ void __launch_bounds__(kPack8Warps * 32) tc_pack8_kernel(
+    const float* __restrict__ x, unsigned char* __restrict__ aimg, float* __restrict__ scale, long long batch,
+    int n, const short* __restrict__ gather, int n_items, const int* __restrict__ pairs, int n_pairs,
+    const int* __restrict__ stage_off, int n_stages, int prec, int nbuf) {
+    extern __shared__ __align__(16) float sbuf[];
+    const int rs = n + 4;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    float* wbuf = sbuf + (size_t)warp * nbuf * 8 * rs;                  // one or two 8-row buffers per warp
+    int* s_pairs = reinterpret_cast<int*>(sbuf + (size_t)kPack8Warps * nbuf * 8 * rs);
+    int* s_soff = s_pairs + 2 * n_pairs;
+    short* s_gather = reinterpret_cast<short*>(s_pairs + ((2 * n_pairs + n_stages + 1 + 3) & ~3));   // 16-byte aligned
     for (int i = tid; i < 2 * n_pairs; i += blockDim.x) s_pairs[i] = pairs[i];
     for (int i = tid; i <= n_stages; i += blockDim.x) s_soff[i] = stage_off[i];
-    for (int i = tid; i < n; i += blockDim.x) s_lab[i] = labels[i];
+    for (int i = tid; i < n_items * 64; i += blockDim.x) s_gather[i] = gather[i];
     __syncthreads();
     const bool fp16 = prec == GFT_PREC_FP16X3, split = prec != GFT_PREC_BF16;
-    const long long n_tiles = (batch + kTcM - 1) / kTcM;
-    const long long rows_total = n_tiles * kTcM;   // padded rows are packed as zeros
-    float* xr = sx + warp * n;
-    const int segs = n_items * 8;
-    for (long long row = blockIdx.x * (long long)kPackWarps + warp; row < rows_total;
-         row += (long long)gridDim.x * kPackWarps) {
-        const bool live = row < batch;
-        for (int c = lane; c < n; c += 32) xr[c] = live ? __ldcs(x + row * n + c) : 0.f;
+    const long long n_groups = (batch + kTcM - 1) / kTcM * (kTcM / 8);
+    const bool vec = (n & 3) == 0;
+    auto issue = [&](long long G, float* buf) {
+        const long long row0 = G * 8;
+        const int valid = (int)max(0LL, min(8LL, batch - row0));
+        if (vec) {
+            const int per = n >> 2;
+            for (int c = lane; c < valid * per; c += 32) {
+                const int r = c / per, k = c - r * per;
+                const unsigned d = (unsigned)__cvta_generic_to_shared(buf + r * rs + 4 * k);
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(x + (row0 + r) * n + 4 * k)
+                             : "memory");
+            }
+        } else {
+            for (int c = lane; c < valid * n; c += 32) {
+                const int r = c / n, k = c - r * n;
+                const unsigned d = (unsigned)__cvta_generic_to_shared(buf + r * rs + k);
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(x + (row0 + r) * n + k) : "memory");
+            }
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    const long long stride = (long long)gridDim.x * kPack8Warps;
+    long long G = blockIdx.x * (long long)kPack8Warps + warp;
+    int cur = 0;
+    if (G < n_groups) issue(G, wbuf);
+    for (; G < n_groups; G += stride) {
+        float* buf = wbuf + cur * 8 * rs;
+        if (nbuf == 2 && G + stride < n_groups) issue(G + stride, wbuf + (cur ^ 1) * 8 * rs);
+        else asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
         __syncwarp();
+        const long long row0 = G * 8;
+        const int valid = (int)max(0LL, min(8LL, batch - row0));
+        float inv[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) inv[r] = 1.f;
+        if (fp16) {
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                float m = 0.f;
+                if (r < valid)
+                    for (int j = lane; j < n; j += 32) m = fmaxf(m, fabsf(buf[r * rs + j]));
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+                const float sc = m > 0.f ? exp2f(ceilf(log2f(m)) + (float)n_stages) : 1.f;
+                inv[r] = 1.f / sc;
+                if (lane == 0 && r < valid) scale[row0 + r] = sc;
+            }
+        }
+        // Haar units: lanes over the pairs of a stage, the 8 rows unrolled
+        // (rows past the batch hold stale values that are never stored)
         for (int s = 0; s < n_stages; ++s) {
-            for (int q = s_soff[s] + lane; q < s_soff[s + 1]; q += 32) {
-                const int i = s_pairs[2 * q], j = s_pairs[2 * q + 1];
-                const float u = xr[i], w = xr[j];
-                xr[i] = u + w;
-                xr[j] = u - w;
+            const int p1 = s_soff[s + 1];
+            for (int pp = s_soff[s] + lane; pp < p1; pp += 32) {
+                const int2 uv = *reinterpret_cast<const int2*>(s_pairs + 2 * pp);
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    float* row = buf + r * rs;
+                    const float xu = row[uv.x], xv = row[uv.y];
+                    row[uv.x] = xu + xv;
+                    row[uv.y] = xu - xv;
+                }
             }
             __syncwarp();
         }
-        const float inv = (fp16 && live) ? 1.f / scale[row] : 1.f;
-        const long long tile = row / kTcM;
-        const int r = (int)(row - tile * kTcM);
-        for (int sg = lane; sg < segs; sg += 32) {
-            const int item = sg >> 3, kg = sg & 7;
-            const TcItem it = items[item];
-            const TcLeaf L = leaves[it.leaf];
+        const long long tile = row0 / kTcM;
+        const int rt = (int)(row0 - tile * kTcM);   // first row of the group within the tile
+        const int r = lane & 7, sub = lane >> 3;
+        const bool live = r < valid;
+        const float* row = buf + r * rs;
+        const float sc = inv[r];
+        for (int kg = sub; kg < n_items * 8; kg += 4) {
             float v[8];
+            const int4 g4 = *reinterpret_cast<const int4*>(s_gather + kg * 8);   // eight slot indices
+            const short* gs = reinterpret_cast<const short*>(&g4);
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int c = it.kc * kTcK + kg * 8 + q;
-                v[q] = c < L.m ? xr[s_lab[L.off + c]] * inv : 0.f;
+            for (int e = 0; e < 8; ++e) {
+                const int lab = gs[e];
+                v[e] = (live && lab >= 0) ? row[lab] * sc : 0.f;
             }
             unsigned hi[4], lo[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
+            for (int q = 0; q < 4; ++q) {   // two values per conversion instruction
                 if (fp16) {
-                    const __half h0 = __float2half_rn(v[2 * q]), h1 = __float2half_rn(v[2 * q + 1]);
-                    const __half l0 = __float2half_rn(v[2 * q] - __half2float(h0));
-                    const __half l1 = __float2half_rn(v[2 * q + 1] - __half2float(h1));
-                    hi[q] = (unsigned)__half_as_ushort(h0) | ((unsigned)__half_as_ushort(h1) << 16);
-                    lo[q] = (unsigned)__half_as_ushort(l0) | ((unsigned)__half_as_ushort(l1) << 16);
+                    const __half2 h = __floats2half2_rn(v[2 * q], v[2 * q + 1]);
+                    const float2 hf = __half22float2(h);
+                    const __half2 l = __floats2half2_rn(v[2 * q] - hf.x, v[2 * q + 1] - hf.y);
+                    hi[q] = *reinterpret_cast<const unsigned*>(&h);
+                    lo[q] = *reinterpret_cast<const unsigned*>(&l);
                 } else {
-                    const __nv_bfloat16 h0 = __float2bfloat16_rn(v[2 * q]), h1 = __float2bfloat16_rn(v[2 * q + 1]);
-                    const __nv_bfloat16 l0 = __float2bfloat16_rn(v[2 * q] - __bfloat162float(h0));
-                    const __nv_bfloat16 l1 = __float2bfloat16_rn(v[2 * q + 1] - __bfloat162float(h1));
-                    hi[q] = (unsigned)__bfloat16_as_ushort(h0) | ((unsigned)__bfloat16_as_ushort(h1) << 16);
-                    lo[q] = (unsigned)__bfloat16_as_ushort(l0) | ((unsigned)__bfloat16_as_ushort(l1) << 16);
+                    const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+                    const float2 hf = __bfloat1622float2(h);
+                    const __nv_bfloat162 l = __floats2bfloat162_rn(v[2 * q] - hf.x, v[2 * q + 1] - hf.y);
+                    hi[q] = *reinterpret_cast<const unsigned*>(&h);
+                    lo[q] = *reinterpret_cast<const unsigned*>(&l);
                 }
             }
-            unsigned char* dst = aimg + ((size_t)tile * n_items + item) * 32768u + core_off(r, kg);
+            const int item = kg >> 3;
+            unsigned char* dst = aimg + ((size_t)tile * n_items + item) * 32768u + core_off(rt + r, kg & 7);
             __stcg(reinterpret_cast<uint4*>(dst), make_uint4(hi[0], hi[1], hi[2], hi[3]));
             if (split) __stcg(reinterpret_cast<uint4*>(dst + 16384), make_uint4(lo[0], lo[1], lo[2], lo[3]));
         }
-        __syncwarp();
+        __syncwarp();   // buffer reusable by the copies issued next
+        if (nbuf == 2) cur ^= 1;
+        else if (G + stride < n_groups) issue(G + stride, wbuf);
     }
-}
-
-// FP16 split: one power-of-two scale per signal bounding its post-stage
-// values (|v| <= 2^S max|x|), so hi and lo keep their precision
-__global__ void tc_scale_kernel(const float* __restrict__ x, float* __restrict__ scale, long long batch, int n,
-                                int n_stages) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (long long r = blockIdx.x * (long long)(blockDim.x >> 5) + warp; r < batch;
-         r += (long long)gridDim.x * (blockDim.x >> 5)) {
-        float m = 0.f;
-        for (int j = lane; j < n; j += 32) m = fmaxf(m, fabsf(x[r * n + j]));
-        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if (lane == 0) scale[r] = m > 0.f ? exp2f(ceilf(log2f(m)) + (float)n_stages) : 1.f;
-    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
 // group mode: y[t][j] = z[t][srcmap[j]] (z leaf ordered)
@@ -492,24 +536,22 @@ __global__ void tc_permute_kernel(const float* __restrict__ z, float* __restrict
 }
 
 struct TcPlan {
-    int n = 0, n_leaves = 0, n_groups = 0, direct = 0, n_items = 0, n_stages = 0, n_terms = 0;
+    int n = 0, n_leaves = 0, n_groups = 0, direct = 0, n_items = 0, n_stages = 0;
     unsigned total_b = 0;   // bytes of all hi B images
     TcLeaf* d_leaves = nullptr;
     TcItem* d_items = nullptr;
     int* d_colmap = nullptr;
     int* d_srcmap = nullptr;
-    int* d_term_off = nullptr;
-    int* d_term_src = nullptr;
-    float* d_term_sign = nullptr;
     __nv_bfloat16* d_bhi = nullptr;
     __nv_bfloat16* d_blo = nullptr;
     __half* d_fhi = nullptr;
     __half* d_flo = nullptr;
+    short* d_gather = nullptr;         // [items][64]: slot feeding each K index (-1: padding)
     TcScratch own;                     // the plan's scratch for its own transforms
     ~TcPlan() {
-        for (void* p : {(void*)d_leaves, (void*)d_items, (void*)d_colmap, (void*)d_srcmap, (void*)d_term_off,
-                        (void*)d_term_src, (void*)d_term_sign, (void*)d_bhi, (void*)d_blo, (void*)d_fhi,
-                        (void*)d_flo})
+        for (void* p : {(void*)d_leaves, (void*)d_items, (void*)d_colmap, (void*)d_srcmap, (void*)d_bhi,
+                        (void*)d_blo, (void*)d_fhi,
+                        (void*)d_flo, (void*)d_gather})
             if (p) cudaFree(p);
     }
 };
@@ -585,28 +627,6 @@ void tc_build(gft_plan_s& p) {
                     srcmap[p.out_pos[i]] = i;
                 }
         }
-        // stage terms: post-stage value at label l as signed sum of inputs
-        std::vector<std::vector<std::pair<int, float>>> comb(n);
-        for (int l = 0; l < n; ++l) comb[l] = {{l, 1.f}};
-        for (auto& st : p.stages)
-            for (auto& pr : st) {
-                auto a = comb[pr.first], b = comb[pr.second];
-                std::vector<std::pair<int, float>> u = a, w = a;
-                for (auto& t : b) u.push_back(t);
-                for (auto& t : b) w.push_back({t.first, -t.second});
-                comb[pr.first] = u;
-                comb[pr.second] = w;
-            }
-        std::vector<int> toff(1, 0), tsrc;
-        std::vector<float> tsign;
-        for (auto& lf : p.leaves)
-            for (int lab : lf.labels) {
-                for (auto& t : comb[lab]) {
-                    tsrc.push_back(t.first);
-                    tsign.push_back(t.second);
-                }
-                toff.push_back((int)tsrc.size());
-            }
         // B images: for each leaf and K chunk, npad rows (outputs c) x 64 K
         // (inputs r) in the smem core-matrix order; B[c][r] = M_k[r][c]
         std::vector<uint16_t> bhi(boff, 0), blo(boff, 0), fhi(boff, 0), flo(boff, 0);
@@ -641,15 +661,23 @@ void tc_build(gft_plan_s& p) {
             }
         T->total_b = bres;
         T->n_items = (int)items.size();
+        {
+            std::vector<short> gat(items.size() * 64, -1);
+            for (size_t it = 0; it < items.size(); ++it) {
+                const TcLeaf& t = L[items[it].leaf];
+                const Leaf& lf = p.leaves[items[it].leaf];
+                for (int k = 0; k < 64; ++k) {
+                    const int c = items[it].kc * kTcK + k;
+                    if (c < t.m) gat[it * 64 + k] = (short)lf.labels[c];
+                }
+            }
+            T->d_gather = upload(gat);
+        }
         T->n_stages = p.n_stages;
         T->d_items = upload(items);
         T->d_leaves = upload(L);
         T->d_colmap = upload(colmap);
         T->d_srcmap = upload(srcmap);
-        T->n_terms = (int)tsrc.size();
-        T->d_term_off = upload(toff);
-        T->d_term_src = upload(tsrc);
-        T->d_term_sign = upload(tsign);
         T->d_bhi = reinterpret_cast<__nv_bfloat16*>(upload(bhi));
         T->d_blo = reinterpret_cast<__nv_bfloat16*>(upload(blo));
         T->d_fhi = reinterpret_cast<__half*>(upload(fhi));
@@ -702,27 +730,25 @@ void launch_tc(gft_plan_s& p, const float* x, float* y, int64_t batch, bool inve
     TcScratch& S = scratch ? *scratch : T->own;
     tc_reserve(p, S, batch);
     const int sms = sm_count();
-    if (precision == GFT_PREC_FP16X3) {
-        tc_scale_kernel<<<sms * 4, 256, 0, st>>>(x, S.d_scale, batch, n, T->n_stages);
-        GFT_CUDA(cudaGetLastError());
-    }
     {
         const DevProgram& d = p.dev;
-        const size_t smem = sizeof(float) * (size_t)kPackWarps * n +
-                            sizeof(int) * (size_t)(2 * d.n_pairs + d.n_stages + 1 + n);
+        const size_t tabs = sizeof(int) * (size_t)((2 * d.n_pairs + d.n_stages + 1 + 3) & ~3) +
+                            sizeof(short) * 64 * T->n_items;
+        const size_t per_buf = sizeof(float) * (size_t)kPack8Warps * 8 * (n + 4);
+        const int nbuf = 2 * per_buf + tabs <= 232448 / 2 ? 2 : 1;   // double buffer if two CTAs still fit
+        const size_t smem = nbuf * per_buf + tabs;
         if (smem > 232448) fail(GFT_ERR_UNSUPPORTED, "tensor-core pack stage does not fit in shared memory");
-        GFT_CUDA(cudaFuncSetAttribute(tc_pack_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        GFT_CUDA(cudaFuncSetAttribute(tc_pack8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int per_sm = 0;
-        GFT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc_pack_kernel, kPackWarps * 32, smem));
-        const long long need = (n_tiles * kTcM + kPackWarps - 1) / kPackWarps;
-        const long long blocks = std::min<long long>(need, (long long)std::max(1, per_sm) * sms);
-        // program tables: [pairs 2P][stage offsets S+1][labels n] at the start of the plan's ints
+        GFT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc_pack8_kernel, kPack8Warps * 32, smem));
+        const long long groups = n_tiles * (kTcM / 8);
+        const long long blocks = std::min<long long>((groups + kPack8Warps - 1) / kPack8Warps,
+                                                     (long long)std::max(1, per_sm) * sms);
         const int* pairs = d.d_ints;
         const int* soff = d.d_ints + 2 * d.n_pairs;
-        const int* labels = d.d_ints + 2 * d.n_pairs + d.n_stages + 1;
-        tc_pack_kernel<<<(unsigned)blocks, kPackWarps * 32, smem, st>>>(
-            x, S.d_aimg, batch, n, T->d_leaves, T->d_items, T->n_items, pairs, d.n_pairs, soff, d.n_stages,
-            labels, S.d_scale, (int)precision);
+        tc_pack8_kernel<<<(unsigned)blocks, kPack8Warps * 32, smem, st>>>(
+            x, S.d_aimg, S.d_scale, batch, n, T->d_gather, T->n_items, pairs, d.n_pairs, soff, d.n_stages,
+            (int)precision, nbuf);
         GFT_CUDA(cudaGetLastError());
     }
     TcArgs a{};
