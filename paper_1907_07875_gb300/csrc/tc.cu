@@ -12,20 +12,17 @@
 //      images: per tile of 128 signals and per item (leaf, K chunk of 64), a
 //      128 x 64 block in the canonical no-swizzle K-major layout (8 x 16-byte
 //      core matrices), hi then lo, with 512-byte coalesced stores;
-//   2. tc_leaf_kernel (persistent, one CTA per SM): one thread bulk-loads
-//      (TMA) the A image and the leaf's pre-split B image of each item into
-//      a two-deep ring of shared-memory buffers, issues tcgen05.mma (M=128,
-//      N=leaf width, K=16 per instruction) into the leaf's TMEM columns --
-//      one product for BF16, three (hi*hi + hi*lo + lo*hi) for the split
-//      precisions -- and commits to mbarriers; loads of the next items
-//      overlap the MMAs and the epilogue.  Every wait is bounded (about 2 s,
-//      then GFT_ERR_TIMEOUT, drain, TMEM freed).
-//   3. Epilogue: when every leaf of the plan fits the 512 TMEM columns, each
-//      warp reads its 32 rows column by column IN COEFFICIENT ORDER
-//      (tcgen05.ld 32x32b) and writes 32 consecutive coefficients per row,
-//      so the ascending-eigenvalue permutation costs nothing; otherwise the
-//      leaves are processed in groups that fit, each group's D is written to
-//      a leaf-ordered scratch, and tc_permute_kernel produces the output.
+//   2. tc_leaf_kernel (persistent, one CTA per SM, warp-specialised): a
+//      copy thread streams the A images (and B images unless they are
+//      resident) through a ring of shared-memory slots with bulk copies, an
+//      MMA thread issues tcgen05.mma (M=128, N=leaf width, K=16 per
+//      instruction) into the leaf's TMEM columns -- one product for BF16,
+//      three (hi*hi + hi*lo + lo*hi) for the split precisions -- and four
+//      epilogue warps read the double-buffered accumulators (groups of
+//      leaves of at most 256 columns) column by column IN COEFFICIENT ORDER
+//      (tcgen05.ld 32x32b), so the ascending-eigenvalue permutation costs
+//      nothing, and store 32 output positions per row.  Every wait is bounded
+//      (about 2 s, then GFT_ERR_TIMEOUT, drain, TMEM freed).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -41,9 +38,10 @@ namespace {
 
 constexpr int kTcM = 128;        // signals per tile = MMA M
 constexpr int kTcK = 64;         // K chunk staged per step
-constexpr int kTcThreads = 128;  // 4 warps = 128 TMEM lanes
+constexpr int kTcThreads = 192;  // warps 0-3 epilogue (128 TMEM lanes), 4 copies, 5 MMAs
 constexpr int kTcMaxN = 256;     // widest leaf handled in one MMA
 constexpr int kTcCols = 512;     // TMEM columns allocated per CTA (one CTA per SM)
+constexpr int kTcGroupCols = 256;   // columns of one accumulator buffer (two buffers)
 
 struct TcLeaf {
     int m;        // leaf size
@@ -56,15 +54,16 @@ struct TcLeaf {
 };
 
 struct TcArgs {
-    float* y;                // [batch, n] output (direct mode) or scratch (group mode)
+    float* y;                // [batch, n] coefficients
     const TcLeaf* leaves;
-    const int* colmap;       // direct mode: TMEM column of coefficient j
+    const int* gmap;         // [2n + 2(G+1)]: per group (outputs sorted): coefficient index, TMEM
+                             // column; then group offsets into those lists, then first item per group
     const __nv_bfloat16* bhi;
     const __nv_bfloat16* blo;
     const __half* fhi;
     const __half* flo;
     long long batch;
-    int n, n_leaves, n_groups, prec, direct;
+    int n, n_leaves, n_groups, prec;
     int* err;
 };
 
@@ -153,22 +152,37 @@ struct TcItem {
     int bres;   // byte offset of this item's B image among the resident images (hi set)
 };
 
-// Persistent tensor-core kernel.  Thread 0 drives a ring of shared-memory
-// buffers: it bulk-loads (TMA) the A image of item q (written by
-// tc_pack8_kernel) -- and, unless every B image is resident, the item's B
-// images -- into buffer q % nbuf, waits for the load, issues the item's MMAs,
-// commits them to the buffer's MMA barrier, and before reusing the buffer
-// waits for those MMAs to finish reading it.  When all B images fit in
-// 96 KB they are loaded once per CTA and the ring holds four A images;
-// otherwise two A+B buffers.  After the MMAs of a tile's leaf group all four
-// warps read TMEM (lane = signal) and write the coefficients.
+// Persistent tensor-core kernel, one CTA per SM, warp-specialised:
+//   warp 4 (one thread) bulk-loads (TMA) the A image of each work item
+//     (leaf, 64-wide K chunk) of each tile -- written by tc_pack8_kernel --
+//     and, unless every B image is resident, the item's B images, into a
+//     ring of shared-memory slots (4 slots of A when all B images fit in
+//     96 KB and are loaded once, else 2 slots of A + B);
+//   warp 5 (one thread) waits for a slot, issues its MMAs (M = 128 signals,
+//     N = leaf width, K = 16 per instruction; one product for BF16, three
+//     -- hi*hi + hi*lo + lo*hi -- for the split precisions) into the TMEM
+//     columns of the item's leaf, and commits them to the slot's "empty"
+//     barrier; after the last item of a leaf group it commits to the group's
+//     "accumulator full" barrier;
+//   warps 0-3 (the epilogue; warp w reads TMEM lanes 32w..32w+31) wait for a
+//     full accumulator, read its columns in coefficient order, transpose
+//     32 x 32 blocks through shared memory and store 32 consecutive output
+//     positions per row, then release the accumulator.
+// Leaves are grouped so that a group needs at most 256 TMEM columns; the
+// accumulator is double buffered (2 x 256 of the 512 columns), so the
+// epilogue of one group overlaps the copies and MMAs of the next.  When all
+// leaves form one group the stores are 128-byte row segments in output
+// order; otherwise each group writes its own (sorted) output positions.
+// Every wait gives up after about two seconds (GFT_ERR_TIMEOUT in the plan's
+// error word; all roles leave their loops; copies and MMAs in flight are
+// awaited, again bounded, before the TMEM columns are freed).
 struct TcRing {
     int resident;       // B images resident in shared memory
     int nbuf;           // ring depth
     unsigned bufsz;     // bytes per ring buffer
     unsigned res_off;   // byte offset of the resident B region
     unsigned total_b;   // bytes of all hi B images (lo images follow)
-    unsigned meta_off;  // byte offset of [items][leaves][colmap][epilogue staging]
+    unsigned meta_off;  // byte offset of [items][leaves][gmap][epilogue staging]
 };
 
 constexpr int kStageLd = 33;   // epilogue staging row stride (floats): conflict-free
@@ -178,25 +192,25 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_leaf_kernel(TcArgs a, const 
                                                                const float* __restrict__ scale, TcRing ring) {
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ unsigned s_tmem;
-    __shared__ __align__(8) unsigned long long bar_load[4];
-    __shared__ __align__(8) unsigned long long bar_mma[4];
-    __shared__ __align__(8) unsigned long long bar_done;
-    __shared__ __align__(8) unsigned long long bar_b;
-    __shared__ int s_bad;
+    __shared__ __align__(8) unsigned long long bar_full[4], bar_empty[4], bar_dfull[2], bar_dfree[2], bar_b;
+    __shared__ int s_abort;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // per-CTA copies of the item list, leaf table and coefficient map
-    // layout (every part 16-byte aligned): items, leaves, colmap, staging
+    // per-CTA copies of the item list, leaf table and output maps (16-byte aligned parts)
     unsigned char* meta = sm + ring.meta_off;
     TcItem* s_items = reinterpret_cast<TcItem*>(meta);
     const size_t items_bytes = (sizeof(TcItem) * n_items + 15) & ~size_t(15);
     TcLeaf* s_leaves = reinterpret_cast<TcLeaf*>(meta + items_bytes);
     const size_t leaves_bytes = (sizeof(TcLeaf) * a.n_leaves + 15) & ~size_t(15);
-    int* s_colmap = reinterpret_cast<int*>(meta + items_bytes + leaves_bytes);
-    float* s_stage = reinterpret_cast<float*>(s_colmap + ((a.n + 3) & ~3));
+    int* s_gmap = reinterpret_cast<int*>(meta + items_bytes + leaves_bytes);
+    const int gmap_ints = 2 * a.n + 2 * (a.n_groups + 1);
+    float* s_stage = reinterpret_cast<float*>(s_gmap + ((gmap_ints + 3) & ~3));
+    const int* s_gpos = s_gmap;                 // coefficient index, group by group
+    const int* s_gcol = s_gmap + a.n;           // TMEM column (within the buffer)
+    const int* s_goff = s_gmap + 2 * a.n;       // [G + 1] offsets into gpos / gcol
+    const int* s_gitem = s_goff + a.n_groups + 1;   // [G + 1] first item of each group
     for (int i = tid; i < n_items; i += blockDim.x) s_items[i] = items[i];
     for (int i = tid; i < a.n_leaves; i += blockDim.x) s_leaves[i] = a.leaves[i];
-    if (a.direct)
-        for (int i = tid; i < a.n; i += blockDim.x) s_colmap[i] = a.colmap[i];
+    for (int i = tid; i < gmap_ints; i += blockDim.x) s_gmap[i] = a.gmap[i];
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
                      "r"(kTcCols)
@@ -205,13 +219,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_leaf_kernel(TcArgs a, const 
     }
     if (tid == 0) {
         for (int i = 0; i < 4; ++i) {
-            mbar_init1(&bar_load[i]);
-            mbar_init1(&bar_mma[i]);
+            mbar_init1(&bar_full[i]);
+            mbar_init1(&bar_empty[i]);
         }
-        mbar_init1(&bar_done);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init1(&bar_dfull[i]);
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_dfree[i])), "r"(4) : "memory");
+        }
         mbar_init1(&bar_b);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        s_bad = 0;
+        s_abort = 0;
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -221,167 +238,166 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_leaf_kernel(TcArgs a, const 
     const bool fp16 = a.prec == GFT_PREC_FP16X3;
     const unsigned a_bytes = split ? 32768u : 16384u;
     const long long n_tiles = (a.batch + kTcM - 1) / kTcM;
-    unsigned ph_load[4] = {0, 0, 0, 0}, ph_mma[4] = {0, 0, 0, 0}, ph_done = 0;
-    long long issued = 0, consumed = 0;
-    bool pending_mma[4] = {false, false, false, false};
     const long long my_tiles = n_tiles > blockIdx.x ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-    const long long total = my_tiles * n_items;
     unsigned char* res = sm + ring.res_off;
     auto bsrc = [&](const TcLeaf& L, const TcItem& it, bool lo) {
         const size_t img = (size_t)L.npad * kTcK;
         if (fp16) return reinterpret_cast<const unsigned char*>((lo ? a.flo : a.fhi) + L.b_off + it.kc * img);
         return reinterpret_cast<const unsigned char*>((lo ? a.blo : a.bhi) + L.b_off + it.kc * img);
     };
-    auto issue = [&](long long q) {
-        const int s = (int)(q % ring.nbuf);
-        const long long tile = blockIdx.x + (q / n_items) * (long long)gridDim.x;
-        const TcItem it = s_items[q % n_items];
-        const TcLeaf L = s_leaves[it.leaf];
-        if (pending_mma[s]) {  // MMAs of item q - nbuf still read this buffer
-            if (!mbar_wait_bounded(&bar_mma[s], ph_mma[s])) s_bad = 1;
-            ph_mma[s] ^= 1u;
-            pending_mma[s] = false;
-        }
-        unsigned char* b = sm + (size_t)s * ring.bufsz;
-        const unsigned b_bytes = (unsigned)L.npad * kTcK * 2u;
-        mbar_expect(&bar_load[s], a_bytes + (ring.resident ? 0u : (split ? 2 * b_bytes : b_bytes)));
-        bulk_load(b, aimg + ((size_t)tile * n_items + (size_t)(q % n_items)) * 32768u, a_bytes, &bar_load[s]);
-        if (!ring.resident) {
-            bulk_load(b + 32768, bsrc(L, it, false), b_bytes, &bar_load[s]);
-            if (split) bulk_load(b + 65536, bsrc(L, it, true), b_bytes, &bar_load[s]);
-        }
+    auto abort_now = [&]() {
+        s_abort = 1;
+        atomicExch(a.err, (int)GFT_ERR_TIMEOUT);
     };
-    if (tid == 0) {
-        if (ring.resident && total > 0) {
-            mbar_expect(&bar_b, split ? 2 * ring.total_b : ring.total_b);
-            for (int i = 0; i < n_items; ++i) {
-                const TcItem it = s_items[i];
-                const TcLeaf L = s_leaves[it.leaf];
-                const unsigned b_bytes = (unsigned)L.npad * kTcK * 2u;
-                bulk_load(res + it.bres, bsrc(L, it, false), b_bytes, &bar_b);
-                if (split) bulk_load(res + ring.total_b + it.bres, bsrc(L, it, true), b_bytes, &bar_b);
-            }
-            if (!mbar_wait_bounded(&bar_b, 0)) s_bad = 1;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        for (; issued < total && issued < ring.nbuf; ++issued) issue(issued);
-    }
-    for (long long t = 0; t < my_tiles; ++t) {
-        const long long tile = blockIdx.x + t * (long long)gridDim.x;
-        const long long r0 = tile * kTcM;
-        for (int g = 0; g < a.n_groups; ++g) {
-            if (tid == 0) {
-                while (consumed < total && consumed < (t + 1) * n_items) {
-                    const TcItem it = s_items[consumed % n_items];
+
+    if (warp == 4) {
+        // ---------------- copies ----------------
+        if (lane == 0) {
+            if (ring.resident && my_tiles > 0) {
+                mbar_expect(&bar_b, split ? 2 * ring.total_b : ring.total_b);
+                for (int i = 0; i < n_items; ++i) {
+                    const TcItem it = s_items[i];
                     const TcLeaf L = s_leaves[it.leaf];
-                    if (L.group != g) break;
-                    const int s = (int)(consumed % ring.nbuf);
-                    if (!mbar_wait_bounded(&bar_load[s], ph_load[s])) s_bad = 1;
-                    ph_load[s] ^= 1u;
+                    const unsigned b_bytes = (unsigned)L.npad * kTcK * 2u;
+                    bulk_load(res + it.bres, bsrc(L, it, false), b_bytes, &bar_b);
+                    if (split) bulk_load(res + ring.total_b + it.bres, bsrc(L, it, true), b_bytes, &bar_b);
+                }
+            }
+            long long q = 0;
+            bool issued[4] = {false, false, false, false};
+            unsigned last_par[4] = {0, 0, 0, 0};
+            for (long long t = 0; t < my_tiles && !s_abort; ++t) {
+                const long long tile = blockIdx.x + t * (long long)gridDim.x;
+                for (int i = 0; i < n_items && !s_abort; ++i, ++q) {
+                    const int s = (int)(q % ring.nbuf);
+                    if (q >= ring.nbuf && !mbar_wait_bounded(&bar_empty[s], (unsigned)(((q / ring.nbuf) - 1) & 1))) {
+                        abort_now();
+                        break;
+                    }
+                    const TcItem it = s_items[i];
+                    const TcLeaf L = s_leaves[it.leaf];
+                    unsigned char* b = sm + (size_t)s * ring.bufsz;
+                    const unsigned b_bytes = (unsigned)L.npad * kTcK * 2u;
+                    mbar_expect(&bar_full[s], a_bytes + (ring.resident ? 0u : (split ? 2 * b_bytes : b_bytes)));
+                    bulk_load(b, aimg + ((size_t)tile * n_items + (size_t)i) * 32768u, a_bytes, &bar_full[s]);
+                    if (!ring.resident) {
+                        bulk_load(b + 32768, bsrc(L, it, false), b_bytes, &bar_full[s]);
+                        if (split) bulk_load(b + 65536, bsrc(L, it, true), b_bytes, &bar_full[s]);
+                    }
+                    issued[s] = true;
+                    last_par[s] = (unsigned)((q / ring.nbuf) & 1);
+                }
+            }
+            for (int s = 0; s < 4; ++s)   // no copy left in flight
+                if (issued[s]) mbar_wait_bounded(&bar_full[s], last_par[s]);
+            if (ring.resident && my_tiles > 0) mbar_wait_bounded(&bar_b, 0);
+        }
+    } else if (warp == 5) {
+        // ---------------- MMAs ----------------
+        if (lane == 0) {
+            if (ring.resident && my_tiles > 0 && !mbar_wait_bounded(&bar_b, 0)) abort_now();
+            long long q = 0, u = 0;
+            bool pending = false;
+            for (long long t = 0; t < my_tiles && !s_abort; ++t) {
+                for (int g = 0; g < a.n_groups && !s_abort; ++g, ++u) {
+                    const int buf = (int)(u & 1);
+                    if (u >= 2 && !mbar_wait_bounded(&bar_dfree[buf], (unsigned)(((u >> 1) - 1) & 1))) {
+                        abort_now();
+                        break;
+                    }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const unsigned id = instr_desc(L.npad, !fp16);
-                    const unsigned dt = tmem + (unsigned)L.tcol;
-                    const unsigned abase = smem_u32(sm + (size_t)s * ring.bufsz);
-                    const unsigned bhi = ring.resident ? smem_u32(res + it.bres) : abase + 32768u;
-                    const unsigned blo = ring.resident ? smem_u32(res + ring.total_b + it.bres) : abase + 65536u;
-                    for (int ks = 0; ks < kTcK / 16; ++ks) {
-                        if (it.kc * kTcK + ks * 16 >= ((L.m + 15) & ~15)) break;
-                        const unsigned koff = ks * 256u;
-                        const unsigned long long ah = smem_desc(abase + koff, 128, 1024);
-                        const unsigned long long bh = smem_desc(bhi + koff, 128, 1024);
-                        mma_f16(dt, ah, bh, id, (it.kc | ks) ? 1u : 0u);
-                        if (split) {
-                            mma_f16(dt, ah, smem_desc(blo + koff, 128, 1024), id, 1u);
-                            mma_f16(dt, smem_desc(abase + 16384u + koff, 128, 1024), bh, id, 1u);
+                    for (int i = s_gitem[g]; i < s_gitem[g + 1]; ++i, ++q) {
+                        const int s = (int)(q % ring.nbuf);
+                        if (!mbar_wait_bounded(&bar_full[s], (unsigned)((q / ring.nbuf) & 1))) {
+                            abort_now();
+                            break;
                         }
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                        const TcItem it = s_items[i];
+                        const TcLeaf L = s_leaves[it.leaf];
+                        const unsigned id = instr_desc(L.npad, !fp16);
+                        const unsigned dt = tmem + (unsigned)(buf * kTcGroupCols + L.tcol);
+                        const unsigned abase = smem_u32(sm + (size_t)s * ring.bufsz);
+                        const unsigned bhi = ring.resident ? smem_u32(res + it.bres) : abase + 32768u;
+                        const unsigned blo = ring.resident ? smem_u32(res + ring.total_b + it.bres) : abase + 65536u;
+                        for (int ks = 0; ks < kTcK / 16; ++ks) {
+                            if (it.kc * kTcK + ks * 16 >= ((L.m + 15) & ~15)) break;
+                            const unsigned koff = ks * 256u;
+                            const unsigned long long ah = smem_desc(abase + koff, 128, 1024);
+                            const unsigned long long bh = smem_desc(bhi + koff, 128, 1024);
+                            mma_f16(dt, ah, bh, id, (it.kc | ks) ? 1u : 0u);
+                            if (split) {
+                                mma_f16(dt, ah, smem_desc(blo + koff, 128, 1024), id, 1u);
+                                mma_f16(dt, smem_desc(abase + 16384u + koff, 128, 1024), bh, id, 1u);
+                            }
+                        }
+                        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                         smem_u32(&bar_empty[s]))
+                                     : "memory");
                     }
                     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                                     smem_u32(&bar_mma[s]))
+                                     smem_u32(&bar_dfull[buf]))
                                  : "memory");
-                    pending_mma[s] = true;
-                    ++consumed;
-                    if (issued < total && issued < consumed + ring.nbuf) issue(issued++);
-                }
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                                 smem_u32(&bar_done))
-                             : "memory");
-            }
-            const bool ok = mbar_wait_bounded(&bar_done, ph_done);
-            ph_done ^= 1u;
-            if (__syncthreads_or(!ok || s_bad)) {
-                if (tid == 0) atomicExch(a.err, (int)GFT_ERR_TIMEOUT);
-                goto teardown;
-            }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            {
-                const long long row = r0 + warp * 32 + lane;
-                const unsigned lane_base = (unsigned)(warp * 32) << 16;
-                const float sc = fp16 ? (row < a.batch ? scale[row] : 1.f) : 1.f;
-                if (a.direct) {
-                    float* stg = s_stage + warp * 32 * kStageLd;
-                    for (int j0 = 0; j0 < a.n; j0 += 32) {
-                        int cm[32];
-#pragma unroll
-                        for (int q = 0; q < 32; ++q) cm[q] = s_colmap[min(j0 + q, a.n - 1)];
-                        float r[32];
-#pragma unroll
-                        for (int q = 0; q < 32; ++q) {
-                            unsigned u;
-                            asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];"
-                                         : "=r"(u)
-                                         : "r"(tmem + lane_base + (unsigned)cm[q]));
-                            r[q] = __uint_as_float(u);
-                        }
-                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                        // transpose through shared memory: lane = row -> lane = column
-#pragma unroll
-                        for (int q = 0; q < 32; ++q) stg[lane * kStageLd + q] = r[q] * sc;
-                        __syncwarp();
-                        const int cnt = min(32, a.n - j0);
-                        for (int rr = 0; rr < 32; ++rr) {
-                            const long long grow = r0 + warp * 32 + rr;
-                            if (grow < a.batch && lane < cnt) __stcs(a.y + grow * a.n + j0 + lane, stg[rr * kStageLd + lane]);
-                        }
-                        __syncwarp();
-                    }
-                } else {
-                    for (int k = 0; k < a.n_leaves; ++k) {
-                        const TcLeaf L = s_leaves[k];
-                        if (L.group != g) continue;
-                        for (int c0 = 0; c0 < L.m; c0 += 32) {
-                            float r[32];
-#pragma unroll
-                            for (int q = 0; q < 32; ++q) {
-                                const unsigned col = (unsigned)(L.tcol + min(c0 + q, L.npad - 1));
-                                unsigned u;
-                                asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];"
-                                             : "=r"(u)
-                                             : "r"(tmem + lane_base + col)
-                                             : "memory");
-                                r[q] = __uint_as_float(u);
-                            }
-                            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                            if (row < a.batch) {
-                                float* dst = a.y + row * a.n + L.off + c0;
-                                const int cnt = min(32, L.m - c0);
-                                for (int q = 0; q < cnt; ++q) dst[q] = r[q] * sc;
-                            }
-                        }
-                    }
+                    pending = true;
                 }
             }
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncthreads();
+            if (pending) {   // every MMA done before the columns are freed
+                const long long last = u - 1;
+                mbar_wait_bounded(&bar_dfull[(int)(last & 1)], (unsigned)((last >> 1) & 1));
+            }
+        }
+    } else {
+        // ---------------- epilogue (warps 0-3) ----------------
+        float* stg = s_stage + warp * 32 * kStageLd;
+        const unsigned lane_base = (unsigned)(warp * 32) << 16;
+        long long u = 0;
+        for (long long t = 0; t < my_tiles && !s_abort; ++t) {
+            const long long tile = blockIdx.x + t * (long long)gridDim.x;
+            const long long r0 = tile * kTcM + warp * 32;
+            const long long row = r0 + lane;
+            const float sc = fp16 ? (row < a.batch ? scale[row] : 1.f) : 1.f;
+            for (int g = 0; g < a.n_groups && !s_abort; ++g, ++u) {
+                const int buf = (int)(u & 1);
+                if (!mbar_wait_bounded(&bar_dfull[buf], (unsigned)((u >> 1) & 1))) {
+                    if (lane == 0) abort_now();
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const int j_end = s_goff[g + 1];
+                for (int j0 = s_goff[g]; j0 < j_end; j0 += 32) {
+                    float r[32];
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) {
+                        const int col = s_gcol[min(j0 + q, j_end - 1)];
+                        unsigned uu;
+                        asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];"
+                                     : "=r"(uu)
+                                     : "r"(tmem + lane_base + (unsigned)(buf * kTcGroupCols + col)));
+                        r[q] = __uint_as_float(uu);
+                    }
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    // transpose through shared memory: lane = row -> lane = output position
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) stg[lane * kStageLd + q] = r[q] * sc;
+                    __syncwarp();
+                    const int cnt = min(32, j_end - j0);
+                    const int pos = lane < cnt ? s_gpos[j0 + lane] : 0;
+                    for (int rr = 0; rr < 32; ++rr) {
+                        const long long grow = r0 + rr;
+                        if (grow < a.batch && lane < cnt) __stcs(a.y + grow * a.n + pos, stg[rr * kStageLd + lane]);
+                    }
+                    __syncwarp();
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bar_dfree[buf])) : "memory");
+            }
         }
     }
-teardown:
-    __syncthreads();
-    if (tid == 0) {
-        for (int s = 0; s < 4; ++s)
-            if (pending_mma[s]) mbar_wait_bounded(&bar_mma[s], ph_mma[s]);
-    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols) : "memory");
     }
 }
@@ -523,25 +539,12 @@ __global__ void __launch_bounds__(kPack8Warps * 32) tc_pack8_kernel(
     asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
-// group mode: y[t][j] = z[t][srcmap[j]] (z leaf ordered)
-__global__ void tc_permute_kernel(const float* __restrict__ z, float* __restrict__ y, long long batch, int n,
-                                  const int* __restrict__ srcmap) {
-    const long long total = batch * n;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x) {
-        const long long t = e / n;
-        const int j = (int)(e - t * n);
-        __stcs(y + e, z[t * n + srcmap[j]]);
-    }
-}
-
 struct TcPlan {
-    int n = 0, n_leaves = 0, n_groups = 0, direct = 0, n_items = 0, n_stages = 0;
+    int n = 0, n_leaves = 0, n_groups = 0, n_items = 0, n_stages = 0, gmap_ints = 0;
     unsigned total_b = 0;   // bytes of all hi B images
     TcLeaf* d_leaves = nullptr;
     TcItem* d_items = nullptr;
-    int* d_colmap = nullptr;
-    int* d_srcmap = nullptr;
+    int* d_gmap = nullptr;             // output maps per leaf group (see TcArgs::gmap)
     __nv_bfloat16* d_bhi = nullptr;
     __nv_bfloat16* d_blo = nullptr;
     __half* d_fhi = nullptr;
@@ -549,7 +552,7 @@ struct TcPlan {
     short* d_gather = nullptr;         // [items][64]: slot feeding each K index (-1: padding)
     TcScratch own;                     // the plan's scratch for its own transforms
     ~TcPlan() {
-        for (void* p : {(void*)d_leaves, (void*)d_items, (void*)d_colmap, (void*)d_srcmap, (void*)d_bhi,
+        for (void* p : {(void*)d_leaves, (void*)d_items, (void*)d_gmap, (void*)d_bhi,
                         (void*)d_blo, (void*)d_fhi,
                         (void*)d_flo, (void*)d_gather})
             if (p) cudaFree(p);
@@ -603,7 +606,7 @@ void tc_build(gft_plan_s& p) {
             t.npad = std::max(16, (t.m + 15) & ~15);
             t.kchunks = (t.m + kTcK - 1) / kTcK;
             t.off = off;
-            if (cols + t.npad > kTcCols) {
+            if (cols + t.npad > kTcGroupCols) {
                 ++group;
                 cols = 0;
             }
@@ -616,16 +619,27 @@ void tc_build(gft_plan_s& p) {
             L.push_back(t);
         }
         T->n_groups = group + 1;
-        T->direct = T->n_groups == 1 ? 1 : 0;
-        // coefficient maps
-        std::vector<int> colmap(n), srcmap(n);
+        // output maps: for each leaf group, its coefficients in ascending
+        // output position with their TMEM columns; group offsets; first item
+        // of each group (items are in leaf order, groups are leaf ranges)
+        std::vector<int> gmap;
         {
+            std::vector<std::vector<std::pair<int, int>>> per(T->n_groups);
             int i = 0;
             for (size_t k = 0; k < p.leaves.size(); ++k)
-                for (int c = 0; c < p.leaves[k].m(); ++c, ++i) {
-                    colmap[p.out_pos[i]] = L[k].tcol + c;
-                    srcmap[p.out_pos[i]] = i;
+                for (int c = 0; c < p.leaves[k].m(); ++c, ++i) per[L[k].group].push_back({p.out_pos[i], L[k].tcol + c});
+            std::vector<int> pos, col, goff(1, 0);
+            for (auto& v : per) {
+                std::sort(v.begin(), v.end());
+                for (auto& e : v) {
+                    pos.push_back(e.first);
+                    col.push_back(e.second);
                 }
+                goff.push_back((int)pos.size());
+            }
+            gmap = pos;
+            gmap.insert(gmap.end(), col.begin(), col.end());
+            gmap.insert(gmap.end(), goff.begin(), goff.end());
         }
         // B images: for each leaf and K chunk, npad rows (outputs c) x 64 K
         // (inputs r) in the smem core-matrix order; B[c][r] = M_k[r][c]
@@ -676,8 +690,15 @@ void tc_build(gft_plan_s& p) {
         T->n_stages = p.n_stages;
         T->d_items = upload(items);
         T->d_leaves = upload(L);
-        T->d_colmap = upload(colmap);
-        T->d_srcmap = upload(srcmap);
+        {
+            // first item of each group, appended to the output maps
+            std::vector<int> gitem(T->n_groups + 1, (int)items.size());
+            for (int it = (int)items.size() - 1; it >= 0; --it) gitem[L[items[it].leaf].group] = it;
+            for (int g = T->n_groups - 1; g >= 0; --g) gitem[g] = std::min(gitem[g], gitem[g + 1]);
+            gmap.insert(gmap.end(), gitem.begin(), gitem.end());
+            T->d_gmap = upload(gmap);
+            T->gmap_ints = (int)gmap.size();
+        }
         T->d_bhi = reinterpret_cast<__nv_bfloat16*>(upload(bhi));
         T->d_blo = reinterpret_cast<__nv_bfloat16*>(upload(blo));
         T->d_fhi = reinterpret_cast<__half*>(upload(fhi));
@@ -705,7 +726,6 @@ void tc_reserve(gft_plan_s& p, TcScratch& S, int64_t batch) {
     const long long tiles_cap = (batch + kTcM - 1) / kTcM;
     GFT_CUDA(cudaMalloc(&S.d_aimg, (size_t)tiles_cap * T->n_items * 32768u));
     GFT_CUDA(cudaMalloc(&S.d_scale, sizeof(float) * (size_t)batch));
-    if (!T->direct) GFT_CUDA(cudaMalloc(&S.d_z, sizeof(float) * (size_t)batch * p.n));
     S.rows_cap = (size_t)batch;
 }
 
@@ -752,9 +772,9 @@ void launch_tc(gft_plan_s& p, const float* x, float* y, int64_t batch, bool inve
         GFT_CUDA(cudaGetLastError());
     }
     TcArgs a{};
-    a.y = T->direct ? y : S.d_z;
+    a.y = y;
     a.leaves = T->d_leaves;
-    a.colmap = T->d_colmap;
+    a.gmap = T->d_gmap;
     a.bhi = T->d_bhi;
     a.blo = T->d_blo;
     a.fhi = T->d_fhi;
@@ -764,13 +784,12 @@ void launch_tc(gft_plan_s& p, const float* x, float* y, int64_t batch, bool inve
     a.n_leaves = T->n_leaves;
     a.n_groups = T->n_groups;
     a.prec = (int)precision;
-    a.direct = T->direct;
     a.err = p.dev.d_err;
     TcRing ring{};
     const bool split = precision != GFT_PREC_BF16;
     const unsigned res_bytes = T->total_b * (split ? 2u : 1u);
     const size_t meta = ((sizeof(TcItem) * T->n_items + 15) & ~size_t(15)) +
-                        ((sizeof(TcLeaf) * T->n_leaves + 15) & ~size_t(15)) + sizeof(int) * ((n + 3) & ~3) +
+                        ((sizeof(TcLeaf) * T->n_leaves + 15) & ~size_t(15)) + sizeof(int) * ((T->gmap_ints + 3) & ~3) +
                         sizeof(float) * (size_t)kTcM * kStageLd;
     const size_t limit = 232448 - 2048;   // leave room for static shared memory
     ring.total_b = T->total_b;
@@ -793,10 +812,6 @@ void launch_tc(gft_plan_s& p, const float* x, float* y, int64_t batch, bool inve
     const int grid = (int)std::min<long long>(n_tiles, sms);
     tc_leaf_kernel<<<grid, kTcThreads, smem, st>>>(a, T->d_items, T->n_items, S.d_aimg, S.d_scale, ring);
     GFT_CUDA(cudaGetLastError());
-    if (!T->direct) {
-        tc_permute_kernel<<<sms * 8, 256, 0, st>>>(S.d_z, y, batch, n, T->d_srcmap);
-        GFT_CUDA(cudaGetLastError());
-    }
 }
 
 }  // namespace gft
