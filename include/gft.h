@@ -251,7 +251,10 @@ gft_status gft_device_error(gft_plan_t plan, int32_t* code);
  *   - leaves of 33..512 nodes: ONE persistent wide-leaf kernel over the
  *     (plan, tile) items of those plans;
  *   - with a tensor-core precision, plans with a leaf of 64 or more nodes
- *     (at most 256): each plan's tensor-core kernels.
+ *     (at most 256): ONE persistent pack kernel and ONE persistent
+ *     tensor-core kernel over the tiles of all of them (per size class,
+ *     n <= 256 and n > 256); a timeout in these kernels is reported in the
+ *     error word of the class's first plan.
  * The groups run on forked streams inside the graph and join at its end.
  *  plans[n_plans]  plans created with device bases; the batch does not own
  *                  them, and they must outlive it.  A plan may appear more
@@ -262,9 +265,8 @@ gft_status gft_device_error(gft_plan_t plan, int32_t* code);
  *                  GFT_PREC_FP16X3.
  * gft_batch_forward: x[i], y[i] device pointers to [batches[i], n_i] FP32
  * (host arrays of n_plans pointers); x[i] != y[i] for tensor-core entries.
- * A replay with the same pointers reuses the captured graph; new pointers
- * are written to the kernels' device descriptors (and trigger a new capture
- * when the batch has tensor-core entries).
+ * The captured graph is reused: new pointers are written to the kernels'
+ * device descriptors before the replay.
  */
 gft_status gft_batch_create(int32_t n_plans, const gft_plan_t* plans, const int64_t* batches,
                             uint32_t flags, gft_batch_t* out);

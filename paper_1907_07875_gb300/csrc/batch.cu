@@ -145,13 +145,10 @@ struct gft_batch_s {
     std::vector<int> table_users, wide_users, tc_users;
     std::vector<gft_plan_s*> tc_plans;
     std::vector<int64_t> tc_batches;
-    std::vector<int> tc_stream;            // stream slot of each tensor-core entry
-    std::vector<std::unique_ptr<gft::TcScratch>> tc_scratch;   // one per distinct tensor-core plan
-    std::vector<int> tc_scr;               // scratch index of each tensor-core entry
-    void* wide = nullptr;
-    static constexpr int kTcStreams = 4;
-    cudaStream_t side[1 + kTcStreams] = {};
-    cudaEvent_t ev_fork = nullptr, ev_join[1 + kTcStreams] = {};
+    void* wide = nullptr;                  // wide-leaf group (wide.cu)
+    void* tcb = nullptr;                   // tensor-core group (tc.cu)
+    cudaStream_t side[2] = {};
+    cudaEvent_t ev_fork = nullptr, ev_join[2] = {};
     // table-driven group
     std::vector<gft_plan_s*> plans;        // table-driven group, group order
     std::vector<int64_t> batches;
@@ -170,6 +167,7 @@ struct gft_batch_s {
     std::vector<const void*> last_x, last_y;
     ~gft_batch_s() {
         if (wide) gft::wide_batch_free(wide);
+        if (tcb) gft::tc_batch_free(tcb);
         for (auto& st : side)
             if (st) cudaStreamDestroy(st);
         if (ev_fork) cudaEventDestroy(ev_fork);
@@ -362,7 +360,6 @@ gft_status gft_batch_create(int32_t n_plans, const gft_plan_t* plans, const int6
         b->precision = flags;
         std::vector<gft_plan_s*> wide_plans;
         std::vector<int64_t> wide_batches;
-        std::map<gft_plan_s*, int> tc_slot;
         for (int i = 0; i < n_plans; ++i) {
             gft_plan_s* p = plans[i];
             if (!p) fail(GFT_ERR_INVALID_ARG, "NULL plan");
@@ -392,19 +389,6 @@ gft_status gft_batch_create(int32_t n_plans, const gft_plan_t* plans, const int6
                 b->tc_users.push_back(i);
                 b->tc_plans.push_back(p);
                 b->tc_batches.push_back(batches[i]);
-                // entries of one plan share one scratch: same stream, in order
-                auto it = tc_slot.find(p);
-                int scr;
-                if (it == tc_slot.end()) {
-                    scr = (int)b->tc_scratch.size();
-                    tc_slot[p] = scr;
-                    b->tc_scratch.emplace_back(new TcScratch);
-                } else {
-                    scr = it->second;
-                }
-                b->tc_scr.push_back(scr);
-                b->tc_stream.push_back(scr % gft_batch_s::kTcStreams);
-                tc_reserve(*p, *b->tc_scratch[scr], batches[i]);
             }
         }
         GFT_CUDA(cudaMalloc(&b->d_desc, sizeof(BatchPlanDev) * std::max<size_t>(1, b->plans.size())));
@@ -415,6 +399,7 @@ gft_status gft_batch_create(int32_t n_plans, const gft_plan_t* plans, const int6
             configure(*b);
         }
         if (!wide_plans.empty()) b->wide = wide_batch_create(wide_plans, wide_batches);
+        if (!b->tc_plans.empty()) b->tcb = tc_batch_create(b->tc_plans, b->tc_batches, b->precision);
         GFT_CUDA(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
         for (auto& st : b->side) GFT_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
         GFT_CUDA(cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming));
@@ -439,11 +424,10 @@ gft_status gft_batch_forward(gft_batch_t b, const float* const* x, float* const*
                           std::equal(x, x + k, b->last_x.begin()) &&
                           std::equal(y, y + k, b->last_y.begin(), [](float* a, const void* c) { return a == c; });
         if (!same) {
-            // table-driven and wide groups read their pointers from device
-            // descriptors; tensor-core launches carry them as arguments, so
-            // a batch with tensor-core entries is captured again
-            std::vector<const float*> tx, wx;
-            std::vector<float*> ty, wy;
+            // every group reads its signal pointers from device descriptors,
+            // so the captured graph stays valid
+            std::vector<const float*> tx, wx, cx;
+            std::vector<float*> ty, wy, cy;
             for (int i : b->table_users) {
                 tx.push_back(x[i]);
                 ty.push_back(y[i]);
@@ -452,14 +436,13 @@ gft_status gft_batch_forward(gft_batch_t b, const float* const* x, float* const*
                 wx.push_back(x[i]);
                 wy.push_back(y[i]);
             }
+            for (int i : b->tc_users) {
+                cx.push_back(x[i]);
+                cy.push_back(y[i]);
+            }
             if (!b->plans.empty()) upload_desc(*b, tx.data(), ty.data(), st);
             if (b->wide) wide_batch_upload(b->wide, wx, wy, st);
-            if (!b->tc_users.empty() && b->exec) {
-                cudaGraphExecDestroy(b->exec);
-                cudaGraphDestroy(b->graph);
-                b->exec = nullptr;
-                b->graph = nullptr;
-            }
+            if (b->tcb) tc_batch_upload(b->tcb, cx, cy, st);
             b->last_x.assign(x, x + k);
             b->last_y.assign(y, y + k);
         }
@@ -470,21 +453,16 @@ gft_status gft_batch_forward(gft_batch_t b, const float* const* x, float* const*
             try {
                 cudaStream_t cs = b->cap_stream;
                 GFT_CUDA(cudaEventRecord(b->ev_fork, cs));
-                bool used[1 + gft_batch_s::kTcStreams] = {};
+                bool used[2] = {false, false};
                 auto fork = [&](int s) {
                     if (!used[s]) GFT_CUDA(cudaStreamWaitEvent(b->side[s], b->ev_fork, 0));
                     used[s] = true;
                     return b->side[s];
                 };
                 if (b->wide) wide_batch_launch(b->wide, fork(0));
-                for (size_t j = 0; j < b->tc_plans.size(); ++j) {
-                    if (b->tc_batches[j] == 0) continue;
-                    const int u = b->tc_users[j];
-                    launch_tc(*b->tc_plans[j], x[u], y[u], b->tc_batches[j], false, fork(1 + b->tc_stream[j]),
-                              b->precision, b->tc_scratch[b->tc_scr[j]].get());
-                }
+                if (b->tcb) tc_batch_launch(b->tcb, fork(1));
                 if (!b->plans.empty()) launch_batch(*b, cs);
-                for (int s = 0; s <= gft_batch_s::kTcStreams; ++s)
+                for (int s = 0; s < 2; ++s)
                     if (used[s]) {
                         GFT_CUDA(cudaEventRecord(b->ev_join[s], b->side[s]));
                         GFT_CUDA(cudaStreamWaitEvent(cs, b->ev_join[s], 0));

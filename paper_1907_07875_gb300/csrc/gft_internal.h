@@ -171,5 +171,10 @@ struct TcScratch {
 void tc_reserve(gft_plan_s& p, TcScratch& s, int64_t batch);   // builds the tensor-core data on first use
 void launch_tc(gft_plan_s& p, const float* x, float* y, int64_t batch, bool inverse, cudaStream_t st,
                uint32_t precision, TcScratch* scratch = nullptr);
+// mixed batches: every tensor-core plan in one pack and one leaf launch per size class
+void* tc_batch_create(const std::vector<gft_plan_s*>& plans, const std::vector<int64_t>& batches, uint32_t precision);
+void tc_batch_upload(void* tb, const std::vector<const float*>& x, const std::vector<float*>& y, cudaStream_t st);
+void tc_batch_launch(void* tb, cudaStream_t st);
+void tc_batch_free(void* tb);
 
 }  // namespace gft

@@ -29,6 +29,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <vector>
 
 #include "gft_internal.h"
@@ -53,19 +54,38 @@ struct TcLeaf {
     long long b_off;  // element offset of the leaf's B image (per precision array)
 };
 
-struct TcArgs {
-    float* y;                // [batch, n] coefficients
-    const TcLeaf* leaves;
-    const int* gmap;         // [2n + 2(G+1)]: per group (outputs sorted): coefficient index, TMEM
-                             // column; then group offsets into those lists, then first item per group
-    const __nv_bfloat16* bhi;
-    const __nv_bfloat16* blo;
-    const __half* fhi;
-    const __half* flo;
+struct TcItem;
+// One plan of a launch (a launch may cover many plans: mixed batches).
+struct TcPlanDev {
+    const float* x;              // [batch, n] signals
+    float* y;                    // [batch, n] coefficients
+    unsigned char* aimg;         // split operand images, [tiles][items] x 32 KB
+    float* scale;                // per-signal FP16 scale
     long long batch;
-    int n, n_leaves, n_groups, prec;
-    int* err;
+    long long tile0, group0;     // first tile / first 8-signal group of this plan in the launch
+    const TcItem* items;
+    const TcLeaf* leaves;
+    const int* gmap;             // [2n + 2(G+1)]: per leaf group (outputs sorted): coefficient index,
+                                 // TMEM column; then group offsets, then the first item of each group
+    const short* gather;         // [items][64]: slot feeding each K index (-1: padding)
+    const int* prog;             // the plan's program head: [pairs 2P][stage offsets S+1]
+    const unsigned char* bhi;    // pre-split B images in this launch's format: hi, lo
+    const unsigned char* blo;
+    int n, n_items, n_leaves, n_groups, n_pairs, n_stages;
+    unsigned total_b;            // bytes of all hi B images (resident mode)
 };
+
+// plan of launch-wide index `v` (first-index array: tile0 or group0)
+template <bool TILES>
+__device__ __forceinline__ int find_plan(const TcPlanDev* P, int n_plans, long long v) {
+    int lo = 0, hi = n_plans - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((TILES ? P[mid].tile0 : P[mid].group0) <= v) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
     return (unsigned)__cvta_generic_to_shared(p);
@@ -177,40 +197,28 @@ struct TcItem {
 // error word; all roles leave their loops; copies and MMAs in flight are
 // awaited, again bounded, before the TMEM columns are freed).
 struct TcRing {
-    int resident;       // B images resident in shared memory
+    int resident;       // B images resident in shared memory (single-plan launches only)
     int nbuf;           // ring depth
     unsigned bufsz;     // bytes per ring buffer
-    unsigned res_off;   // byte offset of the resident B region
-    unsigned total_b;   // bytes of all hi B images (lo images follow)
-    unsigned meta_off;  // byte offset of [items][leaves][gmap][epilogue staging]
+    unsigned bslot;     // streamed mode: byte offset of the B images inside a ring buffer
+    unsigned res_off;   // resident mode: byte offset of the resident B region
+    unsigned stage_off; // byte offset of the epilogue staging
+    unsigned meta_off;  // single-plan launches: byte offset of [items][leaves][gmap]
 };
 
 constexpr int kStageLd = 33;   // epilogue staging row stride (floats): conflict-free
 
-__global__ void __launch_bounds__(kTcThreads, 1) tc_leaf_kernel(TcArgs a, const TcItem* __restrict__ items,
-                                                               int n_items, const unsigned char* __restrict__ aimg,
-                                                               const float* __restrict__ scale, TcRing ring) {
+// Work units are the tiles of every plan of the launch, in plan order; CTA b
+// takes units b, b + grid, ... (every role walks the same sequence).
+__global__ void __launch_bounds__(kTcThreads, 1) tc_leaf_kernel(TcPlanDev one, const TcPlanDev* __restrict__ many,
+                                                               int n_plans, long long total_tiles, int prec,
+                                                               int* err, TcRing ring) {
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ unsigned s_tmem;
     __shared__ __align__(8) unsigned long long bar_full[4], bar_empty[4], bar_dfull[2], bar_dfree[2], bar_b;
     __shared__ int s_abort;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // per-CTA copies of the item list, leaf table and output maps (16-byte aligned parts)
-    unsigned char* meta = sm + ring.meta_off;
-    TcItem* s_items = reinterpret_cast<TcItem*>(meta);
-    const size_t items_bytes = (sizeof(TcItem) * n_items + 15) & ~size_t(15);
-    TcLeaf* s_leaves = reinterpret_cast<TcLeaf*>(meta + items_bytes);
-    const size_t leaves_bytes = (sizeof(TcLeaf) * a.n_leaves + 15) & ~size_t(15);
-    int* s_gmap = reinterpret_cast<int*>(meta + items_bytes + leaves_bytes);
-    const int gmap_ints = 2 * a.n + 2 * (a.n_groups + 1);
-    float* s_stage = reinterpret_cast<float*>(s_gmap + ((gmap_ints + 3) & ~3));
-    const int* s_gpos = s_gmap;                 // coefficient index, group by group
-    const int* s_gcol = s_gmap + a.n;           // TMEM column (within the buffer)
-    const int* s_goff = s_gmap + 2 * a.n;       // [G + 1] offsets into gpos / gcol
-    const int* s_gitem = s_goff + a.n_groups + 1;   // [G + 1] first item of each group
-    for (int i = tid; i < n_items; i += blockDim.x) s_items[i] = items[i];
-    for (int i = tid; i < a.n_leaves; i += blockDim.x) s_leaves[i] = a.leaves[i];
-    for (int i = tid; i < gmap_ints; i += blockDim.x) s_gmap[i] = a.gmap[i];
+    float* s_stage = reinterpret_cast<float*>(sm + ring.stage_off);
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
                      "r"(kTcCols)
@@ -234,55 +242,85 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_leaf_kernel(TcArgs a, const 
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const unsigned tmem = s_tmem;
-    const bool split = a.prec != GFT_PREC_BF16;
-    const bool fp16 = a.prec == GFT_PREC_FP16X3;
+    const bool split = prec != GFT_PREC_BF16;
+    const bool fp16 = prec == GFT_PREC_FP16X3;
     const unsigned a_bytes = split ? 32768u : 16384u;
-    const long long n_tiles = (a.batch + kTcM - 1) / kTcM;
-    const long long my_tiles = n_tiles > blockIdx.x ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const long long my_units = total_tiles > blockIdx.x ? (total_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     unsigned char* res = sm + ring.res_off;
-    auto bsrc = [&](const TcLeaf& L, const TcItem& it, bool lo) {
-        const size_t img = (size_t)L.npad * kTcK;
-        if (fp16) return reinterpret_cast<const unsigned char*>((lo ? a.flo : a.fhi) + L.b_off + it.kc * img);
-        return reinterpret_cast<const unsigned char*>((lo ? a.blo : a.bhi) + L.b_off + it.kc * img);
+    // a single-plan launch reads its tables from shared-memory copies
+    const TcItem* l_items = one.items;
+    const TcLeaf* l_leaves = one.leaves;
+    const int* l_gmap = one.gmap;
+    if (!many) {
+        unsigned char* meta = sm + ring.meta_off;
+        TcItem* s_items = reinterpret_cast<TcItem*>(meta);
+        const size_t items_bytes = (sizeof(TcItem) * one.n_items + 15) & ~size_t(15);
+        TcLeaf* s_leaves = reinterpret_cast<TcLeaf*>(meta + items_bytes);
+        const size_t leaves_bytes = (sizeof(TcLeaf) * one.n_leaves + 15) & ~size_t(15);
+        int* s_gmap = reinterpret_cast<int*>(meta + items_bytes + leaves_bytes);
+        const int gmap_ints = 2 * one.n + 2 * (one.n_groups + 1);
+        for (int i = tid; i < one.n_items; i += blockDim.x) s_items[i] = one.items[i];
+        for (int i = tid; i < one.n_leaves; i += blockDim.x) s_leaves[i] = one.leaves[i];
+        for (int i = tid; i < gmap_ints; i += blockDim.x) s_gmap[i] = one.gmap[i];
+        l_items = s_items;
+        l_leaves = s_leaves;
+        l_gmap = s_gmap;
+        __syncthreads();
+    }
+    auto plan_of = [&](long long t, long long& tile) -> TcPlanDev {
+        if (!many) {
+            tile = t;
+            TcPlanDev D = one;
+            D.items = l_items;
+            D.leaves = l_leaves;
+            D.gmap = l_gmap;
+            return D;
+        }
+        const int p = find_plan<true>(many, n_plans, t);
+        tile = t - many[p].tile0;
+        return many[p];
     };
     auto abort_now = [&]() {
         s_abort = 1;
-        atomicExch(a.err, (int)GFT_ERR_TIMEOUT);
+        atomicExch(err, (int)GFT_ERR_TIMEOUT);
     };
 
     if (warp == 4) {
         // ---------------- copies ----------------
         if (lane == 0) {
-            if (ring.resident && my_tiles > 0) {
-                mbar_expect(&bar_b, split ? 2 * ring.total_b : ring.total_b);
-                for (int i = 0; i < n_items; ++i) {
-                    const TcItem it = s_items[i];
-                    const TcLeaf L = s_leaves[it.leaf];
+            if (ring.resident && my_units > 0) {
+                mbar_expect(&bar_b, split ? 2 * one.total_b : one.total_b);
+                for (int i = 0; i < one.n_items; ++i) {
+                    const TcItem it = l_items[i];
+                    const TcLeaf L = l_leaves[it.leaf];
                     const unsigned b_bytes = (unsigned)L.npad * kTcK * 2u;
-                    bulk_load(res + it.bres, bsrc(L, it, false), b_bytes, &bar_b);
-                    if (split) bulk_load(res + ring.total_b + it.bres, bsrc(L, it, true), b_bytes, &bar_b);
+                    const size_t src = 2 * (size_t)(L.b_off + (long long)it.kc * L.npad * kTcK);
+                    bulk_load(res + it.bres, one.bhi + src, b_bytes, &bar_b);
+                    if (split) bulk_load(res + one.total_b + it.bres, one.blo + src, b_bytes, &bar_b);
                 }
             }
             long long q = 0;
             bool issued[4] = {false, false, false, false};
             unsigned last_par[4] = {0, 0, 0, 0};
-            for (long long t = 0; t < my_tiles && !s_abort; ++t) {
-                const long long tile = blockIdx.x + t * (long long)gridDim.x;
-                for (int i = 0; i < n_items && !s_abort; ++i, ++q) {
+            for (long long k = 0; k < my_units && !s_abort; ++k) {
+                long long tile;
+                const TcPlanDev D = plan_of(blockIdx.x + k * (long long)gridDim.x, tile);
+                for (int i = 0; i < D.n_items && !s_abort; ++i, ++q) {
                     const int s = (int)(q % ring.nbuf);
                     if (q >= ring.nbuf && !mbar_wait_bounded(&bar_empty[s], (unsigned)(((q / ring.nbuf) - 1) & 1))) {
                         abort_now();
                         break;
                     }
-                    const TcItem it = s_items[i];
-                    const TcLeaf L = s_leaves[it.leaf];
+                    const TcItem it = D.items[i];
+                    const TcLeaf L = D.leaves[it.leaf];
                     unsigned char* b = sm + (size_t)s * ring.bufsz;
                     const unsigned b_bytes = (unsigned)L.npad * kTcK * 2u;
                     mbar_expect(&bar_full[s], a_bytes + (ring.resident ? 0u : (split ? 2 * b_bytes : b_bytes)));
-                    bulk_load(b, aimg + ((size_t)tile * n_items + (size_t)i) * 32768u, a_bytes, &bar_full[s]);
+                    bulk_load(b, D.aimg + ((size_t)tile * D.n_items + (size_t)i) * 32768u, a_bytes, &bar_full[s]);
                     if (!ring.resident) {
-                        bulk_load(b + 32768, bsrc(L, it, false), b_bytes, &bar_full[s]);
-                        if (split) bulk_load(b + 65536, bsrc(L, it, true), b_bytes, &bar_full[s]);
+                        const size_t src = 2 * (size_t)(L.b_off + (long long)it.kc * L.npad * kTcK);
+                        bulk_load(b + ring.bslot, D.bhi + src, b_bytes, &bar_full[s]);
+                        if (split) bulk_load(b + ring.bslot + b_bytes, D.blo + src, b_bytes, &bar_full[s]);
                     }
                     issued[s] = true;
                     last_par[s] = (unsigned)((q / ring.nbuf) & 1);
@@ -290,36 +328,40 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_leaf_kernel(TcArgs a, const 
             }
             for (int s = 0; s < 4; ++s)   // no copy left in flight
                 if (issued[s]) mbar_wait_bounded(&bar_full[s], last_par[s]);
-            if (ring.resident && my_tiles > 0) mbar_wait_bounded(&bar_b, 0);
+            if (ring.resident && my_units > 0) mbar_wait_bounded(&bar_b, 0);
         }
     } else if (warp == 5) {
         // ---------------- MMAs ----------------
         if (lane == 0) {
-            if (ring.resident && my_tiles > 0 && !mbar_wait_bounded(&bar_b, 0)) abort_now();
+            if (ring.resident && my_units > 0 && !mbar_wait_bounded(&bar_b, 0)) abort_now();
             long long q = 0, u = 0;
             bool pending = false;
-            for (long long t = 0; t < my_tiles && !s_abort; ++t) {
-                for (int g = 0; g < a.n_groups && !s_abort; ++g, ++u) {
+            for (long long k = 0; k < my_units && !s_abort; ++k) {
+                long long tile;
+                const TcPlanDev D = plan_of(blockIdx.x + k * (long long)gridDim.x, tile);
+                for (int g = 0; g < D.n_groups && !s_abort; ++g, ++u) {
                     const int buf = (int)(u & 1);
                     if (u >= 2 && !mbar_wait_bounded(&bar_dfree[buf], (unsigned)(((u >> 1) - 1) & 1))) {
                         abort_now();
                         break;
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    for (int i = s_gitem[g]; i < s_gitem[g + 1]; ++i, ++q) {
+                    const int* gitem = D.gmap + 2 * D.n + D.n_groups + 1;
+                    for (int i = gitem[g]; i < gitem[g + 1]; ++i, ++q) {
                         const int s = (int)(q % ring.nbuf);
                         if (!mbar_wait_bounded(&bar_full[s], (unsigned)((q / ring.nbuf) & 1))) {
                             abort_now();
                             break;
                         }
                         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                        const TcItem it = s_items[i];
-                        const TcLeaf L = s_leaves[it.leaf];
+                        const TcItem it = D.items[i];
+                        const TcLeaf L = D.leaves[it.leaf];
                         const unsigned id = instr_desc(L.npad, !fp16);
                         const unsigned dt = tmem + (unsigned)(buf * kTcGroupCols + L.tcol);
                         const unsigned abase = smem_u32(sm + (size_t)s * ring.bufsz);
-                        const unsigned bhi = ring.resident ? smem_u32(res + it.bres) : abase + 32768u;
-                        const unsigned blo = ring.resident ? smem_u32(res + ring.total_b + it.bres) : abase + 65536u;
+                        const unsigned b_bytes = (unsigned)L.npad * kTcK * 2u;
+                        const unsigned bhi = ring.resident ? smem_u32(res + it.bres) : abase + ring.bslot;
+                        const unsigned blo = ring.resident ? smem_u32(res + D.total_b + it.bres) : bhi + b_bytes;
                         for (int ks = 0; ks < kTcK / 16; ++ks) {
                             if (it.kc * kTcK + ks * 16 >= ((L.m + 15) & ~15)) break;
                             const unsigned koff = ks * 256u;
@@ -351,24 +393,31 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_leaf_kernel(TcArgs a, const 
         float* stg = s_stage + warp * 32 * kStageLd;
         const unsigned lane_base = (unsigned)(warp * 32) << 16;
         long long u = 0;
-        for (long long t = 0; t < my_tiles && !s_abort; ++t) {
-            const long long tile = blockIdx.x + t * (long long)gridDim.x;
+        for (long long k = 0; k < my_units && !s_abort; ++k) {
+            long long tile;
+            const TcPlanDev D = plan_of(blockIdx.x + k * (long long)gridDim.x, tile);
             const long long r0 = tile * kTcM + warp * 32;
             const long long row = r0 + lane;
-            const float sc = fp16 ? (row < a.batch ? scale[row] : 1.f) : 1.f;
-            for (int g = 0; g < a.n_groups && !s_abort; ++g, ++u) {
+            const float sc = fp16 ? (row < D.batch ? D.scale[row] : 1.f) : 1.f;
+            const int* gpos = D.gmap;
+            const int* gcol = D.gmap + D.n;
+            const int* goff = D.gmap + 2 * D.n;
+            for (int g = 0; g < D.n_groups && !s_abort; ++g, ++u) {
                 const int buf = (int)(u & 1);
                 if (!mbar_wait_bounded(&bar_dfull[buf], (unsigned)((u >> 1) & 1))) {
                     if (lane == 0) abort_now();
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const int j_end = s_goff[g + 1];
-                for (int j0 = s_goff[g]; j0 < j_end; j0 += 32) {
+                const int j_end = goff[g + 1];
+                for (int j0 = goff[g]; j0 < j_end; j0 += 32) {
+                    const int cnt = min(32, j_end - j0);
+                    const int my_col = lane < cnt ? gcol[j0 + lane] : gcol[j_end - 1];
+                    const int pos = lane < cnt ? gpos[j0 + lane] : 0;
                     float r[32];
 #pragma unroll
                     for (int q = 0; q < 32; ++q) {
-                        const int col = s_gcol[min(j0 + q, j_end - 1)];
+                        const int col = __shfl_sync(0xffffffffu, my_col, q);
                         unsigned uu;
                         asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];"
                                      : "=r"(uu)
@@ -380,11 +429,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_leaf_kernel(TcArgs a, const 
 #pragma unroll
                     for (int q = 0; q < 32; ++q) stg[lane * kStageLd + q] = r[q] * sc;
                     __syncwarp();
-                    const int cnt = min(32, j_end - j0);
-                    const int pos = lane < cnt ? s_gpos[j0 + lane] : 0;
                     for (int rr = 0; rr < 32; ++rr) {
                         const long long grow = r0 + rr;
-                        if (grow < a.batch && lane < cnt) __stcs(a.y + grow * a.n + pos, stg[rr * kStageLd + lane]);
+                        if (grow < D.batch && lane < cnt) __stcs(D.y + grow * D.n + pos, stg[rr * kStageLd + lane]);
                     }
                     __syncwarp();
                 }
@@ -413,128 +460,201 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_leaf_kernel(TcArgs a, const 
 // bytes of the image, hi and lo.  gather[item * 64 + k] is the slot whose
 // value feeds K index k of the item (-1: zero padding).
 constexpr int kPack8Warps = 4;
-__global__ void __launch_bounds__(kPack8Warps * 32) tc_pack8_kernel(
-    const float* __restrict__ x, unsigned char* __restrict__ aimg, float* __restrict__ scale, long long batch,
-    int n, const short* __restrict__ gather, int n_items, const int* __restrict__ pairs, int n_pairs,
-    const int* __restrict__ stage_off, int n_stages, int prec, int nbuf) {
-    extern __shared__ __align__(16) float sbuf[];
-    const int rs = n + 4;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    float* wbuf = sbuf + (size_t)warp * nbuf * 8 * rs;                  // one or two 8-row buffers per warp
-    int* s_pairs = reinterpret_cast<int*>(sbuf + (size_t)kPack8Warps * nbuf * 8 * rs);
-    int* s_soff = s_pairs + 2 * n_pairs;
-    short* s_gather = reinterpret_cast<short*>(s_pairs + ((2 * n_pairs + n_stages + 1 + 3) & ~3));   // 16-byte aligned
-    for (int i = tid; i < 2 * n_pairs; i += blockDim.x) s_pairs[i] = pairs[i];
-    for (int i = tid; i <= n_stages; i += blockDim.x) s_soff[i] = stage_off[i];
-    for (int i = tid; i < n_items * 64; i += blockDim.x) s_gather[i] = gather[i];
-    __syncthreads();
-    const bool fp16 = prec == GFT_PREC_FP16X3, split = prec != GFT_PREC_BF16;
-    const long long n_groups = (batch + kTcM - 1) / kTcM * (kTcM / 8);
-    const bool vec = (n & 3) == 0;
-    auto issue = [&](long long G, float* buf) {
-        const long long row0 = G * 8;
-        const int valid = (int)max(0LL, min(8LL, batch - row0));
-        if (vec) {
-            const int per = n >> 2;
-            for (int c = lane; c < valid * per; c += 32) {
-                const int r = c / per, k = c - r * per;
-                const unsigned d = (unsigned)__cvta_generic_to_shared(buf + r * rs + 4 * k);
-                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(x + (row0 + r) * n + 4 * k)
-                             : "memory");
-            }
-        } else {
-            for (int c = lane; c < valid * n; c += 32) {
-                const int r = c / n, k = c - r * n;
-                const unsigned d = (unsigned)__cvta_generic_to_shared(buf + r * rs + k);
-                asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(x + (row0 + r) * n + k) : "memory");
+
+// Copies of the 8 rows starting at row0 of plan D into a warp's staging
+// buffer (row stride rs), one commit group.
+__device__ __forceinline__ void pack_issue(const TcPlanDev& D, long long row0, float* buf, int rs, int lane) {
+    const int n = D.n;
+    const int valid = (int)max(0LL, min(8LL, D.batch - row0));
+    if ((n & 3) == 0) {
+        const int per = n >> 2;
+        for (int c = lane; c < valid * per; c += 32) {
+            const int r = c / per, kk = c - r * per;
+            const unsigned d = (unsigned)__cvta_generic_to_shared(buf + r * rs + 4 * kk);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(D.x + (row0 + r) * n + 4 * kk)
+                         : "memory");
+        }
+    } else {
+        for (int c = lane; c < valid * n; c += 32) {
+            const int r = c / n, kk = c - r * n;
+            const unsigned d = (unsigned)__cvta_generic_to_shared(buf + r * rs + kk);
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(D.x + (row0 + r) * n + kk) : "memory");
+        }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// One group of 8 signals (rows row0.. of plan D, rows rt.. of tile `tile`)
+// already in the warp's buffer: FP16 scales, Haar units in place, split
+// operand rows stored.  s_pairs / s_soff / s_gather: the plan's tables.
+__device__ __forceinline__ void pack_group(const TcPlanDev& D, float* buf, int rs, long long row0, long long tile,
+                                           int rt, const int* s_pairs, const int* s_soff, const short* s_gather,
+                                           bool fp16, bool split, int lane) {
+    const int n = D.n;
+    const int valid = (int)max(0LL, min(8LL, D.batch - row0));
+    float inv[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) inv[r] = 1.f;
+    if (fp16) {
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            float m = 0.f;
+            if (r < valid)
+                for (int c = lane; c < n; c += 32) m = fmaxf(m, fabsf(buf[r * rs + c]));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+            const float sc = m > 0.f ? exp2f(ceilf(log2f(m)) + (float)D.n_stages) : 1.f;
+            inv[r] = 1.f / sc;
+            if (lane == 0 && r < valid) D.scale[row0 + r] = sc;
+        }
+    }
+    // Haar units: lanes over the pairs of a stage, the 8 rows unrolled (rows
+    // past the batch hold stale values that are never stored)
+    for (int s = 0; s < D.n_stages; ++s) {
+        const int p1 = s_soff[s + 1];
+        for (int pp = s_soff[s] + lane; pp < p1; pp += 32) {
+            const int2 uv = *reinterpret_cast<const int2*>(s_pairs + 2 * pp);
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                float* row = buf + r * rs;
+                const float xu = row[uv.x], xv = row[uv.y];
+                row[uv.x] = xu + xv;
+                row[uv.y] = xu - xv;
             }
         }
-        asm volatile("cp.async.commit_group;" ::: "memory");
-    };
+        __syncwarp();
+    }
+    const int r = lane & 7, sub = lane >> 3;
+    const bool live = r < valid;
+    const float* row = buf + r * rs;
+    const float sc = inv[r];
+    for (int kg = sub; kg < D.n_items * 8; kg += 4) {
+        float v[8];
+        const int4 g4 = *reinterpret_cast<const int4*>(s_gather + kg * 8);   // eight slot indices
+        const short* gs = reinterpret_cast<const short*>(&g4);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int lab = gs[e];
+            v[e] = (live && lab >= 0) ? row[lab] * sc : 0.f;
+        }
+        unsigned hi[4], lo[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {   // two values per conversion instruction
+            if (fp16) {
+                const __half2 h = __floats2half2_rn(v[2 * q], v[2 * q + 1]);
+                const float2 hf = __half22float2(h);
+                const __half2 l = __floats2half2_rn(v[2 * q] - hf.x, v[2 * q + 1] - hf.y);
+                hi[q] = *reinterpret_cast<const unsigned*>(&h);
+                lo[q] = *reinterpret_cast<const unsigned*>(&l);
+            } else {
+                const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+                const float2 hf = __bfloat1622float2(h);
+                const __nv_bfloat162 l = __floats2bfloat162_rn(v[2 * q] - hf.x, v[2 * q + 1] - hf.y);
+                hi[q] = *reinterpret_cast<const unsigned*>(&h);
+                lo[q] = *reinterpret_cast<const unsigned*>(&l);
+            }
+        }
+        const int item = kg >> 3;
+        unsigned char* dst = D.aimg + ((size_t)tile * D.n_items + item) * 32768u + core_off(rt + r, kg & 7);
+        __stcg(reinterpret_cast<uint4*>(dst), make_uint4(hi[0], hi[1], hi[2], hi[3]));
+        if (split) __stcg(reinterpret_cast<uint4*>(dst + 16384), make_uint4(lo[0], lo[1], lo[2], lo[3]));
+    }
+    __syncwarp();   // buffer reusable by the copies issued next
+}
+
+// One plan: every warp walks groups G = blockIdx.x * W + warp + k * (grid * W)
+// (consecutive groups on consecutive warps), prefetching its next group
+// while it packs the current one; the tables are loaded once.
+__global__ void __launch_bounds__(kPack8Warps * 32) tc_pack8_kernel(TcPlanDev D, int rs, int nbuf, int prec) {
+    extern __shared__ __align__(16) float sbuf[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    float* wbuf = sbuf + (size_t)warp * nbuf * 8 * rs;
+    const int prog_ints = 2 * D.n_pairs + D.n_stages + 1;
+    int* s_prog = reinterpret_cast<int*>(sbuf + (size_t)kPack8Warps * nbuf * 8 * rs);
+    short* s_gather = reinterpret_cast<short*>(s_prog + ((prog_ints + 3) & ~3));   // 16-byte aligned
+    for (int i = tid; i < prog_ints; i += blockDim.x) s_prog[i] = D.prog[i];
+    for (int i = tid; i < D.n_items * 64; i += blockDim.x) s_gather[i] = D.gather[i];
+    __syncthreads();
+    const bool fp16 = prec == GFT_PREC_FP16X3, split = prec != GFT_PREC_BF16;
+    const long long n_groups = (D.batch + kTcM - 1) / kTcM * (kTcM / 8);
     const long long stride = (long long)gridDim.x * kPack8Warps;
     long long G = blockIdx.x * (long long)kPack8Warps + warp;
     int cur = 0;
-    if (G < n_groups) issue(G, wbuf);
+    if (G < n_groups) pack_issue(D, G * 8, wbuf, rs, lane);
     for (; G < n_groups; G += stride) {
         float* buf = wbuf + cur * 8 * rs;
-        if (nbuf == 2 && G + stride < n_groups) issue(G + stride, wbuf + (cur ^ 1) * 8 * rs);
+        const bool has_next = G + stride < n_groups;
+        if (nbuf == 2 && has_next) pack_issue(D, (G + stride) * 8, wbuf + (cur ^ 1) * 8 * rs, rs, lane);
         else asm volatile("cp.async.commit_group;" ::: "memory");
         asm volatile("cp.async.wait_group 1;" ::: "memory");
         __syncwarp();
         const long long row0 = G * 8;
-        const int valid = (int)max(0LL, min(8LL, batch - row0));
-        float inv[8];
-#pragma unroll
-        for (int r = 0; r < 8; ++r) inv[r] = 1.f;
-        if (fp16) {
-#pragma unroll
-            for (int r = 0; r < 8; ++r) {
-                float m = 0.f;
-                if (r < valid)
-                    for (int j = lane; j < n; j += 32) m = fmaxf(m, fabsf(buf[r * rs + j]));
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-                const float sc = m > 0.f ? exp2f(ceilf(log2f(m)) + (float)n_stages) : 1.f;
-                inv[r] = 1.f / sc;
-                if (lane == 0 && r < valid) scale[row0 + r] = sc;
-            }
-        }
-        // Haar units: lanes over the pairs of a stage, the 8 rows unrolled
-        // (rows past the batch hold stale values that are never stored)
-        for (int s = 0; s < n_stages; ++s) {
-            const int p1 = s_soff[s + 1];
-            for (int pp = s_soff[s] + lane; pp < p1; pp += 32) {
-                const int2 uv = *reinterpret_cast<const int2*>(s_pairs + 2 * pp);
-#pragma unroll
-                for (int r = 0; r < 8; ++r) {
-                    float* row = buf + r * rs;
-                    const float xu = row[uv.x], xv = row[uv.y];
-                    row[uv.x] = xu + xv;
-                    row[uv.y] = xu - xv;
-                }
-            }
-            __syncwarp();
-        }
         const long long tile = row0 / kTcM;
-        const int rt = (int)(row0 - tile * kTcM);   // first row of the group within the tile
-        const int r = lane & 7, sub = lane >> 3;
-        const bool live = r < valid;
-        const float* row = buf + r * rs;
-        const float sc = inv[r];
-        for (int kg = sub; kg < n_items * 8; kg += 4) {
-            float v[8];
-            const int4 g4 = *reinterpret_cast<const int4*>(s_gather + kg * 8);   // eight slot indices
-            const short* gs = reinterpret_cast<const short*>(&g4);
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const int lab = gs[e];
-                v[e] = (live && lab >= 0) ? row[lab] * sc : 0.f;
-            }
-            unsigned hi[4], lo[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {   // two values per conversion instruction
-                if (fp16) {
-                    const __half2 h = __floats2half2_rn(v[2 * q], v[2 * q + 1]);
-                    const float2 hf = __half22float2(h);
-                    const __half2 l = __floats2half2_rn(v[2 * q] - hf.x, v[2 * q + 1] - hf.y);
-                    hi[q] = *reinterpret_cast<const unsigned*>(&h);
-                    lo[q] = *reinterpret_cast<const unsigned*>(&l);
-                } else {
-                    const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
-                    const float2 hf = __bfloat1622float2(h);
-                    const __nv_bfloat162 l = __floats2bfloat162_rn(v[2 * q] - hf.x, v[2 * q + 1] - hf.y);
-                    hi[q] = *reinterpret_cast<const unsigned*>(&h);
-                    lo[q] = *reinterpret_cast<const unsigned*>(&l);
-                }
-            }
-            const int item = kg >> 3;
-            unsigned char* dst = aimg + ((size_t)tile * n_items + item) * 32768u + core_off(rt + r, kg & 7);
-            __stcg(reinterpret_cast<uint4*>(dst), make_uint4(hi[0], hi[1], hi[2], hi[3]));
-            if (split) __stcg(reinterpret_cast<uint4*>(dst + 16384), make_uint4(lo[0], lo[1], lo[2], lo[3]));
-        }
-        __syncwarp();   // buffer reusable by the copies issued next
+        pack_group(D, buf, rs, row0, tile, (int)(row0 - tile * kTcM), s_prog, s_prog + 2 * D.n_pairs, s_gather, fp16,
+                   split, lane);
         if (nbuf == 2) cur ^= 1;
-        else if (G + stride < n_groups) issue(G + stride, wbuf);
+        else if (has_next) pack_issue(D, (G + stride) * 8, wbuf, rs, lane);
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
+// Many plans (mixed batches): work units are the tiles of every plan (in
+// plan order); CTA b takes tiles b, b + grid, ...; warp w packs groups w,
+// w+4, w+8, w+12 of each tile.  A plan's tables are loaded into shared
+// memory when the next tile belongs to another plan.
+__global__ void __launch_bounds__(kPack8Warps * 32) tc_pack8_multi_kernel(const TcPlanDev* __restrict__ many,
+                                                                          int n_plans, long long total_tiles, int rs,
+                                                                          int prog_cap, int prec, int nbuf) {
+    extern __shared__ __align__(16) float sbuf[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    float* wbuf = sbuf + (size_t)warp * nbuf * 8 * rs;
+    int* s_prog = reinterpret_cast<int*>(sbuf + (size_t)kPack8Warps * nbuf * 8 * rs);
+    short* s_gather = reinterpret_cast<short*>(s_prog + ((prog_cap + 3) & ~3));   // 16-byte aligned
+    const bool fp16 = prec == GFT_PREC_FP16X3, split = prec != GFT_PREC_BF16;
+    const long long my_units = total_tiles > blockIdx.x ? (total_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    constexpr int kPer = kTcM / 8 / kPack8Warps;   // groups per warp per tile
+    // rows of step (k, j): tile blockIdx.x + k * grid, group kPack8Warps * j + warp
+    auto step_row0 = [&](long long k, int j, int& p) -> long long {
+        const long long t = blockIdx.x + k * (long long)gridDim.x;
+        p = find_plan<true>(many, n_plans, t);
+        return (t - many[p].tile0) * kTcM + (long long)(kPack8Warps * j + warp) * 8;
+    };
+    int loaded = -1, cur = 0;
+    if (my_units > 0) {
+        int p0;
+        const long long r0 = step_row0(0, 0, p0);
+        pack_issue(many[p0], r0, wbuf, rs, lane);
+    }
+    for (long long k = 0; k < my_units; ++k) {
+        int p;
+        step_row0(k, 0, p);
+        const TcPlanDev& D = many[p];
+        if (p != loaded) {   // every warp reaches this point together
+            __syncthreads();
+            const int prog_ints = 2 * D.n_pairs + D.n_stages + 1;
+            for (int i = tid; i < prog_ints; i += blockDim.x) s_prog[i] = D.prog[i];
+            for (int i = tid; i < D.n_items * 64; i += blockDim.x) s_gather[i] = D.gather[i];
+            __syncthreads();
+            loaded = p;
+        }
+        for (int j = 0; j < kPer; ++j) {
+            float* buf = wbuf + cur * 8 * rs;
+            const bool has_next = j + 1 < kPer || k + 1 < my_units;
+            int pn = 0;
+            long long rn = 0;
+            if (has_next) rn = step_row0(j + 1 < kPer ? k : k + 1, j + 1 < kPer ? j + 1 : 0, pn);
+            if (nbuf == 2 && has_next) pack_issue(many[pn], rn, wbuf + (cur ^ 1) * 8 * rs, rs, lane);
+            else asm volatile("cp.async.commit_group;" ::: "memory");
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+            __syncwarp();
+            int pc;
+            const long long row0 = step_row0(k, j, pc);
+            const long long tile = row0 / kTcM;
+            pack_group(D, buf, rs, row0, tile, (int)(row0 - tile * kTcM), s_prog, s_prog + 2 * D.n_pairs, s_gather,
+                       fp16, split, lane);
+            if (nbuf == 2) cur ^= 1;
+            else if (has_next) pack_issue(many[pn], rn, wbuf, rs, lane);
+        }
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
@@ -738,6 +858,109 @@ void TcScratch::release() {
     rows_cap = 0;
 }
 
+namespace {
+
+TcPlanDev make_plan_dev(const gft_plan_s& p, const float* x, float* y, int64_t batch, unsigned char* aimg,
+                        float* scale, uint32_t precision) {
+    const TcPlan* T = static_cast<const TcPlan*>(p.tc);
+    TcPlanDev D{};
+    D.x = x;
+    D.y = y;
+    D.aimg = aimg;
+    D.scale = scale;
+    D.batch = batch;
+    D.items = T->d_items;
+    D.leaves = T->d_leaves;
+    D.gmap = T->d_gmap;
+    D.gather = T->d_gather;
+    D.prog = p.dev.d_ints;
+    const bool f16 = precision == GFT_PREC_FP16X3;
+    D.bhi = reinterpret_cast<const unsigned char*>(f16 ? (const void*)T->d_fhi : (const void*)T->d_bhi);
+    D.blo = reinterpret_cast<const unsigned char*>(f16 ? (const void*)T->d_flo : (const void*)T->d_blo);
+    D.n = p.n;
+    D.n_items = T->n_items;
+    D.n_leaves = T->n_leaves;
+    D.n_groups = T->n_groups;
+    D.n_pairs = p.dev.n_pairs;
+    D.n_stages = p.dev.n_stages;
+    D.total_b = T->total_b;
+    return D;
+}
+
+int npad_max_of(const gft_plan_s& p) {
+    int v = 16;
+    for (auto& lf : p.leaves) v = std::max(v, (lf.m() + 15) & ~15);
+    return v;
+}
+
+void launch_pack(const TcPlanDev& one, const TcPlanDev* many, int n_plans, long long total_tiles, int nmax,
+                 int prog_cap, int items_cap, uint32_t precision, cudaStream_t st) {
+    if (total_tiles == 0) return;
+    const int rs = nmax + 4;
+    const size_t per_buf = sizeof(float) * (size_t)kPack8Warps * 8 * rs;
+    const size_t tabs = sizeof(int) * (size_t)((prog_cap + 3) & ~3) + sizeof(short) * 64 * (size_t)items_cap;
+    const int nbuf = 2 * per_buf + tabs <= 232448 / 2 ? 2 : 1;   // double buffer if two CTAs still fit
+    const size_t smem = nbuf * per_buf + tabs;
+    if (smem > 232448) fail(GFT_ERR_UNSUPPORTED, "tensor-core pack stage does not fit in shared memory");
+    if (!many) {
+        GFT_CUDA(cudaFuncSetAttribute(tc_pack8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int per_sm = 0;
+        GFT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc_pack8_kernel, kPack8Warps * 32, smem));
+        const long long groups = total_tiles * (kTcM / 8);
+        const long long blocks = std::min<long long>((groups + kPack8Warps - 1) / kPack8Warps,
+                                                     (long long)std::max(1, per_sm) * sm_count());
+        tc_pack8_kernel<<<(unsigned)blocks, kPack8Warps * 32, smem, st>>>(one, rs, nbuf, (int)precision);
+    } else {
+        GFT_CUDA(cudaFuncSetAttribute(tc_pack8_multi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int per_sm = 0;
+        GFT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc_pack8_multi_kernel, kPack8Warps * 32, smem));
+        const long long blocks = std::min<long long>(total_tiles, (long long)std::max(1, per_sm) * sm_count());
+        tc_pack8_multi_kernel<<<(unsigned)blocks, kPack8Warps * 32, smem, st>>>(many, n_plans, total_tiles, rs, prog_cap,
+                                                                              (int)precision, nbuf);
+    }
+    GFT_CUDA(cudaGetLastError());
+}
+
+// resident_b: bytes of all B images of a single plan (0: stream them per item)
+void launch_leaf(const TcPlanDev& one, const TcPlanDev* many, int n_plans, long long total_tiles, int npad_max,
+                 unsigned resident_b, uint32_t precision, int* err, cudaStream_t st) {
+    if (total_tiles == 0) return;
+    const bool split = precision != GFT_PREC_BF16;
+    const size_t meta = many ? 0
+                             : ((sizeof(TcItem) * one.n_items + 15) & ~size_t(15)) +
+                                   ((sizeof(TcLeaf) * one.n_leaves + 15) & ~size_t(15)) +
+                                   sizeof(int) * (size_t)((2 * one.n + 2 * (one.n_groups + 1) + 3) & ~3);
+    const size_t stage = sizeof(float) * (size_t)kTcM * kStageLd + meta;   // staging, then the tables
+    const size_t limit = 232448 - 2048;   // leave room for static shared memory
+    TcRing ring{};
+    const unsigned res_bytes = resident_b * (split ? 2u : 1u);
+    if (!many && resident_b && 4u * 32768u + (size_t)res_bytes + stage <= limit) {
+        ring.resident = 1;   // all B images once per CTA, four A buffers
+        ring.nbuf = 4;
+        ring.bufsz = 32768u;
+        ring.res_off = 4u * 32768u;
+        ring.stage_off = (unsigned)((ring.res_off + res_bytes + 15) & ~size_t(15));
+    } else {
+        ring.resident = 0;   // A and the item's B images in each buffer
+        ring.bslot = 32768u;
+        const unsigned bb = (unsigned)npad_max * kTcK * 2u * (split ? 2u : 1u);
+        ring.bufsz = (32768u + bb + 1023u) & ~1023u;
+        ring.nbuf = (int)std::min<size_t>(4, (limit - stage) / ring.bufsz);
+        if (ring.nbuf < 2) fail(GFT_ERR_UNSUPPORTED, "tensor-core kernel does not fit in shared memory");
+        ring.res_off = 0;
+        ring.stage_off = (unsigned)ring.nbuf * ring.bufsz;
+    }
+    ring.meta_off = ring.stage_off + (unsigned)(sizeof(float) * (size_t)kTcM * kStageLd);
+    const size_t smem = ring.stage_off + stage;
+    if (smem > limit) fail(GFT_ERR_UNSUPPORTED, "tensor-core kernel does not fit in shared memory");
+    GFT_CUDA(cudaFuncSetAttribute(tc_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int grid = (int)std::min<long long>(total_tiles, sm_count());
+    tc_leaf_kernel<<<grid, kTcThreads, smem, st>>>(one, many, n_plans, total_tiles, (int)precision, err, ring);
+    GFT_CUDA(cudaGetLastError());
+}
+
+}  // namespace
+
 void launch_tc(gft_plan_s& p, const float* x, float* y, int64_t batch, bool inverse, cudaStream_t st,
                uint32_t precision, TcScratch* scratch) {
     if (inverse) fail(GFT_ERR_UNSUPPORTED, "tensor-core precisions are implemented for the forward transform");
@@ -745,73 +968,105 @@ void launch_tc(gft_plan_s& p, const float* x, float* y, int64_t batch, bool inve
     if (!p.tc) fail(GFT_ERR_UNSUPPORTED, "tensor-core path needs every leaf to have at most 256 nodes");
     if (x == y) fail(GFT_ERR_UNSUPPORTED, "tensor-core path does not run in place");
     TcPlan* T = static_cast<TcPlan*>(p.tc);
-    const int n = p.n;
-    const long long n_tiles = (batch + kTcM - 1) / kTcM;
     TcScratch& S = scratch ? *scratch : T->own;
     tc_reserve(p, S, batch);
-    const int sms = sm_count();
-    {
-        const DevProgram& d = p.dev;
-        const size_t tabs = sizeof(int) * (size_t)((2 * d.n_pairs + d.n_stages + 1 + 3) & ~3) +
-                            sizeof(short) * 64 * T->n_items;
-        const size_t per_buf = sizeof(float) * (size_t)kPack8Warps * 8 * (n + 4);
-        const int nbuf = 2 * per_buf + tabs <= 232448 / 2 ? 2 : 1;   // double buffer if two CTAs still fit
-        const size_t smem = nbuf * per_buf + tabs;
-        if (smem > 232448) fail(GFT_ERR_UNSUPPORTED, "tensor-core pack stage does not fit in shared memory");
-        GFT_CUDA(cudaFuncSetAttribute(tc_pack8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        int per_sm = 0;
-        GFT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc_pack8_kernel, kPack8Warps * 32, smem));
-        const long long groups = n_tiles * (kTcM / 8);
-        const long long blocks = std::min<long long>((groups + kPack8Warps - 1) / kPack8Warps,
-                                                     (long long)std::max(1, per_sm) * sms);
-        const int* pairs = d.d_ints;
-        const int* soff = d.d_ints + 2 * d.n_pairs;
-        tc_pack8_kernel<<<(unsigned)blocks, kPack8Warps * 32, smem, st>>>(
-            x, S.d_aimg, S.d_scale, batch, n, T->d_gather, T->n_items, pairs, d.n_pairs, soff, d.n_stages,
-            (int)precision, nbuf);
-        GFT_CUDA(cudaGetLastError());
-    }
-    TcArgs a{};
-    a.y = y;
-    a.leaves = T->d_leaves;
-    a.gmap = T->d_gmap;
-    a.bhi = T->d_bhi;
-    a.blo = T->d_blo;
-    a.fhi = T->d_fhi;
-    a.flo = T->d_flo;
-    a.batch = batch;
-    a.n = n;
-    a.n_leaves = T->n_leaves;
-    a.n_groups = T->n_groups;
-    a.prec = (int)precision;
-    a.err = p.dev.d_err;
-    TcRing ring{};
-    const bool split = precision != GFT_PREC_BF16;
-    const unsigned res_bytes = T->total_b * (split ? 2u : 1u);
-    const size_t meta = ((sizeof(TcItem) * T->n_items + 15) & ~size_t(15)) +
-                        ((sizeof(TcLeaf) * T->n_leaves + 15) & ~size_t(15)) + sizeof(int) * ((T->gmap_ints + 3) & ~3) +
-                        sizeof(float) * (size_t)kTcM * kStageLd;
-    const size_t limit = 232448 - 2048;   // leave room for static shared memory
-    ring.total_b = T->total_b;
-    if (4u * 32768u + (size_t)res_bytes + meta <= limit) {
-        ring.resident = 1;   // all B images once per CTA, four A buffers
-        ring.nbuf = 4;
-        ring.bufsz = 32768u;
-        ring.res_off = 4u * 32768u;
-    } else {
-        ring.resident = 0;   // two buffers holding A and the item's B images
-        ring.nbuf = 2;
-        ring.bufsz = 98304u;
-        ring.res_off = 0;
-    }
-    const size_t ring_bytes = ring.resident ? (size_t)ring.res_off + res_bytes : 2u * 98304u;
-    ring.meta_off = (unsigned)((ring_bytes + 15) & ~size_t(15));
-    const size_t smem = ring.meta_off + meta;
-    if (smem > limit) fail(GFT_ERR_UNSUPPORTED, "tensor-core kernel does not fit in shared memory");
-    GFT_CUDA(cudaFuncSetAttribute(tc_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int grid = (int)std::min<long long>(n_tiles, sms);
-    tc_leaf_kernel<<<grid, kTcThreads, smem, st>>>(a, T->d_items, T->n_items, S.d_aimg, S.d_scale, ring);
-    GFT_CUDA(cudaGetLastError());
+    const long long n_tiles = (batch + kTcM - 1) / kTcM;
+    const TcPlanDev D = make_plan_dev(p, x, y, batch, S.d_aimg, S.d_scale, precision);
+    launch_pack(D, nullptr, 1, n_tiles, p.n, 2 * p.dev.n_pairs + p.dev.n_stages + 1, T->n_items, precision, st);
+    launch_leaf(D, nullptr, 1, n_tiles, npad_max_of(p), T->total_b, precision, p.dev.d_err, st);
 }
+
+// ---------------------------------------------------------------------------
+// mixed batches: all tensor-core plans of a batch in one pack launch and one
+// leaf launch per size class (n <= 256, n > 256: the pack stage's shared
+// staging is sized by the class's largest graph)
+// ---------------------------------------------------------------------------
+namespace {
+struct TcBatch {
+    uint32_t prec = 0;
+    struct Class {
+        std::vector<TcPlanDev> desc;
+        std::vector<int> user;           // index in the caller's list
+        TcPlanDev* d_desc = nullptr;
+        long long total_tiles = 0, total_groups = 0;
+        int nmax = 0, npad_max = 16, prog_cap = 1, items_cap = 1;
+        int* err = nullptr;
+    } cls[2];
+    unsigned char* d_aimg = nullptr;
+    float* d_scale = nullptr;
+    ~TcBatch() {
+        for (auto& c : cls)
+            if (c.d_desc) cudaFree(c.d_desc);
+        if (d_aimg) cudaFree(d_aimg);
+        if (d_scale) cudaFree(d_scale);
+    }
+};
+}  // namespace
+
+void* tc_batch_create(const std::vector<gft_plan_s*>& plans, const std::vector<int64_t>& batches,
+                      uint32_t precision) {
+    std::unique_ptr<TcBatch> B(new TcBatch);
+    B->prec = precision;
+    size_t aimg_bytes = 0, scale_elems = 0;
+    std::vector<size_t> a_off(plans.size()), s_off(plans.size());
+    for (size_t i = 0; i < plans.size(); ++i) {
+        gft_plan_s& p = *plans[i];
+        if (!p.tc && tc_eligible(p)) tc_build(p);
+        if (!p.tc) fail(GFT_ERR_UNSUPPORTED, "tensor-core path needs every leaf to have at most 256 nodes");
+        const TcPlan* T = static_cast<const TcPlan*>(p.tc);
+        const long long tiles = (batches[i] + kTcM - 1) / kTcM;
+        a_off[i] = aimg_bytes;
+        s_off[i] = scale_elems;
+        aimg_bytes += (size_t)tiles * T->n_items * 32768u;
+        scale_elems += (size_t)batches[i];
+    }
+    GFT_CUDA(cudaMalloc(&B->d_aimg, std::max<size_t>(aimg_bytes, 256)));
+    GFT_CUDA(cudaMalloc(&B->d_scale, sizeof(float) * std::max<size_t>(scale_elems, 1)));
+    for (size_t i = 0; i < plans.size(); ++i) {
+        gft_plan_s& p = *plans[i];
+        TcBatch::Class& c = B->cls[p.n > 256 ? 1 : 0];
+        TcPlanDev D = make_plan_dev(p, nullptr, nullptr, batches[i], B->d_aimg + a_off[i], B->d_scale + s_off[i],
+                                    precision);
+        const long long tiles = (batches[i] + kTcM - 1) / kTcM;
+        D.tile0 = c.total_tiles;
+        D.group0 = c.total_groups;
+        c.total_tiles += tiles;
+        c.total_groups += tiles * (kTcM / 8);
+        c.nmax = std::max(c.nmax, p.n);
+        c.npad_max = std::max(c.npad_max, npad_max_of(p));
+        c.prog_cap = std::max(c.prog_cap, 2 * p.dev.n_pairs + p.dev.n_stages + 1);
+        c.items_cap = std::max(c.items_cap, D.n_items);
+        if (!c.err) c.err = p.dev.d_err;
+        c.desc.push_back(D);
+        c.user.push_back((int)i);
+    }
+    for (auto& c : B->cls)
+        if (!c.desc.empty()) GFT_CUDA(cudaMalloc(&c.d_desc, sizeof(TcPlanDev) * c.desc.size()));
+    return B.release();
+}
+
+void tc_batch_upload(void* h, const std::vector<const float*>& x, const std::vector<float*>& y, cudaStream_t st) {
+    TcBatch* B = static_cast<TcBatch*>(h);
+    for (auto& c : B->cls) {
+        if (c.desc.empty()) continue;
+        for (size_t j = 0; j < c.desc.size(); ++j) {
+            c.desc[j].x = x[c.user[j]];
+            c.desc[j].y = y[c.user[j]];
+        }
+        GFT_CUDA(cudaMemcpyAsync(c.d_desc, c.desc.data(), sizeof(TcPlanDev) * c.desc.size(), cudaMemcpyHostToDevice, st));
+    }
+}
+
+void tc_batch_launch(void* h, cudaStream_t st) {
+    TcBatch* B = static_cast<TcBatch*>(h);
+    for (auto& c : B->cls) {
+        if (c.desc.empty()) continue;
+        const TcPlanDev none{};
+        launch_pack(none, c.d_desc, (int)c.desc.size(), c.total_tiles, c.nmax, c.prog_cap, c.items_cap, B->prec, st);
+        launch_leaf(none, c.d_desc, (int)c.desc.size(), c.total_tiles, c.npad_max, 0, B->prec, c.err, st);
+    }
+}
+
+void tc_batch_free(void* h) { delete static_cast<TcBatch*>(h); }
 
 }  // namespace gft
