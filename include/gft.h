@@ -151,6 +151,38 @@ gft_status gft_plan_create_many(int32_t count, const int32_t* n, const double* c
                                 const int32_t* n_stages, const int32_t* const* phi, uint32_t flags,
                                 gft_plan_t* out);
 
+/*
+ * Involution search (Sec. V-F): a node involution phi under which L is
+ * symmetric (Definition 2, l_ij = l_phi(i)phi(j) within
+ * 1e-12*max(1,max|L|), self-loops included), pairing as many nodes as the
+ * search finds.  Trees: identical branches with a common or adjacent root
+ * are swapped (rooted at the tree's centre, canonical subtree labels);
+ * other graphs: depth-first search restricted to equal colours of a
+ * colour refinement of the degree list, keeping the involution with the most
+ * pairs within max_steps search steps (<= 0: 10^6).
+ *  n, L      host, n*n row-major symmetric L (copied).
+ *  classes   NULL or n ints: only nodes of equal class may be paired.
+ *  phi       host output, n ints (the identity when nothing is found).
+ *  pairs     NULL or output: number of pairs (i < phi(i)).
+ * Host only; no device work.  Errors: INVALID_ARG, NOT_LAPLACIAN.
+ */
+gft_status gft_find_involution(int32_t n, const double* L, const int32_t* classes, int64_t max_steps, int32_t* phi,
+                               int32_t* pairs);
+
+/*
+ * Stages for gft_plan_create found by search: stage s applies
+ * gft_find_involution to every block left by stages 0..s-1 (their
+ * Laplacians, Eq. 17 stage by stage), pairing only nodes that took part in
+ * equally many earlier stages, and lifts the blocks' involutions to the
+ * original labels (the recursion at the end of Sec. IV-C).  Stops when no
+ * block has a symmetry left or after max_stages (<= 16).
+ *  phis      host output, max_stages*n ints (stage-major, original labels).
+ *  n_stages  output: stages found (pass to gft_plan_create with phis).
+ * Host only.  Errors: INVALID_ARG, NOT_LAPLACIAN.
+ */
+gft_status gft_search_stages(int32_t n, const double* L, int32_t max_stages, int64_t max_steps, int32_t* phis,
+                             int32_t* n_stages);
+
 /* Free a plan and its device memory (NULL is accepted).  The caller must
  * make sure no transform using the plan is still running. */
 gft_status gft_plan_destroy(gft_plan_t plan);

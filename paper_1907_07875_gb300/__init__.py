@@ -232,6 +232,27 @@ class Plan:
         return v.value
 
 
+def find_involution(L, classes=None, max_steps: int = 0):
+    """Involution search (gft_find_involution): (phi, pairs)."""
+    L = _as_f64(L)
+    n = L.shape[0]
+    cl = None if classes is None else np.ascontiguousarray(np.asarray(classes, dtype=np.int32))
+    phi = np.zeros(n, dtype=np.int32)
+    pairs = C.c_int32(0)
+    _check(lib().gft_find_involution(n, _ptr(L), _ptr(cl), int(max_steps), _ptr(phi), C.byref(pairs)))
+    return phi, pairs.value
+
+
+def search_stages(L, max_stages: int = 8, max_steps: int = 0):
+    """Stage involutions found by search (gft_search_stages), for Plan()."""
+    L = _as_f64(L)
+    n = L.shape[0]
+    out = np.zeros((max(max_stages, 1), n), dtype=np.int32)
+    cnt = C.c_int32(0)
+    _check(lib().gft_search_stages(n, _ptr(L), int(max_stages), int(max_steps), _ptr(out), C.byref(cnt)))
+    return [out[s].copy() for s in range(cnt.value)]
+
+
 def plans_from_laplacians(Ls, phis_list, *, split_components: bool = False, order_block: bool = False,
                           analyze_only: bool = False, jit: bool = True, kernel: str = "auto"):
     """Many plans at once (gft_plan_create_many): every graph's leaves are
@@ -372,4 +393,4 @@ def givens_apply(x, theta, net: Givens):
 
 __all__ = ["Plan", "Batch", "Givens", "givens_apply", "laplacian", "GftError", "lib",
            "SPLIT_COMPONENTS", "ORDER_BLOCK", "ANALYZE_ONLY", "NO_JIT", "KERNEL_TABLE",
-           "KERNEL_WIDE", "PRECISIONS", "plans_from_laplacians"]
+           "KERNEL_WIDE", "PRECISIONS", "plans_from_laplacians", "find_involution", "search_stages"]

@@ -33,6 +33,8 @@ SIGNATURES = {
     "gft_laplacian_from_weights": (c_status, [C.c_int32, P, P, P]),
     "gft_plan_create": (c_status, [C.c_int32, P, C.c_int32, P, C.c_uint32, C.POINTER(c_plan)]),
     "gft_plan_create_many": (c_status, [C.c_int32, P, P, P, P, C.c_uint32, P]),
+    "gft_find_involution": (c_status, [C.c_int32, P, P, C.c_int64, P, I32P]),
+    "gft_search_stages": (c_status, [C.c_int32, P, C.c_int32, C.c_int64, P, I32P]),
     "gft_plan_destroy": (c_status, [c_plan]),
     "gft_plan_get_info": (c_status, [c_plan, C.POINTER(PlanInfo)]),
     "gft_plan_get_stage_pairs": (c_status, [c_plan, C.c_int32, P, I32P]),

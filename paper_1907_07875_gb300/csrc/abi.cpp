@@ -56,6 +56,19 @@ void check_device_plan(const gft_plan_s* p) {
     if (!p->has_device) fail(GFT_ERR_NO_DEVICE, "plan was created with GFT_ANALYZE_ONLY");
 }
 
+void check_symmetric_finite(int n, const double* L) {
+    double mx = 0.0;
+    for (size_t e = 0; e < (size_t)n * n; ++e) {
+        if (!std::isfinite(L[e])) fail(GFT_ERR_NOT_LAPLACIAN, "L has a non-finite entry");
+        mx = std::max(mx, std::fabs(L[e]));
+    }
+    const double tol = 1e-12 * std::max(1.0, mx);
+    for (int i = 0; i < n; ++i)
+        for (int j = i + 1; j < n; ++j)
+            if (std::fabs(L[(size_t)i * n + j] - L[(size_t)j * n + i]) > tol)
+                fail(GFT_ERR_NOT_LAPLACIAN, "L is not symmetric");
+}
+
 void check_io(const void* a, const void* b, int64_t batch) {
     if (batch < 0) fail(GFT_ERR_INVALID_ARG, "batch < 0");
     if (batch == 0) return;
@@ -205,6 +218,33 @@ gft_status gft_plan_create_many(int32_t count, const int32_t* n, const double* c
         std::vector<gft_plan_t> tmp(count, nullptr);
         create_plans(count, n, L, n_stages, phi, flags, tmp.data());
         std::copy(tmp.begin(), tmp.end(), out);
+    });
+}
+
+gft_status gft_find_involution(int32_t n, const double* L, const int32_t* classes, int64_t max_steps, int32_t* phi,
+                               int32_t* pairs) {
+    return guard([&] {
+        if (n < 1 || n > 4096) fail(GFT_ERR_INVALID_ARG, "n must be in [1, 4096]");
+        if (!L || !phi) fail(GFT_ERR_INVALID_ARG, "NULL argument");
+        check_symmetric_finite(n, L);
+        std::vector<int> out(n);
+        const int p = find_involution(n, L, classes, max_steps > 0 ? max_steps : 1000000, 0.0, out.data());
+        std::copy(out.begin(), out.end(), phi);
+        if (pairs) *pairs = p;
+    });
+}
+
+gft_status gft_search_stages(int32_t n, const double* L, int32_t max_stages, int64_t max_steps, int32_t* phis,
+                             int32_t* n_stages) {
+    return guard([&] {
+        if (n < 1 || n > 4096) fail(GFT_ERR_INVALID_ARG, "n must be in [1, 4096]");
+        if (!L || !phis || !n_stages) fail(GFT_ERR_INVALID_ARG, "NULL argument");
+        if (max_stages < 0 || max_stages > 16) fail(GFT_ERR_INVALID_ARG, "max_stages must be in [0, 16]");
+        check_symmetric_finite(n, L);
+        std::vector<int> out;
+        const int s = search_stages(n, L, max_stages, max_steps > 0 ? max_steps : 1000000, out);
+        std::copy(out.begin(), out.end(), phis);
+        *n_stages = s;
     });
 }
 

@@ -139,6 +139,10 @@ void jit_info(const gft_plan_s& p, int* jit, int* tile, int* threads);
 bool jit_launch_plain(gft_plan_s& p, const float* x, float* y, int64_t batch, cudaStream_t st);
 std::string jit_source(const gft_plan_s& p, bool f64);
 
+// search.cpp: involution search (Sec. V-F)
+int find_involution(int n, const double* L, const int* classes, long long max_steps, double scale, int* phi);
+int search_stages(int n, const double* L, int max_stages, long long max_steps, std::vector<int>& phis);
+
 // wide.cu: CUDA-core kernel for leaves wider than 32 nodes (up to 512)
 bool wide_eligible(const gft_plan_s& p);
 void wide_build(gft_plan_s& p);

@@ -261,3 +261,24 @@ def test_specialised_kernel_matches_interpreter(env, g, split):
     assert torch.equal(pj.inverse(xd), pi.inverse(xd))
     src = pj.kernel_source()
     assert "gft_jit_fwd_0" in src and "body_fwd" in src
+
+
+@pytest.mark.parametrize("g", [W.skeleton25(), W.grid(8), W.cycle(16), W.path(12),
+                               W.grid(6, weights="sym_uniform", seed=4)], ids=lambda g: g.name)
+def test_searched_stages_parity(env, g):
+    """Plans whose stages come from the involution search (Sec. V-F) --
+    deeper than the hand-given ones for grids and the skeleton -- against the
+    oracle built on the same stages, and against the dense GFT's eigenspaces."""
+    gft, torch = env
+    L = gft.laplacian(g.W, g.s)
+    phis = gft.search_stages(L, max_stages=6)
+    plan = gft.Plan(L, phis)
+    ref = ogft.fast_gft(ograph.laplacian(g.W, g.s), phis)
+    U = check_plan_against_oracle(plan, ref)
+    lam_d, U_d = ogft.dense_gft(ograph.laplacian(g.W, g.s))
+    assert projector_distance(U, U_d, lam_d) <= 1e-10
+    x = W.signals(1001, g.n, 17)
+    err, y = forward_error(gft, torch, plan, ref, U, x)
+    assert err <= FP32_TOL
+    xb = plan.inverse(torch.from_numpy(y.astype(np.float32)).cuda()).cpu().numpy()
+    assert rel_l2(xb, x) <= 2 * FP32_TOL
