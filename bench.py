@@ -541,6 +541,38 @@ def run_ours(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+def run_probe(args):
+    """ncu capture helper: one plan (or Givens network), three forward calls
+    of 2^25 coefficients, nothing timed.  Used by the commands recorded in
+    profiles/."""
+    import torch
+    import paper_1907_07875_gb300 as gft
+    from paper_1907_07875_gb300.build import build
+    build()
+    dev = torch.device("cuda", 0)
+    if args.probe.startswith("givens"):
+        import math
+        from paper_1907_07875_gb300.learned import xor_pairs
+        n = int(args.probe[len("givens"):])
+        S = 2 * int(math.log2(n))
+        net = gft.Givens(n, xor_pairs(n, S))
+        th = torch.rand(S, n // 2, device=dev)
+        x = torch.from_numpy(W.signals((1 << 25) // n, n, 1)).to(dev)
+        y = torch.empty_like(x)
+        for _ in range(3):
+            net.forward(th, x, out=y)
+    else:
+        g = {"skeleton25": W.skeleton25(), "grid16": W.grid(16), "grid32": W.grid(32), "cycle256": W.cycle(256),
+             "grid8": W.grid(8)}[args.probe]
+        plan = gft.Plan(gft.laplacian(g.W, g.s), g.phis, kernel=args.kernel)
+        x = torch.from_numpy(W.signals((1 << 25) // g.n, g.n, 1)).to(dev)
+        y = torch.empty_like(x)
+        for _ in range(3):
+            plan.forward(x, out=y, precision=args.precision)
+    torch.cuda.synchronize()
+    print(json.dumps({"probe": args.probe, "precision": args.precision, "kernel": args.kernel}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -550,6 +582,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the context measurements")
     ap.add_argument("--no-sweep", action="store_true", help="skip the 10^4-graph size sweep in the extras")
+    ap.add_argument("--probe", choices=["skeleton25", "grid8", "grid16", "grid32", "cycle256", "givens16", "givens64"],
+                    help="ncu capture helper: one plan, three forwards of 2^25 coefficients, nothing timed")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "bf16x3", "fp16x3"])
+    ap.add_argument("--kernel", default="auto", choices=["auto", "table", "wide"])
     ap.add_argument("--profile", action="store_true",
                     help="forward steps only, 2 buffer sets (for ncu captures)")
     args = ap.parse_args()
@@ -558,7 +594,9 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.warmup < 3:
         args.warmup = 3
-    if args.impl == "reference":
+    if args.probe:
+        run_probe(args)
+    elif args.impl == "reference":
         run_reference(args, rank, world)
     else:
         run_ours(args, rank, world, local_rank)
