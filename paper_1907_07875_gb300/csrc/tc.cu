@@ -17,7 +17,7 @@
 //      resident) through a ring of shared-memory slots with bulk copies, an
 //      MMA thread issues tcgen05.mma (M=128, N=leaf width, K=16 per
 //      instruction) into the leaf's TMEM columns -- one product for BF16,
-//      three (hi*hi + hi*lo + lo*hi) for the split precisions -- and four
+//      three (hi*hi + hi*lo + lo*hi) for the split precisions -- and eight
 //      epilogue warps read the double-buffered accumulators (groups of
 //      leaves of at most 256 columns) column by column IN COEFFICIENT ORDER
 //      (tcgen05.ld 32x32b), so the ascending-eigenvalue permutation costs
@@ -39,7 +39,8 @@ namespace {
 
 constexpr int kTcM = 128;        // signals per tile = MMA M
 constexpr int kTcK = 64;         // K chunk staged per step
-constexpr int kTcThreads = 192;  // warps 0-3 epilogue (128 TMEM lanes), 4 copies, 5 MMAs
+constexpr int kTcThreads = 320;  // warps 0-7 epilogue (two per 32-lane TMEM quarter), 8 copies, 9 MMAs
+constexpr int kTcEpiWarps = 8;
 constexpr int kTcMaxN = 256;     // widest leaf handled in one MMA
 constexpr int kTcCols = 512;     // TMEM columns allocated per CTA (one CTA per SM)
 constexpr int kTcGroupCols = 256;   // columns of one accumulator buffer (two buffers)
@@ -173,21 +174,22 @@ struct TcItem {
 };
 
 // Persistent tensor-core kernel, one CTA per SM, warp-specialised:
-//   warp 4 (one thread) bulk-loads (TMA) the A image of each work item
+//   warp 8 (one thread) bulk-loads (TMA) the A image of each work item
 //     (leaf, 64-wide K chunk) of each tile -- written by tc_pack8_kernel --
 //     and, unless every B image is resident, the item's B images, into a
 //     ring of shared-memory slots (4 slots of A when all B images fit in
 //     96 KB and are loaded once, else 2 slots of A + B);
-//   warp 5 (one thread) waits for a slot, issues its MMAs (M = 128 signals,
+//   warp 9 (one thread) waits for a slot, issues its MMAs (M = 128 signals,
 //     N = leaf width, K = 16 per instruction; one product for BF16, three
 //     -- hi*hi + hi*lo + lo*hi -- for the split precisions) into the TMEM
 //     columns of the item's leaf, and commits them to the slot's "empty"
 //     barrier; after the last item of a leaf group it commits to the group's
 //     "accumulator full" barrier;
-//   warps 0-3 (the epilogue; warp w reads TMEM lanes 32w..32w+31) wait for a
-//     full accumulator, read its columns in coefficient order, transpose
-//     32 x 32 blocks through shared memory and store 32 consecutive output
-//     positions per row, then release the accumulator.
+//   warps 0-7 (the epilogue; warp w reads TMEM lanes 32 (w & 3) .. + 31, the
+//     two warps of a lane quarter take alternate 16-column chunks) wait for
+//     a full accumulator, read its columns in coefficient order, transpose
+//     32 x 16 blocks through shared memory and store 16 consecutive output
+//     positions of two rows per instruction, then release the accumulator.
 // Leaves are grouped so that a group needs at most 256 TMEM columns; the
 // accumulator is double buffered (2 x 256 of the 512 columns), so the
 // epilogue of one group overlaps the copies and MMAs of the next.  When all
@@ -206,7 +208,7 @@ struct TcRing {
     unsigned meta_off;  // single-plan launches: byte offset of [items][leaves][gmap]
 };
 
-constexpr int kStageLd = 33;   // epilogue staging row stride (floats): conflict-free
+constexpr int kStageLd = 17;   // epilogue staging row stride (floats): 16 columns + 1, conflict-free
 
 // Work units are the tiles of every plan of the launch, in plan order; CTA b
 // takes units b, b + grid, ... (every role walks the same sequence).
@@ -232,7 +234,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_leaf_kernel(TcPlanDev one, c
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init1(&bar_dfull[i]);
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_dfree[i])), "r"(4) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_dfree[i])), "r"(kTcEpiWarps)
+                         : "memory");
         }
         mbar_init1(&bar_b);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -285,7 +288,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_leaf_kernel(TcPlanDev one, c
         atomicExch(err, (int)GFT_ERR_TIMEOUT);
     };
 
-    if (warp == 4) {
+    if (warp == kTcEpiWarps) {
         // ---------------- copies ----------------
         if (lane == 0) {
             if (ring.resident && my_units > 0) {
@@ -330,7 +333,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_leaf_kernel(TcPlanDev one, c
                 if (issued[s]) mbar_wait_bounded(&bar_full[s], last_par[s]);
             if (ring.resident && my_units > 0) mbar_wait_bounded(&bar_b, 0);
         }
-    } else if (warp == 5) {
+    } else if (warp == kTcEpiWarps + 1) {
         // ---------------- MMAs ----------------
         if (lane == 0) {
             if (ring.resident && my_units > 0 && !mbar_wait_bounded(&bar_b, 0)) abort_now();
@@ -389,14 +392,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_leaf_kernel(TcPlanDev one, c
             }
         }
     } else {
-        // ---------------- epilogue (warps 0-3) ----------------
+        // ---------------- epilogue (warps 0-7) ----------------
+        // warp w reads TMEM lanes 32 (w & 3) .. + 31 (its quarter); the two
+        // warps of a quarter take alternate 16-column chunks
+        const int quarter = warp & 3, half = warp >> 2;
         float* stg = s_stage + warp * 32 * kStageLd;
-        const unsigned lane_base = (unsigned)(warp * 32) << 16;
+        const unsigned lane_base = (unsigned)(quarter * 32) << 16;
         long long u = 0;
         for (long long k = 0; k < my_units && !s_abort; ++k) {
             long long tile;
             const TcPlanDev D = plan_of(blockIdx.x + k * (long long)gridDim.x, tile);
-            const long long r0 = tile * kTcM + warp * 32;
+            const long long r0 = tile * kTcM + quarter * 32;
             const long long row = r0 + lane;
             const float sc = fp16 ? (row < D.batch ? D.scale[row] : 1.f) : 1.f;
             const int* gpos = D.gmap;
@@ -410,13 +416,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_leaf_kernel(TcPlanDev one, c
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const int j_end = goff[g + 1];
-                for (int j0 = goff[g]; j0 < j_end; j0 += 32) {
-                    const int cnt = min(32, j_end - j0);
-                    const int my_col = lane < cnt ? gcol[j0 + lane] : gcol[j_end - 1];
-                    const int pos = lane < cnt ? gpos[j0 + lane] : 0;
-                    float r[32];
+                for (int j0 = goff[g] + 16 * half; j0 < j_end; j0 += 32) {
+                    const int cnt = min(16, j_end - j0);
+                    const int c = lane & 15;
+                    const int my_col = c < cnt ? gcol[j0 + c] : gcol[j_end - 1];
+                    const int pos = c < cnt ? gpos[j0 + c] : 0;
+                    float r[16];
 #pragma unroll
-                    for (int q = 0; q < 32; ++q) {
+                    for (int q = 0; q < 16; ++q) {
                         const int col = __shfl_sync(0xffffffffu, my_col, q);
                         unsigned uu;
                         asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];"
@@ -425,13 +432,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_leaf_kernel(TcPlanDev one, c
                         r[q] = __uint_as_float(uu);
                     }
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                    // transpose through shared memory: lane = row -> lane = output position
+                    // transpose through shared memory: lane = row -> (row pair, output position)
 #pragma unroll
-                    for (int q = 0; q < 32; ++q) stg[lane * kStageLd + q] = r[q] * sc;
+                    for (int q = 0; q < 16; ++q) stg[lane * kStageLd + q] = r[q] * sc;
                     __syncwarp();
-                    for (int rr = 0; rr < 32; ++rr) {
-                        const long long grow = r0 + rr;
-                        if (grow < D.batch && lane < cnt) __stcs(D.y + grow * D.n + pos, stg[rr * kStageLd + lane]);
+#pragma unroll 4
+                    for (int rr = 0; rr < 16; ++rr) {
+                        const int rl = 2 * rr + (lane >> 4);
+                        const long long grow = r0 + rl;
+                        if (grow < D.batch && c < cnt) __stcs(D.y + grow * D.n + pos, stg[rl * kStageLd + c]);
                     }
                     __syncwarp();
                 }
@@ -930,7 +939,7 @@ void launch_leaf(const TcPlanDev& one, const TcPlanDev* many, int n_plans, long 
                              : ((sizeof(TcItem) * one.n_items + 15) & ~size_t(15)) +
                                    ((sizeof(TcLeaf) * one.n_leaves + 15) & ~size_t(15)) +
                                    sizeof(int) * (size_t)((2 * one.n + 2 * (one.n_groups + 1) + 3) & ~3);
-    const size_t stage = sizeof(float) * (size_t)kTcM * kStageLd + meta;   // staging, then the tables
+    const size_t stage = sizeof(float) * (size_t)kTcEpiWarps * 32 * kStageLd + meta;   // staging, then the tables
     const size_t limit = 232448 - 2048;   // leave room for static shared memory
     TcRing ring{};
     const unsigned res_bytes = resident_b * (split ? 2u : 1u);
@@ -950,7 +959,7 @@ void launch_leaf(const TcPlanDev& one, const TcPlanDev* many, int n_plans, long 
         ring.res_off = 0;
         ring.stage_off = (unsigned)ring.nbuf * ring.bufsz;
     }
-    ring.meta_off = ring.stage_off + (unsigned)(sizeof(float) * (size_t)kTcM * kStageLd);
+    ring.meta_off = ring.stage_off + (unsigned)(sizeof(float) * (size_t)kTcEpiWarps * 32 * kStageLd);
     const size_t smem = ring.stage_off + stage;
     if (smem > limit) fail(GFT_ERR_UNSUPPORTED, "tensor-core kernel does not fit in shared memory");
     GFT_CUDA(cudaFuncSetAttribute(tc_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
