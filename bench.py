@@ -262,10 +262,38 @@ def extras(torch, gft, dev):
         del bat
     out["config3_mixed_one_graph"] = mixed
     del xs, ys, plans
+    # ---- the paper's runtime table (Sec. VI-A): fast vs matrix GFT on the same graphs
+    out["paper_runtime_table"] = runtime_table_extras(torch, gft, dev)
     # ---- config 4: learned Givens surrogates on the nine nearly symmetric graphs
     out["config4_learned"] = learned_extras(torch, gft, dev)
     torch.backends.cuda.matmul.allow_tf32 = prev
     return out
+
+
+def runtime_table_extras(torch, gft, dev):
+    """The graphs of the paper's runtime table: operation counts (ours, from
+    the plan; printed, from the paper) and the runtime reduction of the fast
+    GFT over the matrix GFT (torch.matmul FP32, TF32 off) on the same GB300 --
+    on the paper's workload (20000 i.i.d. U[0,1] signals: launch-bound here)
+    and on 2^26 coefficients (above L2)."""
+    res = {}
+    for g, split, printed in W.runtime_table_graphs():
+        plan = gft.Plan(gft.laplacian(g.W, g.s), g.phis, split_components=split)
+        inf = plan.info
+        U = torch.from_numpy(plan.basis()).float().to(dev)
+        row = {"n": g.n, "leaves": [len(l) for l in plan.leaves()], "fast_adds": inf["fast_adds"],
+               "fast_mults": inf["fast_mults"], "printed_fast_adds_mults": list(printed[2:4]),
+               "printed_reduction": printed[4]}
+        for tag, nb in (("paper_20000", 20000), ("2^26", (1 << 26) // g.n)):
+            x = torch.from_numpy(W.signals(nb, g.n, 7, dist="uniform")).to(dev)
+            y = torch.empty_like(x)
+            t_f = _timed(torch, lambda: plan.forward(x, out=y))
+            t_d = _timed(torch, lambda: torch.matmul(x, U, out=y))
+            row[tag] = {"fast_gcoeffs_s": round(nb * g.n / t_f / 1e9, 2),
+                        "dense_gcoeffs_s": round(nb * g.n / t_d / 1e9, 2),
+                        "reduction": round(1.0 - t_f / t_d, 3)}
+        res[g.name] = row
+    return res
 
 
 def learned_extras(torch, gft, dev, steps=1500):

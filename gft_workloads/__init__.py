@@ -27,7 +27,7 @@ __all__ = [
     "star", "complete", "near_symmetric_path", "near_symmetric_grid",
     "planted_symmetric", "reversal", "cycle_second_reflection", "grid_lr",
     "grid_ud", "grid_diag", "grid_antidiag", "grid_centro", "involution_count",
-    "all_involutions", "config1", "config2", "config3", "config4", "config5", "config5_specs",
+    "all_involutions", "grid6_bidiag", "zgrid", "runtime_table_graphs", "config1", "config2", "config3", "config4", "config5", "config5_specs",
     "make_graph",
 ]
 
@@ -220,6 +220,37 @@ def grid(N1: int, N2: Optional[int] = None, weights: str = "unit",
                  {"N1": N1, "N2": N2})
 
 
+def grid6_bidiag(N: int, a: float = 0.5) -> Graph:
+    """Bi-diagonally symmetric 6-connected N x N grid (Sec. V-D, Fig. 7; the
+    runtime experiment uses a = 0.5): the 4-connected grid with unit weights
+    plus the (1, 1) diagonals (k, l) - (k+1, l+1) with weight a.  Symmetric
+    under the diagonal and the anti-diagonal reflections."""
+    n = N * N
+    W, s = _empty(n)
+    for i, j in _grid_edges(N, N):
+        _add_edge(W, i, j, 1.0)
+    for k in range(N - 1):
+        for l in range(N - 1):
+            _add_edge(W, k * N + l, (k + 1) * N + l + 1, a)
+    return Graph(f"grid6bidiag{N}x{N}_a{a}", W, s, [grid_diag(N), grid_antidiag(N)], {"N1": N, "N2": N})
+
+
+def zgrid(N: int, w: float = 2.0) -> Graph:
+    """z-shaped N x N grid (Sec. V-D, Fig. 8; the runtime experiment uses
+    w = 2): horizontal edges with weight 1 and anti-diagonal edges
+    (k, l) - (k+1, l-1) with weight w.  Symmetric under the point reflection
+    about the grid centre."""
+    n = N * N
+    W, s = _empty(n)
+    for k in range(N):
+        for l in range(N):
+            if l + 1 < N:
+                _add_edge(W, k * N + l, k * N + l + 1, 1.0)
+            if k + 1 < N and l >= 1:
+                _add_edge(W, k * N + l, (k + 1) * N + l - 1, w)
+    return Graph(f"zgrid{N}x{N}_w{w}", W, s, [grid_centro(N)], {"N1": N, "N2": N})
+
+
 def skeleton25() -> Graph:
     """25-joint skeleton: spine chain 0-4; left arm 5-9 and right arm 10-14
     attached at joint 3; left leg 15-19 and right leg 20-24 attached at
@@ -320,6 +351,24 @@ def planted_symmetric(n: int, phi: np.ndarray, density: float = 0.5,
 # --------------------------------------------------------------------------
 # workload recipes (graph seeds 2000 + config index, signal seeds 1000 + index)
 # --------------------------------------------------------------------------
+def runtime_table_graphs():
+    """The graphs of the paper's runtime table (Sec. VI-A) that the text fixes:
+    cycles 12 and 80, bi-diagonally symmetric 6-connected grids 4x4 and 8x8
+    (a = 0.5), z-shaped grids 4x4 and 8x8 (w = 2), the 25-joint skeleton.
+    (The 15-joint skeleton is drawn only in a figure.)  Each item is
+    (graph, split_components, (matrix adds, matrix mults, fast adds, fast
+    mults, runtime reduction) as printed in the table)."""
+    return [
+        (cycle(12), False, (132, 144, 44, 30, 0.527)),
+        (cycle(80), False, (6320, 6400, 1224, 1078, 0.797)),
+        (grid6_bidiag(4), False, (240, 256, 80, 80, 0.537)),
+        (grid6_bidiag(8), False, (4032, 4096, 1104, 1072, 0.685)),
+        (zgrid(4), False, (240, 256, 128, 112, 0.415)),
+        (zgrid(8), False, (4032, 4096, 2048, 2048, 0.450)),
+        (skeleton25(), True, (600, 625, 272, 282, 0.475)),
+    ]
+
+
 def config1(batch: int = 4096):
     """Uniform path graph N=8 with the reflection involution; N(0,1) signals."""
     g = path(8)

@@ -73,6 +73,8 @@ FAMILIES = [
     (W.bipartite(64, 0.1, seed=2), True), (W.bipartite(30, 0.3, seed=4), False),
     (W.planted_symmetric(11, np.array([10, 9, 2, 7, 4, 5, 6, 3, 8, 1, 0]), seed=2), False),
     (W.star(7), False), (W.complete(6), False), (W.near_symmetric_path(32, 0.05, seed=1), False),
+    (W.grid6_bidiag(4), False), (W.grid6_bidiag(8), False), (W.zgrid(4), False), (W.zgrid(8), False),
+    (W.cycle(80), False),
 ]
 
 
