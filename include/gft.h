@@ -115,8 +115,8 @@ gft_status gft_laplacian_from_weights(int32_t n, const double* W, const double* 
  *            gft_plan_destroy).  Unchanged on error.
  * Unless GFT_ANALYZE_ONLY is set, the leaf Laplacians are eigendecomposed on
  * the current CUDA device by a batched FP64 Jacobi kernel and the bases are
- * uploaded; the call synchronises the device.  For graphs of at most 64
- * nodes (sum of squared leaf sizes <= 2048) and without GFT_NO_JIT, the
+ * uploaded; the call synchronises the device.  For graphs of at most 128
+ * nodes (sum of squared leaf sizes <= 4096) and without GFT_NO_JIT, the
  * call also generates a kernel specialised to this plan (indices and
  * folded leaf matrices as constants), compiles it with NVRTC for sm_103a,
  * and times several launch shapes on a scratch batch to keep the fastest;

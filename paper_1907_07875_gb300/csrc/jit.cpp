@@ -3,7 +3,7 @@
 //
 // The interpreter kernel (apply.cu) reads stage pairs, node lists and leaf
 // matrices from shared memory and spends most of its instructions on index
-// loads and address arithmetic.  For small graphs (n <= 64) the whole plan
+// loads and address arithmetic.  For small graphs (n <= 128) the whole plan
 // fits in straight-line code, so this generator writes one kernel per plan
 // in which every index is a compile-time constant and every leaf-matrix
 // entry is an FMA immediate:
@@ -39,6 +39,12 @@ namespace gft {
 namespace {
 
 constexpr int kSmemLimitJ = 232448;
+// Plans that get straight-line kernels: a signal's n values live in
+// registers (n <= 128 keeps them there under a 255-register cap), and the
+// leaf matrices become sum(m^2) FMA immediates per direction (bounds the
+// code size and the NVRTC compile time).
+constexpr int kJitMaxN = 128;
+constexpr long long kJitMaxLeafEntries = 4096;
 
 struct Cand {
     int rs, threads, nbuf, bulk;
@@ -489,10 +495,10 @@ struct JitPlan {
 bool jit_eligible(const gft_plan_s& p) {
     if (std::getenv("GFT_DISABLE_JIT")) return false;
     if (p.flags & GFT_NO_JIT) return false;
-    if (p.n > 64) return false;
+    if (p.n > kJitMaxN) return false;
     long long fl = 0;
     for (auto& lf : p.leaves) fl += (long long)lf.m() * lf.m();
-    return fl <= 2048;
+    return fl <= kJitMaxLeafEntries;
 }
 
 std::string jit_source(const gft_plan_s& p, bool f64) {

@@ -74,7 +74,7 @@ FAMILIES = [
     (W.planted_symmetric(11, np.array([10, 9, 2, 7, 4, 5, 6, 3, 8, 1, 0]), seed=2), False),
     (W.star(7), False), (W.complete(6), False), (W.near_symmetric_path(32, 0.05, seed=1), False),
     (W.grid6_bidiag(4), False), (W.grid6_bidiag(8), False), (W.zgrid(4), False), (W.zgrid(8), False),
-    (W.cycle(80), False),
+    (W.cycle(80), False), (W.cycle(128), False), (W.grid(10), False), (W.bipartite(72, 0.2, seed=5), False),
 ]
 
 
@@ -96,7 +96,8 @@ def test_forward_inverse_families(env, g, split, batch):
 
 
 @pytest.mark.parametrize("g,split", [(W.path(8), False), (W.skeleton25(), True), (W.grid(8), False),
-                                     (W.cycle(12), False)], ids=lambda v: getattr(v, "name", str(v)))
+                                     (W.cycle(12), False), (W.cycle(80), False), (W.cycle(128), False)],
+                         ids=lambda v: getattr(v, "name", str(v)))
 def test_fp64_path(env, g, split):
     gft, torch = env
     plan = make_plan(gft, g, split)
