@@ -28,7 +28,7 @@ __all__ = [
     "planted_symmetric", "reversal", "cycle_second_reflection", "grid_lr",
     "grid_ud", "grid_diag", "grid_antidiag", "grid_centro", "involution_count",
     "all_involutions", "grid6_bidiag", "zgrid", "runtime_table_graphs", "config1", "config2", "config3", "config4", "config5", "config5_specs",
-    "make_graph",
+    "make_graph", "krbg", "random_bipartite", "hypercube", "right_haar_graphs",
 ]
 
 
@@ -287,6 +287,90 @@ def bipartite(n: int, p: float = 0.1, seed: Optional[int] = None) -> Graph:
     W[h:, :h] = B.T
     phi = ((np.arange(n) + h) % n).astype(np.int32)
     return Graph(f"bipartite{n}", W, s, [phi], {"halves": h})
+
+
+def _relabel(W: np.ndarray, side: np.ndarray, rng) -> tuple:
+    perm = rng.permutation(W.shape[0])          # new label of old node i is perm[i]
+    W2 = np.zeros_like(W)
+    W2[np.ix_(perm, perm)] = W
+    side2 = np.empty_like(side)
+    side2[perm] = side
+    return W2, side2
+
+
+def krbg(m: int, k: int, seed: Optional[int] = None, weighted: bool = True,
+         shuffle: bool = True) -> Graph:
+    """k-regular bipartite graph on 2m nodes (Lemma 1, Thm. 1): the cross
+    block is a sum of k random permutation matrices, each with one weight
+    (U[0.5, 1.5] if weighted, else 1), so every node has the same weighted
+    degree (the sum of the k weights).  shuffle: random node labels, so the
+    two parts are not contiguous.  meta['side'] marks the parts (0 / 1),
+    meta['degree'] the common weighted degree."""
+    rng = np.random.default_rng(seed)
+    w = rng.uniform(0.5, 1.5, size=k) if weighted else np.ones(k)
+    B = np.zeros((m, m))
+    for t in range(k):
+        B[np.arange(m), rng.permutation(m)] += w[t]
+    n = 2 * m
+    W, s = _empty(n)
+    W[:m, m:] = B
+    W[m:, :m] = B.T
+    side = np.repeat(np.array([0, 1], dtype=np.int32), m)
+    if shuffle:
+        W, side = _relabel(W, side, rng)
+    return Graph(f"krbg{n}_k{k}" + ("w" if weighted else ""), W, s, [], {"side": side, "degree": float(w.sum())})
+
+
+def random_bipartite(n1: int, n2: int, p: float = 0.2, seed: Optional[int] = None,
+                     shuffle: bool = True) -> Graph:
+    """Random bipartite graph with parts of n1 and n2 nodes (Thm. 2: any
+    bipartite graph, used with its normalised Laplacian): cross edges with
+    probability p and weights U[0.1, 1]; a node left without an edge gets
+    one to a random node of the other part, so every degree is positive."""
+    rng = np.random.default_rng(seed)
+    mask = rng.random((n1, n2)) < p
+    for i in range(n1):
+        if not mask[i].any():
+            mask[i, rng.integers(n2)] = True
+    for j in range(n2):
+        if not mask[:, j].any():
+            mask[rng.integers(n1), j] = True
+    B = np.where(mask, rng.uniform(0.1, 1.0, size=(n1, n2)), 0.0)
+    n = n1 + n2
+    W, s = _empty(n)
+    W[:n1, n1:] = B
+    W[n1:, :n1] = B.T
+    side = np.concatenate([np.zeros(n1, np.int32), np.ones(n2, np.int32)])
+    if shuffle:
+        W, side = _relabel(W, side, rng)
+    return Graph(f"rbip{n1}x{n2}", W, s, [], {"side": side})
+
+
+def hypercube(d: int) -> Graph:
+    """d-dimensional hypercube (2^d nodes, i ~ i xor 2^b): d-regular and
+    bipartite by the parity of the number of set bits."""
+    n = 1 << d
+    W, s = _empty(n)
+    for i in range(n):
+        for b in range(d):
+            j = i ^ (1 << b)
+            if i < j:
+                _add_edge(W, i, j, 1.0)
+    side = np.array([bin(i).count("1") & 1 for i in range(n)], dtype=np.int32)
+    return Graph(f"hypercube{d}", W, s, [], {"side": side, "degree": float(d)})
+
+
+def right_haar_graphs():
+    """Bipartite cases of the right Haar stage: (graph, normalised) pairs.
+    normalised = False: the combinatorial Laplacian of a k-regular bipartite
+    graph (Thm. 1); True: the normalised Laplacian D^-1/2 L D^-1/2 of any
+    bipartite graph (Thm. 2)."""
+    return [
+        (cycle(12), False), (krbg(8, 3, seed=2101), False), (krbg(20, 4, seed=2102, weighted=False), False),
+        (hypercube(4), False), (random_bipartite(7, 4, 0.4, seed=2103), True),
+        (random_bipartite(30, 18, 0.15, seed=2104), True), (krbg(32, 5, seed=2105), False),
+        (random_bipartite(40, 40, 0.1, seed=2106), True),
+    ]
 
 
 def star(n: int) -> Graph:

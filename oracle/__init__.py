@@ -19,6 +19,9 @@ Everything is plain, slow and in float64:
                   the paper's stage-by-stage decomposition (Sec. IV-C and the
                   recursion at its end), the fast basis U = B_1...B_S diag(U_k),
                   and dense / staged application to signal batches.
+* ``right_haar`` -- the right Haar stage of bipartite graphs (Sec. III-A,
+                  Lemma 1, Thms. 1-2): the two sub-transforms E and F and the
+                  output-side Haar units.
 * ``givens``   -- layered Givens rotations (Eq. 1, Fig. 1) for the learned
                   surrogate: forward, loss and central finite differences.
 * ``metrics``  -- the error measures RE (Eq. 23), delta and epsilon (Sec. VI-B).
@@ -27,4 +30,4 @@ Parity status of each function is stated in its docstring; every function
 has a pin in ``tests/test_oracle_*.py`` except the paper's operation counts,
 which the oracle does not reproduce ("parity unpinned", see the design notes).
 """
-from . import graph, jacobi, gft, givens, metrics  # noqa: F401
+from . import graph, jacobi, gft, givens, metrics, right_haar  # noqa: F401

@@ -200,3 +200,48 @@ def connected_components(L, tol: float = 0.0) -> List[List[int]]:
                     stack.append(u)
         comps.append(sorted(comp))
     return comps
+
+
+def normalized_laplacian(W: np.ndarray, s: np.ndarray) -> np.ndarray:
+    """Symmetric normalised Laplacian D^-1/2 L D^-1/2 (Sec. II-B), with
+    L = D - W + S (Eq. 3) and degrees d_i = sum_j w_ij, the self-loop w_ii = s_i
+    included.  Every degree must be positive."""
+    W = np.asarray(W, dtype=np.float64)
+    s = np.asarray(s, dtype=np.float64)
+    n = W.shape[0]
+    d = np.zeros(n)
+    for i in range(n):
+        d[i] = s[i] + sum(W[i, j] for j in range(n) if j != i)
+        if d[i] <= 0:
+            raise ValueError(f"node {i} has degree {d[i]}")
+    L = laplacian(W, s)
+    N = np.zeros((n, n))
+    for i in range(n):
+        for j in range(n):
+            N[i, j] = L[i, j] / math.sqrt(d[i] * d[j])
+    return N
+
+
+def bipartition(L, tol: float = 0.0):
+    """Two-colouring of the graph whose edges are the nonzero off-diagonal
+    entries of L (Sec. II-B: every edge joins the two parts).  Each
+    connected component gives colour 0 to its smallest node.  Returns an
+    int array of 0 / 1 per node, or None if some component has an odd cycle."""
+    n = L.shape[0]
+    side = [-1] * n
+    for r in range(n):
+        if side[r] >= 0:
+            continue
+        side[r] = 0
+        queue = [r]
+        while queue:
+            v = queue.pop(0)
+            for u in range(n):
+                if u == v or abs(L[v, u]) <= tol:
+                    continue
+                if side[u] < 0:
+                    side[u] = 1 - side[v]
+                    queue.append(u)
+                elif side[u] == side[v]:
+                    return None
+    return np.array(side, dtype=np.int32)
