@@ -55,7 +55,8 @@ typedef enum {
     GFT_ERR_UNSUPPORTED = 9,     /* valid input this build does not handle (see message) */
     GFT_ERR_MISALIGNED = 10,     /* device pointer not 16-byte aligned */
     GFT_ERR_BLOCK_LEAK = 11,     /* a stage involution maps a node out of its block */
-    GFT_ERR_NO_DEVICE = 12       /* plan was created with GFT_ANALYZE_ONLY */
+    GFT_ERR_NO_DEVICE = 12,      /* plan was created with GFT_ANALYZE_ONLY */
+    GFT_ERR_NOT_BIPARTITE = 13   /* no right Haar stage: odd cycle, or part blocks not alpha*I */
 } gft_status;
 
 /* gft_plan_create flags */
@@ -92,6 +93,13 @@ int32_t gft_version(void);
  * NOT_LAPLACIAN if W is not symmetric or not finite.
  */
 gft_status gft_laplacian_from_weights(int32_t n, const double* W, const double* s, double* L);
+
+/*
+ * Symmetric normalised Laplacian D^-1/2 L D^-1/2 (Sec. II-B) of the graph
+ * (W, s) as in gft_laplacian_from_weights, d_i = l_ii.  Errors as there,
+ * plus NOT_LAPLACIAN for a node without positive degree.
+ */
+gft_status gft_normalized_laplacian_from_weights(int32_t n, const double* W, const double* s, double* L);
 
 /*
  * Build a fast-GFT plan (Sec. IV-B, IV-C; recursion at the end of Sec. IV-C).
@@ -152,6 +160,39 @@ gft_status gft_plan_create_many(int32_t count, const int32_t* n, const double* c
                                 gft_plan_t* out);
 
 /*
+ * Bipartite plan with a right Haar stage (Sec. III-A, Lemma 1, Thms. 1-2):
+ * U^T x = B_{n,p} diag(E^T, F^T) x (Eq. 8).  L must split into two parts
+ * S1, S2 with L[S1,S1] = L[S2,S2] = alpha*I (within 1e-12*max(1,max|L|)):
+ * the Laplacian of a k-regular bipartite graph (alpha = k) or the
+ * normalised Laplacian of any bipartite graph (alpha = 1).  With the
+ * coupling block C = -L[S1,S2], E holds the left singular vectors of C on
+ * the larger part, F the right singular vectors on the smaller part
+ * (p = its size); unit c pairs column c of E and of F: coefficient
+ * (e_c.x + f_c.x)/sqrt2 has eigenvalue alpha - sigma_c, (e_c.x - f_c.x)/sqrt2
+ * has alpha + sigma_c; E's columns beyond p have eigenvalue alpha.  The
+ * singular vectors come from the FP64 Jacobi eigendecomposition of
+ * [[0, C], [C^T, 0]] on the device (no squaring of C); singular values below
+ * 1e-9*max(1, sigma_max) count as zero and their vectors are separated by
+ * pivoted Gram-Schmidt.
+ *  n, L      as gft_plan_create.
+ *  side      NULL (parts found by two-colouring the nonzero off-diagonal
+ *            pattern; colour 0 for each component's smallest node), or n
+ *            entries 0 / 1.  The larger part is E's (colour 0 on a tie);
+ *            within a part, nodes are in ascending label order.
+ *  flags     GFT_ORDER_BLOCK | GFT_ANALYZE_ONLY | GFT_NO_JIT |
+ *            GFT_KERNEL_TABLE | GFT_KERNEL_WIDE.
+ * The plan has no left stages (n_stages = 0), two leaves (E, F) and
+ * right_pairs = p.  Transforms run on the CUDA-core kernels (FP32 / FP64;
+ * tensor-core precisions return UNSUPPORTED).  Output order as
+ * gft_plan_create; signs: the sign rule fixes the sum vector (e_c; f_c) of
+ * each unit, and its difference vector (e_c; -f_c) follows.
+ * gft_plan_get_leaf_laplacian is UNSUPPORTED for these plans.
+ * Errors: INVALID_ARG, NOT_LAPLACIAN, NOT_BIPARTITE, NO_CONVERGENCE, CUDA, OOM.
+ */
+gft_status gft_plan_create_bipartite(int32_t n, const double* L, const int32_t* side, uint32_t flags,
+                                     gft_plan_t* out);
+
+/*
  * Involution search (Sec. V-F): a node involution phi under which L is
  * symmetric (Definition 2, l_ij = l_phi(i)phi(j) within
  * 1e-12*max(1,max|L|), self-loops included), pairing as many nodes as the
@@ -203,6 +244,7 @@ typedef struct {
     int32_t tile_signals;   /* FP32 forward launch shape chosen by the autotuner: */
     int32_t threads;        /*   signals per tile and threads per block (0 if none) */
     int32_t wide;           /* 1 if FP32 CUDA-core transforms use the wide-leaf kernel */
+    int32_t right_pairs;    /* right Haar units (bipartite plans), else 0 */
 } gft_plan_info_t;
 
 gft_status gft_plan_get_info(gft_plan_t plan, gft_plan_info_t* info);

@@ -31,7 +31,7 @@ PRECISIONS = {"fp32": 0, "bf16": 1, "bf16x3": 2, "fp16x3": 3}
 STATUS = {0: "GFT_OK", 1: "GFT_ERR_INVALID_ARG", 2: "GFT_ERR_NOT_INVOLUTION", 3: "GFT_ERR_NOT_SYMMETRIC",
           4: "GFT_ERR_NOT_LAPLACIAN", 5: "GFT_ERR_NO_CONVERGENCE", 6: "GFT_ERR_CUDA", 7: "GFT_ERR_OOM",
           8: "GFT_ERR_TIMEOUT", 9: "GFT_ERR_UNSUPPORTED", 10: "GFT_ERR_MISALIGNED", 11: "GFT_ERR_BLOCK_LEAK",
-          12: "GFT_ERR_NO_DEVICE"}
+          12: "GFT_ERR_NO_DEVICE", 13: "GFT_ERR_NOT_BIPARTITE"}
 
 
 class GftError(RuntimeError):
@@ -83,6 +83,16 @@ def laplacian(W, s=None) -> np.ndarray:
     return L
 
 
+def normalized_laplacian(W, s=None) -> np.ndarray:
+    """Symmetric normalised Laplacian D^-1/2 L D^-1/2 (Sec. II-B), host."""
+    W = _as_f64(W)
+    n = W.shape[0]
+    sv = None if s is None else _as_f64(s, (n,))
+    L = np.empty((n, n))
+    _check(lib().gft_normalized_laplacian_from_weights(n, _ptr(W), _ptr(sv), _ptr(L)))
+    return L
+
+
 class Plan:
     """A fast-GFT plan for one graph (gft_plan_create)."""
 
@@ -104,6 +114,24 @@ class Plan:
         _check(lib().gft_plan_create(n, _ptr(L), len(phis), _ptr(ph), flags, C.byref(h)))
         self._h = h
         self.n = n
+
+    @classmethod
+    def bipartite(cls, L, side=None, *, order_block: bool = False, analyze_only: bool = False,
+                  jit: bool = True, kernel: str = "auto") -> "Plan":
+        """Plan with a right Haar stage for a bipartite graph (Sec. III-A,
+        gft_plan_create_bipartite): side = None (two-colouring) or 0 / 1 per node."""
+        L = _as_f64(L)
+        n = L.shape[0]
+        if L.shape != (n, n):
+            raise ValueError("L must be square")
+        sd = None if side is None else np.ascontiguousarray(np.asarray(side, dtype=np.int32))
+        if sd is not None and sd.shape != (n,):
+            raise ValueError("side must have n entries")
+        flags = ((ORDER_BLOCK if order_block else 0) | (ANALYZE_ONLY if analyze_only else 0)
+                 | (0 if jit else NO_JIT) | {"auto": 0, "table": KERNEL_TABLE, "wide": KERNEL_WIDE}[kernel])
+        h = C.c_void_p()
+        _check(lib().gft_plan_create_bipartite(n, _ptr(L), _ptr(sd), flags, C.byref(h)))
+        return cls._wrap(h, n)
 
     @classmethod
     def _wrap(cls, handle, n):
@@ -391,6 +419,6 @@ def givens_apply(x, theta, net: Givens):
     return _GF.apply(x, theta, net)
 
 
-__all__ = ["Plan", "Batch", "Givens", "givens_apply", "laplacian", "GftError", "lib",
+__all__ = ["Plan", "Batch", "Givens", "givens_apply", "laplacian", "normalized_laplacian", "GftError", "lib",
            "SPLIT_COMPONENTS", "ORDER_BLOCK", "ANALYZE_ONLY", "NO_JIT", "KERNEL_TABLE",
            "KERNEL_WIDE", "PRECISIONS", "plans_from_laplacians", "find_involution", "search_stages"]

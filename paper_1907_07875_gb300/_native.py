@@ -17,7 +17,8 @@ class PlanInfo(C.Structure):
                 ("n_pairs", C.c_int32), ("max_leaf", C.c_int32), ("has_device", C.c_int32),
                 ("jacobi_sweeps", C.c_int32), ("flags", C.c_uint32),
                 ("fast_mults", C.c_int64), ("fast_adds", C.c_int64), ("jit", C.c_int32),
-                ("tile_signals", C.c_int32), ("threads", C.c_int32), ("wide", C.c_int32)]
+                ("tile_signals", C.c_int32), ("threads", C.c_int32), ("wide", C.c_int32),
+                ("right_pairs", C.c_int32)]
 
 
 P = C.c_void_p
@@ -31,6 +32,8 @@ SIGNATURES = {
     "gft_last_error": (C.c_char_p, []),
     "gft_version": (C.c_int32, []),
     "gft_laplacian_from_weights": (c_status, [C.c_int32, P, P, P]),
+    "gft_normalized_laplacian_from_weights": (c_status, [C.c_int32, P, P, P]),
+    "gft_plan_create_bipartite": (c_status, [C.c_int32, P, P, C.c_uint32, C.POINTER(c_plan)]),
     "gft_plan_create": (c_status, [C.c_int32, P, C.c_int32, P, C.c_uint32, C.POINTER(c_plan)]),
     "gft_plan_create_many": (c_status, [C.c_int32, P, P, P, P, C.c_uint32, P]),
     "gft_find_involution": (c_status, [C.c_int32, P, P, C.c_int64, P, I32P]),

@@ -100,6 +100,7 @@ const char* gft_status_string(gft_status s) {
         case GFT_ERR_MISALIGNED: return "GFT_ERR_MISALIGNED";
         case GFT_ERR_BLOCK_LEAK: return "GFT_ERR_BLOCK_LEAK";
         case GFT_ERR_NO_DEVICE: return "GFT_ERR_NO_DEVICE";
+        case GFT_ERR_NOT_BIPARTITE: return "GFT_ERR_NOT_BIPARTITE";
     }
     return "GFT_ERR_UNKNOWN";
 }
@@ -129,6 +130,22 @@ gft_status gft_laplacian_from_weights(int32_t n, const double* W, const double* 
                 }
             L[(size_t)i * n + i] = d;
         }
+    });
+}
+
+gft_status gft_normalized_laplacian_from_weights(int32_t n, const double* W, const double* s, double* L) {
+    return guard([&] {
+        const gft_status st = gft_laplacian_from_weights(n, W, s, L);
+        if (st != GFT_OK) fail(st, last_error_cstr());
+        // D^-1/2 L D^-1/2 with d_i = l_ii (the degree, self-loop included)
+        std::vector<double> r(n);
+        for (int i = 0; i < n; ++i) {
+            const double d = L[(size_t)i * n + i];
+            if (!(d > 0.0)) fail(GFT_ERR_NOT_LAPLACIAN, "node " + std::to_string(i) + " has no positive degree");
+            r[i] = 1.0 / std::sqrt(d);
+        }
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) L[(size_t)i * n + j] = (L[(size_t)i * n + j] * r[i]) * r[j];
     });
 }
 
@@ -221,6 +238,39 @@ gft_status gft_plan_create_many(int32_t count, const int32_t* n, const double* c
     });
 }
 
+gft_status gft_plan_create_bipartite(int32_t n, const double* L, const int32_t* side, uint32_t flags,
+                                     gft_plan_t* out) {
+    return guard([&] {
+        if (!out) fail(GFT_ERR_INVALID_ARG, "out is NULL");
+        check_create_args(n, L, 0, nullptr, flags);
+        if (flags & GFT_SPLIT_COMPONENTS) fail(GFT_ERR_INVALID_ARG, "GFT_SPLIT_COMPONENTS does not apply to bipartite plans");
+        std::unique_ptr<gft_plan_s> p(new gft_plan_s);
+        p->n = n;
+        p->flags = flags;
+        Leaf J;
+        analyze_bipartite(*p, L, side, J);
+        if (!(flags & GFT_ANALYZE_ONLY)) {
+            GFT_CUDA(cudaGetDevice(&p->device));
+            cudaStream_t st = nullptr;
+            GFT_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+            try {
+                jacobi_leaf_ptrs({&J}, st);
+            } catch (...) {
+                cudaStreamDestroy(st);
+                throw;
+            }
+            GFT_CUDA(cudaStreamDestroy(st));
+            finish_bipartite(*p, J);
+            finalize_host(*p);
+            upload_plan(*p);
+            jit_build(*p);
+            wide_build(*p);
+            GFT_CUDA(cudaDeviceSynchronize());
+        }
+        *out = p.release();
+    });
+}
+
 gft_status gft_find_involution(int32_t n, const double* L, const int32_t* classes, int64_t max_steps, int32_t* phi,
                                int32_t* pairs) {
     return guard([&] {
@@ -268,7 +318,8 @@ gft_status gft_plan_get_info(gft_plan_t p, gft_plan_info_t* info) {
             r.fast_adds += m * (m - 1);
             r.jacobi_sweeps = std::max(r.jacobi_sweeps, lf.sweeps);
         }
-        r.fast_adds += 2 * (int64_t)r.n_pairs;
+        r.right_pairs = (int32_t)p->rpairs.size();
+        r.fast_adds += 2 * (int64_t)(r.n_pairs + r.right_pairs);
         r.has_device = p->has_device ? 1 : 0;
         r.flags = p->flags;
         jit_info(*p, &r.jit, &r.tile_signals, &r.threads);
@@ -313,6 +364,7 @@ gft_status gft_plan_get_leaf_laplacian(gft_plan_t p, int32_t leaf, double* Lk) {
         check_plan(p);
         if (!Lk) fail(GFT_ERR_INVALID_ARG, "NULL output");
         if (leaf < 0 || leaf >= (int32_t)p->leaves.size()) fail(GFT_ERR_INVALID_ARG, "leaf out of range");
+        if (p->right) fail(GFT_ERR_UNSUPPORTED, "the sub-transforms of a bipartite plan have no leaf Laplacian");
         const auto& v = p->leaves[leaf].L;
         std::memcpy(Lk, v.data(), v.size() * sizeof(double));
     });

@@ -166,6 +166,7 @@ void launch_apply(const ApplyArgs& A, const T* x, T* y, int64_t batch, bool inve
     k.n = A.n;
     k.np = A.n | 1;
     k.n_pairs = A.n_pairs;
+    k.n_pre_pairs = A.n_pre_pairs;
     k.n_leaves = A.n_leaves;
     k.ints_count = A.ints_count;
     k.off_labels = 2 * A.n_pairs + A.n_stages + 1;

@@ -32,6 +32,7 @@ struct KArgs {
     void* y;
     long long batch;
     int n, np, n_pairs, n_leaves, ints_count;
+    int n_pre_pairs;    // pairs before the leaves; the rest are right Haar units on leaf outputs
     int off_labels, off_outpos, off_src, off_desc;
     int mats_smem;      // scalars of one direction's matrices (smem copy)
     int ts;             // signals per tile
@@ -195,42 +196,42 @@ __device__ __forceinline__ void leaf_dispatch(int bk, T* tile, int np, const int
     }
 }
 
-// One tile in place: stages and leaf products for the RS signals of every
-// thread (forward), or leaf products then stages in reverse (inverse).
+// Haar units p0, p0 + step, ... (count of them) on the RS rows of this thread.
+template <class T, int RS, int THREADS>
+__device__ __forceinline__ void haar_units(T* tile, int np, const int* pairs, int p0, int count, int step) {
+    const int tid = threadIdx.x;
+    for (int q = 0; q < count; ++q) {
+        const int p = p0 + q * step;
+        const int i = pairs[2 * p], j = pairs[2 * p + 1];
+#pragma unroll
+        for (int s = 0; s < RS; ++s) {
+            T* row = tile + (tid + s * THREADS) * np;
+            const T u = row[i], v = row[j];
+            row[i] = u + v;
+            row[j] = u - v;
+        }
+    }
+}
+
+// One tile in place for the RS signals of every thread.  Forward: left
+// stages, leaf products, right Haar units (bipartite plans).  Inverse: the
+// right units, leaf products, left stages in reverse (every unit is its own
+// inverse once the 1/sqrt2 factors are folded into the leaf matrices).
 template <class T, int RS, int THREADS>
 __device__ __forceinline__ void compute_tile(const KArgs& a, const int* ints, const T* mats, T* tile) {
-    const int np = a.np, tid = threadIdx.x;
+    const int np = a.np;
     const int* pairs = ints;
     const int* labels = ints + a.off_labels;
     const int* desc = ints + a.off_desc;
-    if (!a.inverse) {
-        for (int p = 0; p < a.n_pairs; ++p) {
-            const int i = pairs[2 * p], j = pairs[2 * p + 1];
-#pragma unroll
-            for (int s = 0; s < RS; ++s) {
-                T* row = tile + (tid + s * THREADS) * np;
-                const T u = row[i], v = row[j];
-                row[i] = u + v;
-                row[j] = u - v;
-            }
-        }
-    }
+    const int pre = a.n_pre_pairs, post = a.n_pairs - a.n_pre_pairs;
+    if (!a.inverse) haar_units<T, RS, THREADS>(tile, np, pairs, 0, pre, 1);
+    else haar_units<T, RS, THREADS>(tile, np, pairs, a.n_pairs - 1, post, -1);
     for (int k = 0; k < a.n_leaves; ++k) {
         const int* d = desc + kLeafDesc * k;
         leaf_dispatch<T, RS, THREADS>(d[1], tile, np, labels + d[2], mats + d[4], d[0]);
     }
-    if (a.inverse) {
-        for (int p = a.n_pairs - 1; p >= 0; --p) {
-            const int i = pairs[2 * p], j = pairs[2 * p + 1];
-#pragma unroll
-            for (int s = 0; s < RS; ++s) {
-                T* row = tile + (tid + s * THREADS) * np;
-                const T u = row[i], v = row[j];
-                row[i] = u + v;
-                row[j] = u - v;
-            }
-        }
-    }
+    if (!a.inverse) haar_units<T, RS, THREADS>(tile, np, pairs, pre, post, 1);
+    else haar_units<T, RS, THREADS>(tile, np, pairs, pre - 1, pre, -1);
 }
 
 

@@ -43,7 +43,7 @@ struct BatchPlanDev {
     float* y;
     long long batch;
     long long item0;      // first item index of this plan
-    int n, np, n_pairs, n_leaves, ints_count;
+    int n, np, n_pairs, n_leaves, ints_count, n_pre_pairs;
     int off_labels, off_outpos, off_src, off_desc;
     int mats_smem, rs, ts;
     float inv_n;
@@ -91,6 +91,7 @@ __global__ void __launch_bounds__(kBatchThreads) gft_batch_kernel(const BatchPla
         a.n = D.n;
         a.np = D.np;
         a.n_pairs = D.n_pairs;
+        a.n_pre_pairs = D.n_pre_pairs;
         a.n_leaves = D.n_leaves;
         a.ints_count = D.ints_count;
         a.off_labels = D.off_labels;
@@ -192,6 +193,7 @@ BatchPlanDev make_desc(const gft_plan_s& p, int rs, int64_t batch) {
     d.n = p.n;
     d.np = p.n | 1;
     d.n_pairs = p.dev.n_pairs;
+    d.n_pre_pairs = p.dev.n_pre_pairs;
     d.n_leaves = p.dev.n_leaves;
     d.ints_count = p.dev.ints_count;
     d.off_labels = 2 * p.dev.n_pairs + p.dev.n_stages + 1;

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
 #include <string>
 #include <utility>
 #include <vector>
@@ -35,12 +36,20 @@ struct Leaf {
     std::vector<int> labels;   // original labels in leaf order
     std::vector<double> L;     // m*m leaf Laplacian, row-major
     std::vector<int> exps;     // per node: Haar stages its lineage took part in
+    std::vector<int> cexps;    // per column: output-side (right) Haar units it feeds (empty = none)
     std::string tag;           // "+"/"-" path (plus ".c" for a component)
     // after eigendecomposition
     std::vector<double> lam;   // ascending
     std::vector<double> V;     // m*m row-major: V[r*m + c] = entry r of eigenvector c
     int sweeps = 0;
     int m() const { return (int)labels.size(); }
+    // Folded matrix entry M[r][c] = 2^(-e_r/2) V[r][c] 2^(-f_c/2): the
+    // 1/sqrt2 of every Haar unit the row's input went through (left stages)
+    // or the column's output goes through (right stage).
+    double fold(int r, int c) const {
+        const int e = exps[r] + (cexps.empty() ? 0 : cexps[c]);
+        return std::pow(2.0, -0.5 * e) * V[(size_t)r * m() + c];
+    }
 };
 
 // Bucketed leaf width used by the CUDA-core kernels (registers are sized at
@@ -50,6 +59,9 @@ constexpr int kMaxCoreLeaf = 64;
 
 // Everything a CUDA-core transform kernel needs, in one device allocation.
 //   ints:  [pairs 2P][stage_off S+1][labels n][out_pos n][src n][leaf desc 5L]
+//   pairs of the first n_pre_stages stages act on the input (before the
+//   leaf products), the rest on the leaf outputs (right Haar units, slot
+//   pairs): P = n_pre_pairs + right pairs, S = n_pre_stages + (0 or 1)
 //   src[j] = tile slot (node label) that holds coefficient j after the
 //          in-place leaf products
 //   leaf desc = {m, bucket, off (into labels/out_pos), off_u (into mats),
@@ -59,6 +71,7 @@ constexpr int kMaxCoreLeaf = 64;
 //          inverse matrix M_i = M_f^T (same padding)
 struct DevProgram {
     int n = 0, n_stages = 0, n_leaves = 0, n_pairs = 0;
+    int n_pre_stages = 0, n_pre_pairs = 0;
     int max_bucket = 0;
     int ints_count = 0;      // int32 entries
     int mats_count = 0;      // scalars per precision (both directions)
@@ -78,6 +91,12 @@ struct gft_plan_s {
     std::vector<double> L;                                  // n*n
     std::vector<std::vector<std::pair<int, int>>> stages;   // (X label, partner)
     std::vector<gft::Leaf> leaves;
+    // right Haar stage (bipartite plans, Sec. III-A): leaves[0] = E on the
+    // larger part, leaves[1] = F on the smaller; column c < p of E and of F
+    // form one unit, its sum in E's slot, its difference in F's slot
+    bool right = false;
+    double alpha = 0.0;                                     // L[S,S] = alpha I on both parts
+    std::vector<std::pair<int, int>> rpairs;                // (slot of E column c, slot of F column c)
     bool has_device = false;
     std::vector<int> out_pos;      // n, leaf-concatenated order -> coefficient
     std::vector<double> lam_out;   // n, coefficient order
@@ -104,6 +123,10 @@ namespace gft {
 
 // plan.cpp
 void analyze(gft_plan_s& p, const double* L, int n_stages, const int32_t* phi);
+// bipartite plan with a right Haar stage: validation, parts, and the
+// coupling-block matrix whose eigendecomposition gives E and F
+void analyze_bipartite(gft_plan_s& p, const double* L, const int32_t* side, Leaf& coupling);
+void finish_bipartite(gft_plan_s& p, const Leaf& coupling);   // E, F, sigma from the solved coupling leaf
 void finalize_host(gft_plan_s& p);           // ordering, signs
 void upload_plan(gft_plan_s& p);             // device program
 void compute_basis(const gft_plan_s& p, double* U);
@@ -118,6 +141,7 @@ struct ApplyArgs {
     const int* ints;
     const void* mats;       // float* or double*
     int n, n_stages, n_leaves, n_pairs, max_bucket;
+    int n_pre_pairs;        // pairs applied before the leaf products
     int ints_count, mats_count, mats_smem;
     int* err;
 };

@@ -306,7 +306,7 @@ std::string gen_bodies(const gft_plan_s& p, bool f64, int mode) {
     }
     auto Mval = [&](int k, int r, int c) {
         const Leaf& lf = p.leaves[k];
-        return std::pow(2.0, -0.5 * lf.exps[r]) * lf.V[(size_t)r * lf.m() + c];
+        return lf.fold(r, c);
     };
     auto load_row = [&](std::ostringstream& o, const char* v) {
         if (mode == kVec4 && !f64) {
@@ -341,7 +341,24 @@ std::string gen_bodies(const gft_plan_s& p, bool f64, int mode) {
         }
         if (first) s << "        " << dst << " = 0;\n";
     };
-    if (mode == kVec4 && !f64) {
+    if (p.right) {
+        // right Haar units: column c of E and of F, then their sum and
+        // difference (the 1/sqrt2 is folded into both columns)
+        const int m1 = p.leaves[0].m(), pr = (int)p.rpairs.size();
+        for (int c = 0; c < pr; ++c) {
+            const int jE = p.out_pos[c], jF = p.out_pos[m1 + c];
+            o << "    { " << T << " a, b;\n";
+            emit_coeff(o, jE, "a");
+            emit_coeff(o, jF, "b");
+            o << "      row[" << jE << "] = a + b; row[" << jF << "] = a - b; }\n";
+        }
+        for (int c = pr; c < m1; ++c) {
+            const int j = p.out_pos[c];
+            o << "    { " << T << " o;\n";
+            emit_coeff(o, j, "o");
+            o << "      row[" << j << "] = o; }\n";
+        }
+    } else if (mode == kVec4 && !f64) {
         for (int q = 0; q < n / 4; ++q) {
             o << "    { float o0, o1, o2, o3;\n";
             for (int t = 0; t < 4; ++t) emit_coeff(o, 4 * q + t, "o" + std::to_string(t));
@@ -361,6 +378,14 @@ std::string gen_bodies(const gft_plan_s& p, bool f64, int mode) {
     o << "    " << T << " ";
     for (int i = 0; i < n; ++i) o << "w" << i << (i + 1 < n ? ", " : ";\n");
     load_row(o, "v");
+    if (p.right) {   // right Haar units first (each is its own inverse once folded)
+        const int m1 = p.leaves[0].m();
+        for (int c = 0; c < (int)p.rpairs.size(); ++c) {
+            const int jE = p.out_pos[c], jF = p.out_pos[m1 + c];
+            o << "    { const " << T << " a = v" << jE << ", b = v" << jF << "; v" << jE << " = a + b; v" << jF
+              << " = a - b; }\n";
+        }
+    }
     {
         int i0 = 0;
         for (size_t k = 0; k < p.leaves.size(); ++k) {

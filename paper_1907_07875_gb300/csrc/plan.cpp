@@ -206,6 +206,15 @@ static void full_column(const gft_plan_s& p, int k, int c, std::vector<double>& 
     const Leaf& lf = p.leaves[k];
     const int m = lf.m();
     v.assign(p.n, 0.0);
+    if (p.right && c < (int)p.rpairs.size()) {
+        // right Haar unit c: (e_c; f_c)/sqrt2 in E's slot, (e_c; -f_c)/sqrt2 in F's (Eq. 9)
+        const Leaf& E = p.leaves[0];
+        const Leaf& F = p.leaves[1];
+        const double sf = k == 0 ? kRsqrt2 : -kRsqrt2;
+        for (int r = 0; r < E.m(); ++r) v[E.labels[r]] = kRsqrt2 * E.V[(size_t)r * E.m() + c];
+        for (int r = 0; r < F.m(); ++r) v[F.labels[r]] = sf * F.V[(size_t)r * F.m() + c];
+        return;
+    }
     for (int r = 0; r < m; ++r) v[lf.labels[r]] = lf.V[(size_t)r * m + c];
     for (int s = p.n_stages - 1; s >= 0; --s)
         for (auto& pr : p.stages[s]) {
@@ -284,19 +293,27 @@ void finalize_host(gft_plan_s& p) {
         for (int q = 0; q < N; ++q) p.out_pos[order[q]] = q;
     }
     // ---- signs: first maximal-magnitude entry of each full vector positive ----
+    // (right Haar units: the rule fixes the sum vector, i.e. E's column and
+    // F's column together; the difference vector follows)
     std::vector<double> v;
     for (size_t k = 0; k < p.leaves.size(); ++k) {
         Leaf& lf = p.leaves[k];
         const int m = lf.m();
         for (int c = 0; c < m; ++c) {
+            if (p.right && k == 1) break;
             full_column(p, (int)k, c, v);
             double mx = 0.0;
             for (double x : v) mx = std::max(mx, std::fabs(x));
             const double thr = (1.0 - kSignTol) * mx;
             int first = 0;
             while (first < n && std::fabs(v[first]) < thr) ++first;
-            if (first < n && v[first] < 0)
+            if (first < n && v[first] < 0) {
                 for (int r = 0; r < m; ++r) lf.V[(size_t)r * m + c] = -lf.V[(size_t)r * m + c];
+                if (p.right && c < (int)p.rpairs.size()) {
+                    Leaf& F = p.leaves[1];
+                    for (int r = 0; r < F.m(); ++r) F.V[(size_t)r * F.m() + c] = -F.V[(size_t)r * F.m() + c];
+                }
+            }
         }
     }
     p.lam_out.assign(n, 0.0);
@@ -307,19 +324,26 @@ void upload_plan(gft_plan_s& p) {
     const int n = p.n;
     DevProgram& d = p.dev;
     d.n = n;
-    d.n_stages = p.n_stages;
     d.n_leaves = (int)p.leaves.size();
+    d.n_pre_stages = p.n_stages;
+    d.n_pre_pairs = 0;
+    for (auto& st : p.stages) d.n_pre_pairs += (int)st.size();
+    // device stages: the left stages, then (bipartite plans) the right
+    // Haar units as one more stage over the leaf output slots
+    std::vector<std::vector<std::pair<int, int>>> dst(p.stages);
+    if (p.right) dst.push_back(p.rpairs);
+    d.n_stages = (int)dst.size();
     d.n_pairs = 0;
-    for (auto& st : p.stages) d.n_pairs += (int)st.size();
+    for (auto& st : dst) d.n_pairs += (int)st.size();
     std::vector<int> ints;
-    for (auto& st : p.stages)
+    for (auto& st : dst)
         for (auto& pr : st) {
             ints.push_back(pr.first);
             ints.push_back(pr.second);
         }
     int acc = 0;
     ints.push_back(0);
-    for (auto& st : p.stages) {
+    for (auto& st : dst) {
         acc += (int)st.size();
         ints.push_back(acc);
     }
@@ -354,9 +378,8 @@ void upload_plan(gft_plan_s& p) {
         d.max_bucket = std::max(d.max_bucket, bk);
         std::vector<double> Mf((size_t)bk * bk, 0.0), Mi((size_t)bk * bk, 0.0);
         for (int r = 0; r < m; ++r) {
-            const double sc = std::pow(2.0, -0.5 * lf.exps[r]);
             for (int c = 0; c < m; ++c) {
-                const double val = sc * lf.V[(size_t)r * m + c];
+                const double val = lf.fold(r, c);
                 Mf[(size_t)r * bk + c] = val;
                 Mi[(size_t)c * bk + r] = val;
             }
@@ -390,6 +413,7 @@ ApplyArgs apply_args(const gft_plan_s& p, bool f64) {
     a.n_stages = p.dev.n_stages;
     a.n_leaves = p.dev.n_leaves;
     a.n_pairs = p.dev.n_pairs;
+    a.n_pre_pairs = p.dev.n_pre_pairs;
     a.max_bucket = p.dev.max_bucket;
     a.ints_count = p.dev.ints_count;
     a.mats_count = p.dev.mats_count;

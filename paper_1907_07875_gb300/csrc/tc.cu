@@ -712,6 +712,7 @@ float bf16_val(uint16_t b) {
 }  // namespace
 
 bool tc_eligible(const gft_plan_s& p) {
+    if (p.right) return false;   // right Haar units: CUDA-core kernels only
     for (auto& lf : p.leaves)
         if (lf.m() > kTcMaxN) return false;
     return p.n >= 2;
@@ -782,7 +783,7 @@ void tc_build(gft_plan_s& p) {
                     for (int kk = 0; kk < kTcK; ++kk) {
                         const int r = kc * kTcK + kk;
                         double val = 0.0;
-                        if (r < m && c < m) val = std::pow(2.0, -0.5 * lf.exps[r]) * lf.V[(size_t)r * m + c];
+                        if (r < m && c < m) val = lf.fold(r, c);
                         const size_t o = (size_t)t.b_off + (size_t)kc * t.npad * kTcK +
                                          (size_t)(((c >> 3) * 8 + (kk >> 3)) * 64 + (c & 7) * 8 + (kk & 7));
                         const float f = (float)val;
@@ -974,6 +975,7 @@ void launch_tc(gft_plan_s& p, const float* x, float* y, int64_t batch, bool inve
                uint32_t precision, TcScratch* scratch) {
     if (inverse) fail(GFT_ERR_UNSUPPORTED, "tensor-core precisions are implemented for the forward transform");
     if (!p.tc && tc_eligible(p)) tc_build(p);   // built on first use
+    if (!p.tc && p.right) fail(GFT_ERR_UNSUPPORTED, "tensor-core precisions do not run bipartite plans (right Haar units)");
     if (!p.tc) fail(GFT_ERR_UNSUPPORTED, "tensor-core path needs every leaf to have at most 256 nodes");
     if (x == y) fail(GFT_ERR_UNSUPPORTED, "tensor-core path does not run in place");
     TcPlan* T = static_cast<TcPlan*>(p.tc);

@@ -60,6 +60,7 @@ struct WArgs {
     const void* mats;      // per leaf: M_f (m x P) then M_i (m x P), zero padded columns
     long long batch;
     int n, tsp, ts, nbuf, n_pairs, n_stages, n_leaves;
+    int n_pre_stages;      // stages before the leaf products; the rest act on leaf outputs (right Haar units)
     int off_labels, off_src;
     int chunk_elems;       // elements of one matrix chunk buffer
     int inverse;
@@ -307,9 +308,10 @@ __device__ __forceinline__ void wide_load_tables(const WArgs& a, int* s_ints) {
     for (int i = threadIdx.x; i < kWDesc * a.n_leaves; i += kWThreads) s_desc[i] = a.wdesc[i];
 }
 
-// Stages and leaf products of one tile already in shared memory (forward:
-// stages then leaves; inverse: leaves then stages in reverse).  Ends with a
-// barrier, so the tile is ready for the store.
+// Stages and leaf products of one tile already in shared memory.  Forward:
+// left stages, leaves, right Haar units (bipartite plans); inverse: right
+// units, leaves, left stages in reverse.  Ends with a barrier, so the tile
+// is ready for the store.
 template <class T>
 __device__ __forceinline__ void wide_compute(const WArgs& a, T* buf, T* mbuf, const int* s_ints) {
     const int* s_pairs = s_ints;
@@ -317,11 +319,11 @@ __device__ __forceinline__ void wide_compute(const WArgs& a, T* buf, T* mbuf, co
     const int* s_lab = s_soff + a.n_stages + 1;
     const int* s_desc = s_lab + 2 * a.n;
     const T* mats = reinterpret_cast<const T*>(a.mats);
-    if (!a.inverse) {
-        for (int s = 0; s < a.n_stages; ++s) {
-            wide_stage(buf, a.tsp, a.ts, s_pairs, s_soff[s], s_soff[s + 1] - s_soff[s]);
-            __syncthreads();
-        }
+    const int pre = a.n_pre_stages;
+    const int s0 = a.inverse ? a.n_stages - 1 : 0, s1 = a.inverse ? pre - 1 : pre, ds = a.inverse ? -1 : 1;
+    for (int s = s0; s != s1; s += ds) {   // left stages (forward) / right units (inverse)
+        wide_stage(buf, a.tsp, a.ts, s_pairs, s_soff[s], s_soff[s + 1] - s_soff[s]);
+        __syncthreads();
     }
     for (int k = 0; k < a.n_leaves; ++k) {
         const int* d = s_desc + kWDesc * k;
@@ -329,11 +331,10 @@ __device__ __forceinline__ void wide_compute(const WArgs& a, T* buf, T* mbuf, co
         wide_leaf_dispatch<T>(d[5], buf, a.tsp, a.ts, s_lab + d[2], M, d[0], d[1], d[6], d[7], mbuf, a.chunk_elems);
     }
     __syncthreads();   // every leaf's outputs written
-    if (a.inverse) {
-        for (int s = a.n_stages - 1; s >= 0; --s) {
-            wide_stage(buf, a.tsp, a.ts, s_pairs, s_soff[s], s_soff[s + 1] - s_soff[s]);
-            __syncthreads();
-        }
+    const int t0 = a.inverse ? pre - 1 : pre, t1 = a.inverse ? -1 : a.n_stages;
+    for (int s = t0; s != t1; s += ds) {   // right units (forward) / left stages in reverse (inverse)
+        wide_stage(buf, a.tsp, a.ts, s_pairs, s_soff[s], s_soff[s + 1] - s_soff[s]);
+        __syncthreads();
     }
 }
 
@@ -533,9 +534,8 @@ void wide_build(gft_plan_s& p) {
             f_off.push_back((int)mats.size());
             std::vector<double> Mf((size_t)m * P, 0.0), Mi((size_t)m * P, 0.0);
             for (int r = 0; r < m; ++r) {
-                const double sc = std::pow(2.0, -0.5 * lf.exps[r]);
                 for (int c = 0; c < m; ++c) {
-                    const double v = sc * lf.V[(size_t)r * m + c];
+                    const double v = lf.fold(r, c);
                     Mf[(size_t)r * P + c] = v;   // forward: y_c = sum_r v_r Mf[r][c]
                     Mi[(size_t)c * P + r] = v;   // inverse: x_r = sum_c y_c Mi[c][r]
                 }
@@ -699,6 +699,7 @@ static void launch_wide_t(gft_plan_s& p, const T* x, T* y, int64_t batch, bool i
     a.nbuf = c.nbuf;
     a.n_pairs = p.dev.n_pairs;
     a.n_stages = p.dev.n_stages;
+    a.n_pre_stages = p.dev.n_pre_stages;
     a.n_leaves = p.dev.n_leaves;
     a.off_labels = 2 * p.dev.n_pairs + p.dev.n_stages + 1;
     a.off_src = a.off_labels + 2 * p.n;
@@ -758,6 +759,7 @@ void* wide_batch_create(const std::vector<gft_plan_s*>& plans, const std::vector
         a.nbuf = 1;
         a.n_pairs = p.dev.n_pairs;
         a.n_stages = p.dev.n_stages;
+        a.n_pre_stages = p.dev.n_pre_stages;
         a.n_leaves = p.dev.n_leaves;
         a.off_labels = 2 * p.dev.n_pairs + p.dev.n_stages + 1;
         a.off_src = a.off_labels + 2 * p.n;

@@ -143,3 +143,60 @@ def test_create_many_analysis_matches_single_and_is_all_or_nothing(gft):
     with pytest.raises(gft.GftError) as e:
         gft.plans_from_laplacians([p6, p6], [[bad[0]], [bad[1]]], analyze_only=True)
     assert e.value.status == "GFT_ERR_NOT_INVOLUTION"
+
+
+def test_normalized_laplacian_matches_oracle(gft):
+    for g in (W.random_bipartite(7, 4, 0.4, seed=2103), W.krbg(8, 3, seed=2101), W.skeleton25()):
+        N = gft.normalized_laplacian(g.W, g.s)
+        assert np.allclose(N, ograph.normalized_laplacian(g.W, g.s), rtol=0, atol=1e-15)
+    Wm = np.zeros((3, 3))
+    Wm[0, 1] = Wm[1, 0] = 1.0                                      # node 2 isolated
+    with pytest.raises(gft.GftError) as e:
+        gft.normalized_laplacian(Wm)
+    assert e.value.status == "GFT_ERR_NOT_LAPLACIAN"
+
+
+@pytest.mark.parametrize("case", range(len(W.right_haar_graphs())))
+def test_bipartite_plan_structure(gft, case):
+    """Parts (two-colouring or given), E / F leaf node lists, the number of
+    right Haar units and the operation counts equal the oracle's."""
+    from oracle import right_haar as orh
+    g, normalised = W.right_haar_graphs()[case]
+    L = ograph.normalized_laplacian(g.W, g.s) if normalised else ograph.laplacian(g.W, g.s)
+    ref = orh.right_haar_gft(L, g.meta.get("side"))
+    for side in (g.meta.get("side"), None):
+        plan = gft.Plan.bipartite(L, side, analyze_only=True)
+        inf = plan.info
+        if side is None and g.meta.get("side") is not None:
+            # two-colouring may name the parts the other way round; the
+            # larger part is E's either way (ties: colour 0 of the colouring)
+            auto = ograph.bipartition(L, 1e-12 * max(1.0, np.abs(L).max()))
+            assert orh.right_structure(L, auto)[1] == plan.leaves()[0]
+            continue
+        assert plan.leaves() == [ref.big, ref.small]
+        assert inf["right_pairs"] == ref.p and inf["n_stages"] == 0 and inf["n_pairs"] == 0
+        assert (inf["fast_adds"], inf["fast_mults"]) == orh.op_counts(ref)
+        with pytest.raises(gft.GftError) as e:
+            plan.leaf_laplacian(0)
+        assert e.value.status == "GFT_ERR_UNSUPPORTED"
+
+
+def test_bipartite_plan_errors(gft):
+    def status(L, side=None, **kw):
+        with pytest.raises(gft.GftError) as e:
+            gft.Plan.bipartite(L, side, analyze_only=True, **kw)
+        return e.value.status
+    assert status(ograph.laplacian(W.cycle(7).W, W.cycle(7).s)) == "GFT_ERR_NOT_BIPARTITE"     # odd cycle
+    assert status(ograph.laplacian(W.path(6).W, W.path(6).s)) == "GFT_ERR_NOT_BIPARTITE"       # degrees 1 and 2
+    g = W.krbg(4, 2, seed=1, shuffle=False)
+    L = ograph.laplacian(g.W, g.s)
+    bad = g.meta["side"].copy()
+    bad[0], bad[4] = bad[4], bad[0]
+    assert status(L, bad) == "GFT_ERR_NOT_BIPARTITE"                                          # edge inside a part
+    assert status(L, np.full(8, 2)) == "GFT_ERR_INVALID_ARG"
+    assert status(L + np.triu(np.ones((8, 8)) * 1e-3, 1)) == "GFT_ERR_NOT_LAPLACIAN"
+    import ctypes as C
+    lib = gft.lib()
+    h = C.c_void_p()
+    assert lib.gft_plan_create_bipartite(8, L.ctypes.data, None, 0x1, C.byref(h)) == 1          # SPLIT flag
+    assert lib.gft_plan_create_bipartite(8, None, None, 0, C.byref(h)) == 1
