@@ -264,6 +264,8 @@ def extras(torch, gft, dev):
     del xs, ys, plans
     # ---- the paper's runtime table (Sec. VI-A): fast vs matrix GFT on the same graphs
     out["paper_runtime_table"] = runtime_table_extras(torch, gft, dev)
+    # ---- right Haar stage (Sec. III-A): bipartite plans vs the matrix GFT
+    out["right_haar_bipartite"] = right_haar_extras(torch, gft, dev)
     # ---- config 4: learned Givens surrogates on the nine nearly symmetric graphs
     out["config4_learned"] = learned_extras(torch, gft, dev)
     torch.backends.cuda.matmul.allow_tf32 = prev
@@ -293,6 +295,40 @@ def runtime_table_extras(torch, gft, dev):
                         "dense_gcoeffs_s": round(nb * g.n / t_d / 1e9, 2),
                         "reduction": round(1.0 - t_f / t_d, 3)}
         res[g.name] = row
+    return res
+
+
+def right_haar_extras(torch, gft, dev):
+    """Bipartite plans with a right Haar stage (Sec. III-A): k-regular
+    bipartite graphs (combinatorial Laplacian) and random bipartite graphs
+    (normalised Laplacian), 2^26 coefficients each; the fast FP32 transform
+    (kernel as chosen by the plan) against the matrix GFT (torch.matmul
+    FP32) on the same basis, and the error against the FP64 basis."""
+    res = {}
+    cases = [(W.krbg(32, 5, seed=2105), False), (W.random_bipartite(40, 24, 0.15, seed=2301), True),
+             (W.krbg(64, 6, seed=2302), False), (W.krbg(256, 8, seed=2201), False),
+             (W.random_bipartite(300, 212, 0.05, seed=2202), True)]
+    for g, normalised in cases:
+        L = gft.normalized_laplacian(g.W, g.s) if normalised else gft.laplacian(g.W, g.s)
+        plan = gft.Plan.bipartite(L, g.meta["side"])
+        inf = plan.info
+        U = torch.from_numpy(plan.basis()).to(dev)
+        nb = (1 << 26) // g.n
+        x = torch.from_numpy(W.signals(nb, g.n, 9)).to(dev)
+        y = torch.empty_like(x)
+        t_f = _timed(torch, lambda: plan.forward(x, out=y))
+        t_i = _timed(torch, lambda: plan.inverse(x, out=y))
+        Uf = U.float()
+        t_d = _timed(torch, lambda: torch.matmul(x, Uf, out=y))
+        ref = x[:2048].double() @ U
+        res[g.name] = {"n": g.n, "parts": [len(v) for v in plan.leaves()], "right_pairs": inf["right_pairs"],
+                       "laplacian": "normalised" if normalised else "combinatorial",
+                       "fp32_kernel": "plan-specialised" if inf["jit"] else ("wide-leaf" if inf["wide"] else "table-driven"),
+                       "fast_mults": inf["fast_mults"], "dense_mults": g.n * g.n,
+                       "fast_gcoeffs_s": round(nb * g.n / t_f / 1e9, 1),
+                       "inverse_gcoeffs_s": round(nb * g.n / t_i / 1e9, 1),
+                       "dense_gcoeffs_s": round(nb * g.n / t_d / 1e9, 1),
+                       "err_vs_fp64": float(f"{_rel(plan.forward(x[:2048].contiguous()).double(), ref):.2e}")}
     return res
 
 

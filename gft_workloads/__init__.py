@@ -369,7 +369,7 @@ def right_haar_graphs():
         (cycle(12), False), (krbg(8, 3, seed=2101), False), (krbg(20, 4, seed=2102, weighted=False), False),
         (hypercube(4), False), (random_bipartite(7, 4, 0.4, seed=2103), True),
         (random_bipartite(30, 18, 0.15, seed=2104), True), (krbg(32, 5, seed=2105), False),
-        (random_bipartite(40, 40, 0.1, seed=2106), True),
+        (random_bipartite(40, 40, 0.1, seed=2106), True), (krbg(64, 6, seed=2302), False),
     ]
 
 

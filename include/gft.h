@@ -124,11 +124,11 @@ gft_status gft_normalized_laplacian_from_weights(int32_t n, const double* W, con
  * Unless GFT_ANALYZE_ONLY is set, the leaf Laplacians are eigendecomposed on
  * the current CUDA device by a batched FP64 Jacobi kernel and the bases are
  * uploaded; the call synchronises the device.  For graphs of at most 128
- * nodes (sum of squared leaf sizes <= 4096) and without GFT_NO_JIT, the
- * call also generates a kernel specialised to this plan (indices and
- * folded leaf matrices as constants), compiles it with NVRTC for sm_103a,
- * and times several launch shapes on a scratch batch to keep the fastest;
- * transforms then use it.  The tensor-core data (pre-split leaf bases) is
+ * nodes (sum of squared leaf sizes <= 8192; <= 4096 for the FP64 kernel)
+ * and without GFT_NO_JIT, the call also generates a kernel specialised to
+ * this plan (indices and folded leaf matrices as constants), compiles it
+ * with NVRTC for sm_103a, and times several launch shapes on a scratch
+ * batch to keep the fastest; transforms then use it.  The tensor-core data (pre-split leaf bases) is
  * built on the first tensor-core transform; make that first call outside
  * any stream capture.  Otherwise, when some leaf has more than 32 nodes
  * (up to 512), a wide-leaf kernel computes each tile's leaf products as a

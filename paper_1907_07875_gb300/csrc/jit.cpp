@@ -42,9 +42,18 @@ constexpr int kSmemLimitJ = 232448;
 // Plans that get straight-line kernels: a signal's n values live in
 // registers (n <= 128 keeps them there under a 255-register cap), and the
 // leaf matrices become sum(m^2) FMA immediates per direction (bounds the
-// code size and the NVRTC compile time).
+// code size and the NVRTC compile time: about 10 s at 8192).  FP64 values
+// take two registers and FP64 FMAs are slow on this part, so the FP64
+// module is built only for the smaller plans.
 constexpr int kJitMaxN = 128;
-constexpr long long kJitMaxLeafEntries = 4096;
+constexpr long long kJitMaxLeafEntries = 8192;
+constexpr long long kJitMaxLeafEntries64 = 4096;
+
+long long leaf_entries(const gft_plan_s& p) {
+    long long fl = 0;
+    for (auto& lf : p.leaves) fl += (long long)lf.m() * lf.m();
+    return fl;
+}
 
 struct Cand {
     int rs, threads, nbuf, bulk;
@@ -521,9 +530,7 @@ bool jit_eligible(const gft_plan_s& p) {
     if (std::getenv("GFT_DISABLE_JIT")) return false;
     if (p.flags & GFT_NO_JIT) return false;
     if (p.n > kJitMaxN) return false;
-    long long fl = 0;
-    for (auto& lf : p.leaves) fl += (long long)lf.m() * lf.m();
-    return fl <= kJitMaxLeafEntries;
+    return leaf_entries(p) <= kJitMaxLeafEntries;
 }
 
 std::string jit_source(const gft_plan_s& p, bool f64) {
@@ -621,7 +628,7 @@ void jit_build(gft_plan_s& p) {
     JitPlan* J = new JitPlan;
     try {
         build_precision(p, *J, false);
-        build_precision(p, *J, true);
+        if (leaf_entries(p) <= kJitMaxLeafEntries64) build_precision(p, *J, true);
     } catch (...) {
         if (J->lib32) cudaLibraryUnload(J->lib32);
         if (J->lib64) cudaLibraryUnload(J->lib64);

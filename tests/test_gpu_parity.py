@@ -75,6 +75,7 @@ FAMILIES = [
     (W.star(7), False), (W.complete(6), False), (W.near_symmetric_path(32, 0.05, seed=1), False),
     (W.grid6_bidiag(4), False), (W.grid6_bidiag(8), False), (W.zgrid(4), False), (W.zgrid(8), False),
     (W.cycle(80), False), (W.cycle(128), False), (W.grid(10), False), (W.bipartite(72, 0.2, seed=5), False),
+    (W.path(100), False), (W.bipartite(128, 0.1, seed=3), False),
 ]
 
 
