@@ -40,6 +40,7 @@ extern "C" {
 typedef struct gft_plan_s* gft_plan_t;
 typedef struct gft_batch_s* gft_batch_t;
 typedef struct gft_givens_s* gft_givens_t;
+typedef struct gft_approx_s* gft_approx_t;
 typedef void* gft_stream_t;
 
 typedef enum {
@@ -351,6 +352,62 @@ gft_status gft_batch_forward(gft_batch_t batch, const float* const* x, float* co
  * the wide-leaf or tensor-core kernels). */
 gft_status gft_batch_get_tile(gft_batch_t batch, int32_t i, int32_t* tile, int32_t* threads);
 gft_status gft_batch_destroy(gft_batch_t batch);
+
+/*
+ * Approximate GFT by layers of Givens rotations (the comparison method of
+ * Sec. VI-B: greedy parallel Jacobi layers), alone (n_stages = 0) or after
+ * the Haar stages of the symmetric decomposition ("Haar + approximate GFT":
+ * the approximation replaces the dense sub-GFTs of the leaves).
+ * Build (host, FP64): the stages and leaf Laplacians as gft_plan_create;
+ * per leaf, n_layers layers, each pairing nodes greedily by the magnitude of
+ * the current off-diagonal entries (largest first, ties by (p, q); entries
+ * <= 1e-14*max(1,max|L_k|) count as zero, and a leaf with none left stops)
+ * and applying the rotations J(p,q,theta) that zero them, all at once
+ * (A <- J^T A J, the symmetric 2x2 Schur rotation); layer t of every leaf
+ * runs side by side.  Output order: ascending diagonal of the final A (the
+ * approximate eigenvalues), clusters by (leaf, index).  Transform: the units
+ * in layer order -- Haar units (x_p, x_q) <- ((x_p + x_q), (x_p - x_q))/sqrt2,
+ * rotations (x_p, x_q) <- (c x_p - s x_q, s x_p + c x_q) -- then the
+ * permutation; coefficients approximate U^T x.
+ *  n, L, n_stages, phi  as gft_plan_create (n <= 1024).
+ *  n_layers  Givens layers per leaf, 0..4096.
+ *  flags     GFT_SPLIT_COMPONENTS | GFT_ANALYZE_ONLY (no device data).
+ * Errors: INVALID_ARG, NOT_LAPLACIAN, NOT_INVOLUTION, BLOCK_LEAK,
+ * NOT_SYMMETRIC, UNSUPPORTED, CUDA, OOM.
+ */
+gft_status gft_approx_create(int32_t n, const double* L, int32_t n_stages, const int32_t* phi, int32_t n_layers,
+                             uint32_t flags, gft_approx_t* out);
+gft_status gft_approx_destroy(gft_approx_t a);
+
+typedef struct {
+    int32_t n;
+    int32_t n_haar_layers;  /* leading layers of Haar units (the stages) */
+    int32_t n_layers;       /* all layers: Haar, then Givens (a leaf may stop early) */
+    int32_t n_units;        /* Haar units + rotations */
+    int32_t has_device;
+    int32_t tile_signals;   /* signals per CTA tile of the transform kernel */
+    int64_t mults;          /* per signal: 4 per rotation, 2 per Haar unit */
+    int64_t adds;           /* per signal: 2 per unit */
+} gft_approx_info_t;
+
+gft_status gft_approx_get_info(gft_approx_t a, gft_approx_info_t* info);
+
+/* The transform: layer_off[n_layers + 1] (units of layer l are
+ * [layer_off[l], layer_off[l+1])), pairs[2 * n_units] (p, q),
+ * coef[4 * n_units] (m00, m01, m10, m11: (x_p, x_q) <- (m00 x_p + m01 x_q,
+ * m10 x_p + m11 x_q), FP64 as built), perm[n] (coefficient j is node
+ * perm[j] after the last layer).  Host outputs sized from get_info. */
+gft_status gft_approx_get_units(gft_approx_t a, int32_t* layer_off, int32_t* pairs, double* coef, int32_t* perm);
+
+/* Approximate eigenvalues (host, n doubles) in coefficient order. */
+gft_status gft_approx_eigenvalues(gft_approx_t a, double* lambda);
+
+/* U_hat (host n*n row-major, FP64): column j = basis vector of coefficient j. */
+gft_status gft_approx_basis(gft_approx_t a, double* U);
+
+/* y[b, :] = U_hat^T x[b, :]: x, y device [batch, n] FP32, 16-byte aligned,
+ * x != y.  FP32 arithmetic (units rounded from FP64).  Asynchronous. */
+gft_status gft_approx_forward(gft_approx_t a, const float* x, float* y, int64_t batch, gft_stream_t stream);
 
 /*
  * Layered Givens rotations (Eq. 1 and Fig. 1) used as a learned surrogate of

@@ -302,6 +302,74 @@ def plans_from_laplacians(Ls, phis_list, *, split_components: bool = False, orde
     return [Plan._wrap(C.c_void_p(out[i]), int(ns[i])) for i in range(k)]
 
 
+class ApproxGFT:
+    """Approximate GFT by greedy layers of Jacobi rotations, alone (phis =
+    []) or after the Haar stages of the symmetric decomposition (Sec. VI-B,
+    gft_approx_create)."""
+
+    def __init__(self, L, phis: Optional[Sequence] = None, n_layers: int = 10, *,
+                 split_components: bool = False, analyze_only: bool = False):
+        L = _as_f64(L)
+        n = L.shape[0]
+        if L.shape != (n, n):
+            raise ValueError("L must be square")
+        phis = [] if phis is None else list(phis)
+        ph = (np.ascontiguousarray(np.stack([np.asarray(p, dtype=np.int32) for p in phis]))
+              if phis else None)
+        flags = (SPLIT_COMPONENTS if split_components else 0) | (ANALYZE_ONLY if analyze_only else 0)
+        h = C.c_void_p()
+        self._h = None
+        _check(lib().gft_approx_create(n, _ptr(L), len(phis), _ptr(ph), int(n_layers), flags, C.byref(h)))
+        self._h = h
+        self.n = n
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().gft_approx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def info(self) -> dict:
+        inf = _native.ApproxInfo()
+        _check(lib().gft_approx_get_info(self._h, C.byref(inf)))
+        return {k: getattr(inf, k) for k, _ in inf._fields_}
+
+    def units(self):
+        """(layer_off, pairs [units, 2], coef [units, 4], perm)."""
+        inf = self.info
+        lo = np.zeros(inf["n_layers"] + 1, dtype=np.int32)
+        pr = np.zeros((max(1, inf["n_units"]), 2), dtype=np.int32)
+        cf = np.zeros((max(1, inf["n_units"]), 4))
+        pm = np.zeros(self.n, dtype=np.int32)
+        _check(lib().gft_approx_get_units(self._h, _ptr(lo), _ptr(pr), _ptr(cf), _ptr(pm)))
+        return lo, pr[:inf["n_units"]], cf[:inf["n_units"]], pm
+
+    def eigenvalues(self) -> np.ndarray:
+        lam = np.zeros(self.n)
+        _check(lib().gft_approx_eigenvalues(self._h, _ptr(lam)))
+        return lam
+
+    def basis(self) -> np.ndarray:
+        U = np.zeros((self.n, self.n))
+        _check(lib().gft_approx_basis(self._h, _ptr(U)))
+        return U
+
+    def forward(self, x, out=None, stream=None):
+        import torch
+        if x.dtype != torch.float32 or not x.is_cuda or x.dim() != 2 or x.shape[1] != self.n:
+            raise ValueError("x must be a CUDA float32 tensor [batch, n]")
+        x = x.contiguous()
+        y = torch.empty_like(x) if out is None else out
+        _check(lib().gft_approx_forward(self._h, _ptr(x), _ptr(y), x.shape[0], _stream_ptr(stream)))
+        return y
+
+
 class Batch:
     """Many plans transformed by one graph-captured launch (gft_batch_create):
     persistent kernels over (plan, tile) work lists, plus the tensor-core
@@ -419,6 +487,6 @@ def givens_apply(x, theta, net: Givens):
     return _GF.apply(x, theta, net)
 
 
-__all__ = ["Plan", "Batch", "Givens", "givens_apply", "laplacian", "normalized_laplacian", "GftError", "lib",
+__all__ = ["Plan", "Batch", "ApproxGFT", "Givens", "givens_apply", "laplacian", "normalized_laplacian", "GftError", "lib",
            "SPLIT_COMPONENTS", "ORDER_BLOCK", "ANALYZE_ONLY", "NO_JIT", "KERNEL_TABLE",
            "KERNEL_WIDE", "PRECISIONS", "plans_from_laplacians", "find_involution", "search_stages"]

@@ -21,6 +21,12 @@ class PlanInfo(C.Structure):
                 ("right_pairs", C.c_int32)]
 
 
+class ApproxInfo(C.Structure):
+    _fields_ = [("n", C.c_int32), ("n_haar_layers", C.c_int32), ("n_layers", C.c_int32),
+                ("n_units", C.c_int32), ("has_device", C.c_int32), ("tile_signals", C.c_int32),
+                ("mults", C.c_int64), ("adds", C.c_int64)]
+
+
 P = C.c_void_p
 I32P = C.POINTER(C.c_int32)
 I64P = C.POINTER(C.c_int64)
@@ -57,6 +63,13 @@ SIGNATURES = {
     "gft_batch_forward": (c_status, [C.c_void_p, P, P, P]),
     "gft_batch_get_tile": (c_status, [C.c_void_p, C.c_int32, I32P, I32P]),
     "gft_batch_destroy": (c_status, [C.c_void_p]),
+    "gft_approx_create": (c_status, [C.c_int32, P, C.c_int32, P, C.c_int32, C.c_uint32, C.POINTER(C.c_void_p)]),
+    "gft_approx_destroy": (c_status, [C.c_void_p]),
+    "gft_approx_get_info": (c_status, [C.c_void_p, C.POINTER(ApproxInfo)]),
+    "gft_approx_get_units": (c_status, [C.c_void_p, P, P, P, P]),
+    "gft_approx_eigenvalues": (c_status, [C.c_void_p, P]),
+    "gft_approx_basis": (c_status, [C.c_void_p, P]),
+    "gft_approx_forward": (c_status, [C.c_void_p, P, P, C.c_int64, P]),
     "gft_givens_create": (c_status, [C.c_int32, C.c_int32, P, C.POINTER(C.c_void_p)]),
     "gft_givens_destroy": (c_status, [C.c_void_p]),
     "gft_givens_forward": (c_status, [C.c_void_p, P, P, P, C.c_int64, P]),

@@ -43,7 +43,10 @@ def _stale(src: str, obj: str, deps) -> bool:
 
 
 def _compile(src: str, obj: str, extra) -> None:
-    cmd = [nvcc(), *ARCH, *COMMON, *extra, "-c", src, "-o", obj]
+    # host C++: no FMA contraction, so host FP64 results (plan build, the
+    # approximate GFT's greedy rotations) are the same on x86 and Arm
+    host = ["-Xcompiler", "-ffp-contract=off"] if src.endswith(".cpp") else []
+    cmd = [nvcc(), *ARCH, *COMMON, *host, *extra, "-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed for {os.path.basename(src)}:\n{r.stdout}\n{r.stderr}")

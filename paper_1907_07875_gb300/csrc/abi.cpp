@@ -579,3 +579,100 @@ gft_status gft_device_error(gft_plan_t p, int32_t* code) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// approximate GFT (approx.cpp, approx.cu)
+// ---------------------------------------------------------------------------
+extern "C" {
+
+gft_status gft_approx_create(int32_t n, const double* L, int32_t n_stages, const int32_t* phi, int32_t n_layers,
+                             uint32_t flags, gft_approx_t* out) {
+    return guard([&] {
+        if (!out) fail(GFT_ERR_INVALID_ARG, "out is NULL");
+        if (n < 1 || n > 1024) fail(GFT_ERR_INVALID_ARG, "n must be in [1, 1024]");
+        if (!L) fail(GFT_ERR_INVALID_ARG, "L is NULL");
+        if (n_stages < 0 || n_stages > 16) fail(GFT_ERR_INVALID_ARG, "n_stages must be in [0, 16]");
+        if (n_stages > 0 && !phi) fail(GFT_ERR_INVALID_ARG, "phi is NULL");
+        if (n_layers < 0 || n_layers > 4096) fail(GFT_ERR_INVALID_ARG, "n_layers must be in [0, 4096]");
+        if (flags & ~(GFT_SPLIT_COMPONENTS | GFT_ANALYZE_ONLY)) fail(GFT_ERR_INVALID_ARG, "unknown flag");
+        std::unique_ptr<gft_approx_s> a(new gft_approx_s);
+        a->n = n;
+        approx_build(*a, L, n_stages, phi, n_layers, flags);
+        if (!(flags & GFT_ANALYZE_ONLY)) approx_upload(*a);
+        *out = a.release();
+    });
+}
+
+gft_status gft_approx_destroy(gft_approx_t a) {
+    return guard([&] { delete a; });
+}
+
+gft_status gft_approx_get_info(gft_approx_t a, gft_approx_info_t* info) {
+    return guard([&] {
+        if (!a || !info) fail(GFT_ERR_INVALID_ARG, "NULL argument");
+        gft_approx_info_t r{};
+        r.n = a->n;
+        r.n_haar_layers = a->n_haar_layers;
+        r.n_layers = (int32_t)a->layer_off.size() - 1;
+        r.n_units = (int32_t)(a->pairs.size() / 2);
+        r.has_device = a->has_device ? 1 : 0;
+        r.tile_signals = a->ts;
+        const int64_t haar = a->layer_off[a->n_haar_layers];
+        r.mults = 2 * haar + 4 * (int64_t)(r.n_units - haar);
+        r.adds = 2 * (int64_t)r.n_units;
+        *info = r;
+    });
+}
+
+gft_status gft_approx_get_units(gft_approx_t a, int32_t* layer_off, int32_t* pairs, double* coef, int32_t* perm) {
+    return guard([&] {
+        if (!a || !layer_off || !pairs || !coef || !perm) fail(GFT_ERR_INVALID_ARG, "NULL argument");
+        std::copy(a->layer_off.begin(), a->layer_off.end(), layer_off);
+        std::copy(a->pairs.begin(), a->pairs.end(), pairs);
+        std::copy(a->coef.begin(), a->coef.end(), coef);
+        std::copy(a->perm.begin(), a->perm.end(), perm);
+    });
+}
+
+gft_status gft_approx_eigenvalues(gft_approx_t a, double* lambda) {
+    return guard([&] {
+        if (!a || !lambda) fail(GFT_ERR_INVALID_ARG, "NULL argument");
+        std::copy(a->lam.begin(), a->lam.end(), lambda);
+    });
+}
+
+gft_status gft_approx_basis(gft_approx_t a, double* U) {
+    return guard([&] {
+        if (!a || !U) fail(GFT_ERR_INVALID_ARG, "NULL argument");
+        const int n = a->n;
+        // row i of the transform of e_i is row i of U_hat (node order), then the permutation
+        std::vector<double> W((size_t)n * n, 0.0);
+        for (int i = 0; i < n; ++i) W[(size_t)i * n + i] = 1.0;
+        const size_t units = a->pairs.size() / 2;
+        for (size_t u = 0; u < units; ++u) {
+            const int p = a->pairs[2 * u], q = a->pairs[2 * u + 1];
+            const double* m = &a->coef[4 * u];
+            for (int i = 0; i < n; ++i) {
+                const double xp = W[(size_t)i * n + p], xq = W[(size_t)i * n + q];
+                W[(size_t)i * n + p] = m[0] * xp + m[1] * xq;
+                W[(size_t)i * n + q] = m[2] * xp + m[3] * xq;
+            }
+        }
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) U[(size_t)i * n + j] = W[(size_t)i * n + a->perm[j]];
+    });
+}
+
+gft_status gft_approx_forward(gft_approx_t a, const float* x, float* y, int64_t batch, gft_stream_t stream) {
+    return guard([&] {
+        if (!a) fail(GFT_ERR_INVALID_ARG, "NULL argument");
+        if (!a->has_device) fail(GFT_ERR_NO_DEVICE, "approximate GFT was created with GFT_ANALYZE_ONLY");
+        check_io(x, y, batch);
+        if (batch > 0 && x == y) fail(GFT_ERR_INVALID_ARG, "x and y must differ");
+        cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+        a->last_stream = st;
+        launch_approx(*a, x, y, batch, st);
+    });
+}
+
+}  // extern "C"

@@ -119,10 +119,42 @@ struct gft_plan_s {
     ~gft_plan_s();
 };
 
+// Approximate GFT (Sec. VI-B): Haar stages, then greedy layers of Jacobi
+// rotations per leaf, then the output permutation (approx.cpp / approx.cu).
+struct gft_approx_s {
+    int n = 0, n_stages = 0, n_haar_layers = 0;
+    std::vector<int> layer_off;     // layers + 1: units of layer l are [layer_off[l], layer_off[l+1])
+    std::vector<int> pairs;         // 2 per unit (p, q)
+    std::vector<double> coef;       // 4 per unit: (x_p, x_q) <- (m00 x_p + m01 x_q, m10 x_p + m11 x_q)
+    std::vector<int> perm;          // coefficient j is read from node perm[j]
+    std::vector<double> lam;        // approximate eigenvalues, output order
+    bool has_device = false;
+    int device = 0;
+    int ts = 0, tsp = 0;            // signals per tile, node-row stride of the shared tile
+    size_t smem = 0;
+    int* d_pairs = nullptr;
+    float* d_coef = nullptr;
+    int* d_layer_off = nullptr;
+    int* d_perm = nullptr;
+    cudaStream_t last_stream = nullptr;
+    ~gft_approx_s();
+};
+
 namespace gft {
+
+// approx.cpp / approx.cu
+void approx_build(gft_approx_s& a, const double* L, int n_stages, const int32_t* phi, int n_layers, uint32_t flags);
+void approx_upload(gft_approx_s& a);
+void approx_free(gft_approx_s& a);
+void launch_approx(const gft_approx_s& a, const float* x, float* y, int64_t batch, cudaStream_t st);
 
 // plan.cpp
 void analyze(gft_plan_s& p, const double* L, int n_stages, const int32_t* phi);
+// output index of every entry (eigenvalue, leaf, index in leaf): ascending
+// eigenvalue; values within 1e-9 max(1, |lam|max) of a neighbour form a
+// cluster ordered by (leaf, index)
+std::vector<int> output_positions(const std::vector<double>& lam, const std::vector<int>& leaf,
+                                  const std::vector<int>& local);
 // bipartite plan with a right Haar stage: validation, parts, and the
 // coupling-block matrix whose eigendecomposition gives E and F
 void analyze_bipartite(gft_plan_s& p, const double* L, const int32_t* side, Leaf& coupling);

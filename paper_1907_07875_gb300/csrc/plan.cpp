@@ -53,6 +53,32 @@ std::vector<std::vector<int>> components(const std::vector<double>& A, int m, do
 
 }  // namespace
 
+std::vector<int> output_positions(const std::vector<double>& lam, const std::vector<int>& leaf,
+                                  const std::vector<int>& local) {
+    const int N = (int)lam.size();
+    double lmax = 0.0;
+    for (double v : lam) lmax = std::max(lmax, std::fabs(v));
+    const double tol = kClusterTol * std::max(1.0, lmax);
+    std::vector<int> idx(N);
+    std::iota(idx.begin(), idx.end(), 0);
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return lam[a] < lam[b]; });
+    std::vector<int> order;
+    int start = 0;
+    for (int j = 1; j <= N; ++j) {
+        if (j == N || lam[idx[j]] - lam[idx[j - 1]] > tol) {
+            std::vector<int> cl(idx.begin() + start, idx.begin() + j);
+            std::sort(cl.begin(), cl.end(), [&](int a, int b) {
+                return leaf[a] != leaf[b] ? leaf[a] < leaf[b] : local[a] < local[b];
+            });
+            order.insert(order.end(), cl.begin(), cl.end());
+            start = j;
+        }
+    }
+    std::vector<int> pos(N);
+    for (int q = 0; q < N; ++q) pos[order[q]] = q;
+    return pos;
+}
+
 int leaf_bucket(int m) {
     static const int b[] = {4, 8, 16, 24, 32, 48, 64};
     for (int v : b)
@@ -263,34 +289,20 @@ void free_device(gft_plan_s& p) {
 void finalize_host(gft_plan_s& p) {
     const int n = p.n;
     // ---- output order: ascending eigenvalue, clusters by (leaf, index) ----
-    struct Ent { double lam; int leaf, local; };
-    std::vector<Ent> ent;
+    std::vector<double> lam_e;
+    std::vector<int> leaf_e, local_e;
     for (size_t k = 0; k < p.leaves.size(); ++k)
-        for (int c = 0; c < p.leaves[k].m(); ++c) ent.push_back({p.leaves[k].lam[c], (int)k, c});
-    const int N = (int)ent.size();
-    p.out_pos.assign(N, 0);
+        for (int c = 0; c < p.leaves[k].m(); ++c) {
+            lam_e.push_back(p.leaves[k].lam[c]);
+            leaf_e.push_back((int)k);
+            local_e.push_back(c);
+        }
+    const int N = (int)lam_e.size();
     if (p.flags & GFT_ORDER_BLOCK) {
+        p.out_pos.assign(N, 0);
         std::iota(p.out_pos.begin(), p.out_pos.end(), 0);
     } else {
-        double lmax = 0.0;
-        for (auto& e : ent) lmax = std::max(lmax, std::fabs(e.lam));
-        const double tol = kClusterTol * std::max(1.0, lmax);
-        std::vector<int> idx(N);
-        std::iota(idx.begin(), idx.end(), 0);
-        std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return ent[a].lam < ent[b].lam; });
-        std::vector<int> order;
-        int start = 0;
-        for (int j = 1; j <= N; ++j) {
-            if (j == N || ent[idx[j]].lam - ent[idx[j - 1]].lam > tol) {
-                std::vector<int> cl(idx.begin() + start, idx.begin() + j);
-                std::sort(cl.begin(), cl.end(), [&](int a, int b) {
-                    return ent[a].leaf != ent[b].leaf ? ent[a].leaf < ent[b].leaf : ent[a].local < ent[b].local;
-                });
-                order.insert(order.end(), cl.begin(), cl.end());
-                start = j;
-            }
-        }
-        for (int q = 0; q < N; ++q) p.out_pos[order[q]] = q;
+        p.out_pos = output_positions(lam_e, leaf_e, local_e);
     }
     // ---- signs: first maximal-magnitude entry of each full vector positive ----
     // (right Haar units: the rule fixes the sum vector, i.e. E's column and
@@ -317,7 +329,7 @@ void finalize_host(gft_plan_s& p) {
         }
     }
     p.lam_out.assign(n, 0.0);
-    for (int q = 0; q < N; ++q) p.lam_out[p.out_pos[q]] = ent[q].lam;
+    for (int q = 0; q < N; ++q) p.lam_out[p.out_pos[q]] = lam_e[q];
 }
 
 void upload_plan(gft_plan_s& p) {

@@ -200,3 +200,130 @@ def test_bipartite_plan_errors(gft):
     h = C.c_void_p()
     assert lib.gft_plan_create_bipartite(8, L.ctypes.data, None, 0x1, C.byref(h)) == 1          # SPLIT flag
     assert lib.gft_plan_create_bipartite(8, None, None, 0, C.byref(h)) == 1
+
+
+def _leaf_runs(lib_layers, n_haar, leaves):
+    """Split the library's Givens layers into per-leaf layer lists (leaf
+    node sets from the oracle's decomposition)."""
+    owner = {}
+    for k, leaf in enumerate(leaves):
+        for lab in leaf.labels:
+            owner[lab] = k
+    runs = [[] for _ in leaves]
+    for layer in lib_layers[n_haar:]:
+        per = [[] for _ in leaves]
+        for p, q, m in layer:
+            assert owner[p] == owner[q]                 # a rotation never leaves its leaf
+            per[owner[p]].append((p, q, m))
+        for k in range(len(leaves)):
+            if per[k]:
+                runs[k].append(per[k])
+    return runs
+
+
+def _check_greedy_run(Lk, labels, layers, tol_rel=1e-9):
+    """Replays one leaf's layers on the oracle's leaf Laplacian: every layer
+    is disjoint, greedy (each pair has the largest |a_pq| among pairs of free
+    nodes, up to rounding), maximal, and its rotations zero the chosen
+    entries (with equal diagonal entries both angles +-pi/4 do); returns the
+    final matrix."""
+    from oracle import approx as oap
+    A = np.array(Lk, dtype=np.float64, copy=True)
+    m = A.shape[0]
+    scale = max(1.0, np.abs(A).max())
+    zero = oap.ZERO_TOL * scale
+    eps = tol_rel * scale
+    loc = {lab: i for i, lab in enumerate(labels)}
+    for layer in layers:
+        free = np.ones(m, dtype=bool)
+        rots = []
+        for gp, gq, (m00, m01, m10, m11) in layer:
+            p, q = sorted((loc[gp], loc[gq]))
+            assert free[p] and free[q]
+            up = np.abs(np.triu(A, 1))
+            best = max((up[r, t] for r in range(m) for t in range(r + 1, m) if free[r] and free[t]), default=0.0)
+            assert up[p, q] >= best - eps and up[p, q] > zero - eps
+            # a rotation (the entry it must zero is checked after the update),
+            # the smaller angle of the symmetric Schur step: |theta| <= pi/4
+            assert m01 == -m10 and m11 == m00 and abs(m00 * m00 + m10 * m10 - 1) <= 1e-15
+            assert m00 >= abs(m10) - 1e-15
+            free[p] = free[q] = False
+            rots.append((loc[gp], loc[gq], m00, m10))
+        up = np.abs(np.triu(A, 1))
+        assert all(up[r, t] <= zero + eps for r in range(m) for t in range(r + 1, m) if free[r] and free[t])
+        for p, q, c, s_ in rots:
+            ap, aq = A[:, p].copy(), A[:, q].copy()
+            A[:, p] = c * ap - s_ * aq
+            A[:, q] = s_ * ap + c * aq
+        for p, q, c, s_ in rots:
+            ap, aq = A[p, :].copy(), A[q, :].copy()
+            A[p, :] = c * ap - s_ * aq
+            A[q, :] = s_ * ap + c * aq
+        for p, q, _, _ in rots:
+            assert abs(A[p, q]) <= 1e-9 * scale
+            A[p, q] = A[q, p] = 0.0
+    return A
+
+
+APPROX_CASES = [(W.grid6_bidiag(8), 20), (W.zgrid(8), 20), (W.skeleton25(), 8),
+                (W.near_symmetric_path(16, 0.05, seed=1), 30), (W.grid6_bidiag(4), 0),
+                (W.grid(6, weights="sym_uniform", seed=9), 12)]
+
+
+@pytest.mark.parametrize("g,J", APPROX_CASES, ids=lambda v: getattr(v, "name", str(v)))
+@pytest.mark.parametrize("haar", [True, False])
+def test_approx_build_is_a_valid_greedy_run(gft, g, J, haar):
+    """The library's host build of the approximate GFT, replayed on the
+    oracle's leaf Laplacians: Haar units exactly Eq. 20's, every Givens
+    layer a valid greedy Jacobi layer, eigenvalues = the replayed diagonal,
+    output order ascending, U_hat = the units applied to the identity.
+    (Where magnitudes tie up to rounding the greedy choice can differ from
+    the oracle's own run; the test_approx_*_matches_oracle cases have none.)"""
+    from oracle import approx as oap
+    from oracle import gft as og
+    L = ograph.laplacian(g.W, g.s)
+    phis = g.phis if haar else []
+    a = gft.ApproxGFT(L, phis, J, analyze_only=True)
+    lo, pairs, coef, perm = a.units()
+    layers = [[(int(pairs[u, 0]), int(pairs[u, 1]), tuple(coef[u])) for u in range(lo[l], lo[l + 1])]
+              for l in range(len(lo) - 1)]
+    fact = og.decompose(L, phis)
+    n_haar = a.info["n_haar_layers"]
+    assert n_haar == len(fact.stages)
+    r = 1 / np.sqrt(2)
+    for st, layer in zip(fact.stages, layers[:n_haar]):
+        assert [(p, q) for p, q, _ in layer] == list(st)
+        assert all(m == (r, r, r, -r) for _, _, m in layer)
+    runs = _leaf_runs(layers, n_haar, fact.leaves)
+    diag = {}
+    for leaf, run in zip(fact.leaves, runs):
+        assert len(run) <= J
+        A = _check_greedy_run(leaf.L, leaf.labels, run)
+        for i, lab in enumerate(leaf.labels):
+            diag[lab] = A[i, i]
+    lam = a.eigenvalues()
+    assert np.max(np.abs(lam - np.array([diag[int(v)] for v in perm]))) <= 1e-9 * max(1.0, np.abs(L).max())
+    assert np.all(np.diff(lam) >= -1e-9 * max(1.0, np.abs(lam).max()))
+    assert sorted(perm.tolist()) == list(range(g.n))
+    assert np.max(np.abs(a.basis() - oap.apply_units(layers, np.eye(g.n))[:, perm])) <= 1e-13
+
+
+@pytest.mark.parametrize("g,J", [(W.near_symmetric_path(16, 0.05, seed=1), 30),
+                                 (W.grid(6, weights="sym_uniform", seed=9), 12), (W.grid6_bidiag(4), 0)],
+                         ids=lambda v: getattr(v, "name", str(v)))
+def test_approx_build_matches_oracle(gft, g, J):
+    """Without ties the library's run and the oracle's are the same: same
+    layers, pairs, permutation; coefficients, eigenvalues and U_hat to 1e-12."""
+    from oracle import approx as oap
+    L = ograph.laplacian(g.W, g.s)
+    ref = oap.haar_approx_gft(L, [], J)
+    a = gft.ApproxGFT(L, [], J, analyze_only=True)
+    lo, pairs, coef, perm = a.units()
+    assert lo.tolist() == np.cumsum([0] + [len(layer) for layer in ref.layers]).tolist()
+    ref_units = [u for layer in ref.layers for u in layer]
+    assert pairs.tolist() == [[p, q] for p, q, _ in ref_units]
+    if ref_units:
+        assert np.max(np.abs(coef - np.array([m for _, _, m in ref_units]))) <= 1e-12
+    assert perm.tolist() == ref.perm.tolist()
+    assert np.max(np.abs(a.eigenvalues() - ref.lam)) <= 1e-12 * max(1.0, np.abs(L).max())
+    assert np.max(np.abs(a.basis() - ref.U)) <= 1e-12
