@@ -266,6 +266,8 @@ def extras(torch, gft, dev):
     out["paper_runtime_table"] = runtime_table_extras(torch, gft, dev)
     # ---- right Haar stage (Sec. III-A): bipartite plans vs the matrix GFT
     out["right_haar_bipartite"] = right_haar_extras(torch, gft, dev)
+    # ---- Sec. VI-B: approximate GFTs (greedy Jacobi layers) with and without the Haar stages
+    out["approx_vs_exact"] = approx_extras(torch, gft, dev)
     # ---- config 4: learned Givens surrogates on the nine nearly symmetric graphs
     out["config4_learned"] = learned_extras(torch, gft, dev)
     torch.backends.cuda.matmul.allow_tf32 = prev
@@ -329,6 +331,52 @@ def right_haar_extras(torch, gft, dev):
                        "inverse_gcoeffs_s": round(nb * g.n / t_i / 1e9, 1),
                        "dense_gcoeffs_s": round(nb * g.n / t_d / 1e9, 1),
                        "err_vs_fp64": float(f"{_rel(plan.forward(x[:2048].contiguous()).double(), ref):.2e}")}
+    return res
+
+
+def approx_extras(torch, gft, dev):
+    """The comparison of Sec. VI-B on its two graphs (8x8 bi-diagonal grid,
+    a = 0.5; 8x8 z-shaped grid, w = 2): matrix GFT, Haar + matrix GFT (the
+    exact fast plan), approximate GFT and Haar + approximate GFT with J
+    Givens layers.  Per implementation: the sign-normalised error delta and
+    the empirical error epsilon against the exact GFT (2000 U[0,1] signals,
+    FP64 on the host from the FP64 bases), and G coeff/s on the paper's
+    20000 signals and on 2^26 coefficients."""
+    res = {}
+    for g in (W.grid6_bidiag(8), W.zgrid(8)):
+        n = g.n
+        L = gft.laplacian(g.W, g.s)
+        exact = gft.Plan(L, g.phis)
+        dense = gft.Plan(L, [], jit=False)
+        U = dense.basis()
+        Uf = torch.from_numpy(U).float().to(dev)
+        xe = W.signals(2000, n, 77, dist="uniform").astype(np.float64)
+        ye = np.abs(xe @ U)
+
+        def errs(Uh):
+            d = float(np.linalg.norm(np.abs(Uh.T @ U) - np.eye(n)) / np.sqrt(n))
+            e = float(np.mean(np.sum((ye - np.abs(xe @ Uh)) ** 2, axis=1)))
+            return round(d, 4), float(f"{e:.3e}")
+
+        def speeds(fn):
+            out = {}
+            for tag, nb in (("paper_20000", 20000), ("2^26", (1 << 26) // n)):
+                x = torch.from_numpy(W.signals(nb, n, 7, dist="uniform")).to(dev)
+                y = torch.empty_like(x)
+                out[tag] = round(nb * n / _timed(torch, lambda: fn(x, y)) / 1e9, 1)
+            return out
+        rows = {"matrix": {"delta": 0.0, "epsilon": 0.0,
+                           "gcoeffs_s": speeds(lambda x, y: torch.matmul(x, Uf, out=y))},
+                "haar_matrix": {"delta": errs(exact.basis())[0], "epsilon": errs(exact.basis())[1],
+                                "gcoeffs_s": speeds(lambda x, y: exact.forward(x, out=y))}}
+        for J in (0, 5, 10, 20, 30, 40):
+            for tag, phis in (("approx", []), ("haar_approx", g.phis)):
+                a = gft.ApproxGFT(L, phis, J)
+                d, e = errs(a.basis())
+                inf = a.info
+                rows[f"{tag}_J{J}"] = {"delta": d, "epsilon": e, "layers": inf["n_layers"], "units": inf["n_units"],
+                                       "gcoeffs_s": speeds(lambda x, y: a.forward(x, out=y))}
+        res[g.name] = rows
     return res
 
 
