@@ -46,6 +46,7 @@ constexpr int kSmemLimitJ = 232448;
 // take two registers and FP64 FMAs are slow on this part, so the FP64
 // module is built only for the smaller plans.
 constexpr int kJitMaxN = 128;
+constexpr int kTuneReps = 5;   // timed launches per candidate shape (after one warm-up)
 constexpr long long kJitMaxLeafEntries = 8192;
 constexpr long long kJitMaxLeafEntries64 = 4096;
 
@@ -569,7 +570,9 @@ static void build_precision(gft_plan_s& p, JitPlan& J, bool f64) {
     const size_t esz = f64 ? 8 : 4;
     // autotune: time every compiled launch shape on a batch larger than L2
     const int n = p.n;
-    const int64_t tb = std::max<int64_t>(4096, (int64_t)(96ll << 20) / (int64_t)(n * esz));
+    // 192 MB in + 192 MB out: about three times the 129 MB L2, so every shape
+    // is timed on HBM traffic, as the transforms of large batches run
+    const int64_t tb = std::max<int64_t>(4096, (int64_t)(192ll << 20) / (int64_t)(n * esz));
     void *dx = nullptr, *dy = nullptr;
     GFT_CUDA(cudaMalloc(&dx, tb * n * esz));
     GFT_CUDA(cudaMalloc(&dy, tb * n * esz));
@@ -596,12 +599,12 @@ static void build_precision(gft_plan_s& p, JitPlan& J, bool f64) {
                 d.bulk = c.bulk;
                 launch_dir(d, dx, dy, tb, p.dev.d_err, st);
                 GFT_CUDA(cudaEventRecord(e0, st));
-                for (int r = 0; r < 3; ++r) launch_dir(d, dx, dy, tb, p.dev.d_err, st);
+                for (int r = 0; r < kTuneReps; ++r) launch_dir(d, dx, dy, tb, p.dev.d_err, st);
                 GFT_CUDA(cudaEventRecord(e1, st));
                 GFT_CUDA(cudaEventSynchronize(e1));
                 float ms = 0.f;
                 GFT_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-                d.us = ms * 1000.f / 3.f;
+                d.us = ms * 1000.f / kTuneReps;
                 if (!best.k || d.us < best.us) best = d;
                 if (!f64 && !c.bulk && (!J.d32_plain[inv].k || d.us < J.d32_plain[inv].us)) J.d32_plain[inv] = d;
             }
