@@ -286,3 +286,25 @@ def test_searched_stages_parity(env, g):
     assert err <= FP32_TOL
     xb = plan.inverse(torch.from_numpy(y.astype(np.float32)).cuda()).cpu().numpy()
     assert rel_l2(xb, x) <= 2 * FP32_TOL
+
+
+@pytest.mark.parametrize("g,split", [(W.skeleton25(), True), (W.grid(8, weights="sym_uniform", seed=3), False),
+                                     (W.bipartite(64, 0.1, seed=2), False), (W.cycle(80), False),
+                                     (W.grid6_bidiag(8), False)],
+                         ids=lambda v: getattr(v, "name", str(v)))
+def test_normalised_laplacian_plans(env, g, split):
+    """GFTs of the normalised Laplacian D^-1/2 L D^-1/2 (Sec. II-B): the
+    symmetric decomposition holds for it too (degrees are phi-invariant), so
+    a plan built on it must match the oracle's fast GFT of the same matrix."""
+    gft, torch = env
+    Ln = gft.normalized_laplacian(g.W, g.s)
+    assert np.allclose(Ln, ograph.normalized_laplacian(g.W, g.s), rtol=0, atol=1e-15)
+    plan = gft.Plan(Ln, g.phis, split_components=split)
+    ref = ogft.fast_gft(ograph.normalized_laplacian(g.W, g.s), g.phis, split_components=split)
+    U = check_plan_against_oracle(plan, ref)
+    x = W.signals(1000, g.n, 55)
+    err, y = forward_error(gft, torch, plan, ref, U, x)
+    assert err <= FP32_TOL, err
+    xb = plan.inverse(torch.from_numpy(y.astype(np.float32)).cuda()).cpu().numpy()
+    assert rel_l2(xb, x) <= 2 * FP32_TOL
+    assert plan.device_error() == 0

@@ -327,3 +327,20 @@ def test_approx_build_matches_oracle(gft, g, J):
     assert perm.tolist() == ref.perm.tolist()
     assert np.max(np.abs(a.eigenvalues() - ref.lam)) <= 1e-12 * max(1.0, np.abs(L).max())
     assert np.max(np.abs(a.basis() - ref.U)) <= 1e-12
+
+
+@pytest.mark.parametrize("g,split", [(W.skeleton25(), True), (W.grid(6, weights="sym_uniform", seed=9), False),
+                                     (W.bipartite(32, 0.2, seed=5), False), (W.zgrid(8), False)],
+                         ids=lambda v: getattr(v, "name", str(v)))
+def test_normalised_laplacian_plan_structure(gft, g, split):
+    """The symmetric decomposition of the normalised Laplacian (Sec. II-B;
+    Thm. 3 holds for it as well): stage pairs and leaves bit-exact, leaf
+    matrices equal to the oracle's."""
+    N = ograph.normalized_laplacian(g.W, g.s)
+    plan = gft.Plan(N, g.phis, split_components=split, analyze_only=True)
+    ref = ogft.decompose(N, g.phis, split_components=split)
+    for s, pairs in enumerate(ref.stages):
+        assert plan.stage_pairs(s).tolist() == [list(p) for p in pairs]
+    assert plan.leaves() == [b.labels for b in ref.leaves]
+    for k, b in enumerate(ref.leaves):
+        assert np.allclose(plan.leaf_laplacian(k), b.L, rtol=0, atol=1e-13)
