@@ -294,7 +294,7 @@ def test_searched_stages_parity(env, g):
                          ids=lambda v: getattr(v, "name", str(v)))
 def test_normalised_laplacian_plans(env, g, split):
     """GFTs of the normalised Laplacian D^-1/2 L D^-1/2 (Sec. II-B): the
-    symmetric decomposition holds for it too (degrees are phi-invariant), so
+    block diagonalisation holds for it too (Sec. IV-B, Thm. 3), so
     a plan built on it must match the oracle's fast GFT of the same matrix."""
     gft, torch = env
     Ln = gft.normalized_laplacian(g.W, g.s)
