@@ -289,7 +289,7 @@ def test_searched_stages_parity(env, g):
 
 
 @pytest.mark.parametrize("g,split", [(W.skeleton25(), True), (W.grid(8, weights="sym_uniform", seed=3), False),
-                                     (W.bipartite(64, 0.1, seed=2), False), (W.cycle(80), False),
+                                     (W.bipartite(64, 0.2, seed=2), False), (W.cycle(80), False),
                                      (W.grid6_bidiag(8), False)],
                          ids=lambda v: getattr(v, "name", str(v)))
 def test_normalised_laplacian_plans(env, g, split):
