@@ -53,7 +53,7 @@ typedef enum {
     GFT_ERR_CUDA = 6,            /* a CUDA runtime call failed */
     GFT_ERR_OOM = 7,             /* device or host allocation failed */
     GFT_ERR_TIMEOUT = 8,         /* a bounded device-side wait gave up */
-    GFT_ERR_UNSUPPORTED = 9,     /* valid input this build does not handle (see message) */
+    GFT_ERR_UNSUPPORTED = 9,     /* valid input the library does not handle (see message) */
     GFT_ERR_MISALIGNED = 10,     /* device pointer not 16-byte aligned */
     GFT_ERR_BLOCK_LEAK = 11,     /* a stage involution maps a node out of its block */
     GFT_ERR_NO_DEVICE = 12,      /* plan was created with GFT_ANALYZE_ONLY */

@@ -7,7 +7,7 @@ angles can stand in for it at O(n log n) cost.  The angles are fitted on the
 GPU, through this library's forward and backward kernels, to the exact basis
 U that a plan computes (``Plan.basis()``): with the identity as input batch,
 the surrogate's outputs are G^T and the loss ||G^T - U||_F^2 equals
-||G - U^T||_F^2.  The exact plan stays the fallback and the judge: callers
+||G - U^T||_F^2.  The exact plan stays the fallback and the reference: callers
 compare the surrogate's error (``delta``) against their tolerance.
 """
 from __future__ import annotations

@@ -94,7 +94,7 @@ def test_training_gains_over_untrained_surrogate(env):
     plan = gft.Plan(gft.laplacian(g.W, g.s), [])      # exact dense GFT, GPU Jacobi
     U = plan.basis()
     lam_o, U_o = ogft.dense_gft(ograph.laplacian(g.W, g.s))
-    assert metrics.delta(U, U_o) < 1e-10               # the exact judge agrees with the oracle
+    assert metrics.delta(U, U_o) < 1e-10               # the exact reference agrees with the oracle
     model = LearnedGFT(16)
     d0 = metrics.delta(model.matrix(), U)
     hist = model.train(U, steps=1500, lr=0.05)
