@@ -344,3 +344,26 @@ def test_normalised_laplacian_plan_structure(gft, g, split):
     assert plan.leaves() == [b.labels for b in ref.leaves]
     for k, b in enumerate(ref.leaves):
         assert np.allclose(plan.leaf_laplacian(k), b.L, rtol=0, atol=1e-13)
+
+
+def test_approx_errors(gft):
+    import ctypes as C
+    lib = gft.lib()
+    g = W.grid6_bidiag(4)
+    L = ograph.laplacian(g.W, g.s)
+    h = C.c_void_p()
+    ptr = L.ctypes.data
+    assert lib.gft_approx_create(16, ptr, 0, None, -1, 0x4, C.byref(h)) == 1          # n_layers < 0
+    assert lib.gft_approx_create(16, ptr, 0, None, 4097, 0x4, C.byref(h)) == 1        # n_layers > 4096
+    assert lib.gft_approx_create(16, ptr, 0, None, 3, 0x8, C.byref(h)) == 1           # NO_JIT is not an approx flag
+    assert lib.gft_approx_create(2000, ptr, 0, None, 3, 0x4, C.byref(h)) == 1         # n > 1024
+    assert lib.gft_approx_create(16, None, 0, None, 3, 0x4, C.byref(h)) == 1
+    assert lib.gft_approx_create(16, ptr, 1, None, 3, 0x4, C.byref(h)) == 1           # stages without phi
+    with pytest.raises(gft.GftError) as e:
+        gft.ApproxGFT(L, [[1, 2, 0] + list(range(3, 16))], 3, analyze_only=True)    # not an involution
+    assert e.value.status == "GFT_ERR_NOT_INVOLUTION"
+    a = gft.ApproxGFT(L, g.phis, 3, analyze_only=True)
+    assert a.info["has_device"] == 0
+    x = np.zeros((4, 16), dtype=np.float32)
+    assert lib.gft_approx_forward(a._h, x.ctypes.data, x.ctypes.data, 4, None) == 12       # GFT_ERR_NO_DEVICE
+    assert lib.gft_approx_destroy(None) == 0
