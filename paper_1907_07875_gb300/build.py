@@ -45,7 +45,7 @@ def _stale(src: str, obj: str, deps) -> bool:
 def _compile(src: str, obj: str, extra) -> None:
     # host C++: no FMA contraction, so host FP64 results (plan build, the
     # approximate GFT's greedy rotations) are the same on x86 and Arm
-    host = ["-Xcompiler", "-ffp-contract=off"] if src.endswith(".cpp") else []
+    host = ["-Xcompiler", "-ffp-contract=off", "-Xcompiler", "-pthread"] if src.endswith(".cpp") else []
     cmd = [nvcc(), *ARCH, *COMMON, *host, *extra, "-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
@@ -77,7 +77,7 @@ def build(force: bool = False, extra_flags=None) -> str:
         tmp = LIB_PATH + ".tmp"
         cuda_lib = os.path.join(os.path.dirname(os.path.dirname(nvcc())), "lib64")
         cmd = [nvcc(), *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs, "-L", cuda_lib, "-lnvrtc",
-               "-Xlinker", "-rpath," + cuda_lib]
+               "-lpthread", "-Xlinker", "-rpath," + cuda_lib]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

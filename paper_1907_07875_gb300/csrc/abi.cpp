@@ -7,7 +7,10 @@
 #include <cstring>
 #include <memory>
 #include <new>
+#include <atomic>
+#include <exception>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "gft_internal.h"
@@ -172,13 +175,39 @@ void create_plans(int32_t count, const int32_t* ns, const double* const* Ls, con
                   const int32_t* const* phis, uint32_t flags, gft_plan_t* out) {
     for (int i = 0; i < count; ++i)
         check_create_args(ns[i], Ls[i], n_stages[i], phis ? phis[i] : nullptr, flags);
-    std::vector<std::unique_ptr<gft_plan_s>> made;
+    std::vector<std::unique_ptr<gft_plan_s>> made(count);
     for (int i = 0; i < count; ++i) {
-        std::unique_ptr<gft_plan_s> p(new gft_plan_s);
-        p->n = ns[i];
-        p->flags = flags;
-        analyze(*p, Ls[i], n_stages[i], phis ? phis[i] : nullptr);
-        made.push_back(std::move(p));
+        made[i].reset(new gft_plan_s);
+        made[i]->n = ns[i];
+        made[i]->flags = flags;
+    }
+    // host decomposition: independent per graph, spread over host threads
+    // (largest graphs first); the first failing graph in input order decides
+    // the error, as in a sequential run
+    {
+        std::vector<int> order(count);
+        for (int i = 0; i < count; ++i) order[i] = i;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return ns[a] > ns[b]; });
+        std::vector<std::exception_ptr> errs(count);
+        std::atomic<int> next{0};
+        auto work = [&] {
+            for (int q = next++; q < count; q = next++) {
+                const int i = order[q];
+                try {
+                    analyze(*made[i], Ls[i], n_stages[i], phis ? phis[i] : nullptr);
+                } catch (...) {
+                    errs[i] = std::current_exception();
+                }
+            }
+        };
+        const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+        const int nt = std::min({hw, 16, std::max(1, count / 8)});
+        std::vector<std::thread> pool;
+        for (int t = 1; t < nt; ++t) pool.emplace_back(work);
+        work();
+        for (auto& th : pool) th.join();
+        for (int i = 0; i < count; ++i)
+            if (errs[i]) std::rethrow_exception(errs[i]);
     }
     if (!(flags & GFT_ANALYZE_ONLY)) {
         int dev = 0;
