@@ -24,6 +24,13 @@ leaves side by side), outputs ordered by approximate eigenvalue with ties by
 The transform is kept as layers of 2x2 units (p, q, m) acting as
 (x_p, x_q) <- (m00 x_p + m01 x_q, m10 x_p + m11 x_q): a Haar unit is
 m = [[1, 1], [1, -1]] / sqrt2, a rotation J^T is m = [[c, -s], [s, c]].
+
+Pins (tests/test_oracle_approx.py): choose_pairs / truncated_jacobi -- the
+2x2 closed form, Jacobi's off-norm identity per layer, greedy order and
+maximality; haar_approx_gft -- convergence to the exact GFT, the Haar-only
+case against Eq. 20's stage matrices and Thm. 3's blocks, Rayleigh-quotient
+eigenvalues, the Sec. VI-B observation on both 8x8 grids; forward /
+apply_units -- equal to the dense product.
 """
 from __future__ import annotations
 

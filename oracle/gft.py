@@ -27,6 +27,16 @@ eigenvalue order, eigenvalues within 1e-9 * max(1, |lam|_max) of their
 neighbour form a cluster ordered by (leaf, index within leaf); the sign of
 each basis vector makes its first entry of maximal magnitude (within a
 relative 1e-9) positive.
+
+Pins (tests/test_oracle_gft.py): dense_gft -- DCT-II closed form for
+uniform paths, real-DFT eigenspaces for cycles, separable 2-D DCT for grids,
+the printed 4-cycle basis; decompose / fast_gft -- DCT-II and DCT-IV / DST-II
+sub-blocks, DST-VII components of the skeleton, fast = dense eigenspaces on
+every family, brute force over all involutions for n <= 8, rejections;
+output_order -- the cluster rule; canonical_sign -- agreement between the
+dense and the staged routes; forward_staged / inverse_staged -- equal to the
+dense product; op_counts -- the runtime table's printed counts where the
+text fixes them (the 25-joint skeleton's printed counts: parity unpinned).
 """
 from __future__ import annotations
 

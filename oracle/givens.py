@@ -7,6 +7,12 @@ transform; the learned surrogate is such a stack, y = G_S ... G_1 x, whose
 angles are fitted to an exact GFT basis.
 
 Signals are rows: Y = X (G_S ... G_1)^T.
+
+Pins (tests/test_oracle_givens.py): the Haar unit as a signed pi/4 rotation,
+rotation algebra (orthogonality, determinant 1, composition of angles, pi/2
+maps e_p to e_q), the layered forward against a rotation-by-rotation loop,
+central differences against the analytic derivative of a single rotation,
+the butterfly pairings as perfect matchings.
 """
 from __future__ import annotations
 

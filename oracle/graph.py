@@ -7,6 +7,15 @@ the permuted butterfly matrix B_phi (Eq. 20), block diagonalisation
 L_phi = B_phi^T L B_phi (Thm. 3).  Sec. IV-C: the weights and self-loops of
 G+ and G- in closed form (Thm. 4, proof in the Appendix), and the even/odd
 components of a signal (Eq. 21).
+
+Pins (tests/test_oracle_graph.py, tests/test_oracle_right_haar.py):
+laplacian -- the quadratic form sum w_ij (x_i - x_j)^2 + sum s_i x_i^2 and the
+Eq. 4 / 5 round trip; is_involution / partition / b_phi -- Definition 1,
+orthogonality, the Haar action; block_diagonalize / thm4_subgraphs -- Thm. 3's
+zero off-blocks and Thm. 4's weights against the congruence, the edge
+removal cases; even_odd -- Eq. 21; connected_components; normalized_laplacian
+-- a hand-computed case and the complete bipartite spectrum {0, 1, 2};
+bipartition -- a hand-checked two-colouring and an odd cycle.
 """
 from __future__ import annotations
 

@@ -6,6 +6,9 @@ textbook cyclic Jacobi method: sweep over all pairs p < q in row order; for
 each nonzero a_pq pick the rotation J(p, q, theta) that zeroes it (the
 symmetric 2x2 Schur decomposition), update A <- J^T A J and V <- V J; stop
 when off(A) <= tol * ||A||_F.
+
+Pins (tests/test_oracle_jacobi.py): LAPACK's eigvalsh on random matrices,
+the 2x2 closed form, degenerate spectra, the sweep limit.
 """
 from __future__ import annotations
 

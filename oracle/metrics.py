@@ -3,6 +3,11 @@
 RE (Eq. 23): ||U - U_hat||_F / ||U||_F.  delta: the sign-normalised version,
 ||(|U_hat^T U|) - I||_F / sqrt(n).  epsilon: mean over signals of the summed
 squared differences of coefficient magnitudes, |u_j^T x| - |u_hat_j^T x|.
+
+Pins (tests/test_oracle_givens.py::test_metrics_identities): Eq. 23's
+identity ||U - U_hat||_F / ||U||_F = ||U_hat^T U - I||_F / sqrt(n) for
+orthogonal matrices, RE(-U, U) = 2 while delta ignores column signs, epsilon
+vanishes for a sign-flipped basis.
 """
 from __future__ import annotations
 

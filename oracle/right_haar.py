@@ -30,6 +30,11 @@ the difference in F's column c.  Output order: ascending eigenvalue with
 clusters ordered by (E before F, column index); signs: the canonical sign
 rule of ``gft`` is applied to each sum vector (and to each unpaired
 vector), the difference vector of a pair follows it.
+
+Pins (tests/test_oracle_right_haar.py): closed-form spectra (even cycles,
+hypercubes, complete bipartite normalised), the mirrored spectrum against
+LAPACK's eigvalsh, Eq. 9's pair structure and E^T C F = diag(sigma), staged
+against dense transforms, op_counts, the structural rejections.
 """
 from __future__ import annotations
 
