@@ -69,6 +69,10 @@ typedef enum {
                                       it fits (leaves of at most 64 nodes) */
 #define GFT_KERNEL_WIDE      0x20u /* CUDA-core transforms: the wide-leaf kernel whenever the
                                       plan has a leaf of more than 32 nodes */
+#define GFT_SEARCH_STAGES    0x40u /* n_stages = 0: find the stages with gft_search_stages
+                                      (up to 16 stages, 10^6 search steps each) */
+#define GFT_NORMALIZED       0x80u /* transform with the normalised Laplacian D^-1/2 L D^-1/2
+                                      (d_i = l_ii > 0) of the given L (Sec. II-B) */
 
 /* transform precision (plan forward / inverse) */
 #define GFT_PREC_FP32    0u  /* CUDA-core FP32 FMA, FP32 accumulation */
@@ -119,7 +123,13 @@ gft_status gft_normalized_laplacian_from_weights(int32_t n, const double* W, con
  *            goes to X, its partner to Y; G+ lists X then the fixed points Z,
  *            G- lists the partners of X in X's order.
  *  flags     GFT_SPLIT_COMPONENTS | GFT_ORDER_BLOCK | GFT_ANALYZE_ONLY | GFT_NO_JIT |
- *            GFT_KERNEL_TABLE | GFT_KERNEL_WIDE (the last two are exclusive).
+ *            GFT_KERNEL_TABLE | GFT_KERNEL_WIDE (these two are exclusive) |
+ *            GFT_SEARCH_STAGES (with n_stages = 0 and phi = NULL: the stages
+ *            gft_search_stages finds, Sec. V-F) | GFT_NORMALIZED (the plan is
+ *            built for D^-1/2 L D^-1/2, d_i = l_ii, which must be positive;
+ *            NOT_LAPLACIAN otherwise).  Stage involutions must then be
+ *            symmetries of the normalised matrix, which holds for every
+ *            symmetry of the graph since degrees are invariant.
  *  out       receives the plan (owned by the caller; free with
  *            gft_plan_destroy).  Unchanged on error.
  * Unless GFT_ANALYZE_ONLY is set, the leaf Laplacians are eigendecomposed on
@@ -181,7 +191,8 @@ gft_status gft_plan_create_many(int32_t count, const int32_t* n, const double* c
  *            entries 0 / 1.  The larger part is E's (colour 0 on a tie);
  *            within a part, nodes are in ascending label order.
  *  flags     GFT_ORDER_BLOCK | GFT_ANALYZE_ONLY | GFT_NO_JIT |
- *            GFT_KERNEL_TABLE | GFT_KERNEL_WIDE.
+ *            GFT_KERNEL_TABLE | GFT_KERNEL_WIDE | GFT_NORMALIZED (pass the
+ *            combinatorial Laplacian of any bipartite graph: Thm. 2).
  * The plan has no left stages (n_stages = 0), two leaves (E, F) and
  * right_pairs = p.  Transforms run on the CUDA-core kernels (FP32 / FP64;
  * tensor-core precisions return UNSUPPORTED).  Output order as

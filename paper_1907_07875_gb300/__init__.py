@@ -26,6 +26,8 @@ ANALYZE_ONLY = 0x4
 NO_JIT = 0x8
 KERNEL_TABLE = 0x10
 KERNEL_WIDE = 0x20
+SEARCH_STAGES = 0x40
+NORMALIZED = 0x80
 PRECISIONS = {"fp32": 0, "bf16": 1, "bf16x3": 2, "fp16x3": 3}
 
 STATUS = {0: "GFT_OK", 1: "GFT_ERR_INVALID_ARG", 2: "GFT_ERR_NOT_INVOLUTION", 3: "GFT_ERR_NOT_SYMMETRIC",
@@ -98,7 +100,10 @@ class Plan:
 
     def __init__(self, L, phis: Optional[Sequence] = None, *, split_components: bool = False,
                  order_block: bool = False, analyze_only: bool = False, jit: bool = True,
-                 kernel: str = "auto"):
+                 kernel: str = "auto", search: bool = False, normalized: bool = False):
+        """L: Laplacian (n x n); phis: stage involutions on the original labels
+        (or search=True to find them, Sec. V-F); normalized=True builds the
+        plan for D^-1/2 L D^-1/2."""
         L = _as_f64(L)
         n = L.shape[0]
         if L.shape != (n, n):
@@ -108,7 +113,8 @@ class Plan:
               if phis else None)
         flags = ((SPLIT_COMPONENTS if split_components else 0) | (ORDER_BLOCK if order_block else 0)
                  | (ANALYZE_ONLY if analyze_only else 0) | (0 if jit else NO_JIT)
-                 | {"auto": 0, "table": KERNEL_TABLE, "wide": KERNEL_WIDE}[kernel])
+                 | {"auto": 0, "table": KERNEL_TABLE, "wide": KERNEL_WIDE}[kernel]
+                 | (SEARCH_STAGES if search else 0) | (NORMALIZED if normalized else 0))
         h = C.c_void_p()
         self._h = None
         _check(lib().gft_plan_create(n, _ptr(L), len(phis), _ptr(ph), flags, C.byref(h)))
@@ -117,7 +123,7 @@ class Plan:
 
     @classmethod
     def bipartite(cls, L, side=None, *, order_block: bool = False, analyze_only: bool = False,
-                  jit: bool = True, kernel: str = "auto") -> "Plan":
+                  jit: bool = True, kernel: str = "auto", normalized: bool = False) -> "Plan":
         """Plan with a right Haar stage for a bipartite graph (Sec. III-A,
         gft_plan_create_bipartite): side = None (two-colouring) or 0 / 1 per node."""
         L = _as_f64(L)
@@ -128,7 +134,8 @@ class Plan:
         if sd is not None and sd.shape != (n,):
             raise ValueError("side must have n entries")
         flags = ((ORDER_BLOCK if order_block else 0) | (ANALYZE_ONLY if analyze_only else 0)
-                 | (0 if jit else NO_JIT) | {"auto": 0, "table": KERNEL_TABLE, "wide": KERNEL_WIDE}[kernel])
+                 | (0 if jit else NO_JIT) | {"auto": 0, "table": KERNEL_TABLE, "wide": KERNEL_WIDE}[kernel]
+                 | (NORMALIZED if normalized else 0))
         h = C.c_void_p()
         _check(lib().gft_plan_create_bipartite(n, _ptr(L), _ptr(sd), flags, C.byref(h)))
         return cls._wrap(h, n)
@@ -282,7 +289,8 @@ def search_stages(L, max_stages: int = 8, max_steps: int = 0):
 
 
 def plans_from_laplacians(Ls, phis_list, *, split_components: bool = False, order_block: bool = False,
-                          analyze_only: bool = False, jit: bool = True, kernel: str = "auto"):
+                          analyze_only: bool = False, jit: bool = True, kernel: str = "auto",
+                          search: bool = False, normalized: bool = False):
     """Many plans at once (gft_plan_create_many): every graph's leaves are
     eigendecomposed in one batched Jacobi solve on the device."""
     k = len(Ls)
@@ -295,7 +303,8 @@ def plans_from_laplacians(Ls, phis_list, *, split_components: bool = False, orde
     Pp = (C.c_void_p * k)(*[(p.ctypes.data if p is not None else None) for p in phs])
     flags = ((SPLIT_COMPONENTS if split_components else 0) | (ORDER_BLOCK if order_block else 0)
              | (ANALYZE_ONLY if analyze_only else 0) | (0 if jit else NO_JIT)
-             | {"auto": 0, "table": KERNEL_TABLE, "wide": KERNEL_WIDE}[kernel])
+             | {"auto": 0, "table": KERNEL_TABLE, "wide": KERNEL_WIDE}[kernel]
+             | (SEARCH_STAGES if search else 0) | (NORMALIZED if normalized else 0))
     out = (C.c_void_p * k)()
     _check(lib().gft_plan_create_many(k, _ptr(ns), C.cast(Lp, C.c_void_p), _ptr(st), C.cast(Pp, C.c_void_p),
                                       flags, C.cast(out, C.c_void_p)))
@@ -489,4 +498,4 @@ def givens_apply(x, theta, net: Givens):
 
 __all__ = ["Plan", "Batch", "ApproxGFT", "Givens", "givens_apply", "laplacian", "normalized_laplacian", "GftError", "lib",
            "SPLIT_COMPONENTS", "ORDER_BLOCK", "ANALYZE_ONLY", "NO_JIT", "KERNEL_TABLE",
-           "KERNEL_WIDE", "PRECISIONS", "plans_from_laplacians", "find_involution", "search_stages"]
+           "KERNEL_WIDE", "SEARCH_STAGES", "NORMALIZED", "PRECISIONS", "plans_from_laplacians", "find_involution", "search_stages"]

@@ -163,10 +163,26 @@ void check_create_args(int32_t n, const double* L, int32_t n_stages, const int32
     if (n_stages < 0 || n_stages > 16) fail(GFT_ERR_INVALID_ARG, "n_stages must be in [0, 16]");
     if (n_stages > 0 && !phi) fail(GFT_ERR_INVALID_ARG, "phi is NULL");
     if (flags & ~(GFT_SPLIT_COMPONENTS | GFT_ORDER_BLOCK | GFT_ANALYZE_ONLY | GFT_NO_JIT | GFT_KERNEL_TABLE |
-                  GFT_KERNEL_WIDE))
+                  GFT_KERNEL_WIDE | GFT_SEARCH_STAGES | GFT_NORMALIZED))
         fail(GFT_ERR_INVALID_ARG, "unknown flag");
     if ((flags & GFT_KERNEL_TABLE) && (flags & GFT_KERNEL_WIDE))
         fail(GFT_ERR_INVALID_ARG, "GFT_KERNEL_TABLE and GFT_KERNEL_WIDE are exclusive");
+    if ((flags & GFT_SEARCH_STAGES) && n_stages != 0)
+        fail(GFT_ERR_INVALID_ARG, "GFT_SEARCH_STAGES finds the stages: pass n_stages = 0");
+}
+
+// D^-1/2 L D^-1/2 with d_i = l_ii (Sec. II-B), as gft_normalized_laplacian_from_weights
+std::vector<double> normalized_copy(int n, const double* L) {
+    std::vector<double> N(L, L + (size_t)n * n), r(n);
+    for (int i = 0; i < n; ++i) {
+        const double d = L[(size_t)i * n + i];
+        if (!(d > 0.0) || !std::isfinite(d))
+            fail(GFT_ERR_NOT_LAPLACIAN, "node " + std::to_string(i) + " has no positive degree");
+        r[i] = 1.0 / std::sqrt(d);
+    }
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) N[(size_t)i * n + j] = (N[(size_t)i * n + j] * r[i]) * r[j];
+    return N;
 }
 
 // Decompose every graph on the host, eigendecompose all their leaves in one
@@ -194,7 +210,21 @@ void create_plans(int32_t count, const int32_t* ns, const double* const* Ls, con
             for (int q = next++; q < count; q = next++) {
                 const int i = order[q];
                 try {
-                    analyze(*made[i], Ls[i], n_stages[i], phis ? phis[i] : nullptr);
+                    const int n = ns[i];
+                    std::vector<double> Ln;
+                    const double* L = Ls[i];
+                    if (flags & GFT_NORMALIZED) {
+                        Ln = normalized_copy(n, L);
+                        L = Ln.data();
+                    }
+                    if (flags & GFT_SEARCH_STAGES) {
+                        check_symmetric_finite(n, L);
+                        std::vector<int> found;
+                        const int s = search_stages(n, L, 16, 1000000, found);
+                        analyze(*made[i], L, s, found.data());
+                    } else {
+                        analyze(*made[i], L, n_stages[i], phis ? phis[i] : nullptr);
+                    }
                 } catch (...) {
                     errs[i] = std::current_exception();
                 }
@@ -272,12 +302,15 @@ gft_status gft_plan_create_bipartite(int32_t n, const double* L, const int32_t* 
     return guard([&] {
         if (!out) fail(GFT_ERR_INVALID_ARG, "out is NULL");
         check_create_args(n, L, 0, nullptr, flags);
-        if (flags & GFT_SPLIT_COMPONENTS) fail(GFT_ERR_INVALID_ARG, "GFT_SPLIT_COMPONENTS does not apply to bipartite plans");
+        if (flags & (GFT_SPLIT_COMPONENTS | GFT_SEARCH_STAGES))
+            fail(GFT_ERR_INVALID_ARG, "GFT_SPLIT_COMPONENTS and GFT_SEARCH_STAGES do not apply to bipartite plans");
         std::unique_ptr<gft_plan_s> p(new gft_plan_s);
         p->n = n;
         p->flags = flags;
         Leaf J;
-        analyze_bipartite(*p, L, side, J);
+        std::vector<double> Ln;
+        if (flags & GFT_NORMALIZED) Ln = normalized_copy(n, L);
+        analyze_bipartite(*p, Ln.empty() ? L : Ln.data(), side, J);
         if (!(flags & GFT_ANALYZE_ONLY)) {
             GFT_CUDA(cudaGetDevice(&p->device));
             cudaStream_t st = nullptr;

@@ -367,3 +367,55 @@ def test_approx_errors(gft):
     x = np.zeros((4, 16), dtype=np.float32)
     assert lib.gft_approx_forward(a._h, x.ctypes.data, x.ctypes.data, 4, None) == 12       # GFT_ERR_NO_DEVICE
     assert lib.gft_approx_destroy(None) == 0
+
+
+@pytest.mark.parametrize("g", [W.skeleton25(), W.grid(6), W.cycle(16), W.grid6_bidiag(4), W.path(12)],
+                         ids=lambda g: g.name)
+def test_search_flag_equals_explicit_search(gft, g):
+    """GFT_SEARCH_STAGES builds the plan on the stages gft_search_stages
+    returns (up to 16 stages): same pairs and leaves as passing them."""
+    L = ograph.laplacian(g.W, g.s)
+    phis = gft.search_stages(L, max_stages=16)
+    a = gft.Plan(L, search=True, analyze_only=True)
+    b = gft.Plan(L, phis, analyze_only=True)
+    assert a.info["n_stages"] == b.info["n_stages"] == len(phis) >= 1
+    for s in range(len(phis)):
+        assert a.stage_pairs(s).tolist() == b.stage_pairs(s).tolist()
+    assert a.leaves() == b.leaves()
+    many = gft.plans_from_laplacians([L, L], [[], []], search=True, analyze_only=True)
+    assert all(p.leaves() == b.leaves() for p in many)
+    with pytest.raises(gft.GftError) as e:
+        gft.Plan(L, g.phis or [list(range(g.n))], search=True, analyze_only=True)
+    assert e.value.status == "GFT_ERR_INVALID_ARG"
+
+
+@pytest.mark.parametrize("g", [W.skeleton25(), W.grid(6, weights="sym_uniform", seed=9), W.zgrid(4)],
+                         ids=lambda g: g.name)
+def test_normalized_flag_equals_normalised_input(gft, g):
+    """GFT_NORMALIZED: the plan of L with the flag is the plan of
+    D^-1/2 L D^-1/2 (same pairs, leaves and leaf matrices, bit for bit)."""
+    L = ograph.laplacian(g.W, g.s)
+    a = gft.Plan(L, g.phis, normalized=True, analyze_only=True)
+    b = gft.Plan(gft.normalized_laplacian(g.W, g.s), g.phis, analyze_only=True)
+    assert a.leaves() == b.leaves()
+    for k in range(len(a.leaves())):
+        assert np.array_equal(a.leaf_laplacian(k), b.leaf_laplacian(k))
+    Z = np.zeros((3, 3))
+    Z[0, 1] = Z[1, 0] = -1.0
+    Z[0, 0] = Z[1, 1] = 1.0                                          # node 2 has degree 0
+    with pytest.raises(gft.GftError) as e:
+        gft.Plan(Z, [], normalized=True, analyze_only=True)
+    assert e.value.status == "GFT_ERR_NOT_LAPLACIAN"
+
+
+def test_bipartite_normalized_flag(gft):
+    """Thm. 2 from the combinatorial Laplacian: the flag gives the plan of the
+    normalised Laplacian (alpha = 1), whose parts need not be regular."""
+    g = W.random_bipartite(7, 4, 0.4, seed=2103)
+    L = ograph.laplacian(g.W, g.s)
+    with pytest.raises(gft.GftError) as e:
+        gft.Plan.bipartite(L, g.meta["side"], analyze_only=True)         # unequal degrees
+    assert e.value.status == "GFT_ERR_NOT_BIPARTITE"
+    a = gft.Plan.bipartite(L, g.meta["side"], normalized=True, analyze_only=True)
+    b = gft.Plan.bipartite(gft.normalized_laplacian(g.W, g.s), g.meta["side"], analyze_only=True)
+    assert a.leaves() == b.leaves() and a.info["right_pairs"] == 4
