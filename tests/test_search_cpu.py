@@ -135,3 +135,26 @@ def test_search_rejects_bad_input(gft):
     with pytest.raises(gft.GftError) as e:
         gft.find_involution(np.array([[1.0, 2.0], [0.0, 1.0]]))
     assert e.value.status == "GFT_ERR_NOT_LAPLACIAN"
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_planted_symmetries_of_larger_graphs(gft, seed):
+    """Random graphs of 12-40 nodes with a planted involution (random pairs,
+    weights copied to image pairs): the search returns a valid symmetry
+    (an involution under which L is symmetric, Definition 2) with at least
+    as many pairs as the planted one."""
+    rng = np.random.default_rng(900 + seed)
+    n = int(rng.integers(12, 41))
+    perm = rng.permutation(n)
+    k = int(rng.integers(1, n // 2 + 1))
+    phi = np.arange(n)
+    for a in range(k):
+        i, j = perm[2 * a], perm[2 * a + 1]
+        phi[i], phi[j] = j, i
+    g = W.planted_symmetric(n, phi, density=float(rng.uniform(0.2, 0.6)), seed=seed)
+    L = ograph.laplacian(g.W, g.s)
+    found, pairs = gft.find_involution(L)
+    assert ograph.is_involution(found)
+    assert ograph.laplacian_is_phi_symmetric(L, [int(v) for v in found], 1e-12 * max(1.0, np.abs(L).max()))
+    assert pairs == sum(1 for i in range(n) if found[i] > i)
+    assert pairs >= k
