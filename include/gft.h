@@ -12,6 +12,11 @@
  * forward transform applies the stages (additions and subtractions only,
  * the 1/sqrt(2) factors folded into the U_k, Sec. III) and then the block
  * products U_k^T, and writes the coefficients in ascending eigenvalue order.
+ * Bipartite graphs give the mirror image, a stage of Haar units on the
+ * OUTPUT side after two sub-transforms (Sec. III-A, gft_plan_create_bipartite);
+ * gft_approx_* replaces the leaves' dense products by greedy layers of
+ * Givens rotations (the comparison of Sec. VI-B), and gft_givens_* applies
+ * and trains layered Givens surrogates.
  *
  * Conventions shared by every call:
  *  - Signals are rows: a batch is a row-major [batch, n] array, one signal
