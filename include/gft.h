@@ -151,8 +151,9 @@ gft_status gft_normalized_laplacian_from_weights(int32_t n, const double* W, con
  * register-blocked GEMM of the whole CTA; for leaves of at most 64 nodes the
  * call times it against the table-driven kernel and keeps the faster
  * (GFT_KERNEL_TABLE / GFT_KERNEL_WIDE force one).  Eigenvector signs: the first
- * entry of largest magnitude (within 1e-9 relative) of every full-length
- * basis vector is made positive.  Output order: ascending eigenvalue;
+ * significant entry (magnitude above 1e-8 of the vector's largest) of every
+ * full-length basis vector is made positive, which keeps the closed forms'
+ * own signs (DCT-II of a uniform path, the printed 4-cycle basis).  Output order: ascending eigenvalue;
  * eigenvalues within 1e-9*max(1,|lambda|max) of a neighbour form a cluster
  * ordered by (leaf in depth-first order with + before -, index in leaf).
  * Errors: INVALID_ARG, NOT_LAPLACIAN, NOT_INVOLUTION, BLOCK_LEAK,

@@ -16,7 +16,7 @@ namespace {
 constexpr double kSymTol = 1e-12;      // phi-symmetry / Laplacian symmetry, x max(1, max|L|)
 constexpr double kZeroTol = 1e-12;     // structural zero for component splitting, same scale
 constexpr double kClusterTol = 1e-9;   // eigenvalue clusters, x max(1, max|lambda|)
-constexpr double kSignTol = 1e-9;      // ties for the sign rule, relative to max|u|
+constexpr double kSignTol = 1e-8;      // sign rule: entries below this fraction of max|u| count as zeros
 const double kRsqrt2 = 0.70710678118654752440;
 
 double max_abs(const std::vector<double>& v) {
@@ -304,7 +304,9 @@ void finalize_host(gft_plan_s& p) {
     } else {
         p.out_pos = output_positions(lam_e, leaf_e, local_e);
     }
-    // ---- signs: first maximal-magnitude entry of each full vector positive ----
+    // ---- signs: first significant entry (|u_i| > 1e-8 max|u|) of each full
+    // vector positive, the convention of the closed forms the paper quotes
+    // (DCT-II, the printed 4-cycle basis of Sec. III) ----
     // (right Haar units: the rule fixes the sum vector, i.e. E's column and
     // F's column together; the difference vector follows)
     std::vector<double> v;
@@ -316,9 +318,9 @@ void finalize_host(gft_plan_s& p) {
             full_column(p, (int)k, c, v);
             double mx = 0.0;
             for (double x : v) mx = std::max(mx, std::fabs(x));
-            const double thr = (1.0 - kSignTol) * mx;
+            const double thr = kSignTol * mx;
             int first = 0;
-            while (first < n && std::fabs(v[first]) < thr) ++first;
+            while (first < n && !(std::fabs(v[first]) > thr)) ++first;
             if (first < n && v[first] < 0) {
                 for (int r = 0; r < m; ++r) lf.V[(size_t)r * m + c] = -lf.V[(size_t)r * m + c];
                 if (p.right && c < (int)p.rpairs.size()) {

@@ -44,6 +44,19 @@ def align(Y_ref, U_test, U_ref, lam, tol: float = 1e-9):
     return out
 
 
+def simple_column_sign_error(U_test, U_ref, lam, tol: float = 1e-9) -> float:
+    """Largest entrywise difference over the columns of simple eigenvalues
+    (clusters of one).  Their vectors are unique up to sign, and the sign
+    rule fixes the sign, so these columns must agree entry by entry: a sign
+    flip shows up as an O(1) difference."""
+    worst = 0.0
+    for S in clusters(lam, tol):
+        if len(S) == 1:
+            j = S[0]
+            worst = max(worst, float(np.max(np.abs(np.asarray(U_test)[:, j] - np.asarray(U_ref)[:, j]))))
+    return worst
+
+
 def rel_l2(a, b) -> float:
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)

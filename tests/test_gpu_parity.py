@@ -5,7 +5,8 @@ FP32 outputs: relative L2 error <= 2e-6 against the FP64 oracle after
 eigenspace alignment (bases are unique only up to rotations inside repeated
 eigenvalues, Sec. III).  FP64 outputs: <= 1e-13.  Integer plan data (stage
 pairs, leaves, output map) bit-exact.  Eigenvalues within 1e-12 * max(1,
-max|lambda|); basis projectors within 1e-10.
+max|lambda|); basis projectors within 1e-10; columns of simple eigenvalues
+equal to the oracle's entry by entry (the sign rule), within 1e-9.
 """
 import numpy as np
 import pytest
@@ -13,7 +14,7 @@ import pytest
 import gft_workloads as W
 from oracle import gft as ogft
 from oracle import graph as ograph
-from _helpers import align, projector_distance, rel_l2
+from _helpers import align, projector_distance, rel_l2, simple_column_sign_error
 
 pytestmark = pytest.mark.gpu
 
@@ -56,6 +57,8 @@ def check_plan_against_oracle(plan, ref):
     U = plan.basis()
     assert np.max(np.abs(U.T @ U - np.eye(plan.n))) <= 1e-12
     assert projector_distance(U, ref.U, ref.lam) <= 1e-10
+    # simple eigenvalues: the library's sign rule gives the oracle's vector
+    assert simple_column_sign_error(U, ref.U, ref.lam) <= 1e-9
     return U
 
 

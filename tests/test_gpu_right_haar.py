@@ -14,7 +14,7 @@ import pytest
 import gft_workloads as W
 from oracle import graph as ograph
 from oracle import right_haar as orh
-from _helpers import align, projector_distance, rel_l2
+from _helpers import align, projector_distance, rel_l2, simple_column_sign_error
 
 pytestmark = pytest.mark.gpu
 
@@ -52,6 +52,9 @@ def _check(torch, plan, ref, batch, seed, tol32=FP32_TOL):
     U = plan.basis()
     assert np.max(np.abs(U.T @ U - np.eye(ref.n))) <= 1e-12
     assert projector_distance(U, ref.U, ref.lam) <= 1e-9
+    # simple eigenvalues, sum and difference vectors of the right units
+    # alike: the sign rule fixes the sum vector and the difference follows
+    assert simple_column_sign_error(U, ref.U, ref.lam) <= 1e-8
     x = W.signals(batch, ref.n, seed)
     xt = torch.from_numpy(x).cuda()
     y = plan.forward(xt).cpu().numpy().astype(np.float64)
@@ -111,6 +114,7 @@ def test_large_bipartite_wide_kernel(env, which):
     assert np.max(np.abs(plan.eigenvalues() - ref.lam)) <= 1e-10 * max(1.0, ref.alpha)
     U = plan.basis()
     assert projector_distance(U, ref.U, ref.lam) <= 1e-8
+    assert simple_column_sign_error(U, ref.U, ref.lam) <= 1e-7
     batch = (1 << 21) // g.n
     x = W.signals(batch, g.n, 33)
     xt = torch.from_numpy(x).cuda()

@@ -12,7 +12,7 @@ import pytest
 import gft_workloads as W
 from oracle import gft as ogft
 from oracle import graph as ograph
-from _helpers import align, projector_distance, rel_l2
+from _helpers import align, projector_distance, rel_l2, simple_column_sign_error
 
 pytestmark = pytest.mark.gpu
 
@@ -48,6 +48,7 @@ CASES = [(W.grid(16), False, True), (W.cycle(256), False, True), (W.path(100), F
 def _check(gft, torch, plan, ref, batch, seed):
     U = plan.basis()
     assert projector_distance(U, ref.U, ref.lam) <= 1e-10
+    assert simple_column_sign_error(U, ref.U, ref.lam) <= 1e-9
     x = W.signals(batch, plan.n, seed)
     xt = torch.from_numpy(x).cuda()
     y = plan.forward(xt).cpu().numpy().astype(np.float64)

@@ -47,6 +47,35 @@ def test_even_cycle_closed_form(n):
     _check_basis(L, f)
 
 
+def test_printed_c4_columns_by_right_haar():
+    """Sec. III: the 4-cycle is bipartite (parts {1, 3} and {2, 4} of the
+    printed labels); the right Haar unit of its first column pair gives the
+    printed lam = 0 column (1, 1, 1, 1)/2 as the sum vector and the printed
+    lam = 4 column (1, -1, 1, -1)/2 as the difference vector, signs included
+    (the sign rule fixes the sum vector, the difference follows it)."""
+    import os
+    from _helpers import read_golden_matrix
+    meta, M = read_golden_matrix(os.path.join(os.path.dirname(__file__), "golden", "u_c4.txt"))
+    Uc4 = M * meta["scale"][0]
+    g = W.cycle(4)
+    f = R.right_haar_gft(_L(g, False))
+    assert np.allclose(f.lam, meta["eigenvalues"], atol=1e-13)
+    for c in (0, 3):
+        assert np.allclose(f.U[:, c], Uc4[:, c], atol=1e-13)
+
+
+@pytest.mark.parametrize("n", [6, 12, 20])
+def test_even_cycle_extreme_columns_signed(n):
+    """Even cycle: the simple eigenvalues 0 and 4 have the closed-form
+    vectors 1/sqrt(n) and (-1)^i / sqrt(n); both start positive, and the
+    second is Lemma 1's image (u1, -u2) of the first."""
+    g = W.cycle(n)
+    f = R.right_haar_gft(_L(g, False))
+    i = np.arange(n)
+    assert np.allclose(f.U[:, 0], np.full(n, 1 / math.sqrt(n)), atol=1e-13)
+    assert np.allclose(f.U[:, n - 1], (-1.0) ** i / math.sqrt(n), atol=1e-13)
+
+
 @pytest.mark.parametrize("d", [2, 3, 4])
 def test_hypercube_closed_form(d):
     g = W.hypercube(d)
