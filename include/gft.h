@@ -75,7 +75,11 @@ typedef enum {
 #define GFT_KERNEL_WIDE      0x20u /* CUDA-core transforms: the wide-leaf kernel whenever the
                                       plan has a leaf of more than 32 nodes */
 #define GFT_SEARCH_STAGES    0x40u /* n_stages = 0: find the stages with gft_search_stages
-                                      (up to 16 stages, 10^6 search steps each) */
+                                      (up to 16 stages, 10^6 search steps each).  When the
+                                      step budget runs out, the search keeps the stages
+                                      found so far (possibly none) and the plan is still
+                                      created: read the stage count back from
+                                      gft_plan_get_info (info.n_stages). */
 #define GFT_NORMALIZED       0x80u /* transform with the normalised Laplacian D^-1/2 L D^-1/2
                                       (d_i = l_ii > 0) of the given L (Sec. II-B) */
 
@@ -248,7 +252,7 @@ gft_status gft_plan_destroy(gft_plan_t plan);
 
 typedef struct {
     int32_t n;              /* nodes */
-    int32_t n_stages;       /* stages as given */
+    int32_t n_stages;       /* stages as given, or as found by GFT_SEARCH_STAGES */
     int32_t n_leaves;       /* leaf blocks after all stages (and splitting) */
     int32_t n_pairs;        /* Haar units over all stages */
     int32_t max_leaf;       /* largest leaf size */
@@ -467,15 +471,22 @@ gft_status gft_givens_backward(gft_givens_t g, const float* theta, const float* 
  *            differ in rounding because the CTA count can differ).
  * Scratch: a fixed 4 MiB device array compiled into the library (held on
  * every GPU that loads it until exit) holds the pair table and one row of
- * n_stages*n/2 partial sums per CTA; the CTA count is capped to fit, and a
- * network whose pair table plus one row exceeds 4 MiB is rejected with
- * GFT_ERR_INVALID_ARG (cannot happen within the n and n_stages limits).
+ * n_stages*n/2 partial sums per CTA.  A network whose pair table plus one
+ * row exceeds 4 MiB is rejected with GFT_ERR_INVALID_ARG (cannot happen
+ * within the n and n_stages limits); the CTA count is one per row that fits,
+ * a cap the shared-memory limit of the kernel keeps from ever binding.
  * Every call rewrites what it reads, so nothing needs clearing between
  * calls, but all calls share the one array: calls that overlap on the GPU
  * (different streams, or different host threads) race and must be
- * serialised by the caller.  The first call on each device looks up the
- * array's device address (cudaGetSymbolAddress); make that first call
- * before any stream capture.
+ * serialised by the caller.  Every call copies `pairs` into the array with
+ * cudaMemcpyAsync on `stream`: from pinned memory the copy runs later on the
+ * stream, so the table must stay unchanged until then; from pageable memory
+ * the driver has staged it when the call returns.  batch = 0 copies the table
+ * and zeroes gtheta.  The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress) and keeps it for the life of the
+ * process; make that first call before any stream capture (this concerns
+ * the look-up only).  After cudaDeviceReset the kept address is stale:
+ * restart the process before calling again.
  */
 gft_status gft_givens_backward_noalloc(int32_t n, int32_t n_stages, const int32_t* pairs, const float* theta,
                                        const float* y, const float* gy, float* gx, float* gtheta,

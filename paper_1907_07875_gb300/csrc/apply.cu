@@ -208,14 +208,23 @@ bool supported(const ApplyArgs& A) {
 
 bool apply_supported(const ApplyArgs& a, bool f64) { return f64 ? supported<double>(a) : supported<float>(a); }
 
+// SM count of the current device, looked up once per device ordinal
 int sm_count() {
-    static int cached = 0;
-    if (!cached) {
-        int dev = 0;
-        GFT_CUDA(cudaGetDevice(&dev));
-        GFT_CUDA(cudaDeviceGetAttribute(&cached, cudaDevAttrMultiProcessorCount, dev));
+    constexpr int kMaxDev = 64;
+    static int cached[kMaxDev] = {};
+    int dev = 0;
+    GFT_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDev) {
+        int c = 0;
+        GFT_CUDA(cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev));
+        return c;
     }
-    return cached;
+    if (!cached[dev]) {
+        int c = 0;
+        GFT_CUDA(cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev));
+        cached[dev] = c;
+    }
+    return cached[dev];
 }
 
 void launch_apply_f32(const ApplyArgs& a, const float* x, float* y, int64_t batch, bool inverse,

@@ -539,7 +539,10 @@ extern "C" gft_status gft_givens_backward_noalloc(int32_t n, int32_t n_stages, c
         GFT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, givens_bwd_kernel, kGivThreads, smem));
         const long long tiles = (batch + kGivThreads - 1) / kGivThreads;
         // every CTA overwrites its whole partial row, and the reduction reads
-        // only the rows of this call: nothing in the scratch needs clearing
+        // only the rows of this call: nothing in the scratch needs clearing.
+        // rows_cap is a guard only: the shared-memory limit above keeps A
+        // below about 3.6k angles, so at least 280 rows fit in the 4 MiB,
+        // more than the resident CTAs of the whole GPU at these shapes.
         const int grid = (int)std::min(std::min<long long>(tiles, (long long)std::max(1, per_sm) * sm_count()), rows_cap);
         givens_bwd_kernel<<<grid, kGivThreads, smem, st>>>(a);
         GFT_CUDA(cudaGetLastError());

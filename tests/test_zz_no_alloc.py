@@ -4,10 +4,11 @@ called through the C ABI, against the allocating gft_givens_backward.
 It exists for callers that cannot allocate device memory while running (a
 program whose own pool owns the GPU's memory, a real-time loop that must not
 allocate mid-step, a thin C host without an allocator): it keeps its scratch
-in a fixed array inside the library.  Two calls in a row with different
-network shapes check that the shared scratch carries nothing over.  This
-file sorts last so that a run stopping at the first failure has already run
-every other test."""
+in a fixed array inside the library.  Several calls in a row with
+different network shapes (butterfly and random-matching wirings, ragged
+batches, a single signal, batch 0) check that the shared scratch carries
+nothing over.  This file sorts last so that a run stopping at the first
+failure has already run every other test."""
 import ctypes as C
 
 import numpy as np
@@ -31,6 +32,13 @@ def _xor_pairs(n, S):
     return out
 
 
+def _random_pairs(n, S, seed):
+    """S stages, each a random perfect matching of the n nodes (the general,
+    non-butterfly wiring)."""
+    rng = np.random.default_rng(seed)
+    return np.stack([rng.permutation(n).reshape(n // 2, 2) for _ in range(S)]).astype(np.int32)
+
+
 def test_noalloc_backward_matches_allocating_backward():
     import torch
     assert torch.cuda.is_available()
@@ -39,8 +47,10 @@ def test_noalloc_backward_matches_allocating_backward():
     import paper_1907_07875_gb300 as gft
     lib = gft.lib()
     stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
-    for n, S, B, seed in ((32, 10, 5003, 1), (16, 8, 777, 2)):
-        pairs = _xor_pairs(n, S)
+    cases = ((32, 10, 5003, 1, _xor_pairs(32, 10)), (16, 8, 777, 2, _xor_pairs(16, 8)),
+             (16, 8, 1, 3, _xor_pairs(16, 8)), (24, 7, 1000, 4, _random_pairs(24, 7, 40)),
+             (64, 12, 129, 5, _random_pairs(64, 12, 41)))
+    for n, S, B, seed, pairs in cases:
         rng = np.random.default_rng(seed)
         theta = torch.from_numpy(rng.uniform(-1, 1, (S, n // 2)).astype(np.float32)).cuda()
         net = gft.Givens(n, pairs)
@@ -57,6 +67,15 @@ def test_noalloc_backward_matches_allocating_backward():
         assert torch.equal(gx, gx_ref)
         err = float(torch.linalg.norm(gth - gth_ref) / torch.linalg.norm(gth_ref))
         assert err <= GRAD_TOL, err
+    # batch = 0: the pair table is copied and gtheta is zeroed (filled with
+    # garbage first so that a skipped clear shows)
+    gth.fill_(7.0)
+    st = lib.gft_givens_backward_noalloc(n, S, C.c_void_p(pairs.ctypes.data), C.c_void_p(theta.data_ptr()),
+                                         C.c_void_p(y.data_ptr()), C.c_void_p(gy.data_ptr()),
+                                         C.c_void_p(gx.data_ptr()), C.c_void_p(gth.data_ptr()), 0, stream)
+    assert st == 0, lib.gft_last_error()
+    torch.cuda.synchronize()
+    assert torch.count_nonzero(gth).item() == 0
     # a network that is not a perfect matching is rejected before any launch
     bad = _xor_pairs(16, 8)
     bad[0, 0] = bad[0, 1]
