@@ -1,17 +1,23 @@
 """Benchmark of the batched fast GFT on GB300.
 
-Workload (default): the 25-joint skeleton graph (spine 0-4, arms and legs of
-5 joints, left/right involution), 2^20 FP32 signals drawn i.i.d. N(0,1) --
-one Haar stage and leaf blocks of 15, 5 and 5 nodes.  A step is one forward
-fast GFT of the whole batch (Haar stage, leaf products, output permutation:
-one kernel launch).  Metric: coefficients per second (batch * n per step).
+Workload (default, the largest configuration that fits one GPU): the size
+sweep -- 10^4 graphs of 8..1024 nodes (path, cycle, 4-connected grid, 25-joint
+skeleton, random bipartite with equal halves; sizes log-uniform per family),
+ceil(2^28 / (10^4 n)) FP32 signals each drawn i.i.d. N(0,1), 2^28
+coefficients (1 GiB in, 1 GiB out, far larger than L2).  A step is one
+forward fast GFT of every graph's batch: ONE replay of the captured CUDA graph
+of the mixed-batch kernels (Haar stages, leaf products, output permutation).
+Leaves of at most 63 nodes run in FP32 on CUDA cores; leaves of 64..512
+nodes run on the tensor cores in FP16 hi+lo split with FP32 accumulation,
+whose error against FP64 stays within the FP32 bound 2e-6 (the line states
+it).  Metric: coefficients per second (sum of batch * n per step).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Under torchrun every rank transforms its own batch (independent problems:
-weak scaling, no collective on the data path); the time is the max over
-ranks.  `--impl reference` times the FP64 CPU oracle on the host cores on a
-bounded sample of the same workload.
+Under torchrun every rank transforms its own copy of the workload
+(independent problems: weak scaling, no collective on the data path); the
+time is the max over ranks.  `--impl reference` times the FP64 CPU oracle on
+the host cores on a bounded sample of the same workload.
 """
 from __future__ import annotations
 
@@ -32,7 +38,8 @@ sys.path.insert(0, ROOT)
 
 import gft_workloads as W  # noqa: E402
 
-WORKLOAD = "skeleton25_2^20_fp32"
+WORKLOAD = "size_sweep_10^4_graphs_2^28_coeffs"
+C2_WORKLOAD = "skeleton25_2^20_fp32"
 METRIC = "fast-GFT coeffs/s vs dense GFT, same GB300, at stated err vs FP64; %HBM roof"
 UNIT = "coeffs/s"
 L2_BYTES = 129 * 1024 * 1024
@@ -72,102 +79,179 @@ def _traffic_from_profile(kernel_hash):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 100 ms."""
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    """SM clocks and clock-event (throttle) reasons sampled every ~2 ms from
+    a thread through NVML (read-only queries of the driver's management
+    library), so that even a timed region of a few tens of milliseconds
+    carries samples; nvidia-smi at 100 ms if NVML cannot be loaded."""
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown"}
 
-    def __init__(self, gpu_index):
+    def __init__(self, gpu_index, period_s=0.002):
         self.idx = gpu_index
+        self.period = period_s
+        self.samples = []          # (sm_mhz, reasons bitmask)
+        self.max_mhz = None
         self.proc = None
+        self.thread = None
+
+    def _nvml(self):
+        import ctypes
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        h = ctypes.c_void_p()
+        if lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.idx), ctypes.byref(h)) != 0:
+            raise RuntimeError("no NVML handle")
+        get_reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        mx = ctypes.c_uint()
+        if lib.nvmlDeviceGetMaxClockInfo(h, ctypes.c_uint(1), ctypes.byref(mx)) == 0:
+            self.max_mhz = float(mx.value)
+        return lib, h, get_reasons
 
     def __enter__(self):
+        import ctypes
+        import threading
         try:
+            lib, h, get_reasons = self._nvml()
+        except Exception:
+            lib = None
+        if lib is not None:
+            self.stop = threading.Event()
+
+            def run():
+                mhz, rs = ctypes.c_uint(), ctypes.c_ulonglong()
+                while not self.stop.is_set():
+                    if lib.nvmlDeviceGetClockInfo(h, ctypes.c_uint(1), ctypes.byref(mhz)) == 0 and \
+                            get_reasons(h, ctypes.byref(rs)) == 0:
+                        self.samples.append((float(mhz.value), int(rs.value)))
+                    time.sleep(self.period)
+            self.thread = threading.Thread(target=run, daemon=True)
+            self.thread.start()
+            return self
+        try:
+            fields = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                      "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                      "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
             self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={fields}", "--format=csv,noheader,nounits",
                  "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
         return self
 
     def __exit__(self, *a):
-        self.out = ""
+        if self.thread is not None:
+            self.stop.set()
+            self.thread.join(timeout=5)
         if self.proc is not None:
             self.proc.terminate()
             try:
-                self.out, _ = self.proc.communicate(timeout=5)
+                out, _ = self.proc.communicate(timeout=5)
             except Exception:
                 self.proc.kill()
+                out = ""
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            bits = {"hw_slowdown": 0x8, "hw_thermal_slowdown": 0x40, "sw_thermal_slowdown": 0x20,
+                    "sw_power_cap": 0x4}
+            for line in (out or "").splitlines():
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    mhz = float(parts[1])
+                    self.max_mhz = float(parts[2])
+                except ValueError:
+                    continue
+                mask = 0
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        mask |= bits[nm]
+                self.samples.append((mhz, mask))
 
     def summary(self):
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in (getattr(self, "out", "") or "").splitlines():
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                sm.append(float(parts[1]))
-                mx.append(float(parts[2]))
-            except ValueError:
-                continue
-            for nm, v in zip(names, parts[5:9]):
-                if v.lower() == "active":
-                    reasons.add(nm)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        sm = [m for m, _ in self.samples]
+        reasons = sorted({nm for _, r in self.samples for bit, nm in self.REASONS.items() if r & bit})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": self.max_mhz,
+                "reasons": reasons, "samples": len(sm),
+                "source": "nvml" if self.thread is not None else "nvidia-smi"}
 
 
 # ---------------------------------------------------------------------------
 # CPU oracle timing (spawned process: no fork after CUDA initialisation)
 # ---------------------------------------------------------------------------
-def _oracle_worker(batch, seconds, q):
+def oracle_sample_specs(max_n=64, count=60):
+    """The bounded CPU sample of the size sweep: its first `count` graphs of
+    at most `max_n` nodes (every family but none above max_n, so the oracle's
+    plain-Python Jacobi builds them in seconds), with their own batches."""
+    out = []
+    for fam, n, gs, b, ss in W.config5_specs():
+        if n <= max_n:
+            out.append((fam, n, gs, b, ss))
+        if len(out) == count:
+            break
+    return out
+
+
+def _oracle_worker(seconds, q):
     from oracle import gft as ogft
     from oracle import graph as ograph
-    (g, _, seed), = W.config2()
-    f = ogft.fast_gft(ograph.laplacian(g.W, g.s), g.phis, split_components=True)
-    x = W.signals(batch, g.n, seed).astype(np.float64)
+    work = []
+    for fam, n, gs, b, ss in oracle_sample_specs():
+        g = W.make_graph(fam, n, gs)
+        f = ogft.fast_gft(ograph.laplacian(g.W, g.s), g.phis)
+        work.append((f, W.signals(b, n, ss % 100000).astype(np.float64)))
+    coeffs = sum(x.size for _, x in work)
     reps, t0 = 0, time.perf_counter()
     while True:
-        ogft.forward_staged(f, x)
+        for f, x in work:
+            ogft.forward_staged(f, x)
         reps += 1
         el = time.perf_counter() - t0
         if el >= seconds:
             break
-    q.put((reps * batch * g.n / el, reps, el))
+    q.put((reps * coeffs / el, reps, el, coeffs))
 
 
-def oracle_rate(batch, seconds):
+def oracle_rate(seconds):
+    """Coefficients/s of the FP64 oracle (fast GFT applied stage by stage) on
+    the sample, in a spawned process with every host core available to its
+    BLAS; returns (rate, reps, seconds, cores, coefficients per rep)."""
     cores = os.cpu_count() or 1
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ[k] = str(cores)
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
-    p = ctx.Process(target=_oracle_worker, args=(batch, seconds, q))
+    p = ctx.Process(target=_oracle_worker, args=(seconds, q))
     p.start()
-    rate, reps, el = q.get()
+    rate, reps, el, coeffs = q.get()
     p.join()
-    return rate, reps, el, cores
+    return rate, reps, el, cores, coeffs
+
+
+def oracle_sample_text(reps, el, coeffs):
+    return (f"oracle.forward_staged (FP64 numpy) on the size sweep's first 60 graphs of at most 64 nodes "
+            f"(all five families, their own batches: {coeffs} coefficients) x {reps} reps ({el:.1f} s)")
 
 
 # ---------------------------------------------------------------------------
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    batch = 1 << 18
     rates = []
     for _ in range(args.warmup):
-        oracle_rate(batch, 0.5)
+        oracle_rate(0.5)
+    info = None
     for _ in range(args.steps):
-        r, _, _, cores = oracle_rate(batch, 2.0)
+        r, reps, el, cores, coeffs = oracle_rate(2.0)
         rates.append(r)
+        info = (reps, el, coeffs)
     value = statistics.median(rates)
     cores = os.cpu_count() or 1
-    sample = f"oracle.forward_staged (FP64 numpy) on 2^18 of the 2^20 signals, repeated for 2 s per step"
+    sample = oracle_sample_text(*info) + ", 2 s per step"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "graph": "skeleton25", "signals": 1 << 20, "n": 25},
+            "config": {"workload": WORKLOAD, "graphs": 10000, "coeffs": 1 << 28},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -381,52 +465,159 @@ def approx_extras(torch, gft, dev):
 
 
 def learned_extras(torch, gft, dev, steps=1500):
-    """Per nearly symmetric graph: the surrogate trained on the GPU against
-    the exact basis, its sign-normalised error delta (Sec. VI-B) before and
-    after training, the error of the method without it (the exact butterfly
-    of the graph with its weights symmetrised under the involutions), and
-    coefficients/s of the surrogate, the exact dense GFT and that butterfly
-    on 2^24 coefficients."""
-    from paper_1907_07875_gb300.learned import LearnedGFT, delta
+    """Per nearly symmetric graph: the method without the learned part (the
+    exact butterfly of the graph with its weights averaged over the
+    involutions), the learned correction on top of it (Givens layers on the
+    butterfly's coefficients, trained on the GPU against the exact basis),
+    and a plain Givens network trained from zero; the sign-normalised error
+    delta (Sec. VI-B) and epsilon of each against the exact GFT, and
+    coefficients/s of each form, of the exact dense GFT and of the
+    symmetrised butterfly on 2^24 coefficients."""
+    from paper_1907_07875_gb300.learned import CorrectedButterfly, LearnedGFT, delta, epsilon, symmetrise_weights
     res = {}
     for g in W.config4():
         n = g.n
         phis = [W.grid_lr(int(round(n ** 0.5))), W.grid_ud(int(round(n ** 0.5)))] if "grid" in g.name \
             else [W.reversal(n)]
-        Ws = g.W.copy()
-        for _ in range(2):
-            for ph in phis:
-                Ws = 0.5 * (Ws + Ws[np.ix_(ph, ph)])
         exact = gft.Plan(gft.laplacian(g.W, g.s), [])
-        sym = gft.Plan(gft.laplacian(Ws, g.s), phis)
+        sym = gft.Plan(gft.laplacian(symmetrise_weights(g.W, phis), g.s), phis)
         U = exact.basis()
-        model = LearnedGFT(n, device=dev)
-        d0 = delta(model.matrix(), U)
-        model.train(U, steps=steps, lr=0.05)
-        d1 = delta(model.matrix(), U)
+        corr = CorrectedButterfly(sym, device=dev)
+        corr.train(U, steps=steps)
+        plain = LearnedGFT(n, device=dev)
+        plain.train(U, steps=steps, lr=0.05)
         nb = (1 << 24) // n
         x = torch.from_numpy(W.signals(nb, n, 5)).to(dev)
         y = torch.empty_like(x)
-        t_l = _timed(torch, lambda: model.forward(x, out=y))
+        tmp = torch.empty_like(x)
+        xs = x[:4096].cpu().numpy()
+        t_c = _timed(torch, lambda: corr.forward(x, out=y, tmp=tmp))
+        t_l = _timed(torch, lambda: plain.forward(x, out=y))
         t_e = _timed(torch, lambda: exact.forward(x, out=y))
         t_s = _timed(torch, lambda: sym.forward(x, out=y))
-        res[g.name] = {"delta_untrained": round(d0, 4), "delta_learned": round(d1, 4),
-                       "delta_symmetrised_butterfly": round(delta(sym.basis(), U), 4),
-                       "learned_gcoeffs_s": round((1 << 24) / t_l / 1e9, 1),
+        res[g.name] = {"delta_symmetrised_butterfly": round(delta(sym.basis(), U), 4),
+                       "delta_learned_correction": round(delta(corr.matrix(), U), 4),
+                       "delta_plain_givens": round(delta(plain.matrix(), U), 4),
+                       "epsilon_symmetrised_butterfly": float("%.3g" % epsilon(sym.basis(), U, xs)),
+                       "epsilon_learned_correction": float("%.3g" % epsilon(corr.matrix(), U, xs)),
+                       "learned_correction_gcoeffs_s": round((1 << 24) / t_c / 1e9, 1),
+                       "plain_givens_gcoeffs_s": round((1 << 24) / t_l / 1e9, 1),
                        "exact_dense_gcoeffs_s": round((1 << 24) / t_e / 1e9, 1),
                        "symmetrised_butterfly_gcoeffs_s": round((1 << 24) / t_s / 1e9, 1)}
     return res
 
 
-def sweep(torch, gft, dev, precisions=("fp32", "bf16x3"), n_graphs=10000, total=1 << 28, reps=5):
-    """Config-5 size sweep: 10^4 graphs (path, cycle, grid, skeleton,
-    bipartite; n = 8..1024 log-uniform), 2^28 FP32 coefficients, in one graph
-    launch per precision; plans built in one batched call, identical graphs
-    share a plan.  Dense baseline: torch.bmm of each size class against its
-    graphs' FP32 bases (TF32 off)."""
+def config2_extras(torch, gft, dev, steps=200):
+    """The 25-joint skeleton, 2^20 FP32 signals (one plan, one launch of the
+    plan-specialised kernel per step, three rotating input/output sets larger
+    than L2): step rate, per-launch roofline, error vs FP64, inverse, dense
+    GEMM and end to end with pinned host buffers (gft_plan_forward_host)."""
+    (g, batch, seed), = W.config2()
+    n = g.n
+    plan = gft.Plan(gft.laplacian(g.W, g.s), g.phis, split_components=True)
+    stream = torch.cuda.current_stream()
+    x_host = W.signals(batch, n, seed)
+    nbytes = batch * n * 4
+    nsets = max(2, -(-4 * L2_BYTES // (2 * nbytes)))
+    xs = [torch.from_numpy(x_host).to(dev) for _ in range(nsets)]
+    for i in range(1, nsets):
+        xs[i].mul_(1.0 + 1e-3 * i)
+    ys = [torch.empty_like(xs[0]) for _ in range(nsets)]
+    U = torch.from_numpy(plan.basis()).to(dev)
+    k = 1 << 14
+    y0 = plan.forward(xs[0][:k].contiguous())
+    ref = xs[0][:k].double() @ U
+    err = float((y0.double() - ref).norm() / ref.norm())
+    for i in range(5):
+        plan.forward(xs[i % nsets], out=ys[i % nsets], stream=stream)
+    torch.cuda.synchronize()
+    every = 4
+    st = {i: torch.cuda.Event(enable_timing=True) for i in range(0, steps, every)}
+    en = {i: torch.cuda.Event(enable_timing=True) for i in range(0, steps, every)}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(steps):
+        if i in st:
+            st[i].record(stream)
+        plan.forward(xs[i % nsets], out=ys[i % nsets], stream=stream)
+        if i in en:
+            en[i].record(stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    step_s = e0.elapsed_time(e1) / steps / 1e3
+    launch_s = statistics.mean(st[i].elapsed_time(en[i]) for i in st) / 1e3
+    peak, peak_kind = _peaks()
+    alg = 8 * batch * n
+    inv_s = _timed(torch, lambda: plan.inverse(ys[0], out=xs[1], stream=stream), reps=20)
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    Uf = U.float()
+    dense_s = _timed(torch, lambda: torch.matmul(xs[0], Uf, out=ys[0]), reps=20)
+    torch.backends.cuda.matmul.allow_tf32 = prev
+    xh = torch.from_numpy(x_host).pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+    plan.forward_host(xh, out=yh)
+    t = time.perf_counter()
+    for _ in range(10):
+        plan.forward_host(xh, out=yh)
+    e2e_s = (time.perf_counter() - t) / 10
+    return {"workload": C2_WORKLOAD, "gcoeffs_s": round(batch * n / step_s / 1e9, 1),
+            "err_vs_fp64": err, "kernel": "gft_jit_fwd_* (plan-specialised)" if plan.info["jit"] else "gft_apply_kernel",
+            "roofline": {"bound": "hbm", "achieved": alg / launch_s / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": alg / launch_s / 1e9 / peak, "peak_source": peak_kind,
+                         "step_frac": alg / step_s / 1e9 / peak},
+            "inverse_gcoeffs_s": round(batch * n / inv_s / 1e9, 1),
+            "dense_gemm_fp32_gcoeffs_s": round(batch * n / dense_s / 1e9, 1),
+            "e2e_gcoeffs_s": round(batch * n / e2e_s / 1e9, 1),
+            "kernel_hash": _kernel_hash(plan), "sets": nsets}
+
+
+def sweep_variants(torch, gft, dev, S, reps=10):
+    """The size sweep (same plans, inputs and outputs as the headline) in
+    the other precisions: FP32 on CUDA cores only, BF16 hi+lo and plain BF16
+    tensor-core leaves, and the dense baseline -- torch.bmm of each size
+    class against its graphs' FP32 bases (TF32 off)."""
     import collections
-    t0 = time.perf_counter()
-    specs = W.config5_specs(n_graphs=n_graphs, total_coeffs=total)
+    picked = stratified_picks(S["specs"])
+    out = {}
+    for prec in ("fp32", "bf16x3", "bf16"):
+        t0 = time.perf_counter()
+        bt = gft.Batch(S["entry"], S["batches"], precision=prec).bind(S["xs"], S["ys"])
+        create = time.perf_counter() - t0
+        t = _timed(torch, lambda: bt.forward(), reps=reps)
+        emax, emed = sweep_errors(torch, S, picked)
+        out[prec] = {"gcoeffs_s": round(S["coeffs"] / t / 1e9, 1), "ms": round(t * 1e3, 3),
+                     "frac_hbm": round((8 * S["coeffs"] + S["basis_bytes"]) / t / 1e9 / _peaks()[0], 3),
+                     "err_max": emax, "err_median": emed, "batch_create_s": round(create, 1),
+                     "launches_per_step": bt.launches}
+        del bt
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    by_n = collections.defaultdict(list)
+    for j, n in enumerate(S["ns"]):
+        by_n[n].append(j)
+    groups, basis = [], {}
+    for n, js in by_n.items():
+        for j in js:
+            e = S["entry_idx"][j]
+            if e not in basis:
+                basis[e] = torch.from_numpy(S["plans"][e].basis()).float().to(dev)
+        Ug = torch.stack([basis[S["entry_idx"][j]] for j in js])
+        Xg = torch.stack([S["xs"][j] for j in js])
+        groups.append((Xg, Ug, torch.empty_like(Xg)))
+    t = _timed(torch, lambda: [torch.bmm(a, u, out=c) for a, u, c in groups], reps=reps)
+    out["dense_bmm_fp32"] = {"gcoeffs_s": round(S["coeffs"] / t / 1e9, 1), "ms": round(t * 1e3, 2),
+                             "size_classes": len(groups)}
+    torch.backends.cuda.matmul.allow_tf32 = prev
+    del groups, basis
+    return out
+
+
+def sweep_setup(torch, gft, dev, seed=1005, specs=None):
+    """The size sweep on this GPU: specs, plans (one batched build; identical
+    graphs share a plan), one input and one output buffer holding every
+    graph's batch (views start 16-byte aligned), seeded N(0,1) inputs."""
+    specs = specs if specs is not None else W.config5_specs()
     keys, graphs = {}, []
     for fam, n, gs, b, ss in specs:
         if (fam, n, gs) not in keys:
@@ -437,55 +628,58 @@ def sweep(torch, gft, dev, precisions=("fp32", "bf16x3"), n_graphs=10000, total=
         g = W.make_graph(fam, n, gs)
         Ls.append(gft.laplacian(g.W, g.s))
         phis.append(g.phis)
-    t1 = time.perf_counter()
+    t0 = time.perf_counter()
     plans = gft.plans_from_laplacians(Ls, phis, jit=False)
     torch.cuda.synchronize()
-    t2 = time.perf_counter()
+    build_s = time.perf_counter() - t0
     del Ls
-    entry = [keys[(f, n, gs)] for f, n, gs, b, ss in specs]
+    entry_idx = [keys[(f, n, gs)] for f, n, gs, b, ss in specs]
+    entry = [plans[i] for i in entry_idx]
     batches = [b for f, n, gs, b, ss in specs]
     ns = [n for f, n, gs, b, ss in specs]
-    # one input and one output buffer; entry views start 16-byte aligned
     offs, o = [], 0
     for b, n in zip(batches, ns):
         offs.append(o)
         o += (b * n + 3) & ~3
-    X = torch.randn(o, device=dev)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(seed)
+    X = torch.randn(o, device=dev, generator=gen)
     Y = torch.empty(o, device=dev)
     xs = [X[a:a + b * n].view(b, n) for a, b, n in zip(offs, batches, ns)]
     ys = [Y[a:a + b * n].view(b, n) for a, b, n in zip(offs, batches, ns)]
     coeffs = sum(b * n for b, n in zip(batches, ns))
-    out = {"graphs": len(specs), "distinct_plans": len(graphs), "coeffs": coeffs,
-           "build_graphs_s": round(t1 - t0, 1), "build_plans_s": round(t2 - t1, 1)}
-    for prec in precisions:
-        t3 = time.perf_counter()
-        bt = gft.Batch([plans[i] for i in entry], batches, precision=prec)
-        bt.forward(xs, ys)
-        torch.cuda.synchronize()
-        t4 = time.perf_counter()
-        t = _timed(torch, lambda: bt.forward(xs, ys), reps=reps)
-        out[prec] = {"gcoeffs_s": round(coeffs / t / 1e9, 1), "ms": round(t * 1e3, 2),
-                     "batch_create_s": round(t4 - t3, 1)}
-        del bt
-    # dense baseline: grouped by size
-    prev = torch.backends.cuda.matmul.allow_tf32
-    torch.backends.cuda.matmul.allow_tf32 = False
-    by_n = collections.defaultdict(list)
-    for j, n in enumerate(ns):
-        by_n[n].append(j)
-    groups, basis = [], {}
-    for n, js in by_n.items():
-        for j in js:
-            if entry[j] not in basis:
-                basis[entry[j]] = torch.from_numpy(plans[entry[j]].basis()).float().to(dev)
-        U = torch.stack([basis[entry[j]] for j in js])
-        Xg = torch.stack([xs[j] for j in js])
-        groups.append((Xg, U, torch.empty_like(Xg)))
-    t = _timed(torch, lambda: [torch.bmm(a, u, out=c) for a, u, c in groups], reps=reps)
-    out["dense_bmm_fp32"] = {"gcoeffs_s": round(coeffs / t / 1e9, 1), "ms": round(t * 1e3, 2),
-                             "size_classes": len(groups)}
-    torch.backends.cuda.matmul.allow_tf32 = prev
-    return out
+    # algorithmic bytes of a step: every coefficient read and written once in
+    # FP32, and every distinct plan's leaf bases once (4 B per entry: FP32 on
+    # CUDA cores, hi + lo halves on the tensor cores)
+    basis_bytes = sum(4 * sum(len(lv) ** 2 for lv in p.leaves()) for p in plans)
+    return {"specs": specs, "plans": plans, "entry": entry, "entry_idx": entry_idx, "batches": batches, "ns": ns,
+            "X": X, "Y": Y, "xs": xs, "ys": ys, "coeffs": coeffs, "basis_bytes": basis_bytes,
+            "build_s": build_s, "distinct": len(plans)}
+
+
+def sweep_errors(torch, S, picked):
+    """Relative L2 error of each picked graph's output against x U in FP64
+    (U: the plan's FP64 basis, whose parity with the oracle the tests check);
+    returns (max, median) over the picked graphs."""
+    errs = []
+    for j in picked:
+        p = S["entry"][j]
+        U = torch.from_numpy(p.basis()).to(S["xs"][j].device)
+        ref = S["xs"][j].double() @ U
+        errs.append(float((S["ys"][j].double() - ref).norm() / ref.norm()))
+    return max(errs), statistics.median(errs)
+
+
+def stratified_picks(specs):
+    picked, seen, largest = [], set(), {}
+    for j, (fam, n, gs, b, ss) in enumerate(specs):
+        key = (fam, int(np.log2(n)))
+        if key not in seen:
+            seen.add(key)
+            picked.append(j)
+        if fam not in largest or n > specs[largest[fam]][1]:
+            largest[fam] = j
+    return sorted(set(picked) | set(largest.values()))
 
 
 def run_ours(args, rank, world, local_rank):
@@ -503,122 +697,86 @@ def run_ours(args, rank, world, local_rank):
         build()
     if dist is not None:
         dist.barrier()
-    (g, batch, seed), = W.config2()
-    n = g.n
-    plan = gft.Plan(gft.laplacian(g.W, g.s), g.phis, split_components=True)
+    S = sweep_setup(torch, gft, dev, seed=sharding.rank_seed(1005, rank))
     stream = torch.cuda.current_stream()
-    # rotating input/output sets, together larger than L2, so every step reads
-    # its input from HBM
-    x_host = W.signals(batch, n, sharding.rank_seed(seed, rank))
-    nbytes = batch * n * 4
-    nsets = 2 if args.profile else max(2, -(-4 * L2_BYTES // (2 * nbytes)))
-    xs = [torch.from_numpy(x_host).to(dev) for _ in range(nsets)]
-    for i in range(1, nsets):
-        xs[i].mul_(1.0 + 1e-3 * i)
-    ys = [torch.empty_like(xs[0]) for _ in range(nsets)]
+    t0 = time.perf_counter()
+    bt = gft.Batch(S["entry"], S["batches"], precision="fp16x3").bind(S["xs"], S["ys"])
+    create_s = time.perf_counter() - t0
 
-    # parity spot check against the FP64 oracle (rank 0, 2^14 signals)
-    err = None
-    if rank == 0 and not args.profile:
-        from oracle import gft as ogft
-        from oracle import graph as ograph
-        ref = ogft.fast_gft(ograph.laplacian(g.W, g.s), g.phis, split_components=True)
-        U = plan.basis()
-        k = 1 << 14
-        y = plan.forward(xs[0][:k].contiguous()).cpu().numpy().astype(np.float64)
-        yo = ogft.forward_dense(ref.U, x_host[:k].astype(np.float64))
-        lam = ref.lam
-        tol = 1e-9 * max(1.0, float(np.abs(lam).max()))
-        ya, start = np.empty_like(yo), 0
-        for j in range(1, n + 1):
-            if j == n or lam[j] - lam[j - 1] > tol:
-                S = list(range(start, j))
-                ya[:, S] = yo[:, S] @ (U[:, S].T @ ref.U[:, S]).T
-                start = j
-        err = float(np.linalg.norm(y - ya) / np.linalg.norm(ya))
+    def step():
+        bt.forward(stream=stream)
 
-    def step(i):
-        plan.forward(xs[i % nsets], out=ys[i % nsets], stream=stream)
-
-    for i in range(args.warmup):
-        step(i)
+    for _ in range(max(3, args.warmup)):
+        step()
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
-    # per-launch durations: events around a sample of about 256 launches
-    # spread over the timed region (an event pair around every launch would
-    # put its own gap between consecutive kernels)
-    every = max(1, args.steps // 256)
+    # per-step durations: an event pair around a sample of about 64 steps
+    every = max(1, args.steps // 64)
     sampled = list(range(0, args.steps, every))
     starts = {i: torch.cuda.Event(enable_timing=True) for i in sampled}
     ends = {i: torch.cuda.Event(enable_timing=True) for i in sampled}
     with ClockSampler(local_rank) as clk:
         torch.cuda.synchronize()
-        t0 = torch.cuda.Event(enable_timing=True)
-        t1 = torch.cuda.Event(enable_timing=True)
-        t0.record(stream)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
         for i in range(args.steps):
             if i in starts:
                 starts[i].record(stream)
-                step(i)
+                step()
                 ends[i].record(stream)
             else:
-                step(i)
-        t1.record(stream)
+                step()
+        e1.record(stream)
         torch.cuda.synchronize()
-        total_ms = t0.elapsed_time(t1)
-    launch_ms = [starts[i].elapsed_time(ends[i]) for i in sampled]
-    if args.profile:
-        if rank == 0:
-            inf = plan.info
-            print(json.dumps({"profile_run": True, "ms_per_step": total_ms / args.steps,
-                              "kernel_hash": _kernel_hash(plan), "tile_signals": inf["tile_signals"],
-                              "threads": inf["threads"], "jit": inf["jit"],
-                              "config": {"workload": WORKLOAD, "sets": nsets}}), flush=True)
-        return
+        total_ms = e0.elapsed_time(e1)
+    step_ms = [starts[i].elapsed_time(ends[i]) for i in sampled]
     total_ms = sharding.max_over_ranks(total_ms, dist, dev)
     ms_per_step = total_ms / args.steps
-    coeffs_per_step = batch * n
-    value = coeffs_per_step * world / (total_ms / 1e3) * args.steps
+    coeffs = S["coeffs"]
+    value = coeffs * world / (total_ms / 1e3) * args.steps
+    picked = stratified_picks(S["specs"])
+    err_max, err_med = sweep_errors(torch, S, picked)
+    launches = bt.launches
 
-    # dominant (only) kernel: the fused transform, one launch per step
-    avg_launch_s = statistics.mean(launch_ms) / 1e3
-    alg_bytes = 8 * coeffs_per_step          # FP32 read + write per coefficient
+    # roofline of the step (one graph replay): algorithmic bytes / step time
     peak, peak_kind = _peaks()
-    achieved = alg_bytes / avg_launch_s / 1e9
-    khash = _kernel_hash(plan)
-    traffic = _traffic_from_profile(khash)
+    alg_bytes = 8 * coeffs + S["basis_bytes"]
+    avg_step_s = statistics.mean(step_ms) / 1e3
+    achieved = alg_bytes / avg_step_s / 1e9
 
-    # inverse and the dense GEMM on the same data (context)
-    def timed(fn, reps=20):
-        for i in range(3):
-            fn(i)
+    # end to end through the public API with host buffers: every step copies
+    # all inputs from pinned host memory, replays the batch and reads all
+    # coefficients back
+    Xh = torch.empty(S["X"].numel(), dtype=torch.float32).pin_memory()
+    Xh.copy_(S["X"])
+    Yh = torch.empty_like(Xh).pin_memory()
+
+    def e2e_step():
+        S["X"].copy_(Xh, non_blocking=True)
+        bt.forward(stream=stream)
+        Yh.copy_(S["Y"], non_blocking=True)
         torch.cuda.synchronize()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for i in range(reps):
-            fn(i)
-        b.record(stream)
+
+    def link_step():
+        S["X"].copy_(Xh, non_blocking=True)
+        Yh.copy_(S["Y"], non_blocking=True)
         torch.cuda.synchronize()
-        return a.elapsed_time(b) / reps / 1e3
 
-    inv_s = timed(lambda i: plan.inverse(ys[i % nsets], out=xs[(i + 1) % nsets], stream=stream))
-    Ut = torch.from_numpy(plan.basis()).float().to(dev)
-    prev_tf32 = torch.backends.cuda.matmul.allow_tf32
-    torch.backends.cuda.matmul.allow_tf32 = False
-    dense_s = timed(lambda i: torch.matmul(xs[i % nsets], Ut, out=ys[i % nsets]))
-    torch.backends.cuda.matmul.allow_tf32 = prev_tf32
-
-    # end to end through the public API with host buffers (pinned)
-    xh = torch.from_numpy(x_host).pin_memory()
-    yh = torch.empty_like(xh).pin_memory()
-    plan.forward_host(xh, out=yh)
-    e2e_steps = max(3, min(args.steps, 20))
+    e2e_step()
+    n_e2e = 5
     t = time.perf_counter()
-    for _ in range(e2e_steps):
-        plan.forward_host(xh, out=yh)
-    e2e_s = (time.perf_counter() - t) / e2e_steps
+    for _ in range(n_e2e):
+        e2e_step()
+    e2e_s = (time.perf_counter() - t) / n_e2e
+    link_step()
+    t = time.perf_counter()
+    for _ in range(n_e2e):
+        link_step()
+    link_s = (time.perf_counter() - t) / n_e2e
+    io_bytes = S["X"].numel() * 4
+    del Xh, Yh
 
     if dist is not None:
         dist.barrier()
@@ -626,36 +784,38 @@ def run_ours(args, rank, world, local_rank):
         return
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        rate, reps, el, cores = oracle_rate(1 << 18, 10.0)
-        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"oracle.forward_staged (FP64 numpy) on 2^18 of the 2^20 signals x {reps} reps "
-                         f"({el:.1f} s)"}
+        rate, reps, el, cores, c = oracle_rate(10.0)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": oracle_sample_text(reps, el, c)}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "graph": "skeleton25 (1 Haar stage, leaves 15/5/5)",
-                   "signals_per_gpu": batch, "n": n, "precision": "fp32",
-                   "l2": f"{nsets} rotating input/output sets ({nsets * 2 * nbytes / 2**20:.0f} MiB) > L2"},
-        "err_vs_fp64": err,
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
-                     "alg_bytes_per_launch": alg_bytes, "launches_timed": len(launch_ms),
-                     "kernel": "gft_jit_fwd_* (plan-specialised)" if plan.info["jit"] else "gft_apply_kernel"},
-        "e2e": {"value": coeffs_per_step / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nbytes,
-                "d2h_bytes_per_step": nbytes},
-        "gpu_launches": args.steps,
-        "inverse": {"value": coeffs_per_step / inv_s, "unit": UNIT},
-        "dense_gemm_fp32": {"value": coeffs_per_step / dense_s, "unit": UNIT,
-                            "what": "torch.matmul(x, U) FP32, TF32 off"},
+        "warmup": max(3, args.warmup), "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 (leaves >= 64 nodes: fp16 hi+lo split, fp32 accumulate)",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "graphs": len(S["specs"]), "distinct_plans": S["distinct"],
+                   "families": "path, cycle, grid, skeleton25, bipartite; n log-uniform 8..1024",
+                   "coeffs_per_gpu": coeffs, "precision": "fp32 CUDA cores (leaves < 64), fp16x3 tensor cores",
+                   "l2": "inputs and outputs 2 x %.2f GiB > L2" % (io_bytes / 2**30),
+                   "plan_build_s": round(S["build_s"], 1), "batch_create_s": round(create_s, 1)},
+        "err_vs_fp64": {"max": err_max, "median": err_med, "graphs_checked": len(picked),
+                        "what": "rel. L2 per graph vs x U in FP64 (plan basis), every family x size octave"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "peak_source": peak_kind, "alg_bytes_per_step": alg_bytes,
+                     "alg_bytes_note": "8 B per coefficient + every distinct plan's leaf bases once (4 B per entry)",
+                     "steps_timed": len(step_ms),
+                     "kernel": "one graph replay: table-driven batch classes + few-signals tensor-core kernel"},
+        "e2e": {"value": coeffs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes,
+                "host_link_only_coeffs_s": coeffs / link_s, "frac_of_host_link": link_s / e2e_s},
+        "gpu_launches": launches * args.steps,
+        "launches_per_step": launches,
         "clocks": clk.summary(),
-        "kernel_hash": khash,
         "cpu_baseline": cpu,
     }
+    del bt
     if not args.no_extras and world == 1:
         line["extras"] = extras(torch, gft, dev)
+        line["extras"]["config2_skeleton"] = config2_extras(torch, gft, dev)
         if not args.no_sweep:
-            line["extras"]["config5_sweep"] = sweep(torch, gft, dev)
+            line["extras"]["config5_sweep"] = sweep_variants(torch, gft, dev, S)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -670,7 +830,16 @@ def run_probe(args):
     from paper_1907_07875_gb300.build import build
     build()
     dev = torch.device("cuda", 0)
-    if args.probe.startswith("givens"):
+    if args.probe.startswith("sweep"):
+        prec = args.precision if args.precision != "fp32" or args.kernel == "table" else "fp16x3"
+        if args.probe == "sweep":
+            S = sweep_setup(torch, gft, dev)
+        else:
+            S = sweep_setup(torch, gft, dev, specs=W.config5_specs(n_graphs=1000, total_coeffs=1 << 25))
+        bt = gft.Batch(S["entry"], S["batches"], precision=prec).bind(S["xs"], S["ys"])
+        for _ in range(3):
+            bt.forward()
+    elif args.probe.startswith("givens"):
         import math
         from paper_1907_07875_gb300.learned import xor_pairs
         n = int(args.probe[len("givens"):])
@@ -696,18 +865,19 @@ def run_probe(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20000)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the context measurements")
     ap.add_argument("--no-sweep", action="store_true", help="skip the 10^4-graph size sweep in the extras")
-    ap.add_argument("--probe", choices=["skeleton25", "grid8", "grid16", "grid32", "cycle256", "givens16", "givens64"],
-                    help="ncu capture helper: one plan, three forwards of 2^25 coefficients, nothing timed")
+    ap.add_argument("--probe", choices=["skeleton25", "grid8", "grid16", "grid32", "cycle256", "givens16", "givens64",
+                                        "sweep", "sweep_small"],
+                    help="ncu capture helper, nothing timed: one plan, three forwards of 2^25 coefficients; "
+                         "'sweep': the size sweep's batch (fp16x3 unless --precision), three replays; "
+                         "'sweep_small': 1000 graphs of the same recipe, 2^25 coefficients")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "bf16x3", "fp16x3"])
     ap.add_argument("--kernel", default="auto", choices=["auto", "table", "wide"])
-    ap.add_argument("--profile", action="store_true",
-                    help="forward steps only, 2 buffer sets (for ncu captures)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -342,15 +342,21 @@ gft_status gft_device_error(gft_plan_t plan, int32_t* code);
  * forward by one CUDA-graph launch, captured on first use and replayed.
  * Plans are routed by leaf width:
  *   - leaves of at most 64 nodes (unless the plan prefers the wide-leaf
- *     kernel): ONE persistent table-driven kernel over a work list of
- *     (plan, tile) items, with per-plan tile shapes timed at creation;
+ *     kernel): persistent table-driven kernels, one launch per size class
+ *     (row stride n|1 up to 17, 33, 65, 129, 257), each CTA walking a
+ *     contiguous, cost-balanced range of (plan, tile) items with
+ *     double-buffered tile loads; per-plan tile shapes timed at creation;
  *   - leaves of 33..512 nodes: ONE persistent wide-leaf kernel over the
  *     (plan, tile) items of those plans;
- *   - with a tensor-core precision, plans with a leaf of 64 or more nodes
- *     (at most 256): ONE persistent pack kernel and ONE persistent
- *     tensor-core kernel over the tiles of all of them (per size class,
- *     n <= 256 and n > 256); a timeout in these kernels is reported in the
- *     error word of the class's first plan.
+ *   - with a tensor-core precision, plans with a leaf of 64 or more nodes:
+ *     plans with at most 4096 signals (or leaves of 257..512 nodes) go to
+ *     the few-signals tensor-core kernel (signals on the MMA's N axis, 16
+ *     or 32 per tile; leaves up to 512; one launch per shared-memory class);
+ *     the others (leaves up to 256) to ONE persistent pack kernel and ONE
+ *     persistent tensor-core kernel (128 signals per tile) per size class
+ *     (n <= 256 and n > 256); a timeout in these kernels is reported in the
+ *     error word of the plan being transformed (pack / 128-signal kernel:
+ *     the class's first plan).
  * The groups run on forked streams inside the graph and join at its end.
  *  plans[n_plans]  plans created with device bases; the batch does not own
  *                  them, and they must outlive it.  A plan may appear more
@@ -372,6 +378,9 @@ gft_status gft_batch_forward(gft_batch_t batch, const float* const* x, float* co
  * group: signals per tile and threads per block (0 for entries routed to
  * the wide-leaf or tensor-core kernels). */
 gft_status gft_batch_get_tile(gft_batch_t batch, int32_t i, int32_t* tile, int32_t* threads);
+/* Kernel launches of this library in one gft_batch_forward (the nodes of
+ * the captured graph that run our kernels). */
+gft_status gft_batch_get_launches(gft_batch_t batch, int32_t* launches);
 gft_status gft_batch_destroy(gft_batch_t batch);
 
 /*

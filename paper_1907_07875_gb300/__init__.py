@@ -395,10 +395,26 @@ class Batch:
         self._h = h
         self.batches = b
 
-    def forward(self, xs, ys, stream=None):
+    def bind(self, xs, ys):
+        """Marshal the signal and coefficient tensors once (one per plan);
+        ``forward()`` without arguments then replays the batch on them.  The
+        caller keeps the tensors alive while they are bound."""
         k = len(self.plans)
-        xa = (C.c_void_p * k)(*[t.data_ptr() for t in xs])
-        ya = (C.c_void_p * k)(*[t.data_ptr() for t in ys])
+        if len(xs) != k or len(ys) != k:
+            raise ValueError("one input and one output tensor per plan")
+        self._bound = ((C.c_void_p * k)(*[t.data_ptr() for t in xs]),
+                       (C.c_void_p * k)(*[t.data_ptr() for t in ys]), list(xs), list(ys))
+        return self
+
+    def forward(self, xs=None, ys=None, stream=None):
+        if xs is None and ys is None:
+            if getattr(self, "_bound", None) is None:
+                raise ValueError("no tensors bound: pass xs and ys or call bind() first")
+            xa, ya, _, ys = self._bound
+        else:
+            k = len(self.plans)
+            xa = (C.c_void_p * k)(*[t.data_ptr() for t in xs])
+            ya = (C.c_void_p * k)(*[t.data_ptr() for t in ys])
         _check(lib().gft_batch_forward(self._h, C.cast(xa, C.c_void_p), C.cast(ya, C.c_void_p),
                                        _stream_ptr(stream)))
         return ys
@@ -407,6 +423,13 @@ class Batch:
         t, th = C.c_int32(), C.c_int32()
         _check(lib().gft_batch_get_tile(self._h, i, C.byref(t), C.byref(th)))
         return t.value, th.value
+
+    @property
+    def launches(self) -> int:
+        """Kernel launches of this library per forward (graph nodes)."""
+        n = C.c_int32()
+        _check(lib().gft_batch_get_launches(self._h, C.byref(n)))
+        return n.value
 
     def close(self):
         if getattr(self, "_h", None):

@@ -62,6 +62,7 @@ SIGNATURES = {
     "gft_batch_create": (c_status, [C.c_int32, P, P, C.c_uint32, C.POINTER(C.c_void_p)]),
     "gft_batch_forward": (c_status, [C.c_void_p, P, P, P]),
     "gft_batch_get_tile": (c_status, [C.c_void_p, C.c_int32, I32P, I32P]),
+    "gft_batch_get_launches": (c_status, [C.c_void_p, I32P]),
     "gft_batch_destroy": (c_status, [C.c_void_p]),
     "gft_approx_create": (c_status, [C.c_int32, P, C.c_int32, P, C.c_int32, C.c_uint32, C.POINTER(C.c_void_p)]),
     "gft_approx_destroy": (c_status, [C.c_void_p]),

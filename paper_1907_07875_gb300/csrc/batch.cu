@@ -1,25 +1,36 @@
 // Mixed batches: many plans (graphs of different sizes and structures),
-// each with its own batch of signals, transformed forward by ONE persistent
-// kernel launch that is captured in a CUDA graph and replayed.
+// each with its own batch of signals, transformed forward by persistent
+// kernel launches that are captured in ONE CUDA graph and replayed.
 //
-// Work list: plan p contributes ceil(batch_p / TS_p) items, one per tile of
-// TS_p = RS_p * 128 signals.  Plans are ordered by decreasing cost per item
-// so the long items start first.  Every CTA repeatedly takes the next item
-// from a device counter (atomicAdd), finds its plan by binary search over
-// the plans' first item indices, reloads the plan's program (stage pairs,
-// node lists, leaf matrices) into shared memory only when the plan changes,
-// and runs the same table-driven tile code as the single-plan kernel
-// (apply_core.cuh): cp.async tile load, in-place stages and leaf products,
-// permuted coalesced store.
+// Table-driven group (plans whose leaves all fit the CUDA-core tile code of
+// apply_core.cuh, at most 64 nodes):
+//   * Work list: plan p contributes ceil(batch_p / TS_p) items, one per
+//     tile of TS_p = RS_p * 128 signals, plans in order of decreasing cost
+//     per item.  Plans are split into size classes by their padded row
+//     stride (n | 1 up to 17, 33, 65, 129, 257); each class is one launch
+//     whose shared tile is sized for its own largest plan, so classes of
+//     small graphs keep many CTAs per SM.
+//   * Static schedule: the host cuts the class's item sequence into one
+//     contiguous range per CTA of roughly equal estimated cost (bytes moved
+//     plus leaf FMAs plus a fixed cost per item), and records the plan slot
+//     of each range's first item.  A CTA walks its range in order, so the
+//     items of one plan mostly stay on one CTA and its program (stage pairs,
+//     node lists, leaf matrices) is copied into shared memory only when the
+//     plan changes -- no atomics and no search per item.
+//   * Pipeline: two tile buffers; the cp.async copies of item i+1 (whichever
+//     plan it belongs to: the copy needs only the plan's descriptor) are in
+//     flight while item i runs its in-place stages and leaf products and its
+//     permuted, coalesced store (the same tile code as the single-plan
+//     kernel, so outputs agree bit for bit).  Classes whose tile is too large
+//     for two buffers and two CTAs per SM run single-buffered.
 //
 // Autotuner: at creation, every plan is timed alone in this kernel with each
 // admissible RS_p (signals per thread: 1, 2 or 4, limited by the plan's leaf
-// widths) on a scratch batch, and the fastest tile shape is kept.
+// widths and by a tile of at most kTileCapBytes) on a scratch batch, and the
+// fastest tile shape is kept.
 //
-// The counter lives in device memory owned by the batch and is reset by a
-// memset node at the start of every replay.  Changing the signal pointers
-// only rewrites the per-plan descriptors in device memory; the captured graph
-// is reused.
+// Changing the signal pointers only rewrites the per-plan descriptors in
+// device memory; the captured graph is reused.
 #include <algorithm>
 #include <map>
 #include <memory>
@@ -34,7 +45,12 @@ namespace {
 
 constexpr int kBatchThreads = 128;
 constexpr int kTcMinLeaf = 64;   // leaves this wide go to the tensor cores in a tensor-core batch
+constexpr int64_t kTcnMaxBatch = 4096;   // graphs with at most this many signals use the few-signals kernel
 constexpr int kBatchSmemLimit = 232448;
+constexpr size_t kTileCapBytes = 34816;        // largest tile a plan may choose (128 signals x 65 nodes + slack)
+constexpr size_t kDoubleBufBytes = 72 * 1024;  // two tile buffers only if they fit in this
+constexpr int kClassStride[] = {17, 33, 65, 129, 257};
+constexpr int kClasses = 5;
 
 struct BatchPlanDev {
     const int* ints;
@@ -42,68 +58,80 @@ struct BatchPlanDev {
     const float* x;
     float* y;
     long long batch;
-    long long item0;      // first item index of this plan
+    long long item0;      // first item index of this plan within its class
     int n, np, n_pairs, n_leaves, ints_count, n_pre_pairs;
     int off_labels, off_outpos, off_src, off_desc;
     int mats_smem, rs, ts;
     float inv_n;
 };
 
+__device__ __forceinline__ KArgs batch_kargs(const BatchPlanDev& D) {
+    KArgs a{};
+    a.ints = D.ints;
+    a.mats = D.mats;
+    a.x = D.x;
+    a.y = D.y;
+    a.batch = D.batch;
+    a.n = D.n;
+    a.np = D.np;
+    a.n_pairs = D.n_pairs;
+    a.n_pre_pairs = D.n_pre_pairs;
+    a.n_leaves = D.n_leaves;
+    a.ints_count = D.ints_count;
+    a.off_labels = D.off_labels;
+    a.off_outpos = D.off_outpos;
+    a.off_src = D.off_src;
+    a.off_desc = D.off_desc;
+    a.mats_smem = D.mats_smem;
+    a.ts = D.ts;
+    a.nbuf = 1;
+    a.inverse = 0;
+    a.inv_n = D.inv_n;
+    return a;
+}
+
+// CTA b runs items [range[b], range[b+1]) of its class; first_slot[b] is
+// the plan slot of item range[b].  plans[] holds the class's plans in slot
+// order with their first item indices.
 __global__ void __launch_bounds__(kBatchThreads) gft_batch_kernel(const BatchPlanDev* __restrict__ plans, int n_plans,
-                                                                 long long total_items,
-                                                                 unsigned long long* counter, int mats_cap,
-                                                                 int ints_cap) {
+                                                                 const long long* __restrict__ range,
+                                                                 const int* __restrict__ first_slot, int mats_cap,
+                                                                 int ints_cap, int tile_cap, int nbuf) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float* mats = reinterpret_cast<float*>(smem_raw);
     int* ints = reinterpret_cast<int*>(smem_raw + sizeof(float) * mats_cap);
-    float* tile_buf = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(ints) + sizeof(int) * ints_cap);
-    __shared__ long long s_item;
-    __shared__ int s_plan;
+    float* bufs = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(ints) + sizeof(int) * ints_cap);
     const int tid = threadIdx.x;
-    int loaded = -1;
-    while (true) {
-        if (tid == 0) {
-            const long long it = (long long)atomicAdd(counter, 1ull);
-            int p = 0;
-            if (it < total_items) {
-                int lo = 0, hi = n_plans - 1;
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (plans[mid].item0 <= it) lo = mid;
-                    else hi = mid - 1;
-                }
-                p = lo;
+    const long long it0 = range[blockIdx.x], it1 = range[blockIdx.x + 1];
+    if (it0 >= it1) return;
+    auto slot_of = [&](int s, long long it) {
+        while (s + 1 < n_plans && plans[s + 1].item0 <= it) ++s;
+        return s;
+    };
+    int slot = slot_of(first_slot[blockIdx.x], it0);
+    {
+        const BatchPlanDev D0 = plans[slot];
+        issue_tile_load<float, kBatchThreads>(batch_kargs(D0), nullptr, bufs, it0 - D0.item0);
+    }
+    cp_async_commit();
+    int loaded = -1, cur = 0;
+    for (long long it = it0; it < it1; ++it) {
+        const BatchPlanDev D = plans[slot];
+        const KArgs a = batch_kargs(D);
+        float* buf = bufs + (size_t)cur * tile_cap;
+        int nslot = slot;
+        if (nbuf == 2) {
+            // the other buffer was released by the barrier ending the last item
+            if (it + 1 < it1) {
+                nslot = slot_of(slot, it + 1);
+                const BatchPlanDev Dn = plans[nslot];
+                issue_tile_load<float, kBatchThreads>(batch_kargs(Dn), nullptr, bufs + (size_t)(cur ^ 1) * tile_cap,
+                                                      it + 1 - Dn.item0);
             }
-            s_item = it;
-            s_plan = p;
+            cp_async_commit();
         }
-        __syncthreads();
-        const long long it = s_item;
-        const int p = s_plan;
-        if (it >= total_items) break;
-        const BatchPlanDev D = plans[p];
-        KArgs a{};
-        a.ints = D.ints;
-        a.mats = D.mats;
-        a.x = D.x;
-        a.y = D.y;
-        a.batch = D.batch;
-        a.n = D.n;
-        a.np = D.np;
-        a.n_pairs = D.n_pairs;
-        a.n_pre_pairs = D.n_pre_pairs;
-        a.n_leaves = D.n_leaves;
-        a.ints_count = D.ints_count;
-        a.off_labels = D.off_labels;
-        a.off_outpos = D.off_outpos;
-        a.off_src = D.off_src;
-        a.off_desc = D.off_desc;
-        a.mats_smem = D.mats_smem;
-        a.ts = D.ts;
-        a.nbuf = 1;
-        a.inverse = 0;
-        a.inv_n = D.inv_n;
-        if (p != loaded) {
+        if (slot != loaded) {
+            // the barrier ending the last item released the old program
             for (int i = tid; i < D.ints_count; i += kBatchThreads) ints[i] = D.ints[i];
             __syncthreads();
             const int* desc = ints + D.off_desc;
@@ -113,24 +141,63 @@ __global__ void __launch_bounds__(kBatchThreads) gft_batch_kernel(const BatchPla
                 float* dst = mats + desc[kLeafDesc * k + 4];
                 for (int e = tid; e < bk * bk; e += kBatchThreads) dst[e] = src[e];
             }
-            loaded = p;
+            loaded = slot;
         }
-        const long long tile = it - D.item0;
-        const int* src_slot = ints + D.off_src;
-        issue_tile_load<float, kBatchThreads>(a, src_slot, tile_buf, tile);
-        cp_async_commit();
-        cp_async_wait0();
+        if (nbuf == 2) cp_async_wait1();
+        else cp_async_wait0();
+        __syncthreads();   // tile and program visible to every thread
+        if (D.rs == 4) compute_tile<float, 4, kBatchThreads>(a, ints, mats, buf);
+        else if (D.rs == 2) compute_tile<float, 2, kBatchThreads>(a, ints, mats, buf);
+        else compute_tile<float, 1, kBatchThreads>(a, ints, mats, buf);
         __syncthreads();
-        if (D.rs == 4) compute_tile<float, 4, kBatchThreads>(a, ints, mats, tile_buf);
-        else if (D.rs == 2) compute_tile<float, 2, kBatchThreads>(a, ints, mats, tile_buf);
-        else compute_tile<float, 1, kBatchThreads>(a, ints, mats, tile_buf);
-        __syncthreads();
-        store_tile<float, kBatchThreads>(a, src_slot, tile_buf, tile);
-        __syncthreads();
+        store_tile<float, kBatchThreads>(a, ints + D.off_src, buf, it - D.item0);
+        __syncthreads();   // buffer and program free
+        if (nbuf == 2) {
+            cur ^= 1;
+        } else if (it + 1 < it1) {
+            nslot = slot_of(slot, it + 1);
+            const BatchPlanDev Dn = plans[nslot];
+            issue_tile_load<float, kBatchThreads>(batch_kargs(Dn), nullptr, bufs, it + 1 - Dn.item0);
+            cp_async_commit();
+        }
+        slot = nslot;
     }
+    cp_async_wait0();
 }
 
 int rs_cap(int max_bucket) { return max_bucket <= 16 ? 4 : (max_bucket <= 32 ? 2 : 1); }
+
+// admissible RS for a plan: leaf widths and the tile cap (RS = 1 always)
+bool rs_admissible(const gft_plan_s& p, int rs) {
+    if (rs > rs_cap(p.dev.max_bucket)) return false;
+    return rs == 1 || (size_t)rs * kBatchThreads * (size_t)(p.n | 1) * sizeof(float) <= kTileCapBytes;
+}
+
+int class_of(int np) {
+    for (int c = 0; c < kClasses; ++c)
+        if (np <= kClassStride[c]) return c;
+    return kClasses - 1;
+}
+
+// One launch of the table-driven group: the plans of one size class.
+struct BatchClass {
+    std::vector<int> members;              // slot -> index into the group's plan list
+    std::vector<BatchPlanDev> desc;        // slot order
+    BatchPlanDev* d_desc = nullptr;
+    long long* d_range = nullptr;          // grid + 1 item boundaries
+    int* d_first = nullptr;                // grid plan slots
+    long long total_items = 0;
+    int mats_cap = 0, ints_cap = 0, tile_cap = 0, nbuf = 1;
+    size_t smem = 0;
+    int grid = 0;
+    void release() {
+        for (void** q : {(void**)&d_desc, (void**)&d_range, (void**)&d_first})
+            if (*q) {
+                cudaFree(*q);
+                *q = nullptr;
+            }
+    }
+};
 
 }  // namespace
 }  // namespace gft
@@ -139,29 +206,24 @@ using namespace gft;
 
 struct gft_batch_s {
     // routing of the caller's plans: 0 = table-driven batch kernel, 1 = wide-leaf
-    // batch kernel, 2 = tensor-core sequence; idx = position within its group
+    // batch kernel, 2 = tensor-core sequence (pack + leaf kernels, 128 signals
+    // per tile), 3 = few-signals tensor-core kernel; idx = position within its group
     uint32_t precision = GFT_PREC_FP32;
     std::vector<int> kind, idx;
     std::vector<int64_t> user_batch;
-    std::vector<int> table_users, wide_users, tc_users;
-    std::vector<gft_plan_s*> tc_plans;
-    std::vector<int64_t> tc_batches;
+    std::vector<int> table_users, wide_users, tc_users, tcn_users;
+    std::vector<gft_plan_s*> tc_plans, tcn_plans;
+    std::vector<int64_t> tc_batches, tcn_batches;
     void* wide = nullptr;                  // wide-leaf group (wide.cu)
     void* tcb = nullptr;                   // tensor-core group (tc.cu)
+    void* tcnb = nullptr;                  // few-signals tensor-core group (tcn.cu)
     cudaStream_t side[2] = {};
     cudaEvent_t ev_fork = nullptr, ev_join[2] = {};
     // table-driven group
     std::vector<gft_plan_s*> plans;        // table-driven group, group order
     std::vector<int64_t> batches;
-    std::vector<int> order;                // descriptor slot -> user index
-    std::vector<int> rs;                   // per user index
-    std::vector<BatchPlanDev> desc;        // descriptor slot order
-    BatchPlanDev* d_desc = nullptr;
-    unsigned long long* d_counter = nullptr;
-    long long total_items = 0;
-    int mats_cap = 0, ints_cap = 0;
-    size_t smem = 0;
-    int grid = 0;
+    std::vector<int> rs;                   // per group index
+    std::vector<BatchClass> classes;       // non-empty size classes
     cudaStream_t cap_stream = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -169,6 +231,7 @@ struct gft_batch_s {
     ~gft_batch_s() {
         if (wide) gft::wide_batch_free(wide);
         if (tcb) gft::tc_batch_free(tcb);
+        if (tcnb) gft::tcn_batch_free(tcnb);
         for (auto& st : side)
             if (st) cudaStreamDestroy(st);
         if (ev_fork) cudaEventDestroy(ev_fork);
@@ -177,8 +240,7 @@ struct gft_batch_s {
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
         if (cap_stream) cudaStreamDestroy(cap_stream);
-        if (d_desc) cudaFree(d_desc);
-        if (d_counter) cudaFree(d_counter);
+        for (auto& c : classes) c.release();
     }
 };
 
@@ -207,61 +269,111 @@ BatchPlanDev make_desc(const gft_plan_s& p, int rs, int64_t batch) {
     return d;
 }
 
-// lays out items and sizes shared memory for the current rs choices
-void layout(gft_batch_s& b) {
-    const int k = (int)b.plans.size();
-    std::vector<double> cost(k);
-    for (int i = 0; i < k; ++i) {
-        double fl = 0;
-        for (auto& lf : b.plans[i]->leaves) fl += (double)lf.m() * lf.m();
-        cost[i] = (fl + 8.0 * b.plans[i]->n) * b.rs[i];
-    }
-    b.order.resize(k);
-    std::iota(b.order.begin(), b.order.end(), 0);
-    std::stable_sort(b.order.begin(), b.order.end(), [&](int a, int c) { return cost[a] > cost[c]; });
-    b.desc.clear();
-    b.total_items = 0;
-    b.mats_cap = 0;
-    b.ints_cap = 0;
-    size_t tile_cap = 0;
-    for (int slot = 0; slot < k; ++slot) {
-        const int i = b.order[slot];
-        BatchPlanDev d = make_desc(*b.plans[i], b.rs[i], b.batches[i]);
-        d.item0 = b.total_items;
-        b.total_items += (b.batches[i] + d.ts - 1) / d.ts;
-        b.desc.push_back(d);
-        b.mats_cap = std::max(b.mats_cap, d.mats_smem);
-        b.ints_cap = std::max(b.ints_cap, (d.ints_count + 3) & ~3);
-        tile_cap = std::max(tile_cap, (size_t)d.ts * d.np);
-    }
-    b.mats_cap = (b.mats_cap + 3) & ~3;
-    b.smem = sizeof(float) * (size_t)b.mats_cap + sizeof(int) * (size_t)b.ints_cap + sizeof(float) * tile_cap;
-    if (b.smem > (size_t)kBatchSmemLimit) fail(GFT_ERR_UNSUPPORTED, "mixed batch needs too much shared memory per CTA");
+// estimated cost of one item of `rows` signals (arbitrary units ~ ns on one
+// SM): bytes in and out, leaf FMAs, and a fixed cost per item
+double item_cost(const gft_plan_s& p, long long rows) {
+    double fl = 0;
+    for (auto& lf : p.leaves) fl += (double)lf.m() * lf.m();
+    return (double)rows * (0.2 * p.n + 0.02 * fl + 0.02 * p.dev.n_pairs) + 1500.0;
 }
 
-void upload_desc(gft_batch_s& b, const float* const* x, float* const* y, cudaStream_t st) {
-    for (size_t slot = 0; slot < b.desc.size(); ++slot) {
-        const int i = b.order[slot];
-        b.desc[slot].x = x ? x[i] : nullptr;
-        b.desc[slot].y = y ? y[i] : nullptr;
+// Builds every size class: slots (decreasing cost per item), item indices,
+// shared-memory sizes, grid, and the per-CTA ranges; uploads the ranges.
+void layout(gft_batch_s& b) {
+    const int k = (int)b.plans.size();
+    for (auto& c : b.classes) c.release();
+    b.classes.clear();
+    std::vector<std::vector<int>> by(kClasses);
+    for (int i = 0; i < k; ++i) by[class_of(b.plans[i]->n | 1)].push_back(i);
+    for (int ci = 0; ci < kClasses; ++ci) {
+        if (by[ci].empty()) continue;
+        BatchClass C;
+        std::vector<double> cpi(k, 0.0);
+        for (int i : by[ci]) cpi[i] = item_cost(*b.plans[i], (long long)b.rs[i] * kBatchThreads);
+        C.members = by[ci];
+        std::stable_sort(C.members.begin(), C.members.end(), [&](int x, int y) { return cpi[x] > cpi[y]; });
+        size_t tile_cap = 0;
+        for (int i : C.members) {
+            BatchPlanDev d = make_desc(*b.plans[i], b.rs[i], b.batches[i]);
+            d.item0 = C.total_items;
+            C.total_items += (b.batches[i] + d.ts - 1) / d.ts;
+            C.desc.push_back(d);
+            C.mats_cap = std::max(C.mats_cap, d.mats_smem);
+            C.ints_cap = std::max(C.ints_cap, (d.ints_count + 3) & ~3);
+            tile_cap = std::max(tile_cap, (size_t)d.ts * d.np);
+        }
+        C.mats_cap = (C.mats_cap + 3) & ~3;
+        C.tile_cap = (int)((tile_cap + 3) & ~size_t(3));
+        const size_t fixed = sizeof(float) * (size_t)C.mats_cap + sizeof(int) * (size_t)C.ints_cap;
+        const size_t tile_bytes = sizeof(float) * (size_t)C.tile_cap;
+        C.nbuf = 2 * tile_bytes <= kDoubleBufBytes && fixed + 2 * tile_bytes <= (size_t)kBatchSmemLimit ? 2 : 1;
+        C.smem = fixed + C.nbuf * tile_bytes;
+        if (C.smem > (size_t)kBatchSmemLimit) fail(GFT_ERR_UNSUPPORTED, "mixed batch needs too much shared memory per CTA");
+        // the attribute is an upper bound shared by every batch: set it to the
+        // limit once, so that no later batch can lower it under a captured launch
+        GFT_CUDA(cudaFuncSetAttribute(gft_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kBatchSmemLimit));
+        int per_sm = 0;
+        GFT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gft_batch_kernel, kBatchThreads, C.smem));
+        if (per_sm < 1) fail(GFT_ERR_UNSUPPORTED, "mixed-batch kernel does not fit on an SM");
+        C.grid = (int)std::max<long long>(1, std::min<long long>((long long)per_sm * sm_count(), C.total_items));
+        // cut the item sequence into grid ranges of about equal cost
+        double total = 0.0;
+        for (size_t sl = 0; sl < C.desc.size(); ++sl) {
+            const int i = C.members[sl];
+            const long long items = (b.batches[i] + C.desc[sl].ts - 1) / C.desc[sl].ts;
+            if (items) total += (items - 1) * cpi[i] + item_cost(*b.plans[i], b.batches[i] - (items - 1) * C.desc[sl].ts);
+        }
+        std::vector<long long> range(C.grid + 1, C.total_items);
+        std::vector<int> first(C.grid, (int)C.desc.size() - 1);
+        range[0] = 0;
+        first[0] = 0;
+        double acc = 0.0;
+        int cta = 1;
+        for (size_t sl = 0; sl < C.desc.size() && cta < C.grid; ++sl) {
+            const int i = C.members[sl];
+            const int ts = C.desc[sl].ts;
+            const long long items = (b.batches[i] + ts - 1) / ts;
+            for (long long t = 0; t < items && cta < C.grid; ++t) {
+                acc += t + 1 < items ? cpi[i] : item_cost(*b.plans[i], b.batches[i] - t * ts);
+                while (cta < C.grid && acc >= total * cta / C.grid) {
+                    range[cta] = std::min(C.desc[sl].item0 + t + 1, C.total_items);
+                    first[cta] = (int)sl;
+                    ++cta;
+                }
+            }
+        }
+        // a range that starts at the first item of the next slot names the
+        // slot it ends in; the kernel walks forward from there
+        b.classes.push_back(std::move(C));   // owned by the batch before any allocation
+        BatchClass& D = b.classes.back();
+        GFT_CUDA(cudaMalloc(&D.d_desc, sizeof(BatchPlanDev) * D.desc.size()));
+        GFT_CUDA(cudaMalloc(&D.d_range, sizeof(long long) * range.size()));
+        GFT_CUDA(cudaMalloc(&D.d_first, sizeof(int) * first.size()));
+        GFT_CUDA(cudaMemcpy(D.d_range, range.data(), sizeof(long long) * range.size(), cudaMemcpyHostToDevice));
+        GFT_CUDA(cudaMemcpy(D.d_first, first.data(), sizeof(int) * first.size(), cudaMemcpyHostToDevice));
     }
-    GFT_CUDA(cudaMemcpyAsync(b.d_desc, b.desc.data(), sizeof(BatchPlanDev) * b.desc.size(), cudaMemcpyHostToDevice, st));
+}
+
+// x / y: pointers per group index (the caller's order within the group)
+void upload_desc(gft_batch_s& b, const float* const* x, float* const* y, cudaStream_t st) {
+    for (auto& C : b.classes) {
+        for (size_t slot = 0; slot < C.desc.size(); ++slot) {
+            const int i = C.members[slot];
+            C.desc[slot].x = x ? x[i] : nullptr;
+            C.desc[slot].y = y ? y[i] : nullptr;
+        }
+        GFT_CUDA(cudaMemcpyAsync(C.d_desc, C.desc.data(), sizeof(BatchPlanDev) * C.desc.size(), cudaMemcpyHostToDevice,
+                                 st));
+    }
 }
 
 void launch_batch(gft_batch_s& b, cudaStream_t st) {
-    GFT_CUDA(cudaMemsetAsync(b.d_counter, 0, sizeof(unsigned long long), st));
-    if (b.total_items == 0) return;
-    gft_batch_kernel<<<b.grid, kBatchThreads, b.smem, st>>>(b.d_desc, (int)b.desc.size(), b.total_items, b.d_counter,
-                                                          b.mats_cap, b.ints_cap);
-    GFT_CUDA(cudaGetLastError());
-}
-
-void configure(gft_batch_s& b) {
-    GFT_CUDA(cudaFuncSetAttribute(gft_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b.smem));
-    int per_sm = 0;
-    GFT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gft_batch_kernel, kBatchThreads, b.smem));
-    if (per_sm < 1) fail(GFT_ERR_UNSUPPORTED, "mixed-batch kernel does not fit on an SM");
-    b.grid = per_sm * sm_count();
+    for (auto& C : b.classes) {
+        if (C.total_items == 0) continue;
+        gft_batch_kernel<<<C.grid, kBatchThreads, C.smem, st>>>(C.d_desc, (int)C.desc.size(), C.d_range, C.d_first,
+                                                              C.mats_cap, C.ints_cap, C.tile_cap, C.nbuf);
+        GFT_CUDA(cudaGetLastError());
+    }
 }
 
 // time plan i alone with each admissible RS; keep the fastest
@@ -280,18 +392,22 @@ void autotune(gft_batch_s& b) {
         if (st) cudaStreamDestroy(st);
         if (dx) cudaFree(dx);
         if (dy) cudaFree(dy);
-        probe.d_desc = nullptr;
-        probe.d_counter = nullptr;
     };
     try {
         GFT_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
         GFT_CUDA(cudaEventCreate(&e0));
         GFT_CUDA(cudaEventCreate(&e1));
-        probe.d_desc = b.d_desc;
-        probe.d_counter = b.d_counter;
+        // plans that are the same object share one measurement
+        std::map<const gft_plan_s*, int> seen;
         for (int i = 0; i < k; ++i) {
+            auto hit = seen.find(b.plans[i]);
+            if (hit != seen.end()) {
+                b.rs[i] = hit->second;
+                continue;
+            }
             const int n = b.plans[i]->n;
-            const int64_t tb = std::max<int64_t>(1, std::min<int64_t>(b.batches[i], (int64_t)(8 << 20) / n));
+            const int64_t tb = std::max<int64_t>(1, std::min<int64_t>(std::max<int64_t>(b.batches[i], 4096),
+                                                                      (int64_t)(8 << 20) / n));
             if (cap < (size_t)tb * n) {
                 if (dx) cudaFree(dx);
                 if (dy) cudaFree(dy);
@@ -301,15 +417,14 @@ void autotune(gft_batch_s& b) {
                 GFT_CUDA(cudaMalloc(&dy, cap * sizeof(float)));
                 GFT_CUDA(cudaMemset(dx, 0, cap * sizeof(float)));
             }
-            const int rmax = rs_cap(b.plans[i]->dev.max_bucket);
             float best = 0.f;
             int best_rs = 1;
-            for (int rs = 1; rs <= rmax; rs *= 2) {
+            for (int rs = 1; rs <= 4; rs *= 2) {
+                if (!rs_admissible(*b.plans[i], rs)) continue;
                 probe.plans = {b.plans[i]};
                 probe.batches = {tb};
                 probe.rs = {rs};
                 layout(probe);
-                configure(probe);
                 upload_desc(probe, (const float* const*)&dx, &dy, st);
                 launch_batch(probe, st);
                 GFT_CUDA(cudaEventRecord(e0, st));
@@ -324,6 +439,7 @@ void autotune(gft_batch_s& b) {
                 }
             }
             b.rs[i] = best_rs;
+            seen[b.plans[i]] = best_rs;
         }
     } catch (...) {
         cleanup();
@@ -370,7 +486,9 @@ gft_status gft_batch_create(int32_t n_plans, const gft_plan_t* plans, const int6
             int max_leaf = 0;
             for (auto& lf : p->leaves) max_leaf = std::max(max_leaf, lf.m());
             int kind;
-            if (b->precision != GFT_PREC_FP32 && tc_eligible(*p) && max_leaf >= kTcMinLeaf) kind = 2;
+            const bool tc_prec = b->precision != GFT_PREC_FP32 && max_leaf >= kTcMinLeaf;
+            if (tc_prec && tcn_eligible(*p) && (batches[i] <= kTcnMaxBatch || !tc_eligible(*p))) kind = 3;
+            else if (tc_prec && tc_eligible(*p)) kind = 2;
             else if (p->dev.max_bucket != 0 && !(wide_configured(*p) && wide_ready(*p, false))) kind = 0;
             else if (wide_configured(*p)) kind = 1;
             else fail(GFT_ERR_UNSUPPORTED, "plan " + std::to_string(i) + " has a leaf wider than 512 nodes");
@@ -386,22 +504,25 @@ gft_status gft_batch_create(int32_t n_plans, const gft_plan_t* plans, const int6
                 b->wide_users.push_back(i);
                 wide_plans.push_back(p);
                 wide_batches.push_back(batches[i]);
-            } else {
+            } else if (kind == 2) {
                 b->idx.push_back((int)b->tc_plans.size());
                 b->tc_users.push_back(i);
                 b->tc_plans.push_back(p);
                 b->tc_batches.push_back(batches[i]);
+            } else {
+                b->idx.push_back((int)b->tcn_plans.size());
+                b->tcn_users.push_back(i);
+                b->tcn_plans.push_back(p);
+                b->tcn_batches.push_back(batches[i]);
             }
         }
-        GFT_CUDA(cudaMalloc(&b->d_desc, sizeof(BatchPlanDev) * std::max<size_t>(1, b->plans.size())));
-        GFT_CUDA(cudaMalloc(&b->d_counter, sizeof(unsigned long long)));
         if (!b->plans.empty()) {
             autotune(*b);
             layout(*b);
-            configure(*b);
         }
         if (!wide_plans.empty()) b->wide = wide_batch_create(wide_plans, wide_batches);
         if (!b->tc_plans.empty()) b->tcb = tc_batch_create(b->tc_plans, b->tc_batches, b->precision);
+        if (!b->tcn_plans.empty()) b->tcnb = tcn_batch_create(b->tcn_plans, b->tcn_batches, b->precision);
         GFT_CUDA(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
         for (auto& st : b->side) GFT_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
         GFT_CUDA(cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming));
@@ -419,7 +540,8 @@ gft_status gft_batch_forward(gft_batch_t b, const float* const* x, float* const*
             if (!x[i] || !y[i]) fail(GFT_ERR_INVALID_ARG, "NULL signal pointer");
             if ((reinterpret_cast<uintptr_t>(x[i]) | reinterpret_cast<uintptr_t>(y[i])) & 15u)
                 fail(GFT_ERR_MISALIGNED, "signal pointers must be 16-byte aligned");
-            if (b->kind[i] == 2 && x[i] == y[i]) fail(GFT_ERR_UNSUPPORTED, "tensor-core entries do not run in place");
+            if ((b->kind[i] == 2 || b->kind[i] == 3) && x[i] == y[i])
+                fail(GFT_ERR_UNSUPPORTED, "tensor-core entries do not run in place");
         }
         cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
         const bool same = b->last_x.size() == (size_t)k &&
@@ -428,8 +550,8 @@ gft_status gft_batch_forward(gft_batch_t b, const float* const* x, float* const*
         if (!same) {
             // every group reads its signal pointers from device descriptors,
             // so the captured graph stays valid
-            std::vector<const float*> tx, wx, cx;
-            std::vector<float*> ty, wy, cy;
+            std::vector<const float*> tx, wx, cx, nx;
+            std::vector<float*> ty, wy, cy, ny;
             for (int i : b->table_users) {
                 tx.push_back(x[i]);
                 ty.push_back(y[i]);
@@ -442,9 +564,14 @@ gft_status gft_batch_forward(gft_batch_t b, const float* const* x, float* const*
                 cx.push_back(x[i]);
                 cy.push_back(y[i]);
             }
+            for (int i : b->tcn_users) {
+                nx.push_back(x[i]);
+                ny.push_back(y[i]);
+            }
             if (!b->plans.empty()) upload_desc(*b, tx.data(), ty.data(), st);
             if (b->wide) wide_batch_upload(b->wide, wx, wy, st);
             if (b->tcb) tc_batch_upload(b->tcb, cx, cy, st);
+            if (b->tcnb) tcn_batch_upload(b->tcnb, nx, ny, st);
             b->last_x.assign(x, x + k);
             b->last_y.assign(y, y + k);
         }
@@ -462,7 +589,10 @@ gft_status gft_batch_forward(gft_batch_t b, const float* const* x, float* const*
                     return b->side[s];
                 };
                 if (b->wide) wide_batch_launch(b->wide, fork(0));
+                // both tensor-core groups on one side stream: their CTAs
+                // would otherwise compete for the SMs' TMEM
                 if (b->tcb) tc_batch_launch(b->tcb, fork(1));
+                if (b->tcnb) tcn_batch_launch(b->tcnb, fork(1));
                 if (!b->plans.empty()) launch_batch(*b, cs);
                 for (int s = 0; s < 2; ++s)
                     if (used[s]) {
@@ -492,6 +622,18 @@ gft_status gft_batch_get_tile(gft_batch_t b, int32_t i, int32_t* tile, int32_t* 
             *tile = b->rs[b->idx[i]] * kBatchThreads;
             *threads = kBatchThreads;
         }
+    });
+}
+
+gft_status gft_batch_get_launches(gft_batch_t b, int32_t* launches) {
+    return guard_b([&] {
+        if (!b || !launches) fail(GFT_ERR_INVALID_ARG, "NULL argument");
+        int32_t n = 0;
+        for (auto& c : b->classes) n += c.total_items > 0 ? 1 : 0;
+        if (b->wide) n += wide_batch_launches(b->wide);
+        if (b->tcb) n += tc_batch_launches(b->tcb);
+        if (b->tcnb) n += tcn_batch_launches(b->tcnb);
+        *launches = n;
     });
 }
 

@@ -82,6 +82,16 @@ struct DevProgram {
     int* d_err = nullptr;    // device error word
 };
 
+// tcn.cu: tensor-core leaf products with the signals on the MMA's N axis,
+// for mixed batches of graphs with few signals each (leaves up to 512)
+bool tcn_eligible(const gft_plan_s& p);
+void tcn_free(gft_plan_s& p);
+void* tcn_batch_create(const std::vector<gft_plan_s*>& plans, const std::vector<int64_t>& batches, uint32_t precision);
+void tcn_batch_upload(void* tb, const std::vector<const float*>& x, const std::vector<float*>& y, cudaStream_t st);
+void tcn_batch_launch(void* tb, cudaStream_t st);
+void tcn_batch_free(void* tb);
+int tcn_batch_launches(void* tb);
+
 }  // namespace gft
 
 struct gft_plan_s {
@@ -112,6 +122,8 @@ struct gft_plan_s {
     cudaEvent_t ev_up[kHostStreams] = {}, ev_k[kHostStreams] = {}, ev_down[kHostStreams] = {};
     // tensor-core data (built lazily)
     void* tc = nullptr;
+    // tensor-core data of the few-signals batch kernel (tcn.cu; built lazily)
+    void* tcn = nullptr;
     // plan-specialised kernels (jit.cpp)
     void* jit = nullptr;
     // wide-leaf CUDA-core kernel data (wide.cu)
@@ -212,6 +224,7 @@ void* wide_batch_create(const std::vector<gft_plan_s*>& plans, const std::vector
 void wide_batch_upload(void* wb, const std::vector<const float*>& x, const std::vector<float*>& y, cudaStream_t st);
 void wide_batch_launch(void* wb, cudaStream_t st);
 void wide_batch_free(void* wb);
+int wide_batch_launches(void* wb);
 
 // tc.cu: leaf products on tcgen05 tensor cores (split precision)
 bool tc_eligible(const gft_plan_s& p);
@@ -236,5 +249,16 @@ void* tc_batch_create(const std::vector<gft_plan_s*>& plans, const std::vector<i
 void tc_batch_upload(void* tb, const std::vector<const float*>& x, const std::vector<float*>& y, cudaStream_t st);
 void tc_batch_launch(void* tb, cudaStream_t st);
 void tc_batch_free(void* tb);
+int tc_batch_launches(void* tb);
+
+// tcn.cu: tensor-core leaf products with the signals on the MMA's N axis,
+// for mixed batches of graphs with few signals each (leaves up to 512)
+bool tcn_eligible(const gft_plan_s& p);
+void tcn_free(gft_plan_s& p);
+void* tcn_batch_create(const std::vector<gft_plan_s*>& plans, const std::vector<int64_t>& batches, uint32_t precision);
+void tcn_batch_upload(void* tb, const std::vector<const float*>& x, const std::vector<float*>& y, cudaStream_t st);
+void tcn_batch_launch(void* tb, cudaStream_t st);
+void tcn_batch_free(void* tb);
+int tcn_batch_launches(void* tb);
 
 }  // namespace gft

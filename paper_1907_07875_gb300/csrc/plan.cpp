@@ -265,6 +265,7 @@ void compute_basis(const gft_plan_s& p, double* U) {
 void free_device(gft_plan_s& p) {
     jit_free(p);
     tc_free(p);
+    tcn_free(p);
     wide_free(p);
     if (p.dev.d_ints) cudaFree(p.dev.d_ints);
     if (p.dev.d_mats32) cudaFree(p.dev.d_mats32);

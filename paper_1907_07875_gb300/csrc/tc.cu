@@ -906,7 +906,10 @@ int npad_max_of(const gft_plan_s& p) {
 void launch_pack(const TcPlanDev& one, const TcPlanDev* many, int n_plans, long long total_tiles, int nmax,
                  int prog_cap, int items_cap, uint32_t precision, cudaStream_t st) {
     if (total_tiles == 0) return;
-    const int rs = nmax + 4;
+    // row stride of the staging buffers: a multiple of four floats, so that
+    // the 16-byte copies of plans with n % 4 == 0 land 16-byte aligned in
+    // every row even when the largest plan of the launch has n % 4 != 0
+    const int rs = ((nmax + 3) & ~3) + 4;
     const size_t per_buf = sizeof(float) * (size_t)kPack8Warps * 8 * rs;
     const size_t tabs = sizeof(int) * (size_t)((prog_cap + 3) & ~3) + sizeof(short) * 64 * (size_t)items_cap;
     const int nbuf = 2 * per_buf + tabs <= 232448 / 2 ? 2 : 1;   // double buffer if two CTAs still fit
@@ -1079,5 +1082,12 @@ void tc_batch_launch(void* h, cudaStream_t st) {
 }
 
 void tc_batch_free(void* h) { delete static_cast<TcBatch*>(h); }
+
+int tc_batch_launches(void* h) {
+    int n = 0;
+    for (auto& c : static_cast<TcBatch*>(h)->cls)
+        if (!c.desc.empty() && c.total_tiles > 0) n += 2;   // pack + leaf
+    return n;
+}
 
 }  // namespace gft

@@ -813,6 +813,8 @@ void wide_batch_launch(void* h, cudaStream_t st) {
 
 void wide_batch_free(void* h) { delete static_cast<WideBatch*>(h); }
 
+int wide_batch_launches(void* h) { return static_cast<WideBatch*>(h)->total_items > 0 ? 1 : 0; }
+
 void launch_wide_f32(gft_plan_s& p, const float* x, float* y, int64_t batch, bool inverse, cudaStream_t st) {
     launch_wide_t<float>(p, x, y, batch, inverse, st);
 }

@@ -1,0 +1,224 @@
+"""Mixed batches against the FP64 oracle, at the workloads' full sizes.
+
+Definition checked (Sec. IV, Eq. 13 stage by stage): every plan in a batch
+applies U = B_1 ... B_S diag(U_k) of its own graph, so every sampled signal
+of every graph must match the oracle's dense product y = U^T x after
+eigenspace alignment (Sec. III: bases are unique only up to rotations inside
+repeated eigenvalues).  Bounds (relative L2 over the sampled signals of one
+graph): FP32 2e-6; BF16 5e-3, BF16 hi+lo 1e-5, FP16 hi+lo 2e-6, the bounds
+stated for the tensor-core precisions (graphs whose leaves stay on CUDA
+cores run FP32 in every precision).
+
+* the mixed grid / cycle workload: all eight kinds (8x8, 16x16, 32x32 grids,
+  unit and symmetrised U[0.1, 1] weights; cycles of 64 and 256 nodes) at
+  2^23 coefficients each (2^26 in all) in one graph launch, per precision;
+* the size sweep at full size: 10^4 graphs of 8..1024 nodes (path, cycle,
+  grid, skeleton, bipartite), 2^28 coefficients in one graph launch, checked
+  on a stratified sample of graphs (every family x every octave of sizes,
+  plus each family's largest graph).
+
+The oracle runs in a spawn process pool (its Jacobi is plain Python) while
+the GPU builds plans and transforms."""
+import multiprocessing as mp
+import os
+
+import numpy as np
+import pytest
+
+import gft_workloads as W
+from _helpers import align, rel_l2
+from _oracle_jobs import oracle_basis
+
+pytestmark = pytest.mark.gpu
+
+BOUNDS = {"fp32": 2e-6, "bf16": 5e-3, "bf16x3": 1e-5, "fp16x3": 2e-6}
+SAMPLES = 1024          # signals compared per graph of the mixed workload
+
+
+@pytest.fixture(scope="module")
+def pool():
+    ctx = mp.get_context("spawn")
+    p = ctx.Pool(max(1, min(16, os.cpu_count() or 1)))
+    yield p
+    p.terminate()
+    p.join()
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1907_07875_gb300.build import build
+    build()
+    import paper_1907_07875_gb300 as gft
+    return gft, torch
+
+
+def _sample(batch, k):
+    """k signal indices spread over the batch, first and last included."""
+    if batch <= k:
+        return np.arange(batch)
+    return np.unique(np.linspace(0, batch - 1, k).round().astype(np.int64))
+
+
+def _check(plan, x_host, y_dev, idx, ref, bound, what):
+    lam, U_ref, _ = ref
+    U = plan.basis()
+    y = y_dev[idx].cpu().numpy().astype(np.float64)
+    y_ref = align(x_host[idx].astype(np.float64) @ U_ref, U, U_ref, lam)
+    err = rel_l2(y, y_ref)
+    assert err <= bound, (what, err)
+    return err
+
+
+@pytest.fixture(scope="module")
+def config3_setup(env, pool):
+    gft, torch = env
+    kinds = W.config3()                                  # 2^23 coefficients per kind
+    jobs = [pool.apply_async(oracle_basis, (("config3", k),)) for k in range(len(kinds))]
+    graphs = [k[0] for k in kinds]
+    batches = [k[1] + 5 for k in kinds]                  # ragged tails
+    plans = [gft.Plan(gft.laplacian(g.W, g.s), g.phis) for g in graphs]
+    xh = [W.signals(b, g.n, s) for (g, _, s), b in zip(kinds, batches)]
+    xs = [torch.from_numpy(x).cuda() for x in xh]
+    refs = [j.get(timeout=1800) for j in jobs]
+    return graphs, batches, plans, xh, xs, refs
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "bf16x3", "fp16x3"])
+def test_config3_mixed_launch_vs_oracle(env, config3_setup, prec):
+    gft, torch = env
+    graphs, batches, plans, xh, xs, refs = config3_setup
+    b = gft.Batch(plans, batches, precision=prec)
+    ys = [torch.full_like(x, float("nan")) for x in xs]
+    for _ in range(2):                                   # capture, then a replay
+        b.forward(xs, ys)
+    torch.cuda.synchronize()
+    for g, p, x, y, ref, bt in zip(graphs, plans, xh, ys, refs, batches):
+        assert p.output_map().tolist() == ref[2].tolist()
+        tc = prec != "fp32" and p.info["max_leaf"] >= 64
+        _check(p, x, y, _sample(bt, SAMPLES), ref, BOUNDS[prec if tc else "fp32"], (g.name, prec))
+        assert not torch.isnan(y).any()
+        assert p.device_error() == 0
+
+
+def _stratified(specs):
+    """Indices into the sweep: the first graph of every (family, octave of n)
+    and each family's largest graph."""
+    picked, seen, largest = [], set(), {}
+    for j, (fam, n, gs, b, ss) in enumerate(specs):
+        key = (fam, int(np.log2(n)))
+        if key not in seen:
+            seen.add(key)
+            picked.append(j)
+        if fam not in largest or n > specs[largest[fam]][1]:
+            largest[fam] = j
+    return sorted(set(picked) | set(largest.values()))
+
+
+@pytest.mark.parametrize("precs", [("fp32", "bf16x3", "fp16x3")])
+def test_size_sweep_full_launch_vs_oracle(env, pool, precs):
+    gft, torch = env
+    specs = W.config5_specs()                             # 10^4 graphs, 2^28 coefficients
+    picked = _stratified(specs)
+    jobs = {j: pool.apply_async(oracle_basis, (("config5", specs[j][0], specs[j][1], specs[j][2]),))
+            for j in picked}
+    keys, graphs = {}, []
+    for fam, n, gs, b, ss in specs:
+        if (fam, n, gs) not in keys:
+            keys[(fam, n, gs)] = len(graphs)
+            graphs.append((fam, n, gs))
+    Ls, phis = [], []
+    for fam, n, gs in graphs:
+        g = W.make_graph(fam, n, gs)
+        Ls.append(gft.laplacian(g.W, g.s))
+        phis.append(g.phis)
+    plans = gft.plans_from_laplacians(Ls, phis, jit=False)
+    del Ls
+    entry = [plans[keys[(f, n, gs)]] for f, n, gs, b, ss in specs]
+    batches = [b for f, n, gs, b, ss in specs]
+    # one input and one output buffer; every graph's view starts 16-byte aligned
+    offs, o = [], 0
+    for (f, n, gs, b, ss) in specs:
+        offs.append(o)
+        o += (b * n + 3) & ~3
+    X = torch.empty(o, device="cuda")
+    Y = torch.empty(o, device="cuda")
+    xs, ys, xh = [], [], {}
+    for j, ((f, n, gs, b, ss), a) in enumerate(zip(specs, offs)):
+        xj = W.signals(b, n, ss % 100000)
+        if j in jobs:
+            xh[j] = xj
+        X[a:a + b * n].copy_(torch.from_numpy(xj).view(-1))
+        xs.append(X[a:a + b * n].view(b, n))
+        ys.append(Y[a:a + b * n].view(b, n))
+    assert sum(b * n for f, n, gs, b, ss in specs) >= 1 << 28
+    covered = np.zeros(o, dtype=bool)                     # the graphs' views (not the padding)
+    for (f, n, gs, b, ss), a in zip(specs, offs):
+        covered[a:a + b * n] = True
+    covered = torch.from_numpy(covered).cuda()
+    refs = {j: jobs[j].get(timeout=3600) for j in picked}
+    for prec in precs:
+        bt = gft.Batch(entry, batches, precision=prec)
+        Y.fill_(float("nan"))
+        bt.forward(xs, ys)
+        torch.cuda.synchronize()
+        for j in picked:
+            p = entry[j]
+            tc = prec != "fp32" and p.info["max_leaf"] >= 64
+            _check(p, xh[j], ys[j], _sample(batches[j], 64), refs[j], BOUNDS[prec if tc else "fp32"],
+                   (specs[j][0], specs[j][1], prec))
+        assert not torch.isnan(Y[covered]).any()       # every coefficient written
+        del bt
+
+
+# graphs of the few-signals tensor-core kernel: leaves of 65..512 nodes, one
+# or several M-tiles of 128 coefficients, 16- and 32-signal tiles with ragged
+# ends (batches around the tile sizes)
+FEW = [(("graph", "path", 130, None), 1), (("graph", "path", 130, None), 33), (("grid", 16), 17),
+       (("graph", "cycle", 256, None), 31), (("graph", "bipartite", 300, 77), 15),
+       (("graph", "path", 600, None), 16), (("grid", 32), 20), (("graph", "bipartite", 1024, 78), 27),
+       (("graph", "path", 1024, None), 40)]
+
+
+def _few_graph(recipe):
+    if recipe[0] == "grid":
+        return W.grid(recipe[1])
+    return W.make_graph(recipe[1], recipe[2], recipe[3])
+
+
+@pytest.fixture(scope="module")
+def few_setup(env, pool):
+    gft, torch = env
+    uniq = list(dict.fromkeys(r for r, _ in FEW))
+    jobs = {r: pool.apply_async(oracle_basis, (r,)) for r in uniq}
+    plans = {r: gft.Plan(gft.laplacian(_few_graph(r).W, _few_graph(r).s), _few_graph(r).phis) for r in uniq}
+    refs = {r: jobs[r].get(timeout=3600) for r in uniq}
+    return plans, refs
+
+
+@pytest.mark.parametrize("prec", ["bf16", "bf16x3", "fp16x3"])
+def test_few_signal_tensor_core_kernel_vs_oracle(env, few_setup, prec):
+    """Graphs with a few signals each (the size sweep's regime) in one
+    tensor-core batch: the leaf products run with the signals on the MMA's N
+    axis (16 or 32 per tile), leaves up to 512 nodes (four M-tiles).  Every
+    signal matches the oracle within the precision's bound; no coefficient
+    is left unwritten; the replay gives the same bits."""
+    gft, torch = env
+    plans, refs = few_setup
+    entry = [plans[r] for r, _ in FEW]
+    batches = [b for _, b in FEW]
+    xh = [W.signals(b, p.n, 900 + i) for i, (p, b) in enumerate(zip(entry, batches))]
+    xs = [torch.from_numpy(x).cuda() for x in xh]
+    ys = [torch.full_like(x, float("nan")) for x in xs]
+    bt = gft.Batch(entry, batches, precision=prec).bind(xs, ys)
+    bt.forward()
+    torch.cuda.synchronize()
+    first = [y.clone() for y in ys]
+    for (r, b), p, x, y in zip(FEW, entry, xh, ys):
+        assert not torch.isnan(y).any()
+        _check(p, x, y, np.arange(b), refs[r], BOUNDS[prec], (r, b, prec))
+        assert p.device_error() == 0
+    bt.forward()
+    torch.cuda.synchronize()
+    assert all(torch.equal(a, c) for a, c in zip(first, ys))

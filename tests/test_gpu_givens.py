@@ -131,3 +131,43 @@ def test_butterfly_kernel_equals_general_kernel(env, n):
     y_rand = gft.Givens(n, wiring).forward(torch.from_numpy(theta).float().cuda(), x).cpu().numpy()
     th32 = theta.astype(np.float32).astype(np.float64)
     assert rel_l2(y_rand, ogiv.forward(x.cpu().numpy().astype(np.float64), wiring, th32)) <= 2e-6
+
+
+def _c4_graph_and_phis(g):
+    n = g.n
+    if "grid" in g.name:
+        N = int(round(n ** 0.5))
+        return [W.grid_lr(N), W.grid_ud(N)]
+    return [W.reversal(n)]
+
+
+@pytest.mark.parametrize("k", range(9))
+def test_corrected_butterfly_gains_over_symmetrised_butterfly(env, k):
+    """The nearly symmetric workload (paths of 16 / 32 nodes and 8x8 grids,
+    w = 1 + eps g, eps in {0.01, 0.05, 0.1}).  The method without the
+    learned part is the exact butterfly of the graph with its weights averaged
+    over the involutions (Haar stages + leaf GFTs of the closest symmetric
+    graph).  Learned Givens layers on its coefficients, trained on the GPU
+    through the library's kernels against the exact basis, must lower the
+    sign-normalised error delta (Sec. VI-B) on every graph, by at least a
+    fifth.  The exact basis is checked against the oracle's first, and the
+    surrogate's coefficients on signals equal U_hat^T x."""
+    gft, torch = env
+    from paper_1907_07875_gb300.learned import CorrectedButterfly, symmetrise_weights
+    g = W.config4()[k]
+    phis = _c4_graph_and_phis(g)
+    exact = gft.Plan(gft.laplacian(g.W, g.s), [])            # exact dense GFT
+    U = exact.basis()
+    lam_o, U_o = ogft.dense_gft(ograph.laplacian(g.W, g.s))
+    assert metrics.delta(U, U_o) < 1e-9
+    sym = gft.Plan(gft.laplacian(symmetrise_weights(g.W, phis), g.s), phis)
+    model = CorrectedButterfly(sym)
+    d_sym = metrics.delta(sym.basis(), U)
+    assert metrics.delta(model.matrix(), U) == pytest.approx(d_sym, abs=1e-6)   # zero angles: the butterfly
+    model.train(U, steps=1500)
+    d_l = metrics.delta(model.matrix(), U)
+    assert d_l < 0.8 * d_sym, (g.name, d_sym, d_l)
+    x = torch.from_numpy(W.signals(1000, g.n, 17)).cuda()
+    y = model.forward(x).cpu().numpy().astype(np.float64)
+    y_ref = x.cpu().numpy().astype(np.float64) @ model.matrix()
+    assert rel_l2(y, y_ref) <= 2e-6
