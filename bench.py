@@ -338,12 +338,19 @@ def extras(torch, gft, dev):
     xs = [torch.from_numpy(W.signals(b, g.n, s)).to(dev) for g, b, s in sel]
     ys = [torch.empty_like(v) for v in xs]
     tot = sum(b * g.n for g, b, _ in sel)
-    mixed = {"coeffs": tot, "graph_launches_per_step": 1}
-    for prec in ("fp32", "bf16", "bf16x3"):
-        bat = gft.Batch(plans, [b for _, b, _ in sel], precision=prec)
-        t = _timed(torch, lambda: bat.forward(xs, ys))
-        mixed[prec] = {"gcoeffs_s": round(tot / t / 1e9, 1), "ms": round(t * 1e3, 3)}
+    basis_bytes = sum(4 * sum(len(lv) ** 2 for lv in p.leaves()) for p in plans)
+    Us = [torch.from_numpy(p.basis()).to(dev) for p in plans]
+    mixed = {"coeffs": tot, "graph_launches_per_step": 1,
+             "roofline_bytes": "8 B per coefficient + each plan's leaf bases once"}
+    for prec in ("fp32", "bf16", "bf16x3", "fp16x3"):
+        bat = gft.Batch(plans, [b for _, b, _ in sel], precision=prec).bind(xs, ys)
+        t = _timed(torch, lambda: bat.forward())
+        errs = [_rel(yv[:2048].double(), xv[:2048].double() @ U) for xv, yv, U in zip(xs, ys, Us)]
+        mixed[prec] = {"gcoeffs_s": round(tot / t / 1e9, 1), "ms": round(t * 1e3, 3),
+                       "frac_hbm": round((8 * tot + basis_bytes) / t / 1e9 / _peaks()[0], 3),
+                       "err_max_vs_fp64": float(f"{max(errs):.2e}"), "launches_per_step": bat.launches}
         del bat
+    del Us
     out["config3_mixed_one_graph"] = mixed
     del xs, ys, plans
     # ---- the paper's runtime table (Sec. VI-A): fast vs matrix GFT on the same graphs
@@ -504,6 +511,35 @@ def learned_extras(torch, gft, dev, steps=1500):
                        "plain_givens_gcoeffs_s": round((1 << 24) / t_l / 1e9, 1),
                        "exact_dense_gcoeffs_s": round((1 << 24) / t_e / 1e9, 1),
                        "symmetrised_butterfly_gcoeffs_s": round((1 << 24) / t_s / 1e9, 1)}
+    return res
+
+
+def recursion_extras(torch, gft, dev):
+    """Recursion inside the DCT-II leaves (Sec. V-B / V-C, end of Sec. IV-C):
+    the same uniform path or cycle transformed with its usual stages and
+    with the sum block's reversal repeated on every level; leaves, the
+    library's multiplication count, FP32 coefficients/s on 2^26
+    coefficients, error vs x U in FP64 on the first 2048 signals."""
+    res = {}
+    for name, g0, g1 in (("path256", W.path(256), W.path_recursive(256)),
+                         ("path1024", W.path(1024), W.path_recursive(1024)),
+                         ("cycle256", W.cycle(256), W.cycle_recursive(256)),
+                         ("cycle1024", W.cycle(1024), W.cycle_recursive(1024))):
+        row = {}
+        for tag, g in (("usual_stages", g0), ("recursive", g1)):
+            plan = gft.Plan(gft.laplacian(g.W, g.s), g.phis)
+            nb = (1 << 26) // g.n
+            x = torch.from_numpy(W.signals(nb, g.n, 7)).to(dev)
+            y = torch.empty_like(x)
+            t = _timed(torch, lambda: plan.forward(x, out=y), reps=10)
+            U = torch.from_numpy(plan.basis()).to(dev)
+            ref = x[:2048].double() @ U
+            inf = plan.info
+            row[tag] = {"stages": len(g.phis), "leaves": sorted((len(lv) for lv in plan.leaves()), reverse=True)[:6],
+                        "mults_per_signal": int(inf["fast_mults"]), "gcoeffs_s": round(g.n * nb / t / 1e9, 1),
+                        "err_vs_fp64": _rel(y[:2048].double(), ref)}
+            del plan, x, y, U
+        res[name] = row
     return res
 
 
@@ -720,6 +756,9 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        # NVTX range: an ncu launch list can keep only the timed replays
+        # (--nvtx --nvtx-include "timed/")
+        torch.cuda.nvtx.range_push("timed")
         e0.record(stream)
         for i in range(args.steps):
             if i in starts:
@@ -730,6 +769,7 @@ def run_ours(args, rank, world, local_rank):
                 step()
         e1.record(stream)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         total_ms = e0.elapsed_time(e1)
     step_ms = [starts[i].elapsed_time(ends[i]) for i in sampled]
     total_ms = sharding.max_over_ranks(total_ms, dist, dev)
@@ -814,6 +854,7 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_extras and world == 1:
         line["extras"] = extras(torch, gft, dev)
         line["extras"]["config2_skeleton"] = config2_extras(torch, gft, dev)
+        line["extras"]["recursion_in_dct_leaves"] = recursion_extras(torch, gft, dev)
         if not args.no_sweep:
             line["extras"]["config5_sweep"] = sweep_variants(torch, gft, dev, S)
     print(json.dumps(line), flush=True)
@@ -837,8 +878,14 @@ def run_probe(args):
         else:
             S = sweep_setup(torch, gft, dev, specs=W.config5_specs(n_graphs=1000, total_coeffs=1 << 25))
         bt = gft.Batch(S["entry"], S["batches"], precision=prec).bind(S["xs"], S["ys"])
+        torch.cuda.synchronize()
+        # the replays sit in an NVTX range, so that a capture can skip the
+        # autotuner's launches (ncu --nvtx --nvtx-include "sweep/")
+        torch.cuda.nvtx.range_push("sweep")
         for _ in range(3):
             bt.forward()
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
     elif args.probe.startswith("givens"):
         import math
         from paper_1907_07875_gb300.learned import xor_pairs

@@ -23,7 +23,7 @@ from typing import List, Optional, Sequence
 import numpy as np
 
 __all__ = [
-    "Graph", "signals", "path", "cycle", "grid", "skeleton25", "bipartite",
+    "Graph", "signals", "path", "path_recursive", "nested_reversals", "cycle", "cycle_recursive", "grid", "skeleton25", "bipartite",
     "star", "complete", "near_symmetric_path", "near_symmetric_grid",
     "planted_symmetric", "reversal", "cycle_second_reflection", "grid_lr",
     "grid_ud", "grid_diag", "grid_antidiag", "grid_centro", "involution_count",
@@ -164,6 +164,44 @@ def path(n: int, weights: Optional[Sequence[float]] = None, s=None) -> Graph:
         _add_edge(W, i, i + 1, w[i])
     s = s0 if s is None else np.asarray(s, dtype=np.float64)
     return Graph(f"path{n}", W, s, [reversal(n)])
+
+
+def nested_reversals(n: int, first: int, min_len: int = 4) -> List[np.ndarray]:
+    """Involutions (on labels 0..n-1) reversing the prefix 0..L-1 for
+    L = first, first/2, first/4, ... while L is even and at least min_len,
+    identity elsewhere.  After a reversal stage of a uniform path, the
+    sum block G+ is again a uniform path on the prefix of the smaller labels
+    (Sec. V-B, recursion at the end of Sec. IV-C), so every prefix reversal
+    is a symmetry of the current G+ block and leaves the other blocks alone."""
+    out, L = [], first
+    while L >= min_len and L % 2 == 0:
+        phi = np.arange(n, dtype=np.int32)
+        phi[:L] = L - 1 - np.arange(L)
+        out.append(phi)
+        L //= 2
+    return out
+
+
+def path_recursive(n: int, min_len: int = 4) -> Graph:
+    """Uniform path with the reversal applied recursively to every sum
+    block: stage s reverses labels 0..n/2^(s-1)-1 (while that length is even
+    and at least min_len).  Leaves: the difference blocks of n/2, n/4, ...
+    nodes (DCT-IV type) and a final small uniform path."""
+    g = path(n)
+    g.name = f"path{n}_rec"
+    g.phis = nested_reversals(n, n, min_len) if n % 2 == 0 else [reversal(n)]
+    return g
+
+
+def cycle_recursive(n: int, min_len: int = 4) -> Graph:
+    """Cycle (n divisible by 4) with its two reflections and then the
+    recursive reversals of the G++ block, a uniform path on labels
+    0..n/4-1 (DCT-II, Sec. V-C)."""
+    g = cycle(n)
+    g.name = f"cycle{n}_rec"
+    if n % 4 == 0:
+        g.phis = list(g.phis) + nested_reversals(n, n // 4, min_len)
+    return g
 
 
 def cycle(n: int) -> Graph:

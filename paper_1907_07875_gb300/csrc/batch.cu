@@ -32,6 +32,7 @@
 // Changing the signal pointers only rewrites the per-plan descriptors in
 // device memory; the captured graph is reused.
 #include <algorithm>
+#include <cstring>
 #include <map>
 #include <memory>
 #include <numeric>
@@ -207,7 +208,7 @@ using namespace gft;
 struct gft_batch_s {
     // routing of the caller's plans: 0 = table-driven batch kernel, 1 = wide-leaf
     // batch kernel, 2 = tensor-core sequence (pack + leaf kernels, 128 signals
-    // per tile), 3 = few-signals tensor-core kernel; idx = position within its group
+    // per tile), 3 = few-signals tensor-core kernels; idx = position within its group
     uint32_t precision = GFT_PREC_FP32;
     std::vector<int> kind, idx;
     std::vector<int64_t> user_batch;

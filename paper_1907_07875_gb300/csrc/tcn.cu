@@ -3,37 +3,38 @@
 // hundred signals per graph), leaves up to 512 nodes.
 //
 // The leaf products y_k = M_k^T v_k (Sec. IV-C, Eq. 13; M_k the folded leaf
-// basis) of a tile of NS signals run with the roles of the operands swapped
-// against tc.cu: the MMA's M axis is the leaf's output coefficients (128 per
-// M-tile), its N axis the tile's signals (NS = 16 or 32), K the leaf's
-// inputs:
+// basis) run with the roles of the operands swapped against tc.cu: the MMA's
+// M axis is the leaf's output coefficients (128 per M-tile), its N axis the
+// signals of a tile (NS = 16..128, the graph's whole batch when it fits), K
+// the leaf's inputs:
 //     D[c][s] (TMEM lane c, column s) = sum_r M_k[r][c] v_k[r][s]
 // so a graph with 27 signals fills a 32-column accumulator instead of 27 of
-// 128 rows, and a 512-node leaf is four M-tiles sharing one B operand.
+// 128 rows, a 512-node leaf is four M-tiles, and each graph's basis crosses
+// HBM once per tile of up to 128 signals.
 //
-// Per CTA (persistent, tiles b, b + grid, ...), warp-specialised:
-//   warps 0-3 (workers): copy the tile's NS signal rows into shared memory
-//     (cp.async), compute the FP16 per-signal scales, run the Haar stages in
-//     place (FP32), and write the B operand of EVERY (leaf, 32-wide K chunk)
-//     of the tile -- the gathered post-stage values, split into hi and lo
-//     (BF16 or scaled FP16), in the canonical no-swizzle K-major layout --
-//     into a resident region; then signal the MMA thread.  After the tile's
-//     last MMA they read the accumulators (tcgen05.ld, warp w = TMEM lanes
-//     32w..32w+31), scatter them to their output positions (ascending
-//     eigenvalue) in a staging copy of the tile's output rows, and write the
-//     rows with coalesced 16-byte stores;
-//   warp 4 (one thread): streams the pre-split basis chunks A = M_k^T
-//     (128 rows x 32 K, hi and lo, 8 KB each) through a ring of shared-memory
-//     slots with bulk copies (TMA), running ahead across tiles;
-//   warp 5: allocates TMEM (256 columns); one thread issues the MMAs
-//     (M = 128, N = NS, K = 16; hi*hi + hi*lo + lo*hi for the split
-//     precisions) into one NS-column accumulator per (leaf, M-tile), and
-//     commits each ring slot back to the copier and the tile's accumulators
-//     to the workers.
+// Two kernels per launch:
+//   tcn_pack_kernel  (CTA per 8 signals of a tile): copies the rows into
+//     shared memory (cp.async), computes the FP16 per-signal scales, runs
+//     the Haar stages in place (FP32), and writes the B operand of every
+//     (leaf, 32-wide K chunk) -- the gathered post-stage values split into
+//     hi and lo (BF16 or scaled FP16) in the canonical no-swizzle K-major
+//     core-matrix layout, NS rows per chunk -- to a scratch buffer, 512
+//     contiguous bytes per 32 consecutive threads;
+//   tcn_kernel  (persistent; work items = (plan, tile, group of M-tile
+//     units), so a large graph's M-tiles spread over several SMs):
+//     warp 4 (one thread) streams each step's basis chunk A = M_k^T (128
+//     rows x 32 K, hi and lo) and signal chunk B (NS rows x 32 K, hi and lo)
+//     through a ring of shared-memory slots with bulk copies (TMA);
+//     warp 5 allocates TMEM (512 columns, two halves used by alternate
+//     items) and one thread issues the MMAs (M = 128, N = NS, K = 16;
+//     hi*hi + hi*lo + lo*hi for the split precisions) into one NS-column
+//     accumulator per unit; warps 0-3 read a finished half (tcgen05.ld, warp
+//     w = TMEM lanes 32w..32w+31), undo the FP16 scale and store each
+//     coefficient at its output position (ascending eigenvalue) of its
+//     signal's row, while the MMAs of the next item fill the other half.
 // Every wait is bounded (about 2 s via %globaltimer); a timeout records
-// GFT_ERR_TIMEOUT in the error word, every role leaves its loop through
-// uniform exits (workers agree through a barrier reduction), copies and MMAs
-// in flight are awaited (bounded), and TMEM is freed.
+// GFT_ERR_TIMEOUT in the plan's error word, every role leaves its loop,
+// copies and MMAs in flight are awaited (bounded), and TMEM is freed.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -49,14 +50,20 @@ namespace gft {
 namespace {
 
 constexpr int kNM = 128;             // coefficient rows per MMA (M)
-constexpr int kNK = 32;              // K per basis chunk
+constexpr int kNK = 32;              // K per chunk
+constexpr int kNMaxNs = 128;         // signals per tile (MMA N)
 constexpr int kNWorkers = 4;         // worker warps 0-3
 constexpr int kNThreads = 192;       // + copier warp 4, MMA warp 5
-constexpr int kNSlots = 3;           // ring slots (A hi + A lo, 8 KB each)
-constexpr int kNCols = 256;          // TMEM columns per CTA (two CTAs per SM fit)
+constexpr int kNSlots = 6;           // ring slots
+constexpr int kNCols = 512;          // TMEM columns per CTA (one CTA per SM): two halves
+constexpr int kNHalf = 256;
 constexpr int kNMaxLeaf = 512;
-constexpr unsigned kNSlotBytes = 2u * kNM * kNK * 2u;   // 16 KB
+constexpr unsigned kNAHalf = kNM * kNK * 2u;          // 8 KB: one of A hi / A lo
+constexpr unsigned kNBHalf = kNMaxNs * kNK * 2u;      // 8 KB: one of B hi / B lo (at most)
+constexpr unsigned kNSlotBytes = 2u * kNAHalf + 2u * kNBHalf;   // 32 KB
 constexpr unsigned long long kNWaitNs = 2000000000ull;
+constexpr int kPackThreads = 256;   // pack CTA: one group of 8 signals at a time
+constexpr int kPackShortNp = 264;    // pack launch of short rows (n <= 260): many CTAs per SM
 
 struct TcnLeaf {
     int m;          // leaf size
@@ -64,24 +71,33 @@ struct TcnLeaf {
     int kchunks;    // ceil(m / 32)
     int mtiles;     // ceil(npad / 128)
     int lab;        // offset of the leaf's nodes in the plan's leaf-ordered label / output-position lists
-    int kc0;        // first B chunk of this leaf within a tile
-    int unit0;      // first accumulator (M-tile) of this leaf within a tile
+    int kc0;        // first chunk of this leaf in a tile's B image
+    int unit0;      // first unit (M-tile) of this leaf
     int pad;
     long long a_off;   // element offset of the leaf's basis images
 };
 
+// one plan of a launch (an entry of the caller's batch)
 struct TcnPlanDev {
     const float* x;
     float* y;
     long long batch;
     long long tile0;           // first tile of this plan in the launch
+    long long item0;           // first work item of this plan in the launch
     const int* prog;           // [pairs 2P][stage offsets S+1][labels n][out_pos n] ...
     const TcnLeaf* leaves;
+    const unsigned short* unit_leaf;   // per unit: its leaf
+    const short* gather;       // per chunk 32 node labels (-1: padding), chunks in leaf order
     const unsigned char* ahi;  // basis images of this launch's precision
     const unsigned char* alo;
+    unsigned char* bimg;       // B images of this plan's tiles (scratch): [tile][chunk][hi ns*64 B | lo]
+    float* scale;              // per signal (scratch)
     int* err;                  // the plan's device error word
     int n, np, ns, n_leaves, n_units, n_chunks, n_stages, n_pairs;
     int off_labels, off_outpos;
+    long long grp0;            // first 8-signal group of this plan in the launch (pack kernel)
+    int upi;                   // units per work item
+    int items_per_tile;
 };
 
 __device__ __forceinline__ unsigned su32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -165,7 +181,6 @@ __device__ __forceinline__ bool workers_any(bool v) {
                  : "memory");
     return r != 0;
 }
-__device__ __forceinline__ void workers_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
 // byte offset of (row, K group) in a [rows x 32] K-major no-swizzle image
 // whose 8-row groups are 512 B apart (4 K groups of 16 B per row)
@@ -173,15 +188,12 @@ __device__ __forceinline__ unsigned coff(int row, int kg) {
     return (unsigned)(((row >> 3) * 4 + kg) * 128 + (row & 7) * 16);
 }
 
-template <bool TILES>
-__device__ __forceinline__ int plan_of_tile(const TcnPlanDev* P, int n_plans, long long t) {
-    int lo = 0, hi = n_plans - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (P[mid].tile0 <= t) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
+// plan slot of work index v, walking forward from slot s (first indices in
+// slot order): WHAT = 0 work items, 1 pack groups
+template <int WHAT>
+__device__ __forceinline__ int slot_of(const TcnPlanDev* P, int n_plans, int s, long long v) {
+    while (s + 1 < n_plans && (WHAT == 0 ? P[s + 1].item0 : P[s + 1].grp0) <= v) ++s;
+    return s;
 }
 
 }  // namespace
@@ -190,24 +202,126 @@ __device__ __forceinline__ int plan_of_tile(const TcnPlanDev* P, int n_plans, lo
 namespace gft {
 namespace {
 
-// Persistent kernel over the tiles of every plan of one launch (plan order;
-// CTA b takes tiles b, b + grid, ...).  Dynamic shared memory:
-//   [ring: kNSlots x (A hi 8 KB | A lo 8 KB)]
-//   [B region: per (leaf, K chunk) of a tile, hi (ns x 64 B) then lo]
-//   [tile: ns rows x np floats -- input, then output staging][scales: 32 floats]
+// B images: one CTA (kPackThreads) per group of 8 signals (rows
+// row0..row0+7 of tile t of a plan; rows past the batch are zeros); CTA b
+// runs groups [range[b], range[b+1]) (first_slot[b]: the plan of the first).  Phases,
+// separated by barriers: copy the 8 rows (cp.async, row stride np), one warp
+// per row for its FP16 scale, the Haar stages (threads over rows x pairs),
+// then the B operand of every (leaf, K chunk): thread (chunk, K group, row)
+// gathers 8 post-stage values through the chunk's gather table and writes 16
+// B of hi and of lo, 32 consecutive threads covering 512 contiguous bytes.
+__global__ void __launch_bounds__(kPackThreads) tcn_pack_kernel(const TcnPlanDev* __restrict__ plans, int n_plans,
+                                                                const long long* __restrict__ range,
+                                                                const int* __restrict__ first_slot, int prec) {
+    extern __shared__ __align__(16) float buf[];
+    __shared__ float s_inv[8];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool fp16 = prec == GFT_PREC_FP16X3, split = prec != GFT_PREC_BF16;
+    int sl = first_slot[blockIdx.x];
+    for (long long g = range[blockIdx.x]; g < range[blockIdx.x + 1]; ++g) {
+        sl = slot_of<1>(plans, n_plans, sl, g);
+        const TcnPlanDev& D = plans[sl];
+        const int n = D.n, np = D.np, ns = D.ns, gpt = ns >> 3;
+        const long long local = g - D.grp0;
+        const long long t = local / gpt;
+        const int rg = (int)(local - t * gpt);
+        const long long row0 = t * ns + rg * 8;
+        const int valid = (int)max(0LL, min(8LL, D.batch - row0));
+        if ((n & 3) == 0) {
+            const int per = n >> 2;
+            for (int e = tid; e < valid * per; e += kPackThreads) {
+                const int r = e / per, c4 = e - r * per;
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(su32(buf + r * np + 4 * c4)),
+                             "l"(D.x + (row0 + r) * n + 4 * c4)
+                             : "memory");
+            }
+        } else {
+            for (int e = tid; e < valid * n; e += kPackThreads) {
+                const int r = e / n, c = e - r * n;
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(su32(buf + r * np + c)),
+                             "l"(D.x + row0 * n + e)
+                             : "memory");
+            }
+        }
+        asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+        __syncthreads();
+        // FP16: a power-of-two scale per signal bounding its post-stage values
+        if (warp < 8) {
+            float mx = 0.f;
+            if (fp16 && warp < valid)
+                for (int c = lane; c < n; c += 32) mx = fmaxf(mx, fabsf(buf[warp * np + c]));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            const float sc = mx > 0.f ? exp2f(ceilf(log2f(mx)) + (float)D.n_stages) : 1.f;
+            if (lane == 0) {
+                s_inv[warp] = 1.f / sc;
+                if (warp < valid) D.scale[row0 + warp] = sc;
+            }
+        }
+        // Haar stages in place (Sec. III; the 1/sqrt2 factors are in the basis)
+        for (int st = 0; st < D.n_stages; ++st) {
+            const int p0 = D.prog[2 * D.n_pairs + st], cnt = D.prog[2 * D.n_pairs + st + 1] - p0;
+            for (int e = tid; e < 8 * cnt; e += kPackThreads) {
+                const int r = e / cnt, pp = p0 + (e - r * cnt);
+                const int2 ij = *reinterpret_cast<const int2*>(D.prog + 2 * pp);
+                float* row = buf + r * np;
+                const float u = row[ij.x], v = row[ij.y];
+                row[ij.x] = u + v;
+                row[ij.y] = u - v;
+            }
+            __syncthreads();
+        }
+        __syncthreads();   // scales and stages visible
+        unsigned char* tb = D.bimg + (size_t)t * D.n_chunks * ns * 128;
+        for (int e = tid; e < D.n_chunks * 32; e += kPackThreads) {
+            const int r = e & 7, kg = (e >> 3) & 3, c = e >> 5;
+            const bool live = r < valid;
+            const float iv = s_inv[r];
+            const float* row = buf + r * np;
+            const int4 g4 = *reinterpret_cast<const int4*>(D.gather + c * kNK + kg * 8);
+            const short* gs = reinterpret_cast<const short*>(&g4);
+            float v[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) v[q] = (live && gs[q] >= 0) ? row[gs[q]] * iv : 0.f;
+            unsigned hi[4], lo[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (fp16) {
+                    const __half2 h = __floats2half2_rn(v[2 * q], v[2 * q + 1]);
+                    const float2 hf = __half22float2(h);
+                    const __half2 l = __floats2half2_rn(v[2 * q] - hf.x, v[2 * q + 1] - hf.y);
+                    hi[q] = *reinterpret_cast<const unsigned*>(&h);
+                    lo[q] = *reinterpret_cast<const unsigned*>(&l);
+                } else {
+                    const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+                    const float2 hf = __bfloat1622float2(h);
+                    const __nv_bfloat162 l = __floats2bfloat162_rn(v[2 * q] - hf.x, v[2 * q + 1] - hf.y);
+                    hi[q] = *reinterpret_cast<const unsigned*>(&h);
+                    lo[q] = *reinterpret_cast<const unsigned*>(&l);
+                }
+            }
+            unsigned char* dst = tb + (size_t)c * ns * 128 + coff(rg * 8 + r, kg);
+            __stcg(reinterpret_cast<uint4*>(dst), make_uint4(hi[0], hi[1], hi[2], hi[3]));
+            if (split) __stcg(reinterpret_cast<uint4*>(dst + ns * 64), make_uint4(lo[0], lo[1], lo[2], lo[3]));
+        }
+        __syncthreads();   // buffer reusable
+    }
+}
+
+// Work item i of a plan: tile t = i / items_per_tile, units
+// [g * upi, min((g + 1) * upi, n_units)) with g = i % items_per_tile.
+// CTA b runs items [range[b], range[b+1]) (first_slot[b]: plan of the first).
+// Shared memory: kNSlots ring slots of [A hi | A lo | B hi | B lo], 8 KB each.
 __global__ void __launch_bounds__(kNThreads, 1) tcn_kernel(const TcnPlanDev* __restrict__ plans, int n_plans,
-                                                          long long total_tiles, int prec, unsigned b_bytes,
-                                                          unsigned tile_floats) {
-    extern __shared__ __align__(128) unsigned char sm[];
-    unsigned char* ring = sm;
-    unsigned char* breg = sm + kNSlots * kNSlotBytes;
-    float* tile = reinterpret_cast<float*>(breg + b_bytes);
-    float* s_scale = tile + tile_floats;
-    __shared__ __align__(8) unsigned long long a_full[kNSlots], empty[kNSlots], b_ready, acc_full, drain;
+                                                          const long long* __restrict__ range,
+                                                          const int* __restrict__ first_slot, int prec) {
+    extern __shared__ __align__(128) unsigned char ring[];
+    __shared__ __align__(8) unsigned long long full[kNSlots], empty[kNSlots], acc_full[2], acc_free[2], drain;
+    __shared__ float s_sc[2][kNMaxNs];   // per-signal scales of the items in the two TMEM halves
     __shared__ unsigned s_tmem;
     __shared__ int s_abort;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    if (warp == 5) {
+    if (warp == kNWorkers + 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&s_tmem)),
                      "r"(kNCols)
                      : "memory");
@@ -215,11 +329,13 @@ __global__ void __launch_bounds__(kNThreads, 1) tcn_kernel(const TcnPlanDev* __r
     }
     if (tid == 0) {
         for (int i = 0; i < kNSlots; ++i) {
-            bar_init(&a_full[i], 1);
+            bar_init(&full[i], 1);
             bar_init(&empty[i], 1);
         }
-        bar_init(&b_ready, kNWorkers);
-        bar_init(&acc_full, 1);
+        for (int h = 0; h < 2; ++h) {
+            bar_init(&acc_full[h], 1);
+            bar_init(&acc_free[h], kNWorkers);
+        }
         bar_init(&drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_abort = 0;
@@ -230,251 +346,173 @@ __global__ void __launch_bounds__(kNThreads, 1) tcn_kernel(const TcnPlanDev* __r
     const unsigned tmem = s_tmem;
     const bool split = prec != GFT_PREC_BF16;
     const bool fp16 = prec == GFT_PREC_FP16X3;
-    const long long my_tiles = total_tiles > blockIdx.x ? (total_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const long long i0 = range[blockIdx.x], i1 = range[blockIdx.x + 1];
+    const int slot0 = first_slot[blockIdx.x];
     auto abort_now = [&](int* err) {
         s_abort = 1;
         atomicExch(err, (int)GFT_ERR_TIMEOUT);
     };
 
     if (warp == kNWorkers) {
-        // ---------------- basis chunks (TMA) ----------------
+        // ---------------- copies (TMA) ----------------
         if (lane == 0) {
             long long q = 0;
             bool issued[kNSlots] = {};
             unsigned par[kNSlots] = {};
             bool stop = false;
-            for (long long j = 0; j < my_tiles && !stop; ++j) {
-                const long long t = blockIdx.x + j * (long long)gridDim.x;
-                const TcnPlanDev& D = plans[plan_of_tile<true>(plans, n_plans, t)];
-                for (int k = 0; k < D.n_leaves && !stop; ++k) {
-                    const TcnLeaf L = D.leaves[k];
-                    for (int mt = 0; mt < L.mtiles && !stop; ++mt) {
-                        const unsigned bytes = (unsigned)min(kNM, L.npad - mt * kNM) * kNK * 2u;
-                        for (int kc = 0; kc < L.kchunks; ++kc, ++q) {
-                            const int s = (int)(q % kNSlots);
-                            const long long use = q / kNSlots;
-                            if (s_abort || (use >= 1 && !bar_wait(&empty[s], (unsigned)((use - 1) & 1)))) {
-                                abort_now(D.err);
-                                stop = true;
-                                break;
-                            }
-                            unsigned char* dst = ring + (size_t)s * kNSlotBytes;
-                            const size_t src =
-                                2 * (size_t)(L.a_off + (long long)kc * L.npad * kNK + (long long)mt * kNM * kNK);
-                            bar_expect(&a_full[s], split ? 2 * bytes : bytes);
-                            bulk(dst, D.ahi + src, bytes, &a_full[s]);
-                            if (split) bulk(dst + kNSlotBytes / 2, D.alo + src, bytes, &a_full[s]);
-                            issued[s] = true;
-                            par[s] = (unsigned)(use & 1);
+            int sl = slot0;
+            for (long long it = i0; it < i1 && !stop; ++it) {
+                sl = slot_of<0>(plans, n_plans, sl, it);
+                const TcnPlanDev& D = plans[sl];
+                const long long local = it - D.item0;
+                const long long t = local / D.items_per_tile;
+                const int g = (int)(local - t * D.items_per_tile);
+                const int u1 = min((g + 1) * D.upi, D.n_units);
+                const unsigned bbytes = (unsigned)D.ns * kNK * 2u;
+                const unsigned char* tb = D.bimg + (size_t)t * D.n_chunks * D.ns * 128;
+                for (int u = g * D.upi; u < u1 && !stop; ++u) {
+                    const TcnLeaf L = D.leaves[D.unit_leaf[u]];
+                    const int mt = u - L.unit0;
+                    const unsigned abytes = (unsigned)min(kNM, L.npad - mt * kNM) * kNK * 2u;
+                    for (int kc = 0; kc < L.kchunks; ++kc, ++q) {
+                        const int s = (int)(q % kNSlots);
+                        const long long use = q / kNSlots;
+                        if (s_abort || (use >= 1 && !bar_wait(&empty[s], (unsigned)((use - 1) & 1)))) {
+                            abort_now(D.err);
+                            stop = true;
+                            break;
                         }
+                        unsigned char* dst = ring + (size_t)s * kNSlotBytes;
+                        const size_t asrc =
+                            2 * (size_t)(L.a_off + (long long)kc * L.npad * kNK + (long long)mt * kNM * kNK);
+                        const unsigned char* bsrc = tb + (size_t)(L.kc0 + kc) * D.ns * 128;
+                        bar_expect(&full[s], split ? 2 * (abytes + bbytes) : abytes + bbytes);
+                        bulk(dst, D.ahi + asrc, abytes, &full[s]);
+                        bulk(dst + 2 * kNAHalf, bsrc, bbytes, &full[s]);
+                        if (split) {
+                            bulk(dst + kNAHalf, D.alo + asrc, abytes, &full[s]);
+                            bulk(dst + 2 * kNAHalf + kNBHalf, bsrc + D.ns * 64, bbytes, &full[s]);
+                        }
+                        issued[s] = true;
+                        par[s] = (unsigned)(use & 1);
                     }
                 }
             }
             for (int s = 0; s < kNSlots; ++s)   // no copy left in flight
-                if (issued[s]) bar_wait(&a_full[s], par[s]);
+                if (issued[s]) bar_wait(&full[s], par[s]);
         }
     } else if (warp == kNWorkers + 1) {
         // ---------------- MMAs ----------------
         if (lane == 0) {
             long long q = 0;
             bool stop = false;
-            for (long long j = 0; j < my_tiles && !stop; ++j) {
-                const long long t = blockIdx.x + j * (long long)gridDim.x;
-                const TcnPlanDev& D = plans[plan_of_tile<true>(plans, n_plans, t)];
-                if (s_abort || !bar_wait(&b_ready, (unsigned)(j & 1))) {
+            int sl = slot0;
+            for (long long it = i0, j = 0; it < i1 && !stop; ++it, ++j) {
+                sl = slot_of<0>(plans, n_plans, sl, it);
+                const TcnPlanDev& D = plans[sl];
+                const int h = (int)(j & 1);
+                const long long use_h = j >> 1;
+                if (s_abort || (use_h >= 1 && !bar_wait(&acc_free[h], (unsigned)((use_h - 1) & 1)))) {
                     abort_now(D.err);
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const long long local = it - D.item0;
+                const long long t = local / D.items_per_tile;
+                const int g = (int)(local - t * D.items_per_tile);
+                const int u0 = g * D.upi, u1 = min(u0 + D.upi, D.n_units);
                 const int ns = D.ns;
                 const unsigned id = idesc(ns, !fp16);
-                const unsigned bbase = su32(breg);
-                for (int k = 0; k < D.n_leaves && !stop; ++k) {
-                    const TcnLeaf L = D.leaves[k];
+                for (int u = u0; u < u1 && !stop; ++u) {
+                    const TcnLeaf L = D.leaves[D.unit_leaf[u]];
                     const int kmax = (L.m + 15) & ~15;
-                    for (int mt = 0; mt < L.mtiles && !stop; ++mt) {
-                        const unsigned dt = tmem + (unsigned)((L.unit0 + mt) * ns);
-                        for (int kc = 0; kc < L.kchunks; ++kc, ++q) {
-                            const int s = (int)(q % kNSlots);
-                            if (s_abort || !bar_wait(&a_full[s], (unsigned)((q / kNSlots) & 1))) {
-                                abort_now(D.err);
-                                stop = true;
-                                break;
-                            }
-                            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                            const unsigned abase = su32(ring + (size_t)s * kNSlotBytes);
-                            const unsigned bch = bbase + (unsigned)((L.kc0 + kc) * ns * 128);
-                            for (int ks = 0; ks < kNK / 16; ++ks) {
-                                if (kc * kNK + ks * 16 >= kmax) break;
-                                const unsigned koff = ks * 256u;
-                                const unsigned long long ah = sdesc(abase + koff, 128, 512);
-                                const unsigned long long bh = sdesc(bch + koff, 128, 512);
-                                mma(dt, ah, bh, id, (kc | ks) ? 1u : 0u);
-                                if (split) {
-                                    mma(dt, ah, sdesc(bch + (unsigned)(ns * 64) + koff, 128, 512), id, 1u);
-                                    mma(dt, sdesc(abase + kNSlotBytes / 2 + koff, 128, 512), bh, id, 1u);
-                                }
-                            }
-                            commit_to(&empty[s]);
+                    const unsigned dt = tmem + (unsigned)(h * kNHalf + (u - u0) * ns);
+                    for (int kc = 0; kc < L.kchunks; ++kc, ++q) {
+                        const int s = (int)(q % kNSlots);
+                        if (s_abort || !bar_wait(&full[s], (unsigned)((q / kNSlots) & 1))) {
+                            abort_now(D.err);
+                            stop = true;
+                            break;
                         }
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                        const unsigned base = su32(ring + (size_t)s * kNSlotBytes);
+                        const unsigned ahi = base, alo = base + kNAHalf;
+                        const unsigned bhi = base + 2 * kNAHalf, blo = bhi + kNBHalf;
+                        for (int ks = 0; ks < kNK / 16; ++ks) {
+                            if (kc * kNK + ks * 16 >= kmax) break;
+                            const unsigned koff = ks * 256u;
+                            const unsigned long long ah = sdesc(ahi + koff, 128, 512);
+                            const unsigned long long bh = sdesc(bhi + koff, 128, 512);
+                            mma(dt, ah, bh, id, (kc | ks) ? 1u : 0u);
+                            if (split) {
+                                mma(dt, ah, sdesc(blo + koff, 128, 512), id, 1u);
+                                mma(dt, sdesc(alo + koff, 128, 512), bh, id, 1u);
+                            }
+                        }
+                        commit_to(&empty[s]);
                     }
                 }
-                if (!stop) commit_to(&acc_full);
+                if (!stop) commit_to(&acc_full[h]);
             }
             commit_to(&drain);             // arrives once every MMA issued above is complete
             bar_wait(&drain, 0);
         }
     } else {
-        // ---------------- workers (warps 0-3) ----------------
-        const int wt = tid;
-        for (long long j = 0; j < my_tiles; ++j) {
-            const long long t = blockIdx.x + j * (long long)gridDim.x;
-            const TcnPlanDev D = plans[plan_of_tile<true>(plans, n_plans, t)];
-            const int n = D.n, np = D.np, ns = D.ns;
-            const long long tp = t - D.tile0;
-            const int rows = (int)min((long long)ns, D.batch - tp * ns);
-            const int* labels = D.prog + D.off_labels;
-            const int* outpos = D.prog + D.off_outpos;
-            // 1. signal rows -> tile (row stride np)
-            const float* src = D.x + tp * ns * (long long)n;
-            if ((n & 3) == 0) {
-                const int per = n >> 2;
-                for (int e = wt; e < rows * per; e += 128) {
-                    const int s = e / per, c4 = e - s * per;
-                    const unsigned d = su32(tile + s * np + 4 * c4);
-                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src + (long long)s * n + 4 * c4)
-                                 : "memory");
-                }
-            } else {
-                for (int e = wt; e < rows * n; e += 128) {
-                    const int s = e / n, c = e - s * n;
-                    const unsigned d = su32(tile + s * np + c);
-                    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src + e) : "memory");
-                }
-            }
-            asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
-            workers_sync();
-            // 2. per-signal scales (FP16: a power of two bounding the post-stage values)
-            for (int s = warp; s < 32; s += kNWorkers) {
-                float mx = 0.f;
-                if (fp16 && s < rows)
-                    for (int c = lane; c < n; c += 32) mx = fmaxf(mx, fabsf(tile[s * np + c]));
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-                if (lane == 0) s_scale[s] = mx > 0.f ? exp2f(ceilf(log2f(mx)) + (float)D.n_stages) : 1.f;
-            }
-            // 3. Haar stages in place (Sec. III; the 1/sqrt2 factors are in the basis)
-            for (int st = 0; st < D.n_stages; ++st) {
-                const int p0 = D.prog[2 * D.n_pairs + st], cnt = D.prog[2 * D.n_pairs + st + 1] - p0;
-                for (int e = wt; e < rows * cnt; e += 128) {
-                    const int s = e / cnt, pp = p0 + (e - s * cnt);
-                    const int i = D.prog[2 * pp], jj = D.prog[2 * pp + 1];
-                    float* row = tile + s * np;
-                    const float u = row[i], v = row[jj];
-                    row[i] = u + v;
-                    row[jj] = u - v;
-                }
-                workers_sync();
-            }
-            workers_sync();   // scales visible
-            // 4. B operand of every (leaf, K chunk): rows = signals, hi then lo
-            const int groups = ns >> 3;
-            for (int k = 0; k < D.n_leaves; ++k) {
-                const TcnLeaf L = D.leaves[k];
-                const int total = L.kchunks * groups * 32;
-                for (int e = wt; e < total; e += 128) {
-                    const int slo = e & 7, kg = (e >> 3) & 3, rest = e >> 5;
-                    const int rg = rest % groups, kc = rest / groups;
-                    const int s = rg * 8 + slo;
-                    const bool live = s < rows;
-                    const float inv = fp16 ? 1.f / s_scale[s] : 1.f;
-                    const int r0 = kc * kNK + kg * 8;
-                    float v[8];
-#pragma unroll
-                    for (int ee = 0; ee < 8; ++ee) {
-                        const int r = r0 + ee;
-                        v[ee] = (live && r < L.m) ? tile[s * np + labels[L.lab + r]] * inv : 0.f;
-                    }
-                    unsigned hi[4], lo[4];
-#pragma unroll
-                    for (int qq = 0; qq < 4; ++qq) {
-                        if (fp16) {
-                            const __half2 h = __floats2half2_rn(v[2 * qq], v[2 * qq + 1]);
-                            const float2 hf = __half22float2(h);
-                            const __half2 l = __floats2half2_rn(v[2 * qq] - hf.x, v[2 * qq + 1] - hf.y);
-                            hi[qq] = *reinterpret_cast<const unsigned*>(&h);
-                            lo[qq] = *reinterpret_cast<const unsigned*>(&l);
-                        } else {
-                            const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * qq], v[2 * qq + 1]);
-                            const float2 hf = __bfloat1622float2(h);
-                            const __nv_bfloat162 l = __floats2bfloat162_rn(v[2 * qq] - hf.x, v[2 * qq + 1] - hf.y);
-                            hi[qq] = *reinterpret_cast<const unsigned*>(&h);
-                            lo[qq] = *reinterpret_cast<const unsigned*>(&l);
-                        }
-                    }
-                    unsigned char* dst = breg + (size_t)(L.kc0 + kc) * ns * 128 + coff(s, kg);
-                    *reinterpret_cast<uint4*>(dst) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-                    if (split) *reinterpret_cast<uint4*>(dst + ns * 64) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-                }
-            }
-            // generic-proxy writes of the B region -> visible to the tensor cores
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            workers_sync();
-            if (lane == 0) bar_arrive(&b_ready);
-            // 5. wait for the tile's accumulators (uniform exit on timeout)
-            const bool bad = !bar_wait(&acc_full, (unsigned)(j & 1));
+        // ---------------- epilogue (warps 0-3) ----------------
+        int sl = slot0;
+        const unsigned lane_base = (unsigned)(warp * 32) << 16;
+        for (long long it = i0, j = 0; it < i1; ++it, ++j) {
+            sl = slot_of<0>(plans, n_plans, sl, it);
+            const TcnPlanDev& D = plans[sl];
+            const int h = (int)(j & 1);
+            const long long local = it - D.item0;
+            const long long t = local / D.items_per_tile;
+            const int g = (int)(local - t * D.items_per_tile);
+            const int u0 = g * D.upi, u1 = min(u0 + D.upi, D.n_units);
+            const int ns = D.ns, n = D.n;
+            const long long row0 = t * ns;
+            const int rows = (int)min((long long)ns, D.batch - row0);
+            // the tile's scales, while the MMAs run (the barrier below orders
+            // these writes before every read; the buffer of the item before
+            // last in this half was released by the previous item's barrier)
+            if (tid < ns) s_sc[h][tid] = (fp16 && tid < rows) ? D.scale[row0 + tid] : 1.f;
+            const bool bad = !bar_wait(&acc_full[h], (unsigned)((j >> 1) & 1));
             if (workers_any(bad || s_abort != 0)) {
-                if (wt == 0) abort_now(D.err);
+                if (tid == 0) abort_now(D.err);
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            // 6. accumulators -> output staging (the tile buffer is free: every
-            //    B chunk was built before the MMAs could complete)
-            const unsigned lane_base = (unsigned)(warp * 32) << 16;
-            for (int k = 0; k < D.n_leaves; ++k) {
-                const TcnLeaf L = D.leaves[k];
-                for (int mt = 0; mt < L.mtiles; ++mt) {
-                    const int c = mt * kNM + warp * 32 + lane;
-                    const bool valid = c < L.m;
-                    const int pos = valid ? outpos[L.lab + c] : 0;
-                    for (int c0 = 0; c0 < ns; c0 += 16) {
-                        unsigned r[16];
-                        asm volatile(
-                            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-                            "[%16];"
-                            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                              "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-                              "=r"(r[14]), "=r"(r[15])
-                            : "r"(tmem + lane_base + (unsigned)((L.unit0 + mt) * ns + c0)));
-                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                        if (valid) {
+            const int* outpos = D.prog + D.off_outpos;
+            for (int u = u0; u < u1; ++u) {
+                const TcnLeaf L = D.leaves[D.unit_leaf[u]];
+                const int c = (u - L.unit0) * kNM + warp * 32 + lane;
+                const bool valid = c < L.m;
+                const int pos = valid ? outpos[L.lab + c] : 0;
+                for (int c0 = 0; c0 < ns; c0 += 16) {
+                    unsigned r[16];
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                        "[%16];"
+                        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                          "=r"(r[14]), "=r"(r[15])
+                        : "r"(tmem + lane_base + (unsigned)(h * kNHalf + (u - u0) * ns + c0)));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    if (valid) {
 #pragma unroll
-                            for (int qq = 0; qq < 16; ++qq) {
-                                const int s = c0 + qq;
-                                if (s < rows) tile[s * np + pos] = __uint_as_float(r[qq]) * s_scale[s];
+                        for (int qq = 0; qq < 16; ++qq) {
+                            const int s = c0 + qq;
+                            if (s < rows) {
+                                const float v = __uint_as_float(r[qq]) * s_sc[h][s];
+                                __stcs(D.y + (row0 + s) * n + pos, v);
                             }
                         }
                     }
                 }
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            workers_sync();
-            // 7. output rows, coalesced
-            float* dst = D.y + tp * ns * (long long)n;
-            if ((n & 3) == 0) {
-                const int per = n >> 2;
-                for (int e = wt; e < rows * per; e += 128) {
-                    const int s = e / per, c4 = e - s * per;
-                    const float4 v = *reinterpret_cast<const float4*>(tile + s * np + 4 * c4);
-                    __stcs(reinterpret_cast<float4*>(dst + (long long)s * n + 4 * c4), v);
-                }
-            } else {
-                for (int e = wt; e < rows * n; e += 128) {
-                    const int s = e / n, c = e - s * n;
-                    __stcs(dst + e, tile[s * np + c]);
-                }
-            }
-            workers_sync();   // tile buffer free for the next load
+            __syncwarp();
+            if (lane == 0) bar_arrive(&acc_free[h]);
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -495,17 +533,19 @@ namespace gft {
 namespace {
 
 constexpr size_t kNSmemLimit = 232448;
-constexpr size_t kNTwoPerSm = 112 * 1024;   // dynamic + static shared memory for two CTAs per SM
-constexpr size_t kNFixed = (size_t)kNSlots * kNSlotBytes + 32 * sizeof(float);
 
 struct TcnPlan {
     std::vector<TcnLeaf> leaves;
     TcnLeaf* d_leaves = nullptr;
+    unsigned short* d_unit_leaf = nullptr;
+    short* d_gather = nullptr;          // per chunk 32 node labels (-1: padding)
     int n_units = 0, n_chunks = 0;
     long long img_elems = 0;
     unsigned char* d_img[2][2] = {};   // [BF16, FP16][hi, lo]
     ~TcnPlan() {
         if (d_leaves) cudaFree(d_leaves);
+        if (d_unit_leaf) cudaFree(d_unit_leaf);
+        if (d_gather) cudaFree(d_gather);
         for (auto& a : d_img)
             for (auto& q : a)
                 if (q) cudaFree(q);
@@ -525,18 +565,14 @@ float bf16_to_float(uint16_t b) {
     return f;
 }
 
-int units_of(const gft_plan_s& p) {
-    int u = 0;
-    for (auto& lf : p.leaves) u += (((lf.m() + 15) & ~15) + kNM - 1) / kNM;
-    return u;
-}
-
 TcnPlan* tcn_prepare(gft_plan_s& p) {
     if (p.tcn) return static_cast<TcnPlan*>(p.tcn);
     std::unique_ptr<TcnPlan> T(new TcnPlan);
     int lab = 0, kc0 = 0, unit0 = 0;
     long long a = 0;
-    for (auto& lf : p.leaves) {
+    std::vector<unsigned short> unit_leaf;
+    for (size_t k = 0; k < p.leaves.size(); ++k) {
+        const Leaf& lf = p.leaves[k];
         TcnLeaf L{};
         L.m = lf.m();
         L.npad = (L.m + 15) & ~15;
@@ -546,6 +582,7 @@ TcnPlan* tcn_prepare(gft_plan_s& p) {
         L.kc0 = kc0;
         L.unit0 = unit0;
         L.a_off = a;
+        for (int mt = 0; mt < L.mtiles; ++mt) unit_leaf.push_back((unsigned short)k);
         lab += L.m;
         kc0 += L.kchunks;
         unit0 += L.mtiles;
@@ -554,16 +591,26 @@ TcnPlan* tcn_prepare(gft_plan_s& p) {
     }
     T->n_units = unit0;
     T->n_chunks = kc0;
+    std::vector<short> gat((size_t)kc0 * kNK, -1);
+    for (size_t k = 0; k < p.leaves.size(); ++k) {
+        const TcnLeaf& L = T->leaves[k];
+        for (int r = 0; r < L.m; ++r) gat[(size_t)(L.kc0 + r / kNK) * kNK + r % kNK] = (short)p.leaves[k].labels[r];
+    }
+    GFT_CUDA(cudaMalloc(&T->d_gather, sizeof(short) * std::max<size_t>(1, gat.size())));
+    GFT_CUDA(cudaMemcpy(T->d_gather, gat.data(), sizeof(short) * gat.size(), cudaMemcpyHostToDevice));
     T->img_elems = a;
     GFT_CUDA(cudaMalloc(&T->d_leaves, sizeof(TcnLeaf) * T->leaves.size()));
     GFT_CUDA(cudaMemcpy(T->d_leaves, T->leaves.data(), sizeof(TcnLeaf) * T->leaves.size(), cudaMemcpyHostToDevice));
+    GFT_CUDA(cudaMalloc(&T->d_unit_leaf, sizeof(unsigned short) * unit_leaf.size()));
+    GFT_CUDA(cudaMemcpy(T->d_unit_leaf, unit_leaf.data(), sizeof(unsigned short) * unit_leaf.size(),
+                        cudaMemcpyHostToDevice));
     p.tcn = T.release();
     return static_cast<TcnPlan*>(p.tcn);
 }
 
 // basis images of one precision: per leaf and 32-wide K chunk, npad rows
-// (output coefficients c) x 32 K (inputs r) in the K-major core-matrix
-// order of the kernel; A[c][r] = M_k[r][c], split into hi and lo
+// (output coefficients c) x 32 K (inputs r) in the kernel's K-major
+// core-matrix order; A[c][r] = M_k[r][c], split into hi and lo
 void tcn_images(gft_plan_s& p, TcnPlan& T, bool fp16) {
     const int w = fp16 ? 1 : 0;
     if (T.d_img[w][0]) return;
@@ -598,29 +645,26 @@ void tcn_images(gft_plan_s& p, TcnPlan& T, bool fp16) {
 
 int np_of(int n) { return ((n + 3) & ~3) + 4; }
 
-// signals per tile: 32 when the accumulators fit in TMEM and the tile stays
-// small, else 16
-int ns_of(const gft_plan_s& p, int64_t batch, int units) {
-    if (batch > 16 && units * 32 <= kNCols && (size_t)32 * np_of(p.n) * sizeof(float) <= 32 * 1024) return 32;
-    return 16;
-}
-
-struct TcnClass {
+struct TcnBatch {
+    uint32_t prec = GFT_PREC_BF16X3;
     std::vector<int> members;            // slot -> index in the batch's plan list
     std::vector<TcnPlanDev> desc;
     TcnPlanDev* d_desc = nullptr;
-    long long total_tiles = 0;
-    unsigned b_cap = 0, tile_cap = 0;
-    size_t smem = 0;
+    long long* d_range = nullptr;        // grid + 1 item boundaries
+    int* d_first = nullptr;              // plan slot of each range's first item
+    unsigned char* d_scratch = nullptr;  // B images and per-signal scales
+    long long total_items = 0, total_groups = 0;
     int grid = 0;
-};
-
-struct TcnBatch {
-    uint32_t prec = GFT_PREC_BF16X3;
-    std::vector<TcnClass> classes;
+    // pack launches: plans with short rows first (many warps per SM), then the rest
+    long long pack_split = 0;
+    int pack_grid[2] = {0, 0}, np_cap[2] = {4, 4};
+    size_t pack_smem[2] = {0, 0};
+    long long* d_pack_range[2] = {nullptr, nullptr};   // per part: grid + 1 group boundaries
+    int* d_pack_first[2] = {nullptr, nullptr};
     ~TcnBatch() {
-        for (auto& c : classes)
-            if (c.d_desc) cudaFree(c.d_desc);
+        for (void* q : {(void*)d_desc, (void*)d_range, (void*)d_first, (void*)d_scratch, (void*)d_pack_range[0],
+                        (void*)d_pack_range[1], (void*)d_pack_first[0], (void*)d_pack_first[1]})
+            if (q) cudaFree(q);
     }
 };
 
@@ -630,13 +674,7 @@ bool tcn_eligible(const gft_plan_s& p) {
     if (p.right || !p.has_device || p.n < 2) return false;
     for (auto& lf : p.leaves)
         if (lf.m() > kNMaxLeaf) return false;
-    if (units_of(p) * 16 > kNCols) return false;
-    const size_t bytes = (size_t)16 * 128 * [&] {
-        int c = 0;
-        for (auto& lf : p.leaves) c += (lf.m() + kNK - 1) / kNK;
-        return c;
-    }() + (size_t)16 * np_of(p.n) * sizeof(float);
-    return kNFixed + bytes + 1024 <= kNSmemLimit;
+    return (size_t)8 * np_of(p.n) * sizeof(float) + 2048 <= kNSmemLimit;
 }
 
 void tcn_free(gft_plan_s& p) {
@@ -650,8 +688,7 @@ void* tcn_batch_create(const std::vector<gft_plan_s*>& plans, const std::vector<
     const bool fp16 = precision == GFT_PREC_FP16X3;
     const int k = (int)plans.size();
     std::vector<TcnPlanDev> d(k);
-    std::vector<int> cls(k);
-    std::vector<double> cost(k);
+    std::vector<double> cost(k);          // per work item: bytes moved + a fixed cost
     for (int i = 0; i < k; ++i) {
         gft_plan_s& p = *plans[i];
         if (!tcn_eligible(p)) fail(GFT_ERR_UNSUPPORTED, "plan not supported by the few-signals tensor-core kernel");
@@ -662,12 +699,15 @@ void* tcn_batch_create(const std::vector<gft_plan_s*>& plans, const std::vector<
         e.batch = batches[i];
         e.prog = p.dev.d_ints;
         e.leaves = T->d_leaves;
+        e.unit_leaf = T->d_unit_leaf;
+        e.gather = T->d_gather;
         e.ahi = T->d_img[fp16 ? 1 : 0][0];
         e.alo = T->d_img[fp16 ? 1 : 0][1];
         e.err = p.dev.d_err;
         e.n = p.n;
         e.np = np_of(p.n);
-        e.ns = ns_of(p, batches[i], T->n_units);
+        // signals per tile: the whole batch up to 128 (a multiple of 16)
+        e.ns = (int)std::min<int64_t>(kNMaxNs, std::max<int64_t>(16, (batches[i] + 15) & ~int64_t(15)));
         e.n_leaves = (int)T->leaves.size();
         e.n_units = T->n_units;
         e.n_chunks = T->n_chunks;
@@ -675,74 +715,157 @@ void* tcn_batch_create(const std::vector<gft_plan_s*>& plans, const std::vector<
         e.n_pairs = p.dev.n_pairs;
         e.off_labels = 2 * p.dev.n_pairs + p.dev.n_stages + 1;
         e.off_outpos = e.off_labels + p.n;
-        const size_t bytes = (size_t)e.n_chunks * e.ns * 128 + (size_t)e.ns * e.np * sizeof(float);
-        cls[i] = kNFixed + bytes + 1024 <= kNTwoPerSm ? 0 : 1;
-        double a_chunks = 0;
-        for (auto& L : T->leaves) a_chunks += (double)L.mtiles * L.kchunks;
-        cost[i] = a_chunks * 16384.0 + (double)e.ns * p.n * 8.0;   // bytes moved per tile
+        e.upi = std::max(1, std::min(T->n_units, kNHalf / e.ns));
+        e.items_per_tile = (T->n_units + e.upi - 1) / e.upi;
+        double steps = 0;
+        for (auto& L : T->leaves) steps += (double)L.mtiles * L.kchunks;
+        cost[i] = steps / e.items_per_tile * (2.0 * kNAHalf + 2.0 * e.ns * kNK * 2) +
+                  (double)e.upi * kNM * e.ns * 4.0 + 20000.0;
     }
-    for (int c = 0; c < 2; ++c) {
-        TcnClass C;
-        for (int i = 0; i < k; ++i)
-            if (cls[i] == c) C.members.push_back(i);
-        if (C.members.empty()) continue;
-        std::stable_sort(C.members.begin(), C.members.end(), [&](int a, int b) { return cost[a] > cost[b]; });
-        for (int i : C.members) {
-            TcnPlanDev e = d[i];
-            e.tile0 = C.total_tiles;
-            C.total_tiles += (e.batch + e.ns - 1) / e.ns;
-            C.b_cap = std::max(C.b_cap, (unsigned)(e.n_chunks * e.ns * 128));
-            C.tile_cap = std::max(C.tile_cap, (unsigned)(e.ns * e.np));
-            C.desc.push_back(e);
+    // slots: plans with rows of at most kPackShortNp floats first, each part
+    // by decreasing cost per item
+    auto part = [&](int i) { return d[i].np <= kPackShortNp ? 0 : 1; };
+    B->members.resize(k);
+    for (int i = 0; i < k; ++i) B->members[i] = i;
+    std::stable_sort(B->members.begin(), B->members.end(), [&](int a, int b) {
+        return part(a) != part(b) ? part(a) < part(b) : cost[a] > cost[b];
+    });
+    size_t scratch = 0;
+    std::vector<size_t> off_img(k), off_scale(k);
+    long long tiles_all = 0;
+    for (int i : B->members) {
+        TcnPlanDev e = d[i];
+        const long long tiles = (e.batch + e.ns - 1) / e.ns;
+        e.tile0 = tiles_all;
+        e.item0 = B->total_items;
+        e.grp0 = B->total_groups;
+        tiles_all += tiles;
+        B->total_items += tiles * e.items_per_tile;
+        B->total_groups += tiles * (e.ns / 8);
+        if (part(i) == 0) B->pack_split = B->total_groups;
+        B->np_cap[part(i)] = std::max(B->np_cap[part(i)], e.np);
+        off_img[i] = scratch;
+        scratch += (size_t)tiles * e.n_chunks * e.ns * 128;
+        scratch = (scratch + 255) & ~size_t(255);
+        off_scale[i] = scratch;
+        scratch += sizeof(float) * (size_t)tiles * e.ns;
+        scratch = (scratch + 255) & ~size_t(255);
+        B->desc.push_back(e);
+    }
+    GFT_CUDA(cudaMalloc(&B->d_scratch, std::max<size_t>(scratch, 256)));
+    for (size_t sl = 0; sl < B->desc.size(); ++sl) {
+        const int i = B->members[sl];
+        B->desc[sl].bimg = B->d_scratch + off_img[i];
+        B->desc[sl].scale = reinterpret_cast<float*>(B->d_scratch + off_scale[i]);
+    }
+    // main kernel: one CTA per SM, contiguous item ranges of about equal cost
+    const size_t smem = (size_t)kNSlots * kNSlotBytes;
+    GFT_CUDA(cudaFuncSetAttribute(tcn_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    B->grid = (int)std::max<long long>(1, std::min<long long>(B->total_items, sm_count()));
+    double total = 0.0;
+    for (size_t sl = 0; sl < B->desc.size(); ++sl) {
+        const TcnPlanDev& e = B->desc[sl];
+        total += cost[B->members[sl]] * (double)((e.batch + e.ns - 1) / e.ns * e.items_per_tile);
+    }
+    std::vector<long long> range(B->grid + 1, B->total_items);
+    std::vector<int> first(B->grid, std::max(0, (int)B->desc.size() - 1));
+    range[0] = 0;
+    first[0] = 0;
+    double acc = 0.0;
+    int cta = 1;
+    for (size_t sl = 0; sl < B->desc.size() && cta < B->grid; ++sl) {
+        const TcnPlanDev& e = B->desc[sl];
+        const long long items = (e.batch + e.ns - 1) / e.ns * e.items_per_tile;
+        for (long long t = 0; t < items && cta < B->grid; ++t) {
+            acc += cost[B->members[sl]];
+            while (cta < B->grid && acc >= total * cta / B->grid) {
+                range[cta] = std::min(e.item0 + t + 1, B->total_items);
+                first[cta] = (int)sl;
+                ++cta;
+            }
         }
-        C.tile_cap = (C.tile_cap + 31) & ~31u;
-        C.smem = kNFixed + C.b_cap + sizeof(float) * (size_t)C.tile_cap;
-        if (C.smem > kNSmemLimit) fail(GFT_ERR_UNSUPPORTED, "few-signals tensor-core batch needs too much shared memory");
-        cudaFuncAttributes fa{};
-        GFT_CUDA(cudaFuncGetAttributes(&fa, tcn_kernel));
-        if (C.smem + fa.sharedSizeBytes > kNSmemLimit)
-            fail(GFT_ERR_UNSUPPORTED, "few-signals tensor-core batch needs too much shared memory");
-        GFT_CUDA(cudaFuncSetAttribute(tcn_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)(kNSmemLimit - fa.sharedSizeBytes)));
-        int per_sm = 0;
-        GFT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tcn_kernel, kNThreads, C.smem));
-        if (per_sm < 1) fail(GFT_ERR_UNSUPPORTED, "few-signals tensor-core kernel does not fit on an SM");
-        per_sm = std::min(per_sm, 2);   // TMEM: 256 columns per CTA
-        C.grid = (int)std::max<long long>(1, std::min<long long>(C.total_tiles, (long long)per_sm * sm_count()));
-        B->classes.push_back(std::move(C));   // owned by the batch before the allocation
-        TcnClass& D = B->classes.back();
-        GFT_CUDA(cudaMalloc(&D.d_desc, sizeof(TcnPlanDev) * D.desc.size()));
     }
+    // pack kernels: contiguous group ranges of about equal cost (row length
+    // plus a fixed cost) per CTA, in each part
+    GFT_CUDA(cudaFuncSetAttribute(tcn_pack_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kNSmemLimit - 1024)));
+    for (int c = 0; c < 2; ++c) {
+        const long long g0 = c == 0 ? 0 : B->pack_split, g1 = c == 0 ? B->pack_split : B->total_groups;
+        B->pack_smem[c] = (size_t)8 * B->np_cap[c] * sizeof(float);
+        int per_sm = 0;
+        GFT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tcn_pack_kernel, kPackThreads, B->pack_smem[c]));
+        per_sm = std::max(1, per_sm);
+        const int grid = (int)std::max<long long>(0, std::min<long long>(g1 - g0, (long long)per_sm * sm_count()));
+        B->pack_grid[c] = grid;
+        if (!grid) continue;
+        double tot = 0.0;
+        for (const TcnPlanDev& e : B->desc)
+            if (e.grp0 >= g0 && e.grp0 < g1) tot += (double)((e.batch + e.ns - 1) / e.ns * (e.ns / 8)) * (e.n + 64.0);
+        std::vector<long long> pr(grid + 1, g1);
+        std::vector<int> pf(grid, 0);
+        pr[0] = g0;
+        int first_sl = 0;
+        while (first_sl + 1 < (int)B->desc.size() && B->desc[first_sl + 1].grp0 <= g0) ++first_sl;
+        pf[0] = first_sl;
+        for (int b = 1; b < grid; ++b) pf[b] = (int)B->desc.size() - 1;
+        double acc = 0.0;
+        int cta = 1;
+        for (size_t sl = first_sl; sl < B->desc.size() && cta < grid; ++sl) {
+            const TcnPlanDev& e = B->desc[sl];
+            if (e.grp0 >= g1) break;
+            const long long groups = (e.batch + e.ns - 1) / e.ns * (e.ns / 8);
+            for (long long q = 0; q < groups && cta < grid; ++q) {
+                acc += e.n + 64.0;
+                while (cta < grid && acc >= tot * cta / grid) {
+                    pr[cta] = e.grp0 + q + 1;
+                    pf[cta] = (int)sl;
+                    ++cta;
+                }
+            }
+        }
+        GFT_CUDA(cudaMalloc(&B->d_pack_range[c], sizeof(long long) * pr.size()));
+        GFT_CUDA(cudaMalloc(&B->d_pack_first[c], sizeof(int) * pf.size()));
+        GFT_CUDA(cudaMemcpy(B->d_pack_range[c], pr.data(), sizeof(long long) * pr.size(), cudaMemcpyHostToDevice));
+        GFT_CUDA(cudaMemcpy(B->d_pack_first[c], pf.data(), sizeof(int) * pf.size(), cudaMemcpyHostToDevice));
+    }
+    GFT_CUDA(cudaMalloc(&B->d_desc, sizeof(TcnPlanDev) * std::max<size_t>(1, B->desc.size())));
+    GFT_CUDA(cudaMalloc(&B->d_range, sizeof(long long) * range.size()));
+    GFT_CUDA(cudaMalloc(&B->d_first, sizeof(int) * first.size()));
+    GFT_CUDA(cudaMemcpy(B->d_range, range.data(), sizeof(long long) * range.size(), cudaMemcpyHostToDevice));
+    GFT_CUDA(cudaMemcpy(B->d_first, first.data(), sizeof(int) * first.size(), cudaMemcpyHostToDevice));
     return B.release();
 }
 
 void tcn_batch_upload(void* h, const std::vector<const float*>& x, const std::vector<float*>& y, cudaStream_t st) {
     TcnBatch* B = static_cast<TcnBatch*>(h);
-    for (auto& C : B->classes) {
-        for (size_t sl = 0; sl < C.desc.size(); ++sl) {
-            C.desc[sl].x = x[C.members[sl]];
-            C.desc[sl].y = y[C.members[sl]];
-        }
-        GFT_CUDA(cudaMemcpyAsync(C.d_desc, C.desc.data(), sizeof(TcnPlanDev) * C.desc.size(), cudaMemcpyHostToDevice, st));
+    for (size_t sl = 0; sl < B->desc.size(); ++sl) {
+        B->desc[sl].x = x[B->members[sl]];
+        B->desc[sl].y = y[B->members[sl]];
     }
+    if (!B->desc.empty())
+        GFT_CUDA(cudaMemcpyAsync(B->d_desc, B->desc.data(), sizeof(TcnPlanDev) * B->desc.size(), cudaMemcpyHostToDevice,
+                                 st));
 }
 
 void tcn_batch_launch(void* h, cudaStream_t st) {
     TcnBatch* B = static_cast<TcnBatch*>(h);
-    for (auto& C : B->classes) {
-        if (C.total_tiles == 0) continue;
-        tcn_kernel<<<C.grid, kNThreads, C.smem, st>>>(C.d_desc, (int)C.desc.size(), C.total_tiles, (int)B->prec,
-                                                       C.b_cap, C.tile_cap);
+    if (B->total_items == 0) return;
+    for (int c = 0; c < 2; ++c) {
+        if (B->pack_grid[c] == 0) continue;
+        tcn_pack_kernel<<<B->pack_grid[c], kPackThreads, B->pack_smem[c], st>>>(
+            B->d_desc, (int)B->desc.size(), B->d_pack_range[c], B->d_pack_first[c], (int)B->prec);
         GFT_CUDA(cudaGetLastError());
     }
+    tcn_kernel<<<B->grid, kNThreads, (size_t)kNSlots * kNSlotBytes, st>>>(B->d_desc, (int)B->desc.size(), B->d_range,
+                                                                         B->d_first, (int)B->prec);
+    GFT_CUDA(cudaGetLastError());
 }
 
 void tcn_batch_free(void* h) { delete static_cast<TcnBatch*>(h); }
 
 int tcn_batch_launches(void* h) {
-    int n = 0;
-    for (auto& c : static_cast<TcnBatch*>(h)->classes) n += c.total_tiles > 0 ? 1 : 0;
-    return n;
+    const TcnBatch* B = static_cast<TcnBatch*>(h);
+    if (B->total_items == 0) return 0;
+    return 1 + (B->pack_grid[0] > 0 ? 1 : 0) + (B->pack_grid[1] > 0 ? 1 : 0);
 }
 
 }  // namespace gft

@@ -235,3 +235,24 @@ def test_tensor_core_batch_with_odd_largest_graph(env, prec):
     torch.cuda.synchronize()
     for p, x, y in zip(plans, xs, ys):
         _check_tc_entry(p, x, y, prec)
+
+
+def test_small_graph_batch_sizes_and_item_edges(env):
+    """Small graphs in one batch: zero to two stages, batches on both sides of
+    every tile size (128, 256, 512 signals) and of the cost-balanced CTA
+    ranges, a single signal, an empty entry; outputs equal the table-driven
+    single-plan forward bit for bit."""
+    gft, torch = env
+    graphs = [W.path(2), W.path(3), W.cycle(8), W.grid(4), W.path(16), W.path(17), W.grid(5, 3), W.cycle(32),
+              W.bipartite(32, 0.3, seed=11), W.skeleton25(), W.star(9), W.complete(6)]
+    plans = _plans(gft, graphs)
+    batches = [1, 127, 128, 129, 511, 512, 513, 1537, 100, 4099, 33, 0]
+    b = gft.Batch(plans, batches)
+    xs = [torch.from_numpy(W.signals(max(bt, 1), g.n, 300 + i)).cuda()[:bt] for i, (g, bt) in
+          enumerate(zip(graphs, batches))]
+    ys = [torch.full_like(x, float("nan")) for x in xs]
+    b.bind(xs, ys).forward()
+    torch.cuda.synchronize()
+    for p, x, y in zip(plans, xs, ys):
+        if x.shape[0]:
+            assert torch.equal(y, p.forward(x)), p.n

@@ -79,6 +79,8 @@ FAMILIES = [
     (W.grid6_bidiag(4), False), (W.grid6_bidiag(8), False), (W.zgrid(4), False), (W.zgrid(8), False),
     (W.cycle(80), False), (W.cycle(128), False), (W.grid(10), False), (W.bipartite(72, 0.2, seed=5), False),
     (W.path(100), False), (W.bipartite(128, 0.1, seed=3), False),
+    (W.path_recursive(64), False), (W.path_recursive(100), False), (W.path_recursive(256), False),
+    (W.cycle_recursive(64), False),
 ]
 
 

@@ -78,6 +78,38 @@ def test_path8_fast_gft_subblocks():
     assert np.allclose(f.U, dct2(8), atol=1e-12)
 
 
+@pytest.mark.parametrize("N,leaves", [(8, [2, 2, 4]), (16, [2, 2, 4, 8]), (24, [3, 3, 6, 12]),
+                                      (64, [2, 2, 4, 8, 16, 32]), (100, [25, 25, 50])])
+def test_recursive_path_stages_reach_dct2(N, leaves):
+    """Recursion inside the DCT-II leaf (Sec. V-B, end of Sec. IV-C): after a
+    reversal stage the sum block of a uniform path is again a uniform path,
+    so reversing it again (and again) is a valid next stage.  The staged
+    factorisation must still give exactly the DCT-II basis, signs included,
+    with difference blocks of N/2, N/4, ... nodes."""
+    g = W.path_recursive(N)
+    L = graph.laplacian(g.W, g.s)
+    f = gft.fast_gft(L, g.phis)
+    assert sorted(len(b.labels) for b in f.fact.leaves) == leaves
+    assert np.allclose(f.U, dct2(N), atol=1e-11)
+    assert max(f.fact.offblock) <= 1e-13 * max(1.0, np.abs(L).max())
+
+
+@pytest.mark.parametrize("N", [16, 32, 64])
+def test_recursive_cycle_stages(N):
+    """Cycle: after its two reflections the G++ block is a uniform path
+    (DCT-II, Sec. V-C); reversing it recursively keeps an exact GFT: the
+    real-DFT eigenspaces of the cycle, spectrum 2 - 2cos(2 pi k / N)."""
+    g = W.cycle_recursive(N)
+    L = graph.laplacian(g.W, g.s)
+    f = gft.fast_gft(L, g.phis)
+    assert len(g.phis) > 2
+    _check_basis(L, f.lam, f.U)
+    lam_cf = np.sort([2 - 2 * math.cos(2 * math.pi * k / N) for k in range(N)])
+    assert np.allclose(f.lam, lam_cf, atol=1e-12)
+    lam_d, U_d = gft.dense_gft(L)
+    assert projector_distance(f.U, U_d, lam_d) < 1e-10
+
+
 @pytest.mark.parametrize("N", [4, 6, 12, 16, 20])
 def test_cycle_real_dft_eigenspaces(N):
     """Cycle: eigenspaces span{cos(2 pi k i/N), sin(2 pi k i/N)} with
