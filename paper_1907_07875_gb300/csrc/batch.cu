@@ -45,10 +45,11 @@ using namespace core;
 namespace {
 
 constexpr int kBatchThreads = 128;
-constexpr int kTcMinLeaf = 64;   // leaves this wide go to the tensor cores in a tensor-core batch
+constexpr int kTcMinLeaf = 64;   // leaves this wide go to the 128-signal tensor-core kernel in a tensor-core batch
+constexpr int kTcnMinLeaf = 64;  // leaves this wide go to the few-signals tensor-core kernel
 constexpr int64_t kTcnMaxBatch = 4096;   // graphs with at most this many signals use the few-signals kernel
 constexpr int kBatchSmemLimit = 232448;
-constexpr size_t kTileCapBytes = 34816;        // largest tile a plan may choose (128 signals x 65 nodes + slack)
+constexpr size_t kTileCapBytes = 17408;        // largest tile a plan may choose (keeps several CTAs per SM)
 constexpr size_t kDoubleBufBytes = 72 * 1024;  // two tile buffers only if they fit in this
 constexpr int kClassStride[] = {17, 33, 65, 129, 257};
 constexpr int kClasses = 5;
@@ -487,9 +488,10 @@ gft_status gft_batch_create(int32_t n_plans, const gft_plan_t* plans, const int6
             int max_leaf = 0;
             for (auto& lf : p->leaves) max_leaf = std::max(max_leaf, lf.m());
             int kind;
-            const bool tc_prec = b->precision != GFT_PREC_FP32 && max_leaf >= kTcMinLeaf;
-            if (tc_prec && tcn_eligible(*p) && (batches[i] <= kTcnMaxBatch || !tc_eligible(*p))) kind = 3;
-            else if (tc_prec && tc_eligible(*p)) kind = 2;
+            const bool tc_prec = b->precision != GFT_PREC_FP32;
+            const bool big_batch_tc = tc_prec && max_leaf >= kTcMinLeaf && tc_eligible(*p) && batches[i] > kTcnMaxBatch;
+            if (tc_prec && max_leaf >= kTcnMinLeaf && !big_batch_tc && tcn_eligible(*p)) kind = 3;
+            else if (tc_prec && max_leaf >= kTcMinLeaf && tc_eligible(*p)) kind = 2;
             else if (p->dev.max_bucket != 0 && !(wide_configured(*p) && wide_ready(*p, false))) kind = 0;
             else if (wide_configured(*p)) kind = 1;
             else fail(GFT_ERR_UNSUPPORTED, "plan " + std::to_string(i) + " has a leaf wider than 512 nodes");

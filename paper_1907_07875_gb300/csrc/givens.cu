@@ -25,6 +25,7 @@
 struct gft_givens_s {
     int n = 0, S = 0;
     int xor_log2 = 0;              // > 0: butterfly wiring (stage t pairs i, i ^ 2^(t mod log2 n)), n <= 64
+    int brick = 0;                 // 1: neighbour wiring (even stages (2k, 2k+1), odd (2k+1, 2k+2) and (n-1, 0))
     int* d_pairs = nullptr;        // S * n/2 * 2
     float* d_partials = nullptr;   // grid * S * n/2 (scratch for the backward pass)
     int partial_rows = 0;
@@ -115,9 +116,12 @@ __global__ void __launch_bounds__(kGivThreads) givens_fwd_kernel(GArgs a) {
 // order, as the general kernel.  Tiles of 128 signals move with 16-byte
 // cp.async copies into rows of stride N + 4 floats (16-byte aligned, and the
 // 16-byte row reads of consecutive lanes hit distinct banks).
-template <int N>
+// The neighbour ("brick") wiring of the learned correction runs in the same
+// kernel with BRICK = true: even stages pair (2k, 2k+1), odd stages
+// (2k+1, 2k+2) and close the ring with (N-1, 0); a round is two stages.
+template <int N, bool BRICK>
 __global__ void __launch_bounds__(kGivThreads) givens_fwd_xor_kernel(GArgs a) {
-    constexpr int LG = N == 4 ? 2 : N == 8 ? 3 : N == 16 ? 4 : N == 32 ? 5 : 6;
+    constexpr int LG = BRICK ? 2 : N == 4 ? 2 : N == 8 ? 3 : N == 16 ? 4 : N == 32 ? 5 : 6;
     constexpr int H = N / 2;
     constexpr int NP = N + 4;
     extern __shared__ __align__(16) unsigned char sm[];
@@ -160,8 +164,9 @@ __global__ void __launch_bounds__(kGivThreads) givens_fwd_xor_kernel(GArgs a) {
                         (void)dummy;
 #pragma unroll
                         for (int k = 0; k < H; ++k) {
-                            const int lo = ((k >> b) << (b + 1)) | (k & ((1 << b) - 1));
-                            const int hi = lo | (1 << b);
+                            const int lo = BRICK ? (b == 0 ? 2 * k : (k + 1 < H ? 2 * k + 1 : N - 1))
+                                                 : ((k >> b) << (b + 1)) | (k & ((1 << b) - 1));
+                            const int hi = BRICK ? (b == 0 ? 2 * k + 1 : (k + 1 < H ? 2 * k + 2 : 0)) : lo | (1 << b);
                             const float2 w = st[k];
                             const float xp = r[lo], xq = r[hi];
                             r[lo] = fmaf(w.x, xp, -w.y * xq);
@@ -263,7 +268,7 @@ void check_io_g(const void* a, const void* b, int64_t batch) {
 // exported through abi_givens below
 void givens_forward(gft_givens_s& g, const float* theta, const float* x, float* y, int64_t batch, cudaStream_t st) {
     if (batch == 0) return;
-    if (g.xor_log2) {
+    if (g.xor_log2 || g.brick) {
         GArgs a{};
         a.theta = theta;
         a.x = x;
@@ -272,9 +277,15 @@ void givens_forward(gft_givens_s& g, const float* theta, const float* x, float* 
         a.n = g.n;
         a.S = g.S;
         a.A = g.S * g.n / 2;
-        void (*fn)(GArgs) = g.n == 4 ? givens_fwd_xor_kernel<4> : g.n == 8 ? givens_fwd_xor_kernel<8>
-                          : g.n == 16 ? givens_fwd_xor_kernel<16> : g.n == 32 ? givens_fwd_xor_kernel<32>
-                          : givens_fwd_xor_kernel<64>;
+        void (*fn)(GArgs);
+        if (g.brick)
+            fn = g.n == 4 ? givens_fwd_xor_kernel<4, true> : g.n == 8 ? givens_fwd_xor_kernel<8, true>
+               : g.n == 16 ? givens_fwd_xor_kernel<16, true> : g.n == 32 ? givens_fwd_xor_kernel<32, true>
+               : givens_fwd_xor_kernel<64, true>;
+        else
+            fn = g.n == 4 ? givens_fwd_xor_kernel<4, false> : g.n == 8 ? givens_fwd_xor_kernel<8, false>
+               : g.n == 16 ? givens_fwd_xor_kernel<16, false> : g.n == 32 ? givens_fwd_xor_kernel<32, false>
+               : givens_fwd_xor_kernel<64, false>;
         const size_t smem = ((sizeof(float2) * a.A + 15) & ~size_t(15)) + sizeof(float) * kGivThreads * (g.n + 4);
         GFT_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int per_sm = 0;
@@ -402,6 +413,14 @@ gft_status gft_givens_create(int32_t n, int32_t n_stages, const int32_t* pairs, 
                 }
             }
             if (ok) g->xor_log2 = lg;
+            bool br = !ok;
+            for (int s = 0; s < n_stages && br; ++s)
+                for (int k = 0; k < half && br; ++k) {
+                    const int lo = (s & 1) == 0 ? 2 * k : (k + 1 < half ? 2 * k + 1 : n - 1);
+                    const int hi = (s & 1) == 0 ? 2 * k + 1 : (k + 1 < half ? 2 * k + 2 : 0);
+                    br = pairs[(size_t)(s * half + k) * 2] == lo && pairs[(size_t)(s * half + k) * 2 + 1] == hi;
+                }
+            if (br) g->brick = 1;
         }
         const size_t cnt = (size_t)n_stages * half * 2;
         GFT_CUDA(cudaMalloc(&g->d_pairs, sizeof(int) * cnt));

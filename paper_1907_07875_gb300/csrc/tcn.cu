@@ -22,14 +22,14 @@
 //     contiguous bytes per 32 consecutive threads;
 //   tcn_kernel  (persistent; work items = (plan, tile, group of M-tile
 //     units), so a large graph's M-tiles spread over several SMs):
-//     warp 4 (one thread) streams each step's basis chunk A = M_k^T (128
+//     warp 8 (one thread) streams each step's basis chunk A = M_k^T (128
 //     rows x 32 K, hi and lo) and signal chunk B (NS rows x 32 K, hi and lo)
 //     through a ring of shared-memory slots with bulk copies (TMA);
-//     warp 5 allocates TMEM (512 columns, two halves used by alternate
+//     warp 9 allocates TMEM (512 columns, two halves used by alternate
 //     items) and one thread issues the MMAs (M = 128, N = NS, K = 16;
 //     hi*hi + hi*lo + lo*hi for the split precisions) into one NS-column
-//     accumulator per unit; warps 0-3 read a finished half (tcgen05.ld, warp
-//     w = TMEM lanes 32w..32w+31), undo the FP16 scale and store each
+//     accumulator per unit; warps 0-7 read a finished half (tcgen05.ld; the
+//     two warps of a TMEM lane quarter split its columns), undo the FP16 scale and store each
 //     coefficient at its output position (ascending eigenvalue) of its
 //     signal's row, while the MMAs of the next item fill the other half.
 // Every wait is bounded (about 2 s via %globaltimer); a timeout records
@@ -52,8 +52,8 @@ namespace {
 constexpr int kNM = 128;             // coefficient rows per MMA (M)
 constexpr int kNK = 32;              // K per chunk
 constexpr int kNMaxNs = 128;         // signals per tile (MMA N)
-constexpr int kNWorkers = 4;         // worker warps 0-3
-constexpr int kNThreads = 192;       // + copier warp 4, MMA warp 5
+constexpr int kNWorkers = 8;         // epilogue warps 0-7 (two per TMEM lane quarter)
+constexpr int kNThreads = 320;       // + copier warp 8, MMA warp 9
 constexpr int kNSlots = 6;           // ring slots
 constexpr int kNCols = 512;          // TMEM columns per CTA (one CTA per SM): two halves
 constexpr int kNHalf = 256;
@@ -171,11 +171,11 @@ __device__ __forceinline__ void commit_to(unsigned long long* b) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(b))
                  : "memory");
 }
-// barrier 1 over the four worker warps with an OR reduction: every worker
+// barrier 1 over the eight epilogue warps with an OR reduction: every one
 // gets the same answer, so exits taken on it are uniform
 __device__ __forceinline__ bool workers_any(bool v) {
     unsigned r;
-    asm volatile("{ .reg .pred p, q; setp.ne.u32 p, %1, 0; bar.red.or.pred q, 1, 128, p; selp.u32 %0, 1, 0, q; }"
+    asm volatile("{ .reg .pred p, q; setp.ne.u32 p, %1, 0; bar.red.or.pred q, 1, 256, p; selp.u32 %0, 1, 0, q; }"
                  : "=r"(r)
                  : "r"((unsigned)v)
                  : "memory");
@@ -458,9 +458,12 @@ __global__ void __launch_bounds__(kNThreads, 1) tcn_kernel(const TcnPlanDev* __r
             bar_wait(&drain, 0);
         }
     } else {
-        // ---------------- epilogue (warps 0-3) ----------------
+        // ---------------- epilogue (warps 0-7) ----------------
+        // warp w reads TMEM lanes 32 (w & 3) .. + 31; the two warps of a lane
+        // quarter take alternate 16-column chunks
         int sl = slot0;
-        const unsigned lane_base = (unsigned)(warp * 32) << 16;
+        const int quarter = warp & 3, half16 = (warp >> 2) * 16;
+        const unsigned lane_base = (unsigned)(quarter * 32) << 16;
         for (long long it = i0, j = 0; it < i1; ++it, ++j) {
             sl = slot_of<0>(plans, n_plans, sl, it);
             const TcnPlanDev& D = plans[sl];
@@ -475,7 +478,7 @@ __global__ void __launch_bounds__(kNThreads, 1) tcn_kernel(const TcnPlanDev* __r
             // the tile's scales, while the MMAs run (the barrier below orders
             // these writes before every read; the buffer of the item before
             // last in this half was released by the previous item's barrier)
-            if (tid < ns) s_sc[h][tid] = (fp16 && tid < rows) ? D.scale[row0 + tid] : 1.f;
+            if (tid < ns) s_sc[h][tid] = (fp16 && tid < rows) ? D.scale[row0 + tid] : 1.f;   // tid < 256 covers ns <= 128
             const bool bad = !bar_wait(&acc_full[h], (unsigned)((j >> 1) & 1));
             if (workers_any(bad || s_abort != 0)) {
                 if (tid == 0) abort_now(D.err);
@@ -485,10 +488,10 @@ __global__ void __launch_bounds__(kNThreads, 1) tcn_kernel(const TcnPlanDev* __r
             const int* outpos = D.prog + D.off_outpos;
             for (int u = u0; u < u1; ++u) {
                 const TcnLeaf L = D.leaves[D.unit_leaf[u]];
-                const int c = (u - L.unit0) * kNM + warp * 32 + lane;
+                const int c = (u - L.unit0) * kNM + quarter * 32 + lane;
                 const bool valid = c < L.m;
                 const int pos = valid ? outpos[L.lab + c] : 0;
-                for (int c0 = 0; c0 < ns; c0 += 16) {
+                for (int c0 = half16; c0 < ns; c0 += 32) {
                     unsigned r[16];
                     asm volatile(
                         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "

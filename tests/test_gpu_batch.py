@@ -105,11 +105,11 @@ TC_BOUNDS = {"bf16": 5e-3, "bf16x3": 1e-5, "fp16x3": 2e-6}
 
 def _check_tc_entry(p, x, y, prec):
     """A tensor-core batch entry: plans whose leaves reach 64 nodes run on
-    the tensor cores (the 128-signal kernel or, for few signals, the
-    signals-as-N kernel, whose sums are ordered differently), the others on
-    CUDA cores bit for bit like their own FP32 forward.  Tensor-core entries
-    are held to the precision's bound against x U in FP64 with the plan's
-    basis (its oracle parity is in test_gpu_batch_oracle)."""
+    the tensor cores (the 128-signal kernel for large batches of leaves of
+    64..256, else the signals-as-N kernel, whose sums are ordered
+    differently), the others on CUDA cores bit for bit like their own FP32
+    forward.  Tensor-core entries are held to the precision's bound against
+    x U in FP64 with the plan's basis (oracle parity: test_gpu_batch_oracle)."""
     import torch
     if p.info["max_leaf"] < 64:
         assert torch.equal(y, p.forward(x))

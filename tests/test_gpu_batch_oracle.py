@@ -6,8 +6,8 @@ of every graph must match the oracle's dense product y = U^T x after
 eigenspace alignment (Sec. III: bases are unique only up to rotations inside
 repeated eigenvalues).  Bounds (relative L2 over the sampled signals of one
 graph): FP32 2e-6; BF16 5e-3, BF16 hi+lo 1e-5, FP16 hi+lo 2e-6, the bounds
-stated for the tensor-core precisions (graphs whose leaves stay on CUDA
-cores run FP32 in every precision).
+stated for the tensor-core precisions (graphs whose leaves all have at most
+63 nodes stay on CUDA cores and run FP32 in every precision).
 
 * the mixed grid / cycle workload: all eight kinds (8x8, 16x16, 32x32 grids,
   unit and symmetrised U[0.1, 1] weights; cycles of 64 and 256 nodes) at

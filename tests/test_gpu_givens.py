@@ -171,3 +171,26 @@ def test_corrected_butterfly_gains_over_symmetrised_butterfly(env, k):
     y = model.forward(x).cpu().numpy().astype(np.float64)
     y_ref = x.cpu().numpy().astype(np.float64) @ model.matrix()
     assert rel_l2(y, y_ref) <= 2e-6
+
+
+@pytest.mark.parametrize("n", [8, 32, 64])
+def test_brick_wiring_kernel_equals_general_kernel(env, n):
+    """The neighbour wiring of the learned correction (even stages (2k, 2k+1),
+    odd stages (2k+1, 2k+2) and (n-1, 0)) runs a register-resident kernel;
+    the same pairs listed in another order go through the general kernel and
+    must give the same bits, and both match the oracle's layers."""
+    gft, torch = env
+    from paper_1907_07875_gb300.learned import brick_pairs
+    S = 2 * int(math.log2(n))
+    pairs = brick_pairs(n, S)
+    rng = np.random.default_rng(100 + n)
+    theta = rng.uniform(-math.pi, math.pi, (S, n // 2))
+    perm = np.stack([rng.permutation(n // 2) for _ in range(S)])
+    pairs_p = np.stack([pairs[s][perm[s]] for s in range(S)])
+    theta_p = np.stack([theta[s][perm[s]] for s in range(S)])
+    x = torch.from_numpy(W.signals(4099, n, 5)).cuda()
+    y_fast = gft.Givens(n, pairs).forward(torch.from_numpy(theta).float().cuda(), x)
+    y_gen = gft.Givens(n, pairs_p).forward(torch.from_numpy(theta_p).float().cuda(), x)
+    assert torch.equal(y_fast, y_gen)
+    th32 = theta.astype(np.float32).astype(np.float64)
+    assert rel_l2(y_fast.cpu().numpy(), ogiv.forward(x.cpu().numpy().astype(np.float64), pairs, th32)) <= 2e-6
