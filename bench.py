@@ -60,19 +60,34 @@ def _kernel_hash(plan):
     return hashlib.sha256(plan.kernel_source().encode()).hexdigest()[:16]
 
 
-def _traffic_from_profile(kernel_hash):
-    """DRAM bytes per launch from the committed ncu summary of the forward
-    kernel, if it was taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "skeleton25_fwd_2e20.md")
+REPLAY_SOURCES = ("gft_internal.h", "batch.cu", "tcn.cu", "wide.cu")
+REPLAY_PROFILE = os.path.join("profiles", "size_sweep_replay_traffic.md")
+
+
+def _replay_source_hash():
+    """Hash of the CUDA sources of the kernels that one size-sweep replay
+    launches (table-driven batch classes, wide leaves, tensor-core pack and
+    MMA kernels)."""
+    h = hashlib.sha256()
+    for f in REPLAY_SOURCES:
+        with open(os.path.join(ROOT, "paper_1907_07875_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _replay_traffic():
+    """DRAM bytes (read + write) of one replay, summed over its launches, from
+    the committed ncu summary -- only if that capture was taken on the current
+    kernel sources (else None)."""
     vals = {}
     try:
-        with open(path) as fh:
+        with open(os.path.join(ROOT, REPLAY_PROFILE)) as fh:
             for line in fh:
                 if ":" in line and line.strip().startswith("- "):
                     k, v = line.strip()[2:].split(":", 1)
                     vals[k.strip()] = v.strip().strip("`")
-        if vals.get("kernel_hash") == kernel_hash:
-            return int(vals["dram_bytes_per_launch"])
+        if vals.get("source_hash") == _replay_source_hash():
+            return int(vals["dram_bytes_per_replay"])
     except Exception:
         pass
     return None
@@ -839,7 +854,8 @@ def run_ours(args, rank, world, local_rank):
         "err_vs_fp64": {"max": err_max, "median": err_med, "graphs_checked": len(picked),
                         "what": "rel. L2 per graph vs x U in FP64 (plan basis), every family x size octave"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "peak_source": peak_kind, "alg_bytes_per_step": alg_bytes,
+                     "traffic": _replay_traffic(), "peak_source": peak_kind, "alg_bytes_per_step": alg_bytes,
+                     "traffic_source": REPLAY_PROFILE, "source_hash": _replay_source_hash(),
                      "alg_bytes_note": "8 B per coefficient + every distinct plan's leaf bases once (4 B per entry)",
                      "steps_timed": len(step_ms),
                      "kernel": "one graph replay: table-driven batch classes + few-signals tensor-core kernel"},
