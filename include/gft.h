@@ -341,22 +341,28 @@ gft_status gft_device_error(gft_plan_t plan, int32_t* code);
  * Mixed batch: many plans, each with its own batch of signals, transformed
  * forward by one CUDA-graph launch, captured on first use and replayed.
  * Plans are routed by leaf width:
- *   - leaves of at most 64 nodes (unless the plan prefers the wide-leaf
- *     kernel): persistent table-driven kernels, one launch per size class
- *     (row stride n|1 up to 17, 33, 65, 129, 257), each CTA walking a
- *     contiguous, cost-balanced range of (plan, tile) items with
- *     double-buffered tile loads; per-plan tile shapes timed at creation;
- *   - leaves of 33..512 nodes: ONE persistent wide-leaf kernel over the
- *     (plan, tile) items of those plans;
  *   - with a tensor-core precision, plans with a leaf of 64 or more nodes:
  *     plans with at most 4096 signals (or leaves of 257..512 nodes) go to
- *     the few-signals tensor-core kernel (signals on the MMA's N axis, 16
- *     or 32 per tile; leaves up to 512; one launch per shared-memory class);
- *     the others (leaves up to 256) to ONE persistent pack kernel and ONE
- *     persistent tensor-core kernel (128 signals per tile) per size class
- *     (n <= 256 and n > 256); a timeout in these kernels is reported in the
- *     error word of the plan being transformed (pack / 128-signal kernel:
- *     the class's first plan).
+ *     the few-signals tensor-core kernels (signals on the MMA's N axis, up
+ *     to 128 per tile; leaves up to 512; two pack launches -- short and long
+ *     rows -- and one persistent MMA kernel); the others (leaves up to 256)
+ *     to ONE persistent pack kernel and ONE persistent tensor-core kernel
+ *     (128 signals per tile) per size class (n <= 256 and n > 256); a timeout
+ *     in these kernels is reported in the error word of the plan being
+ *     transformed (pack / 128-signal kernel: the class's first plan);
+ *   - the other plans of at most 128 nodes with leaves of at most 64 nodes
+ *     and no right Haar units: persistent node-major table-driven kernels,
+ *     one launch per size class (n up to 16, 32, 64, 128), tiles of 32..256
+ *     signals, each CTA walking a contiguous, cost-balanced range of
+ *     (plan, tile) items with double-buffered tile loads;
+ *   - the rest with leaves of at most 64 nodes (unless the plan prefers the
+ *     wide-leaf kernel): persistent thread-per-signal table-driven kernels,
+ *     one launch per size class (row stride n|1 up to 17, 33, 65, 129, 257),
+ *     per-plan tile shapes timed at creation;
+ *   - leaves of 33..512 nodes otherwise: ONE persistent wide-leaf kernel
+ *     over the (plan, tile) items of those plans.
+ * Every CUDA-core group computes each output with the same FMA sequence as
+ * the plan's own FP32 forward, so their results agree bit for bit.
  * The groups run on forked streams inside the graph and join at its end.
  *  plans[n_plans]  plans created with device bases; the batch does not own
  *                  them, and they must outlive it.  A plan may appear more
@@ -374,9 +380,10 @@ gft_status gft_batch_create(int32_t n_plans, const gft_plan_t* plans, const int6
                             uint32_t flags, gft_batch_t* out);
 gft_status gft_batch_forward(gft_batch_t batch, const float* const* x, float* const* y,
                              gft_stream_t stream);
-/* Tile configuration chosen by the autotuner for plan i of the table-driven
- * group: signals per tile and threads per block (0 for entries routed to
- * the wide-leaf or tensor-core kernels). */
+/* Tile configuration of plan i of a table-driven group: signals per tile
+ * and threads per block (thread-per-signal kernel: chosen by the autotuner;
+ * node-major kernel: 256 threads, a power-of-two tile of 32..256 signals);
+ * 0 for entries routed to the wide-leaf or tensor-core kernels. */
 gft_status gft_batch_get_tile(gft_batch_t batch, int32_t i, int32_t* tile, int32_t* threads);
 /* Kernel launches of this library in one gft_batch_forward (the nodes of
  * the captured graph that run our kernels). */

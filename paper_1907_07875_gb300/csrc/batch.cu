@@ -65,6 +65,11 @@ struct BatchPlanDev {
     int off_labels, off_outpos, off_src, off_desc;
     int mats_smem, rs, ts;
     float inv_n;
+    int n_stages;   // node-major kernel: Haar stages before the leaves
+    int lg_g;       // node-major kernel: log2(ts / 4), signal groups of four per tile
+    int tsp;        // node-major kernel: signal stride of a node row (ts + 4)
+    const int* nm;  // node-major kernel: program image (see DevProgram)
+    int nm_words, nm_cg_off, nm_n_cg;
 };
 
 __device__ __forceinline__ KArgs batch_kargs(const BatchPlanDev& D) {
@@ -167,6 +172,223 @@ __global__ void __launch_bounds__(kBatchThreads) gft_batch_kernel(const BatchPla
     cp_async_wait0();
 }
 
+// Node-major variant of the table-driven batch kernel, for plans of at most
+// kNmMaxN nodes without right Haar units (every leaf at most 64 nodes).
+// An item is a tile of TS signals (a power of two, 32..256, about 4096
+// floats per tile) of one plan:
+//   * the rows arrive with 16-byte cp.async copies into a row-major buffer
+//     X, and so does the plan's program image (pairs, stage offsets, node
+//     lists, leaf descriptors, the (leaf, output group) list) into one of
+//     two program buffers when the plan changes: both are in flight for the
+//     next item while this one runs; the leaf matrices are read through L1;
+//   * a shared-memory pass transposes X into T[node][signal] (signal stride
+//     TSP = TS + 4, so node rows stay 16-byte aligned);
+//   * a Haar unit (x_i, x_j) -> (x_i + x_j, x_i - x_j) (Sec. III) works on
+//     four signals with two 16-byte loads and two stores; the CTA takes one
+//     stage at a time (the units of a stage touch disjoint nodes);
+//   * the leaf products of every leaf run in one pass: a thread owns four
+//     outputs c0..c0+3 of one leaf for four signals, reads x_r of the four
+//     signals and row r of the leaf matrix with one 16-byte load each and
+//     issues 16 FMAs; it writes its outputs straight to their coefficient
+//     rows (ascending eigenvalue) of an output tile O, which reuses X;
+//   * the store pass reads O transposed back and writes 16-byte stores.
+// Each output is the same FMA chain (r ascending from zero) as in the
+// thread-per-signal kernel, so the results agree bit for bit.
+constexpr int kNmThreads = 256;
+constexpr int kNmMaxN = 256;
+constexpr int kNmMaxTs = 1024;      // signals per tile: a power of two, 16..1024
+constexpr int kNmTileFloats = 4096;
+
+__global__ void __launch_bounds__(kNmThreads, 4) gft_nm_kernel(const BatchPlanDev* __restrict__ plans, int n_plans,
+                                                           const long long* __restrict__ range,
+                                                           const int* __restrict__ first_slot, int prog_cap,
+                                                           int buf_cap) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    int* progs = reinterpret_cast<int*>(smem_raw);                 // two program buffers of prog_cap words
+    float* xb = reinterpret_cast<float*>(progs + 2 * (size_t)prog_cap);
+    float* T = xb + 2 * (size_t)buf_cap;
+    const int tid = threadIdx.x;
+    const long long it0 = range[blockIdx.x], it1 = range[blockIdx.x + 1];
+    if (it0 >= it1) return;
+    auto slot_of = [&](int s, long long it) {
+        while (s + 1 < n_plans && plans[s + 1].item0 <= it) ++s;
+        return s;
+    };
+    // 16-byte copies of the item's rows (contiguous in global memory: the
+    // tile starts at a multiple of TS rows and the signal pointer is 16-byte
+    // aligned), a 4-byte tail
+    auto issue = [&](const BatchPlanDev& D, float* dst, long long item) {
+        const long long row0 = item * D.ts;
+        const int rows = (int)min((long long)D.ts, D.batch - row0);
+        const int E = rows * D.n;
+        const float* src = D.x + row0 * D.n;
+        for (int q = tid; 4 * q + 3 < E; q += kNmThreads) cp_async16(dst + 4 * q, src + 4 * q);
+        for (int e = (E & ~3) + tid; e < E; e += kNmThreads) cp_async4(dst + e, src + e);
+    };
+    auto issue_prog = [&](const BatchPlanDev& D, int* dst) {
+        for (int q = tid; 4 * q < D.nm_words; q += kNmThreads) cp_async16(dst + 4 * q, D.nm + 4 * q);
+    };
+    int slot = slot_of(first_slot[blockIdx.x], it0);
+    // which program image each buffer holds (or receives); the same in every thread
+    const int* held0 = plans[slot].nm;
+    const int* held1 = nullptr;
+    int pc = 0;
+    issue(plans[slot], xb, it0 - plans[slot].item0);
+    issue_prog(plans[slot], progs);
+    cp_async_commit();
+    int cur = 0;
+    for (long long it = it0; it < it1; ++it) {
+        const BatchPlanDev D = plans[slot];
+        float* X = xb + (size_t)cur * buf_cap;
+        // the other tile and program buffers were released by the barrier
+        // ending the last item
+        int nslot = slot, npc = pc;
+        if (it + 1 < it1) {
+            nslot = slot_of(slot, it + 1);
+            const BatchPlanDev& Dn = plans[nslot];
+            issue(Dn, xb + (size_t)(cur ^ 1) * buf_cap, it + 1 - Dn.item0);
+            if (Dn.nm != (pc ? held1 : held0)) {
+                npc = pc ^ 1;
+                if (Dn.nm != (npc ? held1 : held0)) {
+                    issue_prog(Dn, progs + (size_t)npc * prog_cap);
+                    (npc ? held1 : held0) = Dn.nm;
+                }
+            }
+        }
+        cp_async_commit();
+        cp_async_wait1();   // this item's rows and program (the next item's may stay in flight)
+        __syncthreads();
+        const int* ints = progs + (size_t)pc * prog_cap;
+        const int* cg = ints + D.nm_cg_off;
+        const int* desc = ints + D.off_desc;
+        const int n = D.n, tsp = D.tsp, tsp4 = D.tsp >> 2, lg = D.lg_g, gmask = (1 << D.lg_g) - 1;
+        const long long row0 = (it - D.item0) * D.ts;
+        const int rows = (int)min((long long)D.ts, D.batch - row0);
+        const int E = rows * n;
+        // X (row-major) -> T[node][signal].  n a multiple of 4: a 16-byte
+        // chunk is four nodes of one signal, and (signal, node) of this
+        // thread's chunk advances by a fixed step each pass
+        const bool quad = (n & 3) == 0;
+        const int step_s = 4 * kNmThreads / n, step_j = 4 * kNmThreads - step_s * n;
+        const int s_first = row_of(4 * tid, D.inv_n), j_first = 4 * tid - s_first * n;
+        if (quad) {
+            int s = s_first, j = j_first;
+            for (int q = tid; 4 * q < E; q += kNmThreads) {
+                const float4 v = reinterpret_cast<const float4*>(X)[q];
+                float* t = T + j * tsp + s;
+                t[0] = v.x;
+                t[tsp] = v.y;
+                t[2 * tsp] = v.z;
+                t[3 * tsp] = v.w;
+                s += step_s;
+                j += step_j;
+                if (j >= n) {
+                    j -= n;
+                    ++s;
+                }
+            }
+        } else {
+            for (int q = tid; 4 * q < E; q += kNmThreads) {
+                const int e = 4 * q;
+                int s = row_of(e, D.inv_n), j = e - s * n;
+                const float4 v = *reinterpret_cast<const float4*>(X + e);
+                const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    if (e + i < E) T[j * tsp + s] = vv[i];
+                    if (++j == n) {
+                        j = 0;
+                        ++s;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        float4* T4 = reinterpret_cast<float4*>(T);
+        // Haar stages (the signals past the batch's end carry stale values
+        // that are never stored)
+        for (int st = 0; st < D.n_stages; ++st) {
+            const int p0 = ints[2 * D.n_pairs + st], cnt = ints[2 * D.n_pairs + st + 1] - p0;
+            for (int w = tid; w < (cnt << lg); w += kNmThreads) {
+                const int2 ij = reinterpret_cast<const int2*>(ints)[p0 + (w >> lg)];
+                const int g = w & gmask;
+                const float4 a = T4[ij.x * tsp4 + g], b = T4[ij.y * tsp4 + g];
+                T4[ij.x * tsp4 + g] = make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+                T4[ij.y * tsp4 + g] = make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
+            }
+            __syncthreads();
+        }
+        // leaf products into O (= X, whose rows were consumed above)
+        float4* O4 = reinterpret_cast<float4*>(X);
+        const int* labels = ints + D.off_labels;
+        const int* outpos = ints + D.off_outpos;
+        for (int w = tid; w < (D.nm_n_cg << lg); w += kNmThreads) {
+            const int e = cg[w >> lg], g = w & gmask;
+            const int* d = desc + kLeafDesc * (e >> 16);
+            const int c0 = e & 0xFFFF, m = d[0], bk = d[1];
+            const int* idx = labels + d[2];
+            const float* M = D.mats + d[3] + c0;   // forward leaf matrix (L1-cached)
+            float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0, a2 = a0, a3 = a0;
+#pragma unroll 4
+            for (int r = 0; r < m; ++r) {
+                const float4 x = T4[idx[r] * tsp4 + g];
+                const float4 u = __ldg(reinterpret_cast<const float4*>(M + r * bk));
+                a0.x = fmaf(x.x, u.x, a0.x); a0.y = fmaf(x.y, u.x, a0.y); a0.z = fmaf(x.z, u.x, a0.z); a0.w = fmaf(x.w, u.x, a0.w);
+                a1.x = fmaf(x.x, u.y, a1.x); a1.y = fmaf(x.y, u.y, a1.y); a1.z = fmaf(x.z, u.y, a1.z); a1.w = fmaf(x.w, u.y, a1.w);
+                a2.x = fmaf(x.x, u.z, a2.x); a2.y = fmaf(x.y, u.z, a2.y); a2.z = fmaf(x.z, u.z, a2.z); a2.w = fmaf(x.w, u.z, a2.w);
+                a3.x = fmaf(x.x, u.w, a3.x); a3.y = fmaf(x.y, u.w, a3.y); a3.z = fmaf(x.z, u.w, a3.z); a3.w = fmaf(x.w, u.w, a3.w);
+            }
+            const int* op = outpos + d[2] + c0;
+            O4[op[0] * tsp4 + g] = a0;
+            if (c0 + 1 < m) O4[op[1] * tsp4 + g] = a1;
+            if (c0 + 2 < m) O4[op[2] * tsp4 + g] = a2;
+            if (c0 + 3 < m) O4[op[3] * tsp4 + g] = a3;
+        }
+        __syncthreads();
+        // O[coefficient][signal] -> rows, 16-byte streaming stores
+        const float* O = X;
+        float* dst = D.y + row0 * n;
+        if (quad) {
+            int s = s_first, j = j_first;
+            for (int q = tid; 4 * q < E; q += kNmThreads) {
+                const float* o = O + j * tsp + s;
+                __stcs(reinterpret_cast<float4*>(dst) + q, make_float4(o[0], o[tsp], o[2 * tsp], o[3 * tsp]));
+                s += step_s;
+                j += step_j;
+                if (j >= n) {
+                    j -= n;
+                    ++s;
+                }
+            }
+        }
+        for (int q = quad ? E : tid; 4 * q < E; q += kNmThreads) {
+            const int e = 4 * q;
+            int s = row_of(e, D.inv_n), j = e - s * n;
+            float v[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                v[i] = e + i < E ? O[j * tsp + s] : 0.f;
+                if (++j == n) {
+                    j = 0;
+                    ++s;
+                }
+            }
+            if (e + 3 < E) {
+                __stcs(reinterpret_cast<float4*>(dst + e), make_float4(v[0], v[1], v[2], v[3]));
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    if (e + i < E) __stcs(dst + e + i, v[i]);
+            }
+        }
+        __syncthreads();   // X, T and the program buffer free
+        cur ^= 1;
+        slot = nslot;
+        pc = npc;
+    }
+    cp_async_wait0();
+}
+
 int rs_cap(int max_bucket) { return max_bucket <= 16 ? 4 : (max_bucket <= 32 ? 2 : 1); }
 
 // admissible RS for a plan: leaf widths and the tile cap (RS = 1 always)
@@ -190,6 +412,7 @@ struct BatchClass {
     int* d_first = nullptr;                // grid plan slots
     long long total_items = 0;
     int mats_cap = 0, ints_cap = 0, tile_cap = 0, nbuf = 1;
+    bool nm = false;                       // node-major kernel (tile_cap: floats per buffer)
     size_t smem = 0;
     int grid = 0;
     void release() {
@@ -209,23 +432,31 @@ using namespace gft;
 struct gft_batch_s {
     // routing of the caller's plans: 0 = table-driven batch kernel, 1 = wide-leaf
     // batch kernel, 2 = tensor-core sequence (pack + leaf kernels, 128 signals
-    // per tile), 3 = few-signals tensor-core kernels; idx = position within its group
+    // per tile), 3 = few-signals tensor-core kernels, 4 = node-major table-driven
+    // kernel; idx = position within its group
     uint32_t precision = GFT_PREC_FP32;
     std::vector<int> kind, idx;
     std::vector<int64_t> user_batch;
-    std::vector<int> table_users, wide_users, tc_users, tcn_users;
+    std::vector<int> table_users, wide_users, tc_users, tcn_users, nm_users;
     std::vector<gft_plan_s*> tc_plans, tcn_plans;
     std::vector<int64_t> tc_batches, tcn_batches;
     void* wide = nullptr;                  // wide-leaf group (wide.cu)
     void* tcb = nullptr;                   // tensor-core group (tc.cu)
     void* tcnb = nullptr;                  // few-signals tensor-core group (tcn.cu)
-    cudaStream_t side[2] = {};
-    cudaEvent_t ev_fork = nullptr, ev_join[2] = {};
+    // forked streams of the captured graph: 0 wide-leaf group, 1 tensor-core
+    // groups
+    static constexpr int kSide = 2;
+    cudaStream_t side[kSide] = {};
+    cudaEvent_t ev_fork = nullptr, ev_join[kSide] = {};
     // table-driven group
     std::vector<gft_plan_s*> plans;        // table-driven group, group order
     std::vector<int64_t> batches;
     std::vector<int> rs;                   // per group index
     std::vector<BatchClass> classes;       // non-empty size classes
+    // node-major group
+    std::vector<gft_plan_s*> nm_plans;
+    std::vector<int64_t> nm_batches;
+    std::vector<BatchClass> nm_classes;
     cudaStream_t cap_stream = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -243,6 +474,7 @@ struct gft_batch_s {
         if (graph) cudaGraphDestroy(graph);
         if (cap_stream) cudaStreamDestroy(cap_stream);
         for (auto& c : classes) c.release();
+        for (auto& c : nm_classes) c.release();
     }
 };
 
@@ -279,8 +511,44 @@ double item_cost(const gft_plan_s& p, long long rows) {
     return (double)rows * (0.2 * p.n + 0.02 * fl + 0.02 * p.dev.n_pairs) + 1500.0;
 }
 
-// Builds every size class: slots (decreasing cost per item), item indices,
-// shared-memory sizes, grid, and the per-CTA ranges; uploads the ranges.
+// Cuts a class's item sequence (slots in order, items[sl] items each, item t
+// of slot sl costing cost(sl, t)) into C.grid contiguous ranges of about
+// equal cost, records the plan slot of each range's first item, and hands
+// the class (with its device copies of the ranges) to `out`.
+template <class F>
+void finish_class(BatchClass&& C, const std::vector<long long>& items, F cost, std::vector<BatchClass>& out) {
+    double total = 0.0;
+    for (size_t sl = 0; sl < C.desc.size(); ++sl)
+        for (long long t = 0; t < items[sl]; ++t) total += cost(sl, t);
+    std::vector<long long> range(C.grid + 1, C.total_items);
+    std::vector<int> first(C.grid, (int)C.desc.size() - 1);
+    range[0] = 0;
+    first[0] = 0;
+    double acc = 0.0;
+    int cta = 1;
+    for (size_t sl = 0; sl < C.desc.size() && cta < C.grid; ++sl) {
+        for (long long t = 0; t < items[sl] && cta < C.grid; ++t) {
+            acc += cost(sl, t);
+            while (cta < C.grid && acc >= total * cta / C.grid) {
+                range[cta] = std::min(C.desc[sl].item0 + t + 1, C.total_items);
+                first[cta] = (int)sl;
+                ++cta;
+            }
+        }
+    }
+    // a range that starts at the first item of the next slot names the
+    // slot it ends in; the kernel walks forward from there
+    out.push_back(std::move(C));   // owned by the batch before any allocation
+    BatchClass& D = out.back();
+    GFT_CUDA(cudaMalloc(&D.d_desc, sizeof(BatchPlanDev) * D.desc.size()));
+    GFT_CUDA(cudaMalloc(&D.d_range, sizeof(long long) * range.size()));
+    GFT_CUDA(cudaMalloc(&D.d_first, sizeof(int) * first.size()));
+    GFT_CUDA(cudaMemcpy(D.d_range, range.data(), sizeof(long long) * range.size(), cudaMemcpyHostToDevice));
+    GFT_CUDA(cudaMemcpy(D.d_first, first.data(), sizeof(int) * first.size(), cudaMemcpyHostToDevice));
+}
+
+// Builds every size class of the thread-per-signal kernel: slots (decreasing
+// cost per item), item indices, shared-memory sizes, grid, per-CTA ranges.
 void layout(gft_batch_s& b) {
     const int k = (int)b.plans.size();
     for (auto& c : b.classes) c.release();
@@ -295,10 +563,12 @@ void layout(gft_batch_s& b) {
         C.members = by[ci];
         std::stable_sort(C.members.begin(), C.members.end(), [&](int x, int y) { return cpi[x] > cpi[y]; });
         size_t tile_cap = 0;
+        std::vector<long long> items;
         for (int i : C.members) {
             BatchPlanDev d = make_desc(*b.plans[i], b.rs[i], b.batches[i]);
             d.item0 = C.total_items;
-            C.total_items += (b.batches[i] + d.ts - 1) / d.ts;
+            items.push_back((b.batches[i] + d.ts - 1) / d.ts);
+            C.total_items += items.back();
             C.desc.push_back(d);
             C.mats_cap = std::max(C.mats_cap, d.mats_smem);
             C.ints_cap = std::max(C.ints_cap, (d.ints_count + 3) & ~3);
@@ -318,47 +588,93 @@ void layout(gft_batch_s& b) {
         GFT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gft_batch_kernel, kBatchThreads, C.smem));
         if (per_sm < 1) fail(GFT_ERR_UNSUPPORTED, "mixed-batch kernel does not fit on an SM");
         C.grid = (int)std::max<long long>(1, std::min<long long>((long long)per_sm * sm_count(), C.total_items));
-        // cut the item sequence into grid ranges of about equal cost
-        double total = 0.0;
-        for (size_t sl = 0; sl < C.desc.size(); ++sl) {
-            const int i = C.members[sl];
-            const long long items = (b.batches[i] + C.desc[sl].ts - 1) / C.desc[sl].ts;
-            if (items) total += (items - 1) * cpi[i] + item_cost(*b.plans[i], b.batches[i] - (items - 1) * C.desc[sl].ts);
+        const std::vector<int> mem = C.members;
+        const std::vector<BatchPlanDev> ds = C.desc;
+        finish_class(
+            std::move(C), items,
+            [&](size_t sl, long long t) {
+                const int i = mem[sl];
+                return t + 1 < items[sl] ? cpi[i] : item_cost(*b.plans[i], b.batches[i] - t * ds[sl].ts);
+            },
+            b.classes);
+    }
+}
+
+// node-major kernel: plans it runs and their tile (signals, a power of two)
+bool nm_eligible(const gft_plan_s& p) {
+    return p.has_device && !p.right && p.dev.max_bucket != 0 && p.dev.d_nm && p.dev.n_pre_pairs == p.dev.n_pairs &&
+           p.dev.n_pre_stages == p.dev.n_stages && p.n >= 1 && p.n <= kNmMaxN;
+}
+
+int nm_ts(int n) {
+    int ts = kNmMaxTs;
+    while (ts > 16 && (long long)ts * n > kNmTileFloats) ts >>= 1;
+    return ts;
+}
+
+constexpr int kNmClasses = 5;
+int nm_class_of(int n) { return n <= 16 ? 0 : (n <= 32 ? 1 : (n <= 64 ? 2 : (n <= 128 ? 3 : 4))); }
+
+// Builds the node-major kernel's size classes (n up to 16, 32, 64, 128, 256).
+void layout_nm(gft_batch_s& b) {
+    const int k = (int)b.nm_plans.size();
+    for (auto& c : b.nm_classes) c.release();
+    b.nm_classes.clear();
+    std::vector<std::vector<int>> by(kNmClasses);
+    for (int i = 0; i < k; ++i) by[nm_class_of(b.nm_plans[i]->n)].push_back(i);
+    for (int ci = 0; ci < kNmClasses; ++ci) {
+        if (by[ci].empty()) continue;
+        BatchClass C;
+        std::vector<double> cpi(k, 0.0);
+        for (int i : by[ci]) cpi[i] = item_cost(*b.nm_plans[i], nm_ts(b.nm_plans[i]->n));
+        C.members = by[ci];
+        std::stable_sort(C.members.begin(), C.members.end(), [&](int x, int y) { return cpi[x] > cpi[y]; });
+        size_t buf_cap = 0;
+        std::vector<long long> items;
+        for (int i : C.members) {
+            const gft_plan_s& p = *b.nm_plans[i];
+            BatchPlanDev d = make_desc(p, 1, b.nm_batches[i]);
+            d.ts = nm_ts(p.n);
+            d.tsp = d.ts + 4;
+            d.lg_g = 0;
+            while ((1 << d.lg_g) < d.ts / 4) ++d.lg_g;
+            d.n_stages = p.dev.n_pre_stages;
+            d.nm = p.dev.d_nm;
+            d.nm_words = p.dev.nm_words;
+            d.nm_cg_off = p.dev.nm_cg_off;
+            d.nm_n_cg = p.dev.nm_n_cg;
+            d.item0 = C.total_items;
+            items.push_back((b.nm_batches[i] + d.ts - 1) / d.ts);
+            C.total_items += items.back();
+            C.desc.push_back(d);
+            C.ints_cap = std::max(C.ints_cap, d.nm_words);   // program image words (a multiple of 4)
+            buf_cap = std::max(buf_cap, (size_t)p.n * d.tsp);
         }
-        std::vector<long long> range(C.grid + 1, C.total_items);
-        std::vector<int> first(C.grid, (int)C.desc.size() - 1);
-        range[0] = 0;
-        first[0] = 0;
-        double acc = 0.0;
-        int cta = 1;
-        for (size_t sl = 0; sl < C.desc.size() && cta < C.grid; ++sl) {
-            const int i = C.members[sl];
-            const int ts = C.desc[sl].ts;
-            const long long items = (b.batches[i] + ts - 1) / ts;
-            for (long long t = 0; t < items && cta < C.grid; ++t) {
-                acc += t + 1 < items ? cpi[i] : item_cost(*b.plans[i], b.batches[i] - t * ts);
-                while (cta < C.grid && acc >= total * cta / C.grid) {
-                    range[cta] = std::min(C.desc[sl].item0 + t + 1, C.total_items);
-                    first[cta] = (int)sl;
-                    ++cta;
-                }
-            }
-        }
-        // a range that starts at the first item of the next slot names the
-        // slot it ends in; the kernel walks forward from there
-        b.classes.push_back(std::move(C));   // owned by the batch before any allocation
-        BatchClass& D = b.classes.back();
-        GFT_CUDA(cudaMalloc(&D.d_desc, sizeof(BatchPlanDev) * D.desc.size()));
-        GFT_CUDA(cudaMalloc(&D.d_range, sizeof(long long) * range.size()));
-        GFT_CUDA(cudaMalloc(&D.d_first, sizeof(int) * first.size()));
-        GFT_CUDA(cudaMemcpy(D.d_range, range.data(), sizeof(long long) * range.size(), cudaMemcpyHostToDevice));
-        GFT_CUDA(cudaMemcpy(D.d_first, first.data(), sizeof(int) * first.size(), cudaMemcpyHostToDevice));
+        C.tile_cap = (int)((buf_cap + 3) & ~size_t(3));
+        C.nm = true;
+        C.smem = 2 * sizeof(int) * (size_t)C.ints_cap + 3 * sizeof(float) * (size_t)C.tile_cap;
+        if (C.smem > (size_t)kBatchSmemLimit - 1024)
+            fail(GFT_ERR_UNSUPPORTED, "mixed batch needs too much shared memory per CTA");
+        GFT_CUDA(cudaFuncSetAttribute(gft_nm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kBatchSmemLimit - 1024));
+        int per_sm = 0;
+        GFT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gft_nm_kernel, kNmThreads, C.smem));
+        if (per_sm < 1) fail(GFT_ERR_UNSUPPORTED, "node-major batch kernel does not fit on an SM");
+        C.grid = (int)std::max<long long>(1, std::min<long long>((long long)per_sm * sm_count(), C.total_items));
+        const std::vector<int> mem = C.members;
+        const std::vector<BatchPlanDev> ds = C.desc;
+        finish_class(
+            std::move(C), items,
+            [&](size_t sl, long long t) {
+                const int i = mem[sl];
+                return t + 1 < items[sl] ? cpi[i] : item_cost(*b.nm_plans[i], b.nm_batches[i] - t * ds[sl].ts);
+            },
+            b.nm_classes);
     }
 }
 
 // x / y: pointers per group index (the caller's order within the group)
-void upload_desc(gft_batch_s& b, const float* const* x, float* const* y, cudaStream_t st) {
-    for (auto& C : b.classes) {
+void upload_classes(std::vector<BatchClass>& classes, const float* const* x, float* const* y, cudaStream_t st) {
+    for (auto& C : classes) {
         for (size_t slot = 0; slot < C.desc.size(); ++slot) {
             const int i = C.members[slot];
             C.desc[slot].x = x ? x[i] : nullptr;
@@ -369,10 +685,26 @@ void upload_desc(gft_batch_s& b, const float* const* x, float* const* y, cudaStr
     }
 }
 
-void launch_batch(gft_batch_s& b, cudaStream_t st) {
+void upload_desc(gft_batch_s& b, const float* const* x, float* const* y, cudaStream_t st) {
+    upload_classes(b.classes, x, y, st);
+}
+
+// stream_of(j): the stream of the j-th launched class
+template <class F> void launch_nm(gft_batch_s& b, F stream_of) {
+    int j = 0;
+    for (auto& C : b.nm_classes) {
+        if (C.total_items == 0) continue;
+        gft_nm_kernel<<<C.grid, kNmThreads, C.smem, stream_of(j++)>>>(C.d_desc, (int)C.desc.size(), C.d_range,
+                                                                      C.d_first, C.ints_cap, C.tile_cap);
+        GFT_CUDA(cudaGetLastError());
+    }
+}
+
+template <class F> void launch_batch(gft_batch_s& b, F stream_of) {
+    int j = 0;
     for (auto& C : b.classes) {
         if (C.total_items == 0) continue;
-        gft_batch_kernel<<<C.grid, kBatchThreads, C.smem, st>>>(C.d_desc, (int)C.desc.size(), C.d_range, C.d_first,
+        gft_batch_kernel<<<C.grid, kBatchThreads, C.smem, stream_of(j++)>>>(C.d_desc, (int)C.desc.size(), C.d_range, C.d_first,
                                                               C.mats_cap, C.ints_cap, C.tile_cap, C.nbuf);
         GFT_CUDA(cudaGetLastError());
     }
@@ -428,9 +760,9 @@ void autotune(gft_batch_s& b) {
                 probe.rs = {rs};
                 layout(probe);
                 upload_desc(probe, (const float* const*)&dx, &dy, st);
-                launch_batch(probe, st);
+                launch_batch(probe, [&](int) { return st; });
                 GFT_CUDA(cudaEventRecord(e0, st));
-                for (int r = 0; r < 3; ++r) launch_batch(probe, st);
+                for (int r = 0; r < 3; ++r) launch_batch(probe, [&](int) { return st; });
                 GFT_CUDA(cudaEventRecord(e1, st));
                 GFT_CUDA(cudaEventSynchronize(e1));
                 float ms = 0.f;
@@ -492,6 +824,7 @@ gft_status gft_batch_create(int32_t n_plans, const gft_plan_t* plans, const int6
             const bool big_batch_tc = tc_prec && max_leaf >= kTcMinLeaf && tc_eligible(*p) && batches[i] > kTcnMaxBatch;
             if (tc_prec && max_leaf >= kTcnMinLeaf && !big_batch_tc && tcn_eligible(*p)) kind = 3;
             else if (tc_prec && max_leaf >= kTcMinLeaf && tc_eligible(*p)) kind = 2;
+            else if (nm_eligible(*p)) kind = 4;
             else if (p->dev.max_bucket != 0 && !(wide_configured(*p) && wide_ready(*p, false))) kind = 0;
             else if (wide_configured(*p)) kind = 1;
             else fail(GFT_ERR_UNSUPPORTED, "plan " + std::to_string(i) + " has a leaf wider than 512 nodes");
@@ -507,6 +840,11 @@ gft_status gft_batch_create(int32_t n_plans, const gft_plan_t* plans, const int6
                 b->wide_users.push_back(i);
                 wide_plans.push_back(p);
                 wide_batches.push_back(batches[i]);
+            } else if (kind == 4) {
+                b->idx.push_back((int)b->nm_plans.size());
+                b->nm_users.push_back(i);
+                b->nm_plans.push_back(p);
+                b->nm_batches.push_back(batches[i]);
             } else if (kind == 2) {
                 b->idx.push_back((int)b->tc_plans.size());
                 b->tc_users.push_back(i);
@@ -523,6 +861,7 @@ gft_status gft_batch_create(int32_t n_plans, const gft_plan_t* plans, const int6
             autotune(*b);
             layout(*b);
         }
+        if (!b->nm_plans.empty()) layout_nm(*b);
         if (!wide_plans.empty()) b->wide = wide_batch_create(wide_plans, wide_batches);
         if (!b->tc_plans.empty()) b->tcb = tc_batch_create(b->tc_plans, b->tc_batches, b->precision);
         if (!b->tcn_plans.empty()) b->tcnb = tcn_batch_create(b->tcn_plans, b->tcn_batches, b->precision);
@@ -553,8 +892,8 @@ gft_status gft_batch_forward(gft_batch_t b, const float* const* x, float* const*
         if (!same) {
             // every group reads its signal pointers from device descriptors,
             // so the captured graph stays valid
-            std::vector<const float*> tx, wx, cx, nx;
-            std::vector<float*> ty, wy, cy, ny;
+            std::vector<const float*> tx, wx, cx, nx, mx;
+            std::vector<float*> ty, wy, cy, ny, my;
             for (int i : b->table_users) {
                 tx.push_back(x[i]);
                 ty.push_back(y[i]);
@@ -571,7 +910,12 @@ gft_status gft_batch_forward(gft_batch_t b, const float* const* x, float* const*
                 nx.push_back(x[i]);
                 ny.push_back(y[i]);
             }
+            for (int i : b->nm_users) {
+                mx.push_back(x[i]);
+                my.push_back(y[i]);
+            }
             if (!b->plans.empty()) upload_desc(*b, tx.data(), ty.data(), st);
+            if (!b->nm_plans.empty()) upload_classes(b->nm_classes, mx.data(), my.data(), st);
             if (b->wide) wide_batch_upload(b->wide, wx, wy, st);
             if (b->tcb) tc_batch_upload(b->tcb, cx, cy, st);
             if (b->tcnb) tcn_batch_upload(b->tcnb, nx, ny, st);
@@ -585,7 +929,7 @@ gft_status gft_batch_forward(gft_batch_t b, const float* const* x, float* const*
             try {
                 cudaStream_t cs = b->cap_stream;
                 GFT_CUDA(cudaEventRecord(b->ev_fork, cs));
-                bool used[2] = {false, false};
+                bool used[gft_batch_s::kSide] = {};
                 auto fork = [&](int s) {
                     if (!used[s]) GFT_CUDA(cudaStreamWaitEvent(b->side[s], b->ev_fork, 0));
                     used[s] = true;
@@ -596,8 +940,13 @@ gft_status gft_batch_forward(gft_batch_t b, const float* const* x, float* const*
                 // would otherwise compete for the SMs' TMEM
                 if (b->tcb) tc_batch_launch(b->tcb, fork(1));
                 if (b->tcnb) tcn_batch_launch(b->tcnb, fork(1));
-                if (!b->plans.empty()) launch_batch(*b, cs);
-                for (int s = 0; s < 2; ++s)
+                // the CUDA-core size classes one after another on the capture
+                // stream (launched concurrently they take the SMs' shared
+                // memory that the tensor-core kernels wait for)
+                auto class_stream = [&](int) { return cs; };
+                if (!b->nm_plans.empty()) launch_nm(*b, class_stream);
+                if (!b->plans.empty()) launch_batch(*b, class_stream);
+                for (int s = 0; s < gft_batch_s::kSide; ++s)
                     if (used[s]) {
                         GFT_CUDA(cudaEventRecord(b->ev_join[s], b->side[s]));
                         GFT_CUDA(cudaStreamWaitEvent(cs, b->ev_join[s], 0));
@@ -624,6 +973,9 @@ gft_status gft_batch_get_tile(gft_batch_t b, int32_t i, int32_t* tile, int32_t* 
         if (b->kind[i] == 0) {
             *tile = b->rs[b->idx[i]] * kBatchThreads;
             *threads = kBatchThreads;
+        } else if (b->kind[i] == 4) {
+            *tile = nm_ts(b->nm_plans[b->idx[i]]->n);
+            *threads = kNmThreads;
         }
     });
 }
@@ -633,6 +985,7 @@ gft_status gft_batch_get_launches(gft_batch_t b, int32_t* launches) {
         if (!b || !launches) fail(GFT_ERR_INVALID_ARG, "NULL argument");
         int32_t n = 0;
         for (auto& c : b->classes) n += c.total_items > 0 ? 1 : 0;
+        for (auto& c : b->nm_classes) n += c.total_items > 0 ? 1 : 0;
         if (b->wide) n += wide_batch_launches(b->wide);
         if (b->tcb) n += tc_batch_launches(b->tcb);
         if (b->tcnb) n += tcn_batch_launches(b->tcnb);

@@ -80,6 +80,11 @@ struct DevProgram {
     float* d_mats32 = nullptr;
     double* d_mats64 = nullptr;
     int* d_err = nullptr;    // device error word
+    // node-major batch kernel's program image (CUDA-core plans only):
+    // [ints, padded to 4][(leaf << 16 | first output) per group of four
+    // outputs, padded to 4]
+    int* d_nm = nullptr;
+    int nm_words = 0, nm_cg_off = 0, nm_n_cg = 0;
 };
 
 // tcn.cu: tensor-core leaf products with the signals on the MMA's N axis,

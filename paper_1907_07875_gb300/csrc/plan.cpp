@@ -270,6 +270,7 @@ void free_device(gft_plan_s& p) {
     if (p.dev.d_ints) cudaFree(p.dev.d_ints);
     if (p.dev.d_mats32) cudaFree(p.dev.d_mats32);
     if (p.dev.d_mats64) cudaFree(p.dev.d_mats64);
+    if (p.dev.d_nm) cudaFree(p.dev.d_nm);
     if (p.dev.d_err) cudaFree(p.dev.d_err);
     p.dev = DevProgram{};
     for (int b = 0; b < gft_plan_s::kHostStreams; ++b) {
@@ -414,6 +415,20 @@ void upload_plan(gft_plan_s& p) {
         GFT_CUDA(cudaMemcpy(d.d_mats32, mats32.data(), sizeof(float) * mats32.size(), cudaMemcpyHostToDevice));
         GFT_CUDA(cudaMalloc(&d.d_mats64, sizeof(double) * mats.size()));
         GFT_CUDA(cudaMemcpy(d.d_mats64, mats.data(), sizeof(double) * mats.size(), cudaMemcpyHostToDevice));
+    }
+    if (core_ok) {
+        // node-major program image: [ints][(leaf, 4-output group) list], each
+        // part padded to 4 words, so that one run of 16-byte copies brings it in
+        std::vector<int32_t> img(ints.begin(), ints.end());
+        img.resize((img.size() + 3) & ~size_t(3), 0);
+        d.nm_cg_off = (int)img.size();
+        d.nm_n_cg = 0;
+        for (size_t k = 0; k < p.leaves.size(); ++k)
+            for (int c0 = 0; c0 < p.leaves[k].m(); c0 += 4, ++d.nm_n_cg) img.push_back((int32_t)((k << 16) | c0));
+        img.resize((img.size() + 3) & ~size_t(3), 0);
+        d.nm_words = (int)img.size();
+        GFT_CUDA(cudaMalloc(&d.d_nm, sizeof(int32_t) * img.size()));
+        GFT_CUDA(cudaMemcpy(d.d_nm, img.data(), sizeof(int32_t) * img.size(), cudaMemcpyHostToDevice));
     }
     GFT_CUDA(cudaMalloc(&d.d_err, sizeof(int)));
     GFT_CUDA(cudaMemset(d.d_err, 0, sizeof(int)));

@@ -58,6 +58,7 @@ constexpr int kNSlots = 6;           // ring slots
 constexpr int kNCols = 512;          // TMEM columns per CTA (one CTA per SM): two halves
 constexpr int kNHalf = 256;
 constexpr int kNMaxLeaf = 512;
+constexpr int kNItemSteps = 16;      // K chunks of the widest leaf per work item (at most)
 constexpr unsigned kNAHalf = kNM * kNK * 2u;          // 8 KB: one of A hi / A lo
 constexpr unsigned kNBHalf = kNMaxNs * kNK * 2u;      // 8 KB: one of B hi / B lo (at most)
 constexpr unsigned kNSlotBytes = 2u * kNAHalf + 2u * kNBHalf;   // 32 KB
@@ -77,6 +78,17 @@ struct TcnLeaf {
     long long a_off;   // element offset of the leaf's basis images
 };
 
+// one M-tile of a leaf (a unit): what the copier and the MMA issuer need
+struct TcnUnit {
+    long long a_off;   // element offset of this M-tile's rows in the leaf's first K chunk image
+    int a_kstride;     // elements between consecutive K chunk images of the leaf (npad * 32)
+    int abytes;        // bytes of one of A hi / A lo per chunk (rows * 32 * 2)
+    int kchunks;       // K chunks of the leaf
+    int kc0;           // the leaf's first chunk in a tile's B image
+    int kmax;          // the leaf's K rounded up to 16
+    int pad;
+};
+
 // one plan of a launch (an entry of the caller's batch)
 struct TcnPlanDev {
     const float* x;
@@ -85,16 +97,15 @@ struct TcnPlanDev {
     long long tile0;           // first tile of this plan in the launch
     long long item0;           // first work item of this plan in the launch
     const int* prog;           // [pairs 2P][stage offsets S+1][labels n][out_pos n] ...
-    const TcnLeaf* leaves;
-    const unsigned short* unit_leaf;   // per unit: its leaf
+    const TcnUnit* units;      // per unit (M-tile of a leaf)
+    const int* upos;           // per unit 128 output positions (-1 past the leaf's end)
     const short* gather;       // per chunk 32 node labels (-1: padding), chunks in leaf order
     const unsigned char* ahi;  // basis images of this launch's precision
     const unsigned char* alo;
     unsigned char* bimg;       // B images of this plan's tiles (scratch): [tile][chunk][hi ns*64 B | lo]
     float* scale;              // per signal (scratch)
     int* err;                  // the plan's device error word
-    int n, np, ns, n_leaves, n_units, n_chunks, n_stages, n_pairs;
-    int off_labels, off_outpos;
+    int n, np, ns, n_units, n_chunks, n_stages, n_pairs;
     long long grp0;            // first 8-signal group of this plan in the launch (pack kernel)
     int upi;                   // units per work item
     int items_per_tile;
@@ -204,12 +215,13 @@ namespace {
 
 // B images: one CTA (kPackThreads) per group of 8 signals (rows
 // row0..row0+7 of tile t of a plan; rows past the batch are zeros); CTA b
-// runs groups [range[b], range[b+1]) (first_slot[b]: the plan of the first).  Phases,
-// separated by barriers: copy the 8 rows (cp.async, row stride np), one warp
-// per row for its FP16 scale, the Haar stages (threads over rows x pairs),
-// then the B operand of every (leaf, K chunk): thread (chunk, K group, row)
-// gathers 8 post-stage values through the chunk's gather table and writes 16
-// B of hi and of lo, 32 consecutive threads covering 512 contiguous bytes.
+// runs groups [range[b], range[b+1]) (first_slot[b]: the plan of the first).
+// Warp r copies row r (cp.async, row stride np), takes its FP16 scale and
+// runs the Haar stages on it (lanes over the units of a stage); after a
+// barrier, thread (chunk, K group, row) gathers 8 post-stage values through
+// the chunk's gather table and writes 16 B of hi and of lo of the B operand
+// of every (leaf, K chunk), 32 consecutive threads covering 512 contiguous
+// bytes.
 __global__ void __launch_bounds__(kPackThreads) tcn_pack_kernel(const TcnPlanDev* __restrict__ plans, int n_plans,
                                                                 const long long* __restrict__ range,
                                                                 const int* __restrict__ first_slot, int prec) {
@@ -227,29 +239,29 @@ __global__ void __launch_bounds__(kPackThreads) tcn_pack_kernel(const TcnPlanDev
         const int rg = (int)(local - t * gpt);
         const long long row0 = t * ns + rg * 8;
         const int valid = (int)max(0LL, min(8LL, D.batch - row0));
-        if ((n & 3) == 0) {
-            const int per = n >> 2;
-            for (int e = tid; e < valid * per; e += kPackThreads) {
-                const int r = e / per, c4 = e - r * per;
-                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(su32(buf + r * np + 4 * c4)),
-                             "l"(D.x + (row0 + r) * n + 4 * c4)
-                             : "memory");
-            }
-        } else {
-            for (int e = tid; e < valid * n; e += kPackThreads) {
-                const int r = e / n, c = e - r * n;
-                asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(su32(buf + r * np + c)),
-                             "l"(D.x + row0 * n + e)
-                             : "memory");
+        // warp r owns row r: its copy, its scale and its Haar stages need
+        // only warp-level ordering
+        float* row = buf + warp * np;
+        if (warp < valid) {
+            const float* src = D.x + (row0 + warp) * n;
+            if ((n & 3) == 0) {
+                for (int c4 = lane; 4 * c4 < n; c4 += 32)
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(su32(row + 4 * c4)),
+                                 "l"(src + 4 * c4)
+                                 : "memory");
+            } else {
+                for (int c = lane; c < n; c += 32)
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(su32(row + c)), "l"(src + c)
+                                 : "memory");
             }
         }
         asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
-        __syncthreads();
+        __syncwarp();
         // FP16: a power-of-two scale per signal bounding its post-stage values
-        if (warp < 8) {
+        {
             float mx = 0.f;
             if (fp16 && warp < valid)
-                for (int c = lane; c < n; c += 32) mx = fmaxf(mx, fabsf(buf[warp * np + c]));
+                for (int c = lane; c < n; c += 32) mx = fmaxf(mx, fabsf(row[c]));
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
             const float sc = mx > 0.f ? exp2f(ceilf(log2f(mx)) + (float)D.n_stages) : 1.f;
@@ -258,18 +270,20 @@ __global__ void __launch_bounds__(kPackThreads) tcn_pack_kernel(const TcnPlanDev
                 if (warp < valid) D.scale[row0 + warp] = sc;
             }
         }
-        // Haar stages in place (Sec. III; the 1/sqrt2 factors are in the basis)
-        for (int st = 0; st < D.n_stages; ++st) {
-            const int p0 = D.prog[2 * D.n_pairs + st], cnt = D.prog[2 * D.n_pairs + st + 1] - p0;
-            for (int e = tid; e < 8 * cnt; e += kPackThreads) {
-                const int r = e / cnt, pp = p0 + (e - r * cnt);
-                const int2 ij = *reinterpret_cast<const int2*>(D.prog + 2 * pp);
-                float* row = buf + r * np;
-                const float u = row[ij.x], v = row[ij.y];
-                row[ij.x] = u + v;
-                row[ij.y] = u - v;
+        // Haar stages in place (Sec. III; the 1/sqrt2 factors are in the
+        // basis): the units of a stage touch disjoint nodes
+        if (warp < valid) {
+            const int* st_off = D.prog + 2 * D.n_pairs;
+            for (int st = 0; st < D.n_stages; ++st) {
+                const int p1 = st_off[st + 1];
+                for (int pp = st_off[st] + lane; pp < p1; pp += 32) {
+                    const int2 ij = *reinterpret_cast<const int2*>(D.prog + 2 * pp);
+                    const float u = row[ij.x], v = row[ij.y];
+                    row[ij.x] = u + v;
+                    row[ij.y] = u - v;
+                }
+                __syncwarp();
             }
-            __syncthreads();
         }
         __syncthreads();   // scales and stages visible
         unsigned char* tb = D.bimg + (size_t)t * D.n_chunks * ns * 128;
@@ -277,12 +291,12 @@ __global__ void __launch_bounds__(kPackThreads) tcn_pack_kernel(const TcnPlanDev
             const int r = e & 7, kg = (e >> 3) & 3, c = e >> 5;
             const bool live = r < valid;
             const float iv = s_inv[r];
-            const float* row = buf + r * np;
+            const float* rr = buf + r * np;
             const int4 g4 = *reinterpret_cast<const int4*>(D.gather + c * kNK + kg * 8);
             const short* gs = reinterpret_cast<const short*>(&g4);
             float v[8];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) v[q] = (live && gs[q] >= 0) ? row[gs[q]] * iv : 0.f;
+            for (int q = 0; q < 8; ++q) v[q] = (live && gs[q] >= 0) ? rr[gs[q]] * iv : 0.f;
             unsigned hi[4], lo[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
@@ -318,6 +332,7 @@ __global__ void __launch_bounds__(kNThreads, 1) tcn_kernel(const TcnPlanDev* __r
     extern __shared__ __align__(128) unsigned char ring[];
     __shared__ __align__(8) unsigned long long full[kNSlots], empty[kNSlots], acc_full[2], acc_free[2], drain;
     __shared__ float s_sc[2][kNMaxNs];   // per-signal scales of the items in the two TMEM halves
+    __shared__ __align__(16) int s_pos[2][kNHalf / 16 * kNM];   // their output positions (at most 16 units)
     __shared__ unsigned s_tmem;
     __shared__ int s_abort;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -371,10 +386,9 @@ __global__ void __launch_bounds__(kNThreads, 1) tcn_kernel(const TcnPlanDev* __r
                 const unsigned bbytes = (unsigned)D.ns * kNK * 2u;
                 const unsigned char* tb = D.bimg + (size_t)t * D.n_chunks * D.ns * 128;
                 for (int u = g * D.upi; u < u1 && !stop; ++u) {
-                    const TcnLeaf L = D.leaves[D.unit_leaf[u]];
-                    const int mt = u - L.unit0;
-                    const unsigned abytes = (unsigned)min(kNM, L.npad - mt * kNM) * kNK * 2u;
-                    for (int kc = 0; kc < L.kchunks; ++kc, ++q) {
+                    const TcnUnit U = D.units[u];
+                    const unsigned abytes = (unsigned)U.abytes;
+                    for (int kc = 0; kc < U.kchunks; ++kc, ++q) {
                         const int s = (int)(q % kNSlots);
                         const long long use = q / kNSlots;
                         if (s_abort || (use >= 1 && !bar_wait(&empty[s], (unsigned)((use - 1) & 1)))) {
@@ -383,9 +397,8 @@ __global__ void __launch_bounds__(kNThreads, 1) tcn_kernel(const TcnPlanDev* __r
                             break;
                         }
                         unsigned char* dst = ring + (size_t)s * kNSlotBytes;
-                        const size_t asrc =
-                            2 * (size_t)(L.a_off + (long long)kc * L.npad * kNK + (long long)mt * kNM * kNK);
-                        const unsigned char* bsrc = tb + (size_t)(L.kc0 + kc) * D.ns * 128;
+                        const size_t asrc = 2 * (size_t)(U.a_off + (long long)kc * U.a_kstride);
+                        const unsigned char* bsrc = tb + (size_t)(U.kc0 + kc) * D.ns * 128;
                         bar_expect(&full[s], split ? 2 * (abytes + bbytes) : abytes + bbytes);
                         bulk(dst, D.ahi + asrc, abytes, &full[s]);
                         bulk(dst + 2 * kNAHalf, bsrc, bbytes, &full[s]);
@@ -424,10 +437,10 @@ __global__ void __launch_bounds__(kNThreads, 1) tcn_kernel(const TcnPlanDev* __r
                 const int ns = D.ns;
                 const unsigned id = idesc(ns, !fp16);
                 for (int u = u0; u < u1 && !stop; ++u) {
-                    const TcnLeaf L = D.leaves[D.unit_leaf[u]];
-                    const int kmax = (L.m + 15) & ~15;
+                    const TcnUnit U = D.units[u];
+                    const int kmax = U.kmax;
                     const unsigned dt = tmem + (unsigned)(h * kNHalf + (u - u0) * ns);
-                    for (int kc = 0; kc < L.kchunks; ++kc, ++q) {
+                    for (int kc = 0; kc < U.kchunks; ++kc, ++q) {
                         const int s = (int)(q % kNSlots);
                         if (s_abort || !bar_wait(&full[s], (unsigned)((q / kNSlots) & 1))) {
                             abort_now(D.err);
@@ -460,10 +473,29 @@ __global__ void __launch_bounds__(kNThreads, 1) tcn_kernel(const TcnPlanDev* __r
     } else {
         // ---------------- epilogue (warps 0-7) ----------------
         // warp w reads TMEM lanes 32 (w & 3) .. + 31; the two warps of a lane
-        // quarter take alternate 16-column chunks
-        int sl = slot0;
+        // quarter take alternate 16-column chunks.  An item's output
+        // positions (cp.async) and signal scales are staged into the buffers
+        // of its TMEM half while the item before it is stored.
         const int quarter = warp & 3, half16 = (warp >> 2) * 16;
         const unsigned lane_base = (unsigned)(quarter * 32) << 16;
+        int sl = slot0, sl_st = slot0;
+        auto stage = [&](long long it, int hh) {
+            sl_st = slot_of<0>(plans, n_plans, sl_st, it);
+            const TcnPlanDev& D = plans[sl_st];
+            const long long local = it - D.item0;
+            const long long t = local / D.items_per_tile;
+            const int g = (int)(local - t * D.items_per_tile);
+            const int u0 = g * D.upi, nu = min(u0 + D.upi, D.n_units) - u0;
+            const int* src = D.upos + (size_t)u0 * kNM;
+            for (int e = 4 * tid; e < nu * kNM; e += 4 * kNWorkers * 32)
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(su32(&s_pos[hh][e])), "l"(src + e)
+                             : "memory");
+            asm volatile("cp.async.commit_group;" ::: "memory");
+            const long long row0 = t * D.ns;
+            const int rows = (int)min((long long)D.ns, D.batch - row0);
+            if (tid < D.ns) s_sc[hh][tid] = (fp16 && tid < rows) ? D.scale[row0 + tid] : 1.f;   // tid < 256 covers ns <= 128
+        };
+        if (i0 < i1) stage(i0, 0);
         for (long long it = i0, j = 0; it < i1; ++it, ++j) {
             sl = slot_of<0>(plans, n_plans, sl, it);
             const TcnPlanDev& D = plans[sl];
@@ -475,22 +507,19 @@ __global__ void __launch_bounds__(kNThreads, 1) tcn_kernel(const TcnPlanDev* __r
             const int ns = D.ns, n = D.n;
             const long long row0 = t * ns;
             const int rows = (int)min((long long)ns, D.batch - row0);
-            // the tile's scales, while the MMAs run (the barrier below orders
-            // these writes before every read; the buffer of the item before
-            // last in this half was released by the previous item's barrier)
-            if (tid < ns) s_sc[h][tid] = (fp16 && tid < rows) ? D.scale[row0 + tid] : 1.f;   // tid < 256 covers ns <= 128
+            asm volatile("cp.async.wait_all;" ::: "memory");   // this thread's staging of the item
             const bool bad = !bar_wait(&acc_full[h], (unsigned)((j >> 1) & 1));
+            // the barrier also makes every thread's staging visible, and
+            // every warp has finished the item before (the other half)
             if (workers_any(bad || s_abort != 0)) {
                 if (tid == 0) abort_now(D.err);
                 break;
             }
+            if (it + 1 < i1) stage(it + 1, h ^ 1);
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const int* outpos = D.prog + D.off_outpos;
             for (int u = u0; u < u1; ++u) {
-                const TcnLeaf L = D.leaves[D.unit_leaf[u]];
-                const int c = (u - L.unit0) * kNM + quarter * 32 + lane;
-                const bool valid = c < L.m;
-                const int pos = valid ? outpos[L.lab + c] : 0;
+                const int pos = s_pos[h][(u - u0) * kNM + quarter * 32 + lane];
+                const bool valid = pos >= 0;
                 for (int c0 = half16; c0 < ns; c0 += 32) {
                     unsigned r[16];
                     asm volatile(
@@ -517,6 +546,7 @@ __global__ void __launch_bounds__(kNThreads, 1) tcn_kernel(const TcnPlanDev* __r
             __syncwarp();
             if (lane == 0) bar_arrive(&acc_free[h]);
         }
+        asm volatile("cp.async.wait_all;" ::: "memory");   // no staging copy left in flight
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -539,15 +569,15 @@ constexpr size_t kNSmemLimit = 232448;
 
 struct TcnPlan {
     std::vector<TcnLeaf> leaves;
-    TcnLeaf* d_leaves = nullptr;
-    unsigned short* d_unit_leaf = nullptr;
+    TcnUnit* d_units = nullptr;         // per unit (M-tile of a leaf)
+    int* d_upos = nullptr;              // per unit 128 output positions (-1 past the leaf's end)
     short* d_gather = nullptr;          // per chunk 32 node labels (-1: padding)
     int n_units = 0, n_chunks = 0;
     long long img_elems = 0;
     unsigned char* d_img[2][2] = {};   // [BF16, FP16][hi, lo]
     ~TcnPlan() {
-        if (d_leaves) cudaFree(d_leaves);
-        if (d_unit_leaf) cudaFree(d_unit_leaf);
+        if (d_units) cudaFree(d_units);
+        if (d_upos) cudaFree(d_upos);
         if (d_gather) cudaFree(d_gather);
         for (auto& a : d_img)
             for (auto& q : a)
@@ -573,7 +603,8 @@ TcnPlan* tcn_prepare(gft_plan_s& p) {
     std::unique_ptr<TcnPlan> T(new TcnPlan);
     int lab = 0, kc0 = 0, unit0 = 0;
     long long a = 0;
-    std::vector<unsigned short> unit_leaf;
+    std::vector<TcnUnit> units;
+    std::vector<int> upos;
     for (size_t k = 0; k < p.leaves.size(); ++k) {
         const Leaf& lf = p.leaves[k];
         TcnLeaf L{};
@@ -585,7 +616,20 @@ TcnPlan* tcn_prepare(gft_plan_s& p) {
         L.kc0 = kc0;
         L.unit0 = unit0;
         L.a_off = a;
-        for (int mt = 0; mt < L.mtiles; ++mt) unit_leaf.push_back((unsigned short)k);
+        for (int mt = 0; mt < L.mtiles; ++mt) {
+            TcnUnit U{};
+            U.a_off = L.a_off + (long long)mt * kNM * kNK;
+            U.a_kstride = L.npad * kNK;
+            U.abytes = std::min(kNM, L.npad - mt * kNM) * kNK * 2;
+            U.kchunks = L.kchunks;
+            U.kc0 = L.kc0;
+            U.kmax = (L.m + 15) & ~15;
+            units.push_back(U);
+            for (int r = 0; r < kNM; ++r) {
+                const int c = mt * kNM + r;
+                upos.push_back(c < L.m ? p.out_pos[(size_t)L.lab + c] : -1);
+            }
+        }
         lab += L.m;
         kc0 += L.kchunks;
         unit0 += L.mtiles;
@@ -602,11 +646,10 @@ TcnPlan* tcn_prepare(gft_plan_s& p) {
     GFT_CUDA(cudaMalloc(&T->d_gather, sizeof(short) * std::max<size_t>(1, gat.size())));
     GFT_CUDA(cudaMemcpy(T->d_gather, gat.data(), sizeof(short) * gat.size(), cudaMemcpyHostToDevice));
     T->img_elems = a;
-    GFT_CUDA(cudaMalloc(&T->d_leaves, sizeof(TcnLeaf) * T->leaves.size()));
-    GFT_CUDA(cudaMemcpy(T->d_leaves, T->leaves.data(), sizeof(TcnLeaf) * T->leaves.size(), cudaMemcpyHostToDevice));
-    GFT_CUDA(cudaMalloc(&T->d_unit_leaf, sizeof(unsigned short) * unit_leaf.size()));
-    GFT_CUDA(cudaMemcpy(T->d_unit_leaf, unit_leaf.data(), sizeof(unsigned short) * unit_leaf.size(),
-                        cudaMemcpyHostToDevice));
+    GFT_CUDA(cudaMalloc(&T->d_units, sizeof(TcnUnit) * units.size()));
+    GFT_CUDA(cudaMemcpy(T->d_units, units.data(), sizeof(TcnUnit) * units.size(), cudaMemcpyHostToDevice));
+    GFT_CUDA(cudaMalloc(&T->d_upos, sizeof(int) * upos.size()));
+    GFT_CUDA(cudaMemcpy(T->d_upos, upos.data(), sizeof(int) * upos.size(), cudaMemcpyHostToDevice));
     p.tcn = T.release();
     return static_cast<TcnPlan*>(p.tcn);
 }
@@ -701,8 +744,8 @@ void* tcn_batch_create(const std::vector<gft_plan_s*>& plans, const std::vector<
         e = TcnPlanDev{};
         e.batch = batches[i];
         e.prog = p.dev.d_ints;
-        e.leaves = T->d_leaves;
-        e.unit_leaf = T->d_unit_leaf;
+        e.units = T->d_units;
+        e.upos = T->d_upos;
         e.gather = T->d_gather;
         e.ahi = T->d_img[fp16 ? 1 : 0][0];
         e.alo = T->d_img[fp16 ? 1 : 0][1];
@@ -711,14 +754,16 @@ void* tcn_batch_create(const std::vector<gft_plan_s*>& plans, const std::vector<
         e.np = np_of(p.n);
         // signals per tile: the whole batch up to 128 (a multiple of 16)
         e.ns = (int)std::min<int64_t>(kNMaxNs, std::max<int64_t>(16, (batches[i] + 15) & ~int64_t(15)));
-        e.n_leaves = (int)T->leaves.size();
         e.n_units = T->n_units;
         e.n_chunks = T->n_chunks;
         e.n_stages = p.dev.n_pre_stages;
         e.n_pairs = p.dev.n_pairs;
-        e.off_labels = 2 * p.dev.n_pairs + p.dev.n_stages + 1;
-        e.off_outpos = e.off_labels + p.n;
-        e.upi = std::max(1, std::min(T->n_units, kNHalf / e.ns));
+        // units per item: one TMEM half, and at most kNItemSteps K chunks for
+        // the widest leaf, so that a large graph spreads over many SMs and the
+        // static ranges balance
+        int kcmax = 1;
+        for (auto& L : T->leaves) kcmax = std::max(kcmax, L.kchunks);
+        e.upi = std::max(1, std::min({T->n_units, kNHalf / e.ns, kNItemSteps / kcmax}));
         e.items_per_tile = (T->n_units + e.upi - 1) / e.upi;
         double steps = 0;
         for (auto& L : T->leaves) steps += (double)L.mtiles * L.kchunks;

@@ -40,9 +40,12 @@ def test_config3_core_kinds_in_one_launch(env):
     torch.cuda.synchronize()
     for p, x, y in zip(plans, xs, ys):
         assert torch.equal(y, p.forward(x))
-    for i in range(len(plans)):
+    for p, i in zip(plans, range(len(plans))):
         tile, threads = b.tile(i)
-        assert threads == 128 and tile in (128, 256, 512)
+        if p.n <= 256:        # node-major kernel: a power-of-two tile
+            assert threads == 256 and tile in (16, 32, 64, 128, 256, 512, 1024)
+        else:                 # thread-per-signal kernel (autotuned tile) or wide-leaf kernel
+            assert (threads, tile) == (0, 0) or (threads == 128 and tile in (128, 256, 512))
 
 
 def test_pointer_change_reuses_graph(env):
@@ -256,3 +259,36 @@ def test_small_graph_batch_sizes_and_item_edges(env):
     for p, x, y in zip(plans, xs, ys):
         if x.shape[0]:
             assert torch.equal(y, p.forward(x)), p.n
+
+
+def test_node_major_kernel_tiles_and_leaf_widths(env):
+    """The node-major table-driven kernel: graphs of 2..256 nodes (tiles of
+    1024 down to 16 signals), leaves from 1 to 64 nodes (widths that are not
+    multiples of four included), zero to several Haar stages, batches on
+    both sides of every tile size and a single signal, mixed with a plan
+    that has right Haar units (thread-per-signal kernel) in one launch.
+    Outputs equal the table-driven single-plan forward bit for bit (the same
+    FMA chain per output)."""
+    gft, torch = env
+    graphs = [W.path(2), W.path(3), W.path(5), W.cycle(12), W.path(33), W.grid(6), W.path(70), W.cycle(100),
+              W.path(128), W.grid(11), W.bipartite(90, 0.2, seed=3), W.skeleton25(), W.path(127), W.cycle(256),
+              W.grid(14), W.path(130)]
+    plans = _plans(gft, graphs)
+    right = W.krbg(16, 3, seed=7)
+    plans.append(gft.Plan.bipartite(gft.laplacian(right.W, right.s), right.meta["side"]))
+    graphs.append(right)
+    batches = [1025, 1024, 255, 1, 129, 128, 65, 64, 33, 31, 97, 1025, 2, 17, 16, 15, 300]
+    b = gft.Batch(plans, batches)
+    xs = [torch.from_numpy(W.signals(bt, g.n, 700 + i)).cuda() for i, (g, bt) in enumerate(zip(graphs, batches))]
+    ys = [torch.full_like(x, float("nan")) for x in xs]
+    b.bind(xs, ys).forward()
+    torch.cuda.synchronize()
+    for p, x, y, i in zip(plans, xs, ys, range(len(plans))):
+        assert torch.equal(y, p.forward(x)), (p.n, p.info["max_leaf"])
+    tiles = [b.tile(i) for i in range(len(plans))]
+    assert tiles[0] == (1024, 256) and tiles[8] == (32, 256) and tiles[13] == (16, 256)   # 2, 128, 256 nodes
+    assert tiles[-1][1] != 256                                     # right Haar plan: not node-major
+    b.forward()                                                    # replay: same bits
+    torch.cuda.synchronize()
+    for p, x, y in zip(plans, xs, ys):
+        assert torch.equal(y, p.forward(x))
