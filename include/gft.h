@@ -88,6 +88,7 @@ typedef enum {
 #define GFT_PREC_BF16    1u  /* leaf products on tensor cores, BF16 operands */
 #define GFT_PREC_BF16X3  2u  /* BF16 hi+lo split, three products (hi*hi + hi*lo + lo*hi) */
 #define GFT_PREC_FP16X3  3u  /* FP16 hi+lo split (scaled), three products */
+#define GFT_BATCH_NO_JIT 0x100u /* mixed batches: no plan-specialised group (or'ed into the precision) */
 
 /* Human-readable name of a status code (static string, never NULL). */
 const char* gft_status_string(gft_status s);
@@ -350,11 +351,17 @@ gft_status gft_device_error(gft_plan_t plan, int32_t* code);
  *     (128 signals per tile) per size class (n <= 256 and n > 256); a timeout
  *     in these kernels is reported in the error word of the plan being
  *     transformed (pack / 128-signal kernel: the class's first plan);
- *   - the other plans of at most 128 nodes with leaves of at most 64 nodes
+ *   - plans of at most 64 nodes (leaf matrices of at most 2048 entries)
+ *     whose entries hold at least 2^19 coefficients in all: ONE persistent
+ *     kernel of a module generated and compiled (NVRTC) at creation, with
+ *     the straight-line forward code of each such plan (the single-plan
+ *     specialised kernel's), over all their (entry, tile) items; unless
+ *     GFT_BATCH_NO_JIT;
+ *   - the other plans of at most 256 nodes with leaves of at most 64 nodes
  *     and no right Haar units: persistent node-major table-driven kernels,
- *     one launch per size class (n up to 16, 32, 64, 128), tiles of 32..256
- *     signals, each CTA walking a contiguous, cost-balanced range of
- *     (plan, tile) items with double-buffered tile loads;
+ *     one launch per size class (n up to 16, 32, 64, 128, 256), tiles of
+ *     16..1024 signals, each CTA walking a contiguous, cost-balanced range
+ *     of (plan, tile) items with double-buffered tile and program loads;
  *   - the rest with leaves of at most 64 nodes (unless the plan prefers the
  *     wide-leaf kernel): persistent thread-per-signal table-driven kernels,
  *     one launch per size class (row stride n|1 up to 17, 33, 65, 129, 257),
@@ -370,7 +377,8 @@ gft_status gft_device_error(gft_plan_t plan, int32_t* code);
  *  batches[n_plans] signals per plan.
  *  flags           precision of the tensor-core leaves: GFT_PREC_FP32 (0:
  *                  CUDA cores only), GFT_PREC_BF16, GFT_PREC_BF16X3,
- *                  GFT_PREC_FP16X3.
+ *                  GFT_PREC_FP16X3; or'ed with GFT_BATCH_NO_JIT to keep
+ *                  every plan off the plan-specialised group.
  * gft_batch_forward: x[i], y[i] device pointers to [batches[i], n_i] FP32
  * (host arrays of n_plans pointers); x[i] != y[i] for tensor-core entries.
  * The captured graph is reused: new pointers are written to the kernels'

@@ -382,16 +382,20 @@ class ApproxGFT:
 class Batch:
     """Many plans transformed by one graph-captured launch (gft_batch_create):
     persistent kernels over (plan, tile) work lists, plus the tensor-core
-    kernels of wide plans when a tensor-core precision is asked for."""
+    kernels of wide plans when a tensor-core precision is asked for.
+    ``jit=False`` keeps every plan off the plan-specialised group (small
+    plans shared by many entries, compiled into one module at creation)."""
 
-    def __init__(self, plans: Sequence[Plan], batches: Sequence[int], precision: str = "fp32"):
+    BATCH_NO_JIT = 0x100
+
+    def __init__(self, plans: Sequence[Plan], batches: Sequence[int], precision: str = "fp32", jit: bool = True):
         self.plans = list(plans)
         arr = (C.c_void_p * len(plans))(*[p.handle for p in plans])
         b = np.ascontiguousarray(np.asarray(batches, dtype=np.int64))
         h = C.c_void_p()
         self._h = None
-        _check(lib().gft_batch_create(len(plans), C.cast(arr, C.c_void_p), _ptr(b), PRECISIONS[precision],
-                                      C.byref(h)))
+        flags = PRECISIONS[precision] | (0 if jit else self.BATCH_NO_JIT)
+        _check(lib().gft_batch_create(len(plans), C.cast(arr, C.c_void_p), _ptr(b), flags, C.byref(h)))
         self._h = h
         self.batches = b
 

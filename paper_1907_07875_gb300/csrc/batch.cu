@@ -195,6 +195,7 @@ __global__ void __launch_bounds__(kBatchThreads) gft_batch_kernel(const BatchPla
 // Each output is the same FMA chain (r ascending from zero) as in the
 // thread-per-signal kernel, so the results agree bit for bit.
 constexpr int kNmThreads = 256;
+constexpr double kGroupMinCoeffs = 524288.0;   // plan-specialised group: coefficients of a plan over its entries
 constexpr int kNmMaxN = 256;
 constexpr int kNmMaxTs = 1024;      // signals per tile: a power of two, 16..1024
 constexpr int kNmTileFloats = 4096;
@@ -433,11 +434,14 @@ struct gft_batch_s {
     // routing of the caller's plans: 0 = table-driven batch kernel, 1 = wide-leaf
     // batch kernel, 2 = tensor-core sequence (pack + leaf kernels, 128 signals
     // per tile), 3 = few-signals tensor-core kernels, 4 = node-major table-driven
-    // kernel; idx = position within its group
+    // kernel, 5 = plan-specialised group; idx = position within its group
     uint32_t precision = GFT_PREC_FP32;
     std::vector<int> kind, idx;
     std::vector<int64_t> user_batch;
-    std::vector<int> table_users, wide_users, tc_users, tcn_users, nm_users;
+    std::vector<int> table_users, wide_users, tc_users, tcn_users, nm_users, jg_users;
+    std::vector<gft_plan_s*> jg_plans;
+    std::vector<int64_t> jg_batches;
+    void* jgroup = nullptr;                // plan-specialised group (jit.cpp)
     std::vector<gft_plan_s*> tc_plans, tcn_plans;
     std::vector<int64_t> tc_batches, tcn_batches;
     void* wide = nullptr;                  // wide-leaf group (wide.cu)
@@ -465,6 +469,7 @@ struct gft_batch_s {
         if (wide) gft::wide_batch_free(wide);
         if (tcb) gft::tc_batch_free(tcb);
         if (tcnb) gft::tcn_batch_free(tcnb);
+        if (jgroup) gft::jit_group_free(jgroup);
         for (auto& st : side)
             if (st) cudaStreamDestroy(st);
         if (ev_fork) cudaEventDestroy(ev_fork);
@@ -807,9 +812,15 @@ gft_status gft_batch_create(int32_t n_plans, const gft_plan_t* plans, const int6
                             gft_batch_t* out) {
     return guard_b([&] {
         if (!out || !plans || !batches || n_plans < 1) fail(GFT_ERR_INVALID_ARG, "bad arguments");
-        if (flags > GFT_PREC_FP16X3) fail(GFT_ERR_INVALID_ARG, "unknown flag");
+        if ((flags & ~GFT_BATCH_NO_JIT) > GFT_PREC_FP16X3) fail(GFT_ERR_INVALID_ARG, "unknown flag");
         std::unique_ptr<gft_batch_s> b(new gft_batch_s);
-        b->precision = flags;
+        b->precision = flags & ~GFT_BATCH_NO_JIT;
+        const bool group_ok = !(flags & GFT_BATCH_NO_JIT);
+        // coefficients per plan over its entries: the plan-specialised group
+        // takes the small plans that many entries share
+        std::map<const gft_plan_s*, double> coeffs;
+        for (int i = 0; i < n_plans; ++i)
+            if (plans[i] && batches[i] > 0) coeffs[plans[i]] += (double)batches[i] * plans[i]->n;
         std::vector<gft_plan_s*> wide_plans;
         std::vector<int64_t> wide_batches;
         for (int i = 0; i < n_plans; ++i) {
@@ -824,6 +835,7 @@ gft_status gft_batch_create(int32_t n_plans, const gft_plan_t* plans, const int6
             const bool big_batch_tc = tc_prec && max_leaf >= kTcMinLeaf && tc_eligible(*p) && batches[i] > kTcnMaxBatch;
             if (tc_prec && max_leaf >= kTcnMinLeaf && !big_batch_tc && tcn_eligible(*p)) kind = 3;
             else if (tc_prec && max_leaf >= kTcMinLeaf && tc_eligible(*p)) kind = 2;
+            else if (group_ok && coeffs[p] >= kGroupMinCoeffs && jit_group_eligible(*p)) kind = 5;
             else if (nm_eligible(*p)) kind = 4;
             else if (p->dev.max_bucket != 0 && !(wide_configured(*p) && wide_ready(*p, false))) kind = 0;
             else if (wide_configured(*p)) kind = 1;
@@ -840,6 +852,11 @@ gft_status gft_batch_create(int32_t n_plans, const gft_plan_t* plans, const int6
                 b->wide_users.push_back(i);
                 wide_plans.push_back(p);
                 wide_batches.push_back(batches[i]);
+            } else if (kind == 5) {
+                b->idx.push_back((int)b->jg_plans.size());
+                b->jg_users.push_back(i);
+                b->jg_plans.push_back(p);
+                b->jg_batches.push_back(batches[i]);
             } else if (kind == 4) {
                 b->idx.push_back((int)b->nm_plans.size());
                 b->nm_users.push_back(i);
@@ -862,6 +879,7 @@ gft_status gft_batch_create(int32_t n_plans, const gft_plan_t* plans, const int6
             layout(*b);
         }
         if (!b->nm_plans.empty()) layout_nm(*b);
+        if (!b->jg_plans.empty()) b->jgroup = jit_group_create(b->jg_plans, b->jg_batches);
         if (!wide_plans.empty()) b->wide = wide_batch_create(wide_plans, wide_batches);
         if (!b->tc_plans.empty()) b->tcb = tc_batch_create(b->tc_plans, b->tc_batches, b->precision);
         if (!b->tcn_plans.empty()) b->tcnb = tcn_batch_create(b->tcn_plans, b->tcn_batches, b->precision);
@@ -892,8 +910,8 @@ gft_status gft_batch_forward(gft_batch_t b, const float* const* x, float* const*
         if (!same) {
             // every group reads its signal pointers from device descriptors,
             // so the captured graph stays valid
-            std::vector<const float*> tx, wx, cx, nx, mx;
-            std::vector<float*> ty, wy, cy, ny, my;
+            std::vector<const float*> tx, wx, cx, nx, mx, gx;
+            std::vector<float*> ty, wy, cy, ny, my, gy;
             for (int i : b->table_users) {
                 tx.push_back(x[i]);
                 ty.push_back(y[i]);
@@ -914,8 +932,13 @@ gft_status gft_batch_forward(gft_batch_t b, const float* const* x, float* const*
                 mx.push_back(x[i]);
                 my.push_back(y[i]);
             }
+            for (int i : b->jg_users) {
+                gx.push_back(x[i]);
+                gy.push_back(y[i]);
+            }
             if (!b->plans.empty()) upload_desc(*b, tx.data(), ty.data(), st);
             if (!b->nm_plans.empty()) upload_classes(b->nm_classes, mx.data(), my.data(), st);
+            if (b->jgroup) jit_group_upload(b->jgroup, gx, gy, st);
             if (b->wide) wide_batch_upload(b->wide, wx, wy, st);
             if (b->tcb) tc_batch_upload(b->tcb, cx, cy, st);
             if (b->tcnb) tcn_batch_upload(b->tcnb, nx, ny, st);
@@ -944,6 +967,7 @@ gft_status gft_batch_forward(gft_batch_t b, const float* const* x, float* const*
                 // stream (launched concurrently they take the SMs' shared
                 // memory that the tensor-core kernels wait for)
                 auto class_stream = [&](int) { return cs; };
+                if (b->jgroup) jit_group_launch(b->jgroup, cs);
                 if (!b->nm_plans.empty()) launch_nm(*b, class_stream);
                 if (!b->plans.empty()) launch_batch(*b, class_stream);
                 for (int s = 0; s < gft_batch_s::kSide; ++s)
@@ -976,6 +1000,9 @@ gft_status gft_batch_get_tile(gft_batch_t b, int32_t i, int32_t* tile, int32_t* 
         } else if (b->kind[i] == 4) {
             *tile = nm_ts(b->nm_plans[b->idx[i]]->n);
             *threads = kNmThreads;
+        } else if (b->kind[i] == 5) {
+            *tile = jit_group_tile(b->jgroup, b->idx[i]);
+            *threads = 128;
         }
     });
 }
@@ -986,6 +1013,7 @@ gft_status gft_batch_get_launches(gft_batch_t b, int32_t* launches) {
         int32_t n = 0;
         for (auto& c : b->classes) n += c.total_items > 0 ? 1 : 0;
         for (auto& c : b->nm_classes) n += c.total_items > 0 ? 1 : 0;
+        if (b->jgroup) n += jit_group_launches(b->jgroup);
         if (b->wide) n += wide_batch_launches(b->wide);
         if (b->tcb) n += tc_batch_launches(b->tcb);
         if (b->tcnb) n += tcn_batch_launches(b->tcnb);

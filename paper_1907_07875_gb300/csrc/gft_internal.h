@@ -211,6 +211,14 @@ bool jit_launch(gft_plan_s& p, bool f64, const void* x, void* y, int64_t batch, 
 void jit_info(const gft_plan_s& p, int* jit, int* tile, int* threads);
 bool jit_launch_plain(gft_plan_s& p, const float* x, float* y, int64_t batch, cudaStream_t st);
 std::string jit_source(const gft_plan_s& p, bool f64);
+// plan-specialised group of a mixed batch (small plans shared by many entries)
+bool jit_group_eligible(const gft_plan_s& p);
+void* jit_group_create(const std::vector<gft_plan_s*>& plans, const std::vector<int64_t>& batches);
+void jit_group_upload(void* g, const std::vector<const float*>& x, const std::vector<float*>& y, cudaStream_t st);
+void jit_group_launch(void* g, cudaStream_t st);
+void jit_group_free(void* g);
+int jit_group_launches(void* g);
+int jit_group_tile(void* g, int entry);
 
 // search.cpp: involution search (Sec. V-F)
 int find_involution(int n, const double* L, const int* classes, long long max_steps, double scale, int* phi);

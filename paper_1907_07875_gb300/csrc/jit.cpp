@@ -27,6 +27,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <sstream>
 #include <string>
@@ -144,6 +145,10 @@ __device__ __forceinline__ void bulk_s2g(void* dst, const void* src, unsigned by
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+)";
+
+// tile movers of one plan's row layout (macros N, NP, MODE)
+const char* kTileFns = R"(
 // one thread: whole-tile load (16-byte multiple by TMA, the < 16-byte rest by plain copies)
 template <int TS>
 __device__ __forceinline__ void bulk_load_tile(const T* __restrict__ x, T* buf, i64 tile, i64 batch, unsigned long long* bar) {
@@ -300,7 +305,7 @@ std::string replace_all(std::string s, const std::string& a, const std::string& 
 }
 
 // per-row straight-line code
-std::string gen_bodies(const gft_plan_s& p, bool f64, int mode) {
+std::string gen_bodies(const gft_plan_s& p, bool f64, int mode, bool with_inverse = true) {
     const int n = p.n;
     const char* T = f64 ? "double" : "float";
     const char* FMA = f64 ? "fma" : "fmaf";
@@ -382,6 +387,7 @@ std::string gen_bodies(const gft_plan_s& p, bool f64, int mode) {
         }
     }
     o << "}\n";
+    if (!with_inverse) return o.str();
     // ---------------- inverse ----------------
     o << "__device__ __noinline__ void body_inv(" << T << "* __restrict__ row) {\n    " << T << " ";
     for (int i = 0; i < n; ++i) o << "v" << i << (i + 1 < n ? ", " : ";\n");
@@ -450,7 +456,7 @@ std::string gen_module(const gft_plan_s& p, bool f64, const Layout& L, std::vect
     std::ostringstream s;
     s << "#define T " << (f64 ? "double" : "float") << "\n#define N " << p.n << "\n#define NP " << L.np
       << "\n#define MODE " << L.mode << "\n";
-    s << kHelpers;
+    s << kHelpers << kTileFns;
     s << gen_bodies(p, f64, L.mode);
     const size_t esz = f64 ? 8 : 4;
     for (int ci = 0; ci < (int)(sizeof(kCands) / sizeof(kCands[0])); ++ci) {
@@ -677,6 +683,253 @@ void jit_info(const gft_plan_s& p, int* jit, int* tile, int* threads) {
     *jit = J->d32[0].bulk ? 2 : 1;
     *tile = J->d32[0].rs * J->d32[0].threads;
     *threads = J->d32[0].threads;
+}
+
+// ---------------------------------------------------------------------------
+// Batch group: the graphs of a mixed batch whose plans are small and shared
+// by many entries (the size sweep's deterministic families: thousands of
+// skeletons, dozens of cycles or grids of each size).  One module holds the
+// straight-line forward body of every such plan (in a namespace of its own,
+// with its row layout) and ONE persistent kernel over all their (entry,
+// tile) items: a CTA walks a contiguous range of items, switching on the
+// item's plan for the tile load, the body and the store, with the next
+// item's tile in flight (cp.async) while this one runs.  The bodies are the
+// single-plan kernel's, so the outputs agree with the plan's own forward bit
+// for bit.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kGroupThreads = 128;
+constexpr int kGroupMaxN = 64;
+constexpr long long kGroupMaxEntries = 2048;
+constexpr int kGroupBufFloats = 8448;   // one tile buffer: 33 KB
+
+struct JSegHost {   // same layout as the module's JSeg
+    const float* x;
+    float* y;
+    long long batch;
+    long long item0;
+    int plan;
+    int ts;
+};
+
+const char* kGroupKernel = R"(
+extern "C" __global__ void __launch_bounds__(128) gft_jit_group(const JSeg* __restrict__ segs, int nseg,
+                                                               const i64* __restrict__ range,
+                                                               const int* __restrict__ first, int buf_cap) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* tiles = reinterpret_cast<float*>(smem_raw);
+    const i64 it0 = range[blockIdx.x], it1 = range[blockIdx.x + 1];
+    if (it0 >= it1) return;
+    int s = first[blockIdx.x];
+    while (s + 1 < nseg && segs[s + 1].item0 <= it0) ++s;
+    g_load(segs[s], it0 - segs[s].item0, tiles);
+    commit();
+    int cur = 0;
+    for (i64 it = it0; it < it1; ++it) {
+        const JSeg S = segs[s];
+        float* buf = tiles + cur * buf_cap;
+        int ns = s;
+        if (it + 1 < it1) {
+            while (ns + 1 < nseg && segs[ns + 1].item0 <= it + 1) ++ns;
+            g_load(segs[ns], it + 1 - segs[ns].item0, tiles + (cur ^ 1) * buf_cap);
+        }
+        commit();
+        wait1();
+        __syncthreads();
+        g_compute(S.plan, buf);
+        __syncthreads();
+        g_store(S, it - S.item0, buf);
+        __syncthreads();
+        cur ^= 1;
+        s = ns;
+    }
+    wait0();
+}
+)";
+
+int group_rs(int np) { return np <= 16 ? 4 : (np <= 33 ? 2 : 1); }
+
+}  // namespace
+
+bool jit_group_eligible(const gft_plan_s& p) {
+    if (std::getenv("GFT_DISABLE_JIT")) return false;
+    if (!p.has_device || p.n > kGroupMaxN || p.n < 1) return false;
+    if (leaf_entries(p) > kGroupMaxEntries) return false;
+    const Layout L = row_layout(p.n, false);
+    return (size_t)group_rs(L.np) * kGroupThreads * L.np <= (size_t)kGroupBufFloats;
+}
+
+struct JitGroup {
+    cudaLibrary_t lib = nullptr;
+    cudaKernel_t k = nullptr;
+    std::vector<JSegHost> segs;    // slot order
+    std::vector<int> members;      // slot -> entry index
+    JSegHost* d_segs = nullptr;
+    long long* d_range = nullptr;
+    int* d_first = nullptr;
+    long long total_items = 0;
+    int grid = 0, buf_cap = 0;
+    size_t smem = 0;
+    ~JitGroup() {
+        if (d_segs) cudaFree(d_segs);
+        if (d_range) cudaFree(d_range);
+        if (d_first) cudaFree(d_first);
+        if (lib) cudaLibraryUnload(lib);
+    }
+};
+
+std::string jit_group_source(const std::vector<const gft_plan_s*>& uniq) {
+    std::ostringstream s;
+    s << "#define T float\n#define N 4\n#define NP 4\n#define MODE 0\n" << kHelpers << "#undef N\n#undef NP\n#undef MODE\n";
+    std::vector<int> rs(uniq.size()), np(uniq.size());
+    for (size_t k = 0; k < uniq.size(); ++k) {
+        const gft_plan_s& p = *uniq[k];
+        const Layout L = row_layout(p.n, false);
+        rs[k] = group_rs(L.np);
+        np[k] = L.np;
+        s << "namespace jg" << k << " {\n#define N " << p.n << "\n#define NP " << L.np << "\n#define MODE " << L.mode
+          << "\n";
+        s << kTileFns << gen_bodies(p, false, L.mode, false);
+        s << "#undef N\n#undef NP\n#undef MODE\n}\n";
+    }
+    s << "struct JSeg { const float* x; float* y; i64 batch; i64 item0; int plan; int ts; };\n";
+    s << "__device__ __forceinline__ void g_load(const JSeg& S, i64 tile, float* buf) {\n    switch (S.plan) {\n";
+    for (size_t k = 0; k < uniq.size(); ++k)
+        s << "    case " << k << ": jg" << k << "::load_tile<128, " << rs[k] * kGroupThreads
+          << ">(S.x, buf, tile, S.batch); break;\n";
+    s << "    }\n}\n";
+    s << "__device__ __forceinline__ void g_compute(int plan, float* buf) {\n    switch (plan) {\n";
+    for (size_t k = 0; k < uniq.size(); ++k)
+        s << "    case " << k << ":\n#pragma unroll\n        for (int r = 0; r < " << rs[k] << "; ++r) jg" << k
+          << "::body_fwd(buf + (threadIdx.x + r * 128) * " << np[k] << ");\n        break;\n";
+    s << "    }\n}\n";
+    s << "__device__ __forceinline__ void g_store(const JSeg& S, i64 tile, const float* buf) {\n    switch (S.plan) {\n";
+    for (size_t k = 0; k < uniq.size(); ++k)
+        s << "    case " << k << ": jg" << k << "::store_tile<128, " << rs[k] * kGroupThreads
+          << ">(buf, S.y, tile, S.batch); break;\n";
+    s << "    }\n}\n";
+    s << kGroupKernel;
+    return s.str();
+}
+
+void* jit_group_create(const std::vector<gft_plan_s*>& plans, const std::vector<int64_t>& batches) {
+    std::unique_ptr<JitGroup> G(new JitGroup);
+    const int k = (int)plans.size();
+    std::vector<const gft_plan_s*> uniq;
+    std::map<const gft_plan_s*, int> id;
+    for (auto* p : plans) {
+        if (!jit_group_eligible(*p)) fail(GFT_ERR_UNSUPPORTED, "plan not eligible for the plan-specialised batch group");
+        if (!id.count(p)) {
+            id[p] = (int)uniq.size();
+            uniq.push_back(p);
+        }
+    }
+    const std::string src = jit_group_source(uniq);
+    std::vector<char> bin;
+    {
+        std::lock_guard<std::mutex> g(g_cache_mu);
+        auto it = cubin_cache().find(src);
+        if (it != cubin_cache().end()) bin = it->second;
+    }
+    if (bin.empty()) {
+        bin = nvrtc_compile(src);
+        std::lock_guard<std::mutex> g(g_cache_mu);
+        cubin_cache()[src] = bin;
+    }
+    GFT_CUDA(cudaLibraryLoadData(&G->lib, bin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0));
+    GFT_CUDA(cudaLibraryGetKernel(&G->k, G->lib, "gft_jit_group"));
+    // slots: plans by decreasing cost per item, the entries of one plan together
+    std::vector<double> cpi(uniq.size());
+    std::vector<int> ts(uniq.size());
+    for (size_t u = 0; u < uniq.size(); ++u) {
+        const Layout L = row_layout(uniq[u]->n, false);
+        ts[u] = group_rs(L.np) * kGroupThreads;
+        G->buf_cap = std::max(G->buf_cap, ts[u] * L.np);
+        cpi[u] = (double)ts[u] * (8.0 * uniq[u]->n + 0.1 * (double)leaf_entries(*uniq[u])) + 2000.0;
+    }
+    G->buf_cap = (G->buf_cap + 3) & ~3;
+    G->members.resize(k);
+    for (int i = 0; i < k; ++i) G->members[i] = i;
+    std::stable_sort(G->members.begin(), G->members.end(), [&](int a, int b) {
+        const int ua = id[plans[a]], ub = id[plans[b]];
+        return cpi[ua] != cpi[ub] ? cpi[ua] > cpi[ub] : ua < ub;
+    });
+    std::vector<long long> items;
+    double total = 0.0;
+    for (int i : G->members) {
+        const int u = id[plans[i]];
+        JSegHost e{};
+        e.batch = batches[i];
+        e.item0 = G->total_items;
+        e.plan = u;
+        e.ts = ts[u];
+        items.push_back((batches[i] + ts[u] - 1) / ts[u]);
+        G->total_items += items.back();
+        total += cpi[u] * (double)items.back();
+        G->segs.push_back(e);
+    }
+    G->smem = 2 * sizeof(float) * (size_t)G->buf_cap;
+    GFT_CUDA(cudaFuncSetAttribute((const void*)G->k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G->smem));
+    int per_sm = 0;
+    GFT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)G->k, kGroupThreads, G->smem));
+    if (per_sm < 1) fail(GFT_ERR_UNSUPPORTED, "plan-specialised batch group does not fit on an SM");
+    G->grid = (int)std::max<long long>(1, std::min<long long>(G->total_items, (long long)per_sm * sm_count()));
+    // contiguous item ranges of about equal cost, the slot of each range's first item
+    std::vector<long long> range(G->grid + 1, G->total_items);
+    std::vector<int> first(G->grid, std::max(0, k - 1));
+    range[0] = 0;
+    first[0] = 0;
+    double acc = 0.0;
+    int cta = 1;
+    for (size_t sl = 0; sl < G->segs.size() && cta < G->grid; ++sl) {
+        const double c = cpi[G->segs[sl].plan];
+        for (long long t = 0; t < items[sl] && cta < G->grid; ++t) {
+            acc += c;
+            while (cta < G->grid && acc >= total * cta / G->grid) {
+                range[cta] = std::min(G->segs[sl].item0 + t + 1, G->total_items);
+                first[cta] = (int)sl;
+                ++cta;
+            }
+        }
+    }
+    GFT_CUDA(cudaMalloc(&G->d_segs, sizeof(JSegHost) * std::max<size_t>(1, G->segs.size())));
+    GFT_CUDA(cudaMalloc(&G->d_range, sizeof(long long) * range.size()));
+    GFT_CUDA(cudaMalloc(&G->d_first, sizeof(int) * first.size()));
+    GFT_CUDA(cudaMemcpy(G->d_range, range.data(), sizeof(long long) * range.size(), cudaMemcpyHostToDevice));
+    GFT_CUDA(cudaMemcpy(G->d_first, first.data(), sizeof(int) * first.size(), cudaMemcpyHostToDevice));
+    return G.release();
+}
+
+void jit_group_upload(void* h, const std::vector<const float*>& x, const std::vector<float*>& y, cudaStream_t st) {
+    JitGroup* G = static_cast<JitGroup*>(h);
+    for (size_t sl = 0; sl < G->segs.size(); ++sl) {
+        G->segs[sl].x = x[G->members[sl]];
+        G->segs[sl].y = y[G->members[sl]];
+    }
+    if (!G->segs.empty())
+        GFT_CUDA(cudaMemcpyAsync(G->d_segs, G->segs.data(), sizeof(JSegHost) * G->segs.size(), cudaMemcpyHostToDevice,
+                                 st));
+}
+
+void jit_group_launch(void* h, cudaStream_t st) {
+    JitGroup* G = static_cast<JitGroup*>(h);
+    if (G->total_items == 0) return;
+    int nseg = (int)G->segs.size();
+    int cap = G->buf_cap;
+    void* args[] = {(void*)&G->d_segs, (void*)&nseg, (void*)&G->d_range, (void*)&G->d_first, (void*)&cap};
+    GFT_CUDA(cudaLaunchKernel((const void*)G->k, dim3((unsigned)G->grid), dim3(kGroupThreads), args, G->smem, st));
+}
+
+void jit_group_free(void* h) { delete static_cast<JitGroup*>(h); }
+
+int jit_group_launches(void* h) { return static_cast<JitGroup*>(h)->total_items > 0 ? 1 : 0; }
+
+int jit_group_tile(void* h, int entry) {
+    const JitGroup* G = static_cast<const JitGroup*>(h);
+    for (size_t sl = 0; sl < G->segs.size(); ++sl)
+        if (G->members[sl] == entry) return G->segs[sl].ts;
+    return 0;
 }
 
 }  // namespace gft

@@ -292,3 +292,43 @@ def test_node_major_kernel_tiles_and_leaf_widths(env):
     torch.cuda.synchronize()
     for p, x, y in zip(plans, xs, ys):
         assert torch.equal(y, p.forward(x))
+
+
+def test_plan_specialised_group_for_shared_small_plans(env):
+    """Small plans shared by many entries (at least 2^19 coefficients per plan
+    over its entries) run in the batch's plan-specialised group: one module
+    with the straight-line forward of each such plan and one persistent
+    kernel over all their (entry, tile) items.  Entries: eight skeletons,
+    five cycles, a path, a grid of odd size, a right Haar plan (three
+    entries), batches on both sides of the tile sizes; next to them a plan
+    below the threshold (node-major kernel).  Every output equals the plan's
+    own table-driven forward bit for bit, with the group and without it."""
+    gft, torch = env
+    sk, cy, pa, gr = W.skeleton25(), W.cycle(16), W.path(40), W.grid(7)
+    rb = W.krbg(16, 3, seed=9)
+    p_sk, p_cy, p_pa, p_gr, p_small = _plans(gft, [sk, cy, pa, gr, W.path(12)])
+    p_rb = gft.Plan.bipartite(gft.laplacian(rb.W, rb.s), rb.meta["side"])
+    entries = [(p_sk, sk.n, b) for b in (6000, 5999, 6001, 256, 257, 4096, 8000, 1)]      # 778 K coefficients
+    entries += [(p_cy, cy.n, b) for b in (14000, 13999, 14001, 511, 512)]                # 704 K
+    entries += [(p_pa, pa.n, 14000), (p_gr, gr.n, 11000), (p_small, 12, 300)]
+    entries += [(p_rb, rb.n, b) for b in (6000, 6001, 5999)]
+    plans = [e[0] for e in entries]
+    xs = [torch.from_numpy(W.signals(b, n, 900 + i)).cuda() for i, (_, n, b) in enumerate(entries)]
+    outs = {}
+    for jit in (True, False):
+        bt = gft.Batch(plans, [e[2] for e in entries], jit=jit)
+        ys = [torch.full_like(x, float("nan")) for x in xs]
+        bt.bind(xs, ys).forward()
+        bt.forward()
+        torch.cuda.synchronize()
+        for p, x, y in zip(plans, xs, ys):
+            assert torch.equal(y, p.forward(x)), (p.n, jit)
+        outs[jit] = ys
+        tiles = [bt.tile(i) for i in range(len(plans))]
+        group = [t[1] == 128 and t[0] in (128, 256, 512) for t in tiles]
+        if jit:
+            assert all(group[:-4]) and all(group[-3:])     # the group, right Haar plan included
+            assert tiles[-4][1] == 256                      # below the threshold: node-major kernel
+        else:
+            assert all(t[1] == 256 for t in tiles[:-3])     # node-major kernel
+    assert all(torch.equal(a, b) for a, b in zip(outs[True], outs[False]))
