@@ -54,7 +54,7 @@ constexpr int kNK = 32;              // K per chunk
 constexpr int kNMaxNs = 128;         // signals per tile (MMA N)
 constexpr int kNWorkers = 8;         // epilogue warps 0-7 (two per TMEM lane quarter)
 constexpr int kNThreads = 320;       // + copier warp 8, MMA warp 9
-constexpr int kNSlots = 6;           // ring slots
+constexpr int kNSlots = 4;           // ring slots (146 KB of shared memory with the static part: a CUDA-core CTA fits beside)
 constexpr int kNCols = 512;          // TMEM columns per CTA (one CTA per SM): two halves
 constexpr int kNHalf = 256;
 constexpr int kNMaxLeaf = 512;
