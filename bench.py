@@ -60,14 +60,14 @@ def _kernel_hash(plan):
     return hashlib.sha256(plan.kernel_source().encode()).hexdigest()[:16]
 
 
-REPLAY_SOURCES = ("gft_internal.h", "batch.cu", "tcn.cu", "wide.cu")
+REPLAY_SOURCES = ("gft_internal.h", "apply_core.cuh", "batch.cu", "tcn.cu", "wide.cu", "jit.cpp")
 REPLAY_PROFILE = os.path.join("profiles", "size_sweep_replay_traffic.md")
 
 
 def _replay_source_hash():
-    """Hash of the CUDA sources of the kernels that one size-sweep replay
-    launches (table-driven batch classes, wide leaves, tensor-core pack and
-    MMA kernels)."""
+    """Hash of the sources of the kernels that one size-sweep replay launches
+    (plan-specialised group and its generator, node-major and table-driven
+    batch classes, wide leaves, tensor-core pack and MMA kernels)."""
     h = hashlib.sha256()
     for f in REPLAY_SOURCES:
         with open(os.path.join(ROOT, "paper_1907_07875_gb300", "csrc", f), "rb") as fh:
