@@ -661,7 +661,46 @@ def sweep_variants(torch, gft, dev, S, reps=10):
                              "size_classes": len(groups)}
     torch.backends.cuda.matmul.allow_tf32 = prev
     del groups, basis
+    out["learned_givens"] = sweep_learned(torch, gft, dev, S, reps=reps)
     return out
+
+
+def sweep_learned(torch, gft, dev, S, reps=10, steps=800):
+    """Learned forms on the size sweep: the entries whose graph has 16, 32 or
+    64 nodes in a deterministic family (path, cycle, grid -- the sizes a
+    butterfly-wired Givens network takes), one network of 2 log2 n layers
+    trained per distinct graph against its exact basis, then every entry's
+    signals transformed by its graph's network (one launch per distinct
+    graph over the rows of all its entries, gathered into one buffer beside
+    the timed region); against the fast GFT of the same entries (one batch
+    launch on their own buffers).  delta: Sec. VI-B, sign-normalised."""
+    from paper_1907_07875_gb300.learned import LearnedGFT, delta
+    sel = [j for j, (f, n, gs, b, ss) in enumerate(S["specs"]) if f in ("path", "cycle", "grid") and n in (16, 32, 64)]
+    if not sel:
+        return None
+    by_plan = {}
+    for j in sel:
+        by_plan.setdefault(S["entry_idx"][j], []).append(j)
+    nets, bufs, deltas = [], [], []
+    for e, js in by_plan.items():
+        plan = S["plans"][e]
+        U = plan.basis()
+        net = LearnedGFT(plan.n, device=dev)
+        net.train(U, steps=steps, lr=0.05)
+        deltas.append(delta(net.matrix(), U))
+        X = torch.cat([S["xs"][j] for j in js])
+        nets.append((net, X, torch.empty_like(X)))
+    coeffs = sum(S["batches"][j] * S["ns"][j] for j in sel)
+    t_l = _timed(torch, lambda: [net.forward(X, out=Y) for net, X, Y in nets], reps=reps)
+    bt = gft.Batch([S["entry"][j] for j in sel], [S["batches"][j] for j in sel], precision="fp32")
+    bt.bind([S["xs"][j] for j in sel], [S["ys"][j] for j in sel])
+    t_e = _timed(torch, lambda: bt.forward(), reps=reps)
+    del bt, nets
+    return {"entries": len(sel), "distinct_graphs": len(by_plan), "coeffs": coeffs, "train_steps": steps,
+            "learned_gcoeffs_s": round(coeffs / t_l / 1e9, 1), "learned_launches": len(by_plan),
+            "exact_fast_gft_gcoeffs_s": round(coeffs / t_e / 1e9, 1),
+            "delta_learned_median": round(float(np.median(deltas)), 4), "delta_learned_max": round(max(deltas), 4),
+            "delta_exact": 0.0}
 
 
 def sweep_setup(torch, gft, dev, seed=1005, specs=None):
