@@ -23,6 +23,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import multiprocessing as mp
 import os
@@ -64,14 +65,23 @@ REPLAY_SOURCES = ("gft_internal.h", "apply_core.cuh", "batch.cu", "tcn.cu", "wid
 REPLAY_PROFILE = os.path.join("profiles", "size_sweep_replay_traffic.md")
 
 
+def _code_only(text):
+    """Source text without comments and blank lines (a comment edit does not
+    change the kernels whose counters a profile recorded)."""
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    lines = (re.sub(r"//.*$", "", ln).rstrip() for ln in text.splitlines())
+    return "\n".join(ln for ln in lines if ln)
+
+
 def _replay_source_hash():
-    """Hash of the sources of the kernels that one size-sweep replay launches
-    (plan-specialised group and its generator, node-major and table-driven
-    batch classes, wide leaves, tensor-core pack and MMA kernels)."""
+    """Hash of the code (comments stripped) of the kernels that one
+    size-sweep replay launches (plan-specialised group and its generator,
+    node-major and table-driven batch classes, wide leaves, tensor-core pack
+    and MMA kernels)."""
     h = hashlib.sha256()
     for f in REPLAY_SOURCES:
-        with open(os.path.join(ROOT, "paper_1907_07875_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1907_07875_gb300", "csrc", f)) as fh:
+            h.update(_code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

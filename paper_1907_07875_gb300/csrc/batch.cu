@@ -2,8 +2,15 @@
 // each with its own batch of signals, transformed forward by persistent
 // kernel launches that are captured in ONE CUDA graph and replayed.
 //
-// Table-driven group (plans whose leaves all fit the CUDA-core tile code of
-// apply_core.cuh, at most 64 nodes):
+// Groups, in routing order: the tensor-core kernels (tc.cu, tcn.cu) for
+// plans with a leaf of 64 or more nodes in a tensor-core precision; the
+// plan-specialised group (jit.cpp) for small plans that many entries share;
+// the node-major kernel below for the other plans of at most 256 nodes
+// without right Haar units; the thread-per-signal kernel below; the
+// wide-leaf kernel (wide.cu).
+//
+// Thread-per-signal group (plans whose leaves all fit the CUDA-core tile
+// code of apply_core.cuh, at most 64 nodes):
 //   * Work list: plan p contributes ceil(batch_p / TS_p) items, one per
 //     tile of TS_p = RS_p * 128 signals, plans in order of decreasing cost
 //     per item.  Plans are split into size classes by their padded row
@@ -174,8 +181,8 @@ __global__ void __launch_bounds__(kBatchThreads) gft_batch_kernel(const BatchPla
 
 // Node-major variant of the table-driven batch kernel, for plans of at most
 // kNmMaxN nodes without right Haar units (every leaf at most 64 nodes).
-// An item is a tile of TS signals (a power of two, 32..256, about 4096
-// floats per tile) of one plan:
+// An item is a tile of TS signals (a power of two, 16..1024, at most 4096
+// floats per tile unless TS = 16) of one plan:
 //   * the rows arrive with 16-byte cp.async copies into a row-major buffer
 //     X, and so does the plan's program image (pairs, stage offsets, node
 //     lists, leaf descriptors, the (leaf, output group) list) into one of

@@ -31,7 +31,11 @@
 //     accumulator per unit; warps 0-7 read a finished half (tcgen05.ld; the
 //     two warps of a TMEM lane quarter split its columns), undo the FP16 scale and store each
 //     coefficient at its output position (ascending eigenvalue) of its
-//     signal's row, while the MMAs of the next item fill the other half.
+//     signal's row, while the MMAs of the next item fill the other half;
+//     the positions (a table of 128 per unit) and the scales of the next
+//     item are staged into shared memory (cp.async) while this one is
+//     stored.  A work item holds at most kNItemSteps / (K chunks of the
+//     plan's widest leaf) units, so that a large graph spreads over many SMs.
 // Every wait is bounded (about 2 s via %globaltimer); a timeout records
 // GFT_ERR_TIMEOUT in the plan's error word, every role leaves its loop,
 // copies and MMAs in flight are awaited (bounded), and TMEM is freed.
