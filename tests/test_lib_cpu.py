@@ -419,3 +419,23 @@ def test_bipartite_normalized_flag(gft):
     a = gft.Plan.bipartite(L, g.meta["side"], normalized=True, analyze_only=True)
     b = gft.Plan.bipartite(gft.normalized_laplacian(g.W, g.s), g.meta["side"], analyze_only=True)
     assert a.leaves() == b.leaves() and a.info["right_pairs"] == 4
+
+
+def test_batch_flags_and_device_check(gft):
+    """gft_batch_create: an unknown flag bit is rejected before anything
+    else; GFT_BATCH_NO_JIT or'ed into a precision is a known flag, so a plan
+    without device data is then reported as such."""
+    import ctypes as C
+    g = W.path(8)
+    plan = gft.Plan(ograph.laplacian(g.W, g.s), g.phis, analyze_only=True)
+    lib = gft.lib()
+    arr = (C.c_void_p * 1)(plan.handle)
+    b = np.array([16], dtype=np.int64)
+    out = C.c_void_p()
+    status = lambda flags: lib.gft_batch_create(1, C.cast(arr, C.c_void_p), b.ctypes.data_as(C.c_void_p), flags,
+                                                C.byref(out))
+    assert gft.STATUS[status(0x200)] == "GFT_ERR_INVALID_ARG"
+    assert gft.STATUS[status(4)] == "GFT_ERR_INVALID_ARG"                  # precision past GFT_PREC_FP16X3
+    assert gft.STATUS[status(gft.Batch.BATCH_NO_JIT | 3)] == "GFT_ERR_NO_DEVICE"
+    assert gft.STATUS[status(gft.Batch.BATCH_NO_JIT)] == "GFT_ERR_NO_DEVICE"
+    assert gft.STATUS[status(3)] == "GFT_ERR_NO_DEVICE"
