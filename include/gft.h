@@ -370,7 +370,9 @@ gft_status gft_device_error(gft_plan_t plan, int32_t* code);
  *     over the (plan, tile) items of those plans.
  * Every CUDA-core group computes each output with the same FMA sequence as
  * the plan's own FP32 forward, so their results agree bit for bit.
- * The groups run on forked streams inside the graph and join at its end.
+ * The CUDA-core groups run one after another on the capture stream, the
+ * wide-leaf and tensor-core groups on forked streams; all join at the end
+ * of the graph.
  *  plans[n_plans]  plans created with device bases; the batch does not own
  *                  them, and they must outlive it.  A plan may appear more
  *                  than once (its entries then run one after another).
@@ -388,9 +390,10 @@ gft_status gft_batch_create(int32_t n_plans, const gft_plan_t* plans, const int6
                             uint32_t flags, gft_batch_t* out);
 gft_status gft_batch_forward(gft_batch_t batch, const float* const* x, float* const* y,
                              gft_stream_t stream);
-/* Tile configuration of plan i of a table-driven group: signals per tile
- * and threads per block (thread-per-signal kernel: chosen by the autotuner;
- * node-major kernel: 256 threads, a power-of-two tile of 32..256 signals);
+/* Tile configuration of entry i of a CUDA-core group: signals per tile and
+ * threads per block (thread-per-signal kernel: 128 threads, a tile chosen by
+ * the autotuner; node-major kernel: 256 threads, a power-of-two tile of
+ * 16..1024 signals; plan-specialised group: 128 threads, 128..512 signals);
  * 0 for entries routed to the wide-leaf or tensor-core kernels. */
 gft_status gft_batch_get_tile(gft_batch_t batch, int32_t i, int32_t* tile, int32_t* threads);
 /* Kernel launches of this library in one gft_batch_forward (the nodes of
